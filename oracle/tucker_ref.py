@@ -1,0 +1,369 @@
+"""Plain FP64 statement of the randomized Tucker methods of "Parallel
+Randomized Tucker Decomposition Algorithms" (arXiv 2211.13028).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by
+the CPU-baseline leg of bench.py, never by the product path.  It shares no code
+with the CUDA path.
+
+Every step is written in the paper's order and notation with NumPy (float64,
+LAPACK for QR and SVD as single library steps) and without any blocking,
+fusion or reordering beyond what the definitions state.  Tensors are numpy
+arrays indexed ``X[i1, ..., id]`` with zero-based modes 0..d-1 standing for the
+paper's modes 1..d.
+
+Pins (tests/test_oracle_*.py):
+  * unfold / ttm / multi_ttm: elementwise brute-force loops, the multi-TTM
+    Kronecker unfolding identity of Section 2.1, round trips.
+  * thin_qr: Q^T Q = I, Q R = Y, R upper triangular with positive diagonal
+    (which fixes Q uniquely), classical Gram-Schmidt on tiny inputs.
+  * sthosvd: closed-form error 0.4^r on the Section 6.1 tensor, the STHOSVD
+    error identity (sum of discarded squared singular values).
+  * rhkron / rsthkron / rhkron_noreuse: exact recovery of exactly low-rank
+    tensors, the Section 5 invariants (core singular values bounded by those
+    of X, the core error bound Eq. core_svals, Pythagoras for orthonormal
+    factors), the Section 6.1 medians (statistical).
+  * subranks_reuse / subranks_matrix: the vectors and matrices printed for
+    the Miranda and SP runs (Sections 6.5-6.6).
+  * loss_grads: central finite differences in FP64.
+"""
+from __future__ import annotations
+
+import itertools
+from typing import Dict, List, Sequence, Tuple
+
+import numpy as np
+
+__all__ = [
+    "unfold", "fold", "ttm", "ttm_loops", "multi_ttm", "kron_unfolded_multi_ttm", "kron_omega",
+    "thin_qr", "leading_left_singular_vectors", "sthosvd", "canonical_signs",
+    "subranks_reuse", "subranks_matrix", "balanced_factors",
+    "rhkron", "rsthkron", "rhkron_noreuse",
+    "reconstruct", "rel_err", "loss", "loss_grads",
+]
+
+
+# ---------------------------------------------------------------- Section 2.1
+
+def unfold(X: np.ndarray, j: int) -> np.ndarray:
+    """Mode-j unfolding X_(j) (Section 2.1).
+
+    n_j x prod_{k != j} n_k; its columns are the mode-j fibres, ordered with the
+    lowest remaining mode varying fastest.
+    """
+    return np.reshape(np.moveaxis(X, j, 0), (X.shape[j], -1), order="F")
+
+
+def fold(M: np.ndarray, j: int, shape: Sequence[int]) -> np.ndarray:
+    """Inverse of ``unfold`` for a tensor of the given shape."""
+    rest = [int(shape[k]) for k in range(len(shape)) if k != j]
+    return np.moveaxis(np.reshape(M, [int(shape[j])] + rest, order="F"), 0, j)
+
+
+def ttm(X: np.ndarray, A: np.ndarray, j: int) -> np.ndarray:
+    """Tensor-times-matrix Y = X x_j A, defined by Y_(j) = A X_(j) (Section 2.1).
+
+    A is m x n_j; Y has mode j of size m.
+    """
+    if A.shape[1] != X.shape[j]:
+        raise ValueError("ttm: A has %d columns, mode %d has size %d" % (A.shape[1], j, X.shape[j]))
+    shape = list(X.shape)
+    shape[j] = A.shape[0]
+    return fold(A @ unfold(X, j), j, shape)
+
+
+def ttm_loops(X: np.ndarray, A: np.ndarray, j: int) -> np.ndarray:
+    """Elementwise TTM: Y[..., a, ...] = sum_i A[a, i] X[..., i, ...] (pure Python loops)."""
+    shape = list(X.shape)
+    shape[j] = A.shape[0]
+    Y = np.zeros(shape)
+    for idx in itertools.product(*[range(s) for s in shape]):
+        acc = 0.0
+        for i in range(X.shape[j]):
+            src = list(idx)
+            src[j] = i
+            acc += A[idx[j], i] * X[tuple(src)]
+        Y[idx] = acc
+    return Y
+
+
+def multi_ttm(X: np.ndarray, mats: Sequence[Tuple[int, np.ndarray]]) -> np.ndarray:
+    """Multi-TTM X x_{j1} A_{j1} x_{j2} A_{j2} ... applied in the listed order (Section 2.1)."""
+    Y = X
+    for j, A in mats:
+        Y = ttm(Y, A, j)
+    return Y
+
+
+def kron_unfolded_multi_ttm(X: np.ndarray, A: Sequence[np.ndarray], j: int) -> np.ndarray:
+    """Mode-j unfolding of X x_1 A_1 ... x_d A_d by the Kronecker formula of Section 2.1.
+
+    A_j X_(j) (A_d kron ... kron A_{j+1} kron A_{j-1} kron ... kron A_1)^T, with the
+    Kronecker product formed explicitly (test-sized inputs only).
+    """
+    d = X.ndim
+    K = np.ones((1, 1))
+    for k in range(d - 1, -1, -1):
+        if k != j:
+            K = np.kron(K, A[k])
+    return A[j] @ unfold(X, j) @ K.T
+
+
+def kron_omega(phis: Sequence[np.ndarray], j: int) -> np.ndarray:
+    """Omega_j = (Phi_d kron ... kron Phi_{j+1} kron Phi_{j-1} kron ... kron Phi_1)^T (Section 3.2)."""
+    K = np.ones((1, 1))
+    for k in range(len(phis) - 1, -1, -1):
+        if k != j:
+            K = np.kron(K, phis[k])
+    return K.T
+
+
+# ------------------------------------------------------- Algorithms RRF, STHOSVD
+
+def thin_qr(Y: np.ndarray) -> np.ndarray:
+    """Q of the thin QR Y = Q R with diag(R) >= 0 (Algorithm RRF, second step).
+
+    Reading: when Y has at least as many columns as rows its columns already
+    span the whole space and Q is the identity (the sketch width is
+    min(n_j, number of sketch columns)).
+    """
+    m, k = Y.shape
+    if k >= m:
+        return np.eye(m)
+    Q, R = np.linalg.qr(Y, mode="reduced")
+    return Q * np.where(np.diag(R) < 0.0, -1.0, 1.0)[None, :]
+
+
+def leading_left_singular_vectors(M: np.ndarray, r: int) -> np.ndarray:
+    """First r left singular vectors of M (LAPACK SVD)."""
+    u, _, _ = np.linalg.svd(M, full_matrices=False)
+    return u[:, :r]
+
+
+def sthosvd(X: np.ndarray, r: Sequence[int], order: Sequence[int] | None = None):
+    """Algorithm STHOSVD: for each mode in ``order``, U_j = first r_j left singular
+    vectors of the current G_(j), then G <- G x_j U_j^T.
+
+    Returns (G, [U_j], discarded) where discarded[t] is the sum of the squared
+    singular values dropped at step t.
+    """
+    d = X.ndim
+    order = list(range(d)) if order is None else list(order)
+    G = X
+    U: List[np.ndarray] = [None] * d  # type: ignore
+    discarded = []
+    for j in order:
+        u, sv, _ = np.linalg.svd(unfold(G, j), full_matrices=False)
+        U[j] = u[:, : r[j]]
+        discarded.append(float(np.sum(sv[r[j]:] ** 2)))
+        G = ttm(G, U[j].T, j)
+    return G, U, discarded
+
+
+def canonical_signs(G: np.ndarray, U: Sequence[np.ndarray]):
+    """Fix the sign gauge: each column of U_j has its largest-magnitude entry
+    (lowest row on ties) positive; the matching slice of G flips with it."""
+    G = G.copy()
+    U = [u.copy() for u in U]
+    for j, u in enumerate(U):
+        for c in range(u.shape[1]):
+            i = int(np.argmax(np.abs(u[:, c])))
+            if u[i, c] < 0:
+                u[:, c] = -u[:, c]
+                sl = [slice(None)] * G.ndim
+                sl[j] = c
+                G[tuple(sl)] = -G[tuple(sl)]
+    return G, U
+
+
+# --------------------------------------------------------------- subranks
+
+def _ceil_root_ratio(P: int, ell: int, d: int) -> int:
+    """Smallest integer s with s >= P^(1/(d-1)) / ell, i.e. (s*ell)^(d-1) >= P."""
+    s = max(1, int((P ** (1.0 / (d - 1))) / ell))
+    while s > 1 and ((s - 1) * ell) ** (d - 1) >= P:
+        s -= 1
+    while (s * ell) ** (d - 1) < P:
+        s += 1
+    return s
+
+
+def subranks_reuse(r: Sequence[int], p: int):
+    """Subrank vector of Algorithm rHKron-re (Section 3.3).
+
+    The paper's formula s_i = ceil((prod_j l_j)^(1/(d-1)) / l_i), then (reading)
+    each entry, largest first (ties: lowest mode), is lowered to the smallest
+    value that keeps prod_{k != j} s_k >= l_j for every mode j.
+    Returns (s, widths) with widths[j] = prod_{k != j} s_k.
+    """
+    d = len(r)
+    ell = [int(x) + int(p) for x in r]
+    P = 1
+    for x in ell:
+        P *= x
+    s = [_ceil_root_ratio(P, ell[i], d) for i in range(d)]
+    for i in sorted(range(d), key=lambda t: (-s[t], t)):
+        need = 1
+        for j in range(d):
+            if j == i:
+                continue
+            rest = 1
+            for k in range(d):
+                if k != i and k != j:
+                    rest *= s[k]
+            need = max(need, -(-ell[j] // rest))
+        s[i] = min(s[i], need)
+    widths = []
+    for j in range(d):
+        w = 1
+        for k in range(d):
+            if k != j:
+                w *= s[k]
+        widths.append(w)
+    return s, widths
+
+
+def balanced_factors(ell: int, m: int):
+    """Smallest L >= ell that is a product of m integers >= 2, and its most balanced
+    such factorisation (smallest largest factor, compared as sorted-descending
+    tuples).  Reading of Section 3.2's subrank heuristic."""
+    def facts(n, m, lo):
+        if m == 1:
+            if n >= lo:
+                yield (n,)
+            return
+        f = lo
+        while f ** m <= n:
+            if n % f == 0:
+                for rest in facts(n // f, m - 1, f):
+                    yield (f,) + rest
+            f += 1
+
+    L = max(int(ell), 2 ** m)
+    while True:
+        best = None
+        for fs in facts(L, m, 2):
+            key = tuple(sorted(fs, reverse=True))
+            if best is None or key < best:
+                best = key
+        if best is not None:
+            return L, list(best)
+        L += 1
+
+
+def subranks_matrix(r: Sequence[int], p: int, order: Sequence[int] | None = None):
+    """Subrank matrix S of Algorithm rSTHKron (Section 3.2).
+
+    Row j holds d-1 integer factors (each >= 2) of l_j' >= l_j = r_j + p, l_j' the
+    smallest such value, most balanced factorisation.  Reading: the factors
+    go in descending order to the other modes taken in processing order.  The
+    diagonal is 1.  Returns (S, widths) with widths[j] = l_j'.
+    """
+    d = len(r)
+    order = list(range(d)) if order is None else list(order)
+    S = np.ones((d, d), dtype=np.int64)
+    widths = []
+    for j in range(d):
+        L, fs = balanced_factors(int(r[j]) + int(p), d - 1)
+        others = [k for k in order if k != j]
+        for k, f in zip(others, fs):
+            S[j, k] = f
+        widths.append(L)
+    return S, widths
+
+
+# ------------------------------------------------------ Algorithms rHKron-re, rSTHKron
+
+def rhkron(X: np.ndarray, r: Sequence[int], omegas: Sequence[np.ndarray], order: Sequence[int] | None = None):
+    """Algorithm rHKron-re (randomized HOSVD, Kronecker sketch, reused factors).
+
+    omegas[j] = Phi_j^T (n_j x s_j).  For each mode n: Y = X x_{j != n} Phi_j,
+    Q_n from the thin QR of Y_(n); then Ghat = X x_1 Q_1^T ... x_d Q_d^T,
+    [G, {V_j}] = STHOSVD(Ghat, r) and U_j = Q_j V_j.
+    """
+    d = X.ndim
+    order = list(range(d)) if order is None else list(order)
+    Q, Ys = [], []
+    for n in range(d):
+        Y = multi_ttm(X, [(j, omegas[j].T) for j in range(d) if j != n])
+        Ys.append(Y)
+        Q.append(thin_qr(unfold(Y, n)))
+    Ghat = multi_ttm(X, [(j, Q[j].T) for j in range(d)])
+    G, V, _ = sthosvd(Ghat, r, order)
+    U = [Q[j] @ V[j] for j in range(d)]
+    G, U = canonical_signs(G, U)
+    return dict(G=G, U=U, Q=Q, Y=Ys, Ghat=Ghat)
+
+
+def rsthkron(X: np.ndarray, r: Sequence[int], omegas: Dict[Tuple[int, int], np.ndarray],
+             order: Sequence[int] | None = None):
+    """Algorithm rSTHKron (randomized STHOSVD with a Kronecker sketch).
+
+    Modes are processed in ``order``.  For mode j: Y = Ghat x_{k != j} Phi_{j,k}
+    with omegas[(j, k)] = Phi_{j,k}^T sized to the current mode k of Ghat;
+    Q_j from the thin QR of Y_(j); Ghat <- Ghat x_j Q_j^T.  Then
+    [G, {V_j}] = STHOSVD(Ghat, r) in the same order and U_j = Q_j V_j.
+    """
+    d = X.ndim
+    order = list(range(d)) if order is None else list(order)
+    Ghat = X
+    Q: List[np.ndarray] = [None] * d  # type: ignore
+    Ys = {}
+    for j in order:
+        Y = multi_ttm(Ghat, [(k, omegas[(j, k)].T) for k in range(d) if k != j])
+        Ys[j] = Y
+        Q[j] = thin_qr(unfold(Y, j))
+        Ghat = ttm(Ghat, Q[j].T, j)
+    G, V, _ = sthosvd(Ghat, r, order)
+    U = [Q[j] @ V[j] for j in range(d)]
+    G, U = canonical_signs(G, U)
+    return dict(G=G, U=U, Q=Q, Y=Ys, Ghat=Ghat)
+
+
+def rhkron_noreuse(X: np.ndarray, r: Sequence[int], omegas: Dict[Tuple[int, int], np.ndarray],
+                   order: Sequence[int] | None = None):
+    """Appendix Algorithm rHKron: like rHKron-re but with fresh factors per mode,
+    omegas[(j, k)] = Phi_{j,k}^T (n_k x s_{j,k})."""
+    d = X.ndim
+    order = list(range(d)) if order is None else list(order)
+    Q = []
+    for n in range(d):
+        Y = multi_ttm(X, [(k, omegas[(n, k)].T) for k in range(d) if k != n])
+        Q.append(thin_qr(unfold(Y, n)))
+    Ghat = multi_ttm(X, [(j, Q[j].T) for j in range(d)])
+    G, V, _ = sthosvd(Ghat, r, order)
+    U = [Q[j] @ V[j] for j in range(d)]
+    G, U = canonical_signs(G, U)
+    return dict(G=G, U=U, Q=Q, Ghat=Ghat)
+
+
+# ------------------------------------------------ reconstruction, error, loss
+
+def reconstruct(G: np.ndarray, U: Sequence[np.ndarray]) -> np.ndarray:
+    """T = G x_1 U_1 ... x_d U_d (Section 2.2)."""
+    return multi_ttm(G, [(j, U[j]) for j in range(G.ndim)])
+
+
+def rel_err(X: np.ndarray, G: np.ndarray, U: Sequence[np.ndarray]) -> float:
+    """||X - G x_1 U_1 ... x_d U_d|| / ||X|| with the residual formed explicitly."""
+    return float(np.linalg.norm(X - reconstruct(G, U)) / np.linalg.norm(X))
+
+
+def loss(X: np.ndarray, G: np.ndarray, U: Sequence[np.ndarray]) -> float:
+    """||X - G x_1 U_1 ... x_d U_d||^2."""
+    R = X - reconstruct(G, U)
+    return float(np.sum(R * R))
+
+
+def loss_grads(X: np.ndarray, G: np.ndarray, U: Sequence[np.ndarray]):
+    """Gradients of ||X - G x_j U_j||^2 with R = X - G x_j U_j:
+    dX = 2R, dG = -2 R x_1 U_1^T ... x_d U_d^T,
+    dU_n = -2 (R x_{j != n} U_j^T)_(n) G_(n)^T  (from the unfolding identity of Section 2.1).
+    """
+    d = X.ndim
+    R = X - reconstruct(G, U)
+    dG = -2.0 * multi_ttm(R, [(j, U[j].T) for j in range(d)])
+    dU = []
+    for n in range(d):
+        Z = multi_ttm(R, [(j, U[j].T) for j in range(d) if j != n])
+        dU.append(-2.0 * unfold(Z, n) @ unfold(G, n).T)
+    return dict(dX=2.0 * R, dG=dG, dU=dU)
