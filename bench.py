@@ -1,0 +1,334 @@
+"""Benchmark of the randomized Tucker hot path on one GB300 (or N replicas).
+
+One step = the whole path on the 512^3 FP32 smooth-field workload:
+  rHKron-re (sketch, thin QR, core, FP64 truncation, relative error)
+  + rSTHKron (per-mode sketch / QR / TTM, truncation, relative error)
+  + the loss gradient at the rHKron-re result (dG, dU, dX).
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_FULL = 512
+RANKS = (32, 32, 32)
+P_OVER = 8
+SEED = 0
+WORKLOAD = ("bumps512_f32: 512^3 FP32 field, sum of 200 anisotropic Gaussian bumps + 1e-4 relative noise; "
+            "rHKron-re and rSTHKron at r=(32,32,32), p=8 (s=(6,7,7); S rows {5,8}); loss gradient at the rHKron-re result")
+METRIC = "rHKron-re + rSTHKron (+ loss gradient) wall time per step, 512^3 FP32, r=32, p=8"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), float(pk["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def oracle_step(n: int):
+    """One oracle step on an n^3 sample of the workload; returns (seconds, rel_errs)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2211_13028_gb300 import synth
+
+    x = synth.from_fortran(synth.gaussian_bumps(n, 3, 200, SEED, 1e-4, "cpu", "f32"))
+    r, p = RANKS, P_OVER
+    s, _ = O.subranks_reuse(r, p)
+    S, w = O.subranks_matrix(r, p)
+    k = [min(n, ww) for ww in w]
+    om = synth.sketch_factors_reuse(x.shape, s, SEED + 1, "f32")
+    oms = synth.sketch_factors_matrix(x.shape, S, k, [0, 1, 2], SEED + 2, "f32")
+    t0 = time.perf_counter()
+    a = O.rhkron(x, r, om)
+    ea = O.rel_err(x, a["G"], a["U"])
+    b = O.rsthkron(x, r, oms)
+    eb = O.rel_err(x, b["G"], b["U"])
+    O.loss_grads(x, a["G"], a["U"])
+    dt = time.perf_counter() - t0
+    del np
+    return dt, (ea, eb)
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(n_sample: int, budget_s: float = 20.0):
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        dt, errs = oracle_step(n_sample)
+        times.append(dt)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 5:
+            break
+    times.sort()
+    med = times[len(times) // 2]
+    scale = (N_FULL / n_sample) ** 3
+    return dict(value=med * 1e3 * scale, unit="ms", cores=cpu_cores(), kind="oracle",
+                sample=(f"{n_sample}^3 sample of the same generator and ranks ({len(times)} runs, median "
+                        f"{med:.2f} s), scaled by the element ratio {scale:.0f} to the 512^3 workload; "
+                        f"oracle rel_err rHKron-re {errs[0]:.3e}, rSTHKron {errs[1]:.3e}"))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_sample = args.sample
+    for _ in range(args.warmup):
+        oracle_step(n_sample)
+    times = []
+    for _ in range(args.steps):
+        dt, errs = oracle_step(n_sample)
+        times.append(dt)
+    scale = (N_FULL / n_sample) ** 3
+    ms = sum(times) / len(times) * 1e3 * scale
+    line = dict(metric=METRIC, value=ms, unit="ms", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, sample=f"{n_sample}^3, time scaled by {scale:.0f}"),
+                cpu_baseline=dict(value=ms, unit="ms", cores=cpu_cores(), kind="oracle",
+                                  sample=f"{n_sample}^3 sample per step, scaled by the element ratio {scale:.0f}"),
+                e2e=dict(value=ms, unit="ms", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                rel_err=dict(rhkron=errs[0], rsthkron=errs[1]))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sms.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sms.sort()
+        return dict(sm_mhz=sms[len(sms) // 2] if sms else None, sm_max_mhz=mx, reasons=sorted(reasons),
+                    samples=len(sms))
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--sample", type=int, default=256, help="oracle sample edge (CPU legs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # CPU baseline first (before any CUDA work in this process), rank 0 at N=1 only.
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.sample)
+
+    import torch
+
+    from paper_2211_13028_gb300 import synth
+    from paper_2211_13028_gb300 import tucker as T
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    T.load()
+
+    r, p = RANKS, P_OVER
+    X = synth.gaussian_bumps(N_FULL, 3, 200, SEED, 1e-4, dev, "f32")
+    dims = tuple(X.shape)
+    s, _ = T.tucker_subranks_reuse(r, p)
+    S, w = T.tucker_subranks_matrix(r, p)
+    k = [min(n, ww) for n, ww in zip(dims, w)]
+    om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(dims, s, SEED + 1, "f32")]
+    oms = {key: synth.fmat(v, "f32", dev)
+           for key, v in synth.sketch_factors_matrix(dims, S, k, [0, 1, 2], SEED + 2, "f32").items()}
+    torch.cuda.synchronize()
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(Xin, marks=None):
+        if marks:
+            marks[0].record()
+        G1, U1, e1 = T.tucker_rhkron(Xin, r, p, om)
+        if marks:
+            marks[1].record()
+        G2, U2, e2 = T.tucker_rsthkron(Xin, r, p, oms)
+        if marks:
+            marks[2].record()
+        dG, dU, dX = T.tucker_reconstruct_backward(Xin, G1, U1, 1.0)
+        if marks:
+            marks[3].record()
+        return (G1, U1, e1, G2, U2, e2, dG, dU)
+
+    for _ in range(args.warmup):
+        out = step(X)
+    torch.cuda.synchronize()
+    errs = (out[2], out[5])
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-timed region (inputs resident in HBM; X = 512 MiB > L2)
+    marks = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = T.tk_launch_count(dev)
+    T.tk_profile(True, dev)
+    t0, t1 = ev(), ev()
+    t0.record()
+    for i in range(args.steps):
+        step(X, marks[i])
+    t1.record()
+    torch.cuda.synchronize()
+    prof = T.tk_profile_read(dev)
+    T.tk_profile(False, dev)
+    launches = T.tk_launch_count(dev) - l0
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    ph = [sum(marks[i][a].elapsed_time(marks[i][a + 1]) for i in range(args.steps)) / args.steps for a in range(3)]
+    if dist is not None:
+        tt = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # ---- end to end through the public API with host buffers
+    Xh = X.detach().permute(2, 1, 0).contiguous().cpu().pin_memory()
+    Xd = torch.empty_like(X.permute(2, 1, 0).contiguous())
+    res_bytes = 0
+    e0, e1 = ev(), ev()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(args.steps):
+        Xd.copy_(Xh, non_blocking=True)
+        out = step(Xd.permute(2, 1, 0))
+        host = [t.detach().to("cpu", non_blocking=True) for t in [out[0], *out[1], out[3], *out[4], out[6], *out[7]]]
+        torch.cuda.current_stream().synchronize()
+        res_bytes = sum(t.numel() * t.element_size() for t in host) + 16
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    # ---- roofline of the dominant kernel class
+    hbm, bf16, peak_src = _peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else ("none", dict(ms=0, launches=1, bytes=0, flops=0))
+    name, d = dom
+    per_launch_ms = d["ms"] / max(1, d["launches"])
+    ach = (d["bytes"] / max(1, d["launches"])) / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
+    ttm = [v for kname, v in prof.items() if kname.startswith("ttm")]
+    ttm_ms = sum(v["ms"] for v in ttm)
+    ttm_tflops = (sum(v["flops"] for v in ttm) / (ttm_ms * 1e-3) / 1e12) if ttm_ms > 0 else 0.0
+    step_ms_total = sum(v["ms"] for v in prof.values())
+    shares = {kname: round(v["ms"] / step_ms_total, 4) for kname, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    if rank != 0:
+        return
+    line = dict(
+        metric=METRIC, value=ms, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+        higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload=WORKLOAD, l2="X is 512 MiB, larger than the 129 MB L2: no flush between steps",
+                    parallelism=("replicas" if world > 1 else "single GPU")),
+        phases_ms=dict(rhkron=ph[0], rsthkron=ph[1], backward=ph[2]),
+        rel_err=dict(rhkron=errs[0], rsthkron=errs[1]),
+        multi_ttm=dict(tflops=ttm_tflops, ms_per_step=ttm_ms / args.steps,
+                       frac_of_bf16_peak=ttm_tflops / bf16),
+        roofline=dict(bound="hbm" if name.startswith(("ttm", "residual", "elementwise")) else "alu",
+                      kernel=name, achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, traffic=None,
+                      peak_source=f"{peak_src} hbm_gbs", bytes_per_launch=d["bytes"] / max(1, d["launches"]),
+                      ms_per_launch=per_launch_ms),
+        kernel_shares=shares,
+        e2e=dict(value=e2e_ms, unit="ms", h2d_bytes_per_step=Xh.numel() * Xh.element_size(),
+                 d2h_bytes_per_step=res_bytes),
+        gpu_launches=launches,
+        clocks=clk,
+    )
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

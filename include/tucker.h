@@ -1,0 +1,234 @@
+/*
+ * tucker.h -- C ABI of libtucker, a GB300 (sm_103a) implementation of the
+ * randomized Tucker decompositions of "Parallel Randomized Tucker
+ * Decomposition Algorithms" (arXiv 2211.13028): rHKron-re (Section 3.3,
+ * Algorithm rHKron-re) and rSTHKron (Section 3.2, Algorithm rSTHKron), their
+ * building blocks (Kronecker sketch multi-TTM, thin QR of a sketch, core
+ * multi-TTM, core truncation) and the reconstruction loss with its gradient.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Tensors are dense and column-major: mode 1 varies fastest, element
+ *    (i1,...,id) sits at i1 + n1*(i2 + n2*(i3 + ...)).  The mode-j unfolding
+ *    X_(j) is n_j x prod_{k!=j} n_k with the remaining modes in the same
+ *    order (Section 2.1).
+ *  - Matrices are column-major with leading dimension ld >= rows.
+ *  - Every data pointer in tk_tensor / tk_matrix is a DEVICE pointer owned by
+ *    the caller; the library never frees it.  Outputs must not alias inputs.
+ *  - Scalar results (rel_err, loss, info) are written to HOST memory; an entry
+ *    point with a host result synchronises the handle's stream before it
+ *    returns.  All other work is queued asynchronously on that stream.
+ *  - Sketch factors are inputs: Omega_j = Phi_j^T (n_j x s_j), drawn by the
+ *    caller, so any generator (and the tests' FP64 oracle) sees the same values.
+ *  - A call validates shapes, dtypes, strides and alignment before it queues
+ *    any work and returns a non-zero tk_status on the first violation, with a
+ *    message available from tk_last_error().  No C++ exception crosses the ABI.
+ *  - Numerical conditions found on the device (a Cholesky breakdown that sent a
+ *    QR to the Householder fallback, a Jacobi solve that hit its sweep limit)
+ *    are recorded in the handle and reported by tk_sync_status().
+ *  - The handle owns a device workspace that grows on demand (cudaMalloc).
+ *    A handle must not be used from two host threads at once.
+ */
+#ifndef TUCKER_H
+#define TUCKER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TK_MAX_D 8
+
+#if defined(__GNUC__)
+#define TK_API __attribute__((visibility("default")))
+#else
+#define TK_API
+#endif
+
+typedef enum {
+    TK_OK = 0,
+    TK_ERR_ARG = 1,           /* null pointer, bad option or count            */
+    TK_ERR_SHAPE = 2,         /* inconsistent or unsupported sizes            */
+    TK_ERR_DTYPE = 3,         /* dtype combination not supported              */
+    TK_ERR_ALIGN = 4,         /* pointer or leading dimension misaligned      */
+    TK_ERR_WORKSPACE = 5,     /* workspace allocation failed                  */
+    TK_ERR_CUDA = 6,          /* a CUDA runtime call failed                   */
+    TK_ERR_NOT_CONVERGED = 7, /* Jacobi eigensolver hit its sweep limit        */
+    TK_ERR_TIMEOUT = 8        /* a bounded device wait gave up                */
+} tk_status;
+
+typedef enum { TK_F64 = 0, TK_F32 = 1, TK_BF16 = 2, TK_FP8_E4M3 = 3 } tk_dtype;
+
+/* Dense column-major tensor on the device.  For TK_FP8_E4M3 the stored value
+ * q represents q / scale (scale > 0); scale is ignored for other dtypes. */
+typedef struct {
+    int d;
+    int64_t dims[TK_MAX_D];
+    tk_dtype dtype;
+    void* data;
+    float scale;
+} tk_tensor;
+
+/* Column-major matrix on the device, element (i, j) at data[i + j*ld]. */
+typedef struct {
+    int64_t rows, cols, ld;
+    tk_dtype dtype;
+    void* data;
+} tk_matrix;
+
+/* Options; a zero-initialised struct selects the defaults.
+ *  mode_order        processing order of the modes (0-based, d entries) for
+ *                    rSTHKron and for the final STHOSVD of the core; NULL = 0..d-1.
+ *  qr_method         0 = CholeskyQR2 with Householder fallback on breakdown,
+ *                    1 = always Householder, 2 = CholeskyQR2 only.
+ *  refine            bulk TTMs on BF16/FP8 data: 0 = apply Q as a BF16 hi+lo
+ *                    pair (refinement pass), -1 = BF16 Q only.
+ *  max_jacobi_sweeps 0 = default (40); > 0 = limit; -1 = zero sweeps (makes the
+ *                    solver report non-convergence, for testing).          */
+typedef struct {
+    const int* mode_order;
+    int qr_method;
+    int refine;
+    int max_jacobi_sweeps;
+    int reserved[5];
+} tk_opts;
+
+typedef struct tk_handle tk_handle;
+
+/* Create a handle bound to a CUDA stream (cudaStream_t passed as void*, NULL =
+ * legacy default stream) on the current device.  *h receives the handle. */
+TK_API tk_status tk_create(tk_handle** h, void* cuda_stream);
+/* Destroy a handle and free its workspace (synchronises its stream). */
+TK_API tk_status tk_destroy(tk_handle* h);
+/* Rebind the handle to another stream. */
+TK_API tk_status tk_set_stream(tk_handle* h, void* cuda_stream);
+/* Message of the last failing call on this handle ("" if none).  The string
+ * is owned by the handle and valid until the next call. */
+TK_API const char* tk_last_error(const tk_handle* h);
+/* Synchronise the handle's stream, then report device-side conditions
+ * recorded since the previous tk_sync_status: TK_ERR_NOT_CONVERGED if a
+ * Jacobi solve hit its sweep limit, TK_ERR_TIMEOUT if a bounded wait gave up,
+ * TK_ERR_CUDA for an asynchronous CUDA error, else TK_OK.  If qr_info is not
+ * NULL it receives, for the last QR of each mode (up to TK_MAX_D entries),
+ * 0 = CholeskyQR2, 1 = Householder, 2 = identity (full-width sketch). */
+TK_API tk_status tk_sync_status(tk_handle* h, int* qr_info);
+/* Bytes of device workspace the handle currently holds. */
+TK_API int64_t tk_workspace_bytes(const tk_handle* h);
+/* Number of kernel launches queued through this handle since creation. */
+TK_API int64_t tk_launch_count(const tk_handle* h);
+
+/* Per-kernel-class timing.  tk_profile(h, 1) clears and starts recording a
+ * CUDA event pair on the handle's stream around every kernel the handle
+ * launches; tk_profile(h, 0) stops.  tk_profile_read synchronises the stream
+ * and fills up to max entries (one per class, in first-seen order) with the
+ * launch count, summed device milliseconds and summed algorithmic bytes
+ * (inputs read once + outputs written once) and flops; it returns the number
+ * of classes (or -1 on error) and clears the records. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double ms;
+    double bytes;
+    double flops;
+} tk_prof_entry;
+TK_API tk_status tk_profile(tk_handle* h, int enable);
+TK_API int tk_profile_read(tk_handle* h, tk_prof_entry* out, int max);
+
+/* ---- host-side integer planning (no device work; h may be NULL) -------- */
+
+/* Subrank vector of Algorithm rHKron-re (Section 3.3, the formula
+ * s_i = ceil((prod_j l_j)^(1/(d-1)) / l_i) with l_j = r_j + p), followed by a
+ * reduction: entries taken largest first (ties: lowest mode) are each lowered
+ * to the smallest value that keeps prod_{k!=j} s_k >= l_j for every mode j.
+ * r: d target ranks.  s_out: d subranks.  width_out (may be NULL): d sketch
+ * column counts prod_{k!=j} s_k.  Errors: TK_ERR_ARG for d < 2, d > TK_MAX_D,
+ * r_j < 1 or p < 0. */
+TK_API tk_status tucker_subranks_reuse(int d, const int64_t* r, int p, int64_t* s_out, int64_t* width_out);
+
+/* Subrank matrix of Algorithm rSTHKron (Section 3.2, "Choosing subranks"):
+ * row j holds d-1 integer factors >= 2 of the smallest l_j' >= r_j + p that
+ * has such a factorisation, the most balanced one (smallest largest factor).
+ * The factors are given in descending order to the other modes taken in
+ * processing order (order: d entries, NULL = 0..d-1).  S_out: d*d, row-major,
+ * S_out[j*d+k] = s_{j,k}, diagonal 1.  width_out (may be NULL): l_j'.  */
+TK_API tk_status tucker_subranks_matrix(int d, const int64_t* r, int p, const int* order,
+                                 int64_t* S_out, int64_t* width_out);
+
+/* ---- building blocks ---------------------------------------------------- */
+
+/* Kronecker-structured sketches of Algorithm rHKron-re (sketch line):
+ * for every mode n, Y_n = X x_1 Phi_1 ... x_{n-1} Phi_{n-1} x_{n+1} Phi_{n+1} ... x_d Phi_d,
+ * equivalently Y_n(n) = X_(n) (Phi_d kron ... kron Phi_1, skipping n)^T
+ * (Section 3.2), computed with the dimension tree of Section 4.4 and never
+ * forming the Kronecker product.
+ * X: d-way tensor (F64, F32, BF16 or FP8_E4M3).  Omega: d matrices
+ * Omega_j = Phi_j^T, n_j x s_j, dtype F64 for F64 data else F32 or BF16.
+ * Y: d tensors; Y[n] has dims (s_1,..,s_{n-1}, n_n, s_{n+1},..,s_d) and dtype
+ * F64 (F64 data) or F32 (otherwise). */
+TK_API tk_status tucker_sketch(tk_handle* h, const tk_tensor* X, const tk_matrix* Omega, tk_tensor* Y);
+
+/* Thin QR of a tall sketch, Y = Q R with R_ii > 0 (Algorithm RRF):
+ * CholeskyQR2 with an FP64 Gram matrix and FP64 Cholesky; Householder QR in
+ * FP64 when the Cholesky factorisation breaks down or a pivot falls below
+ * 1e-12 of its column's squared norm; Q = I when Y has at least as many
+ * columns as rows.  Y: rows x cols (F64 or F32).  Q: rows x min(rows, cols),
+ * F64 or F32.  info (host, may be NULL): 0 CholeskyQR2, 1 Householder,
+ * 2 identity; a non-NULL info synchronises. */
+TK_API tk_status tucker_orth(tk_handle* h, const tk_matrix* Y, tk_matrix* Q, int* info, const tk_opts* opts);
+
+/* Core multi-TTM Ghat = X x_1 Q_1^T x_2 Q_2^T ... x_d Q_d^T (Algorithm
+ * rHKron-re, core line).  Q: d matrices n_j x k_j (F64 for F64 data, else F32).
+ * G: tensor (k_1,...,k_d), F64 or F32. */
+TK_API tk_status tucker_core(tk_handle* h, const tk_tensor* X, const tk_matrix* Q, tk_tensor* G);
+
+/* ---- the two algorithms -------------------------------------------------- */
+
+/* Algorithm rHKron-re: sketches with the d reused factors Omega_j = Phi_j^T
+ * (n_j x s_j), thin QR of each sketch unfolding into Q_n (n_n x k_n,
+ * k_n = min(n_n, prod_{j!=n} s_j)), core Ghat = X x_j Q_j^T, STHOSVD of Ghat to
+ * ranks r in FP64 (Gram matrix + Jacobi eigensolver per mode), U_j = Q_j V_j
+ * (Section 3, holistic truncation).  Each column of U_j is signed so that its
+ * largest-magnitude entry is positive; G's slices follow.
+ * X: F64, F32, BF16 or FP8_E4M3.  r: d host ranks, 1 <= r_j <= k_j.
+ * p: oversampling, only checked against the Omega widths (prod_{j!=n} s_j >= r_n + p).
+ * G: (r_1..r_d) F64 or F32.  U: d matrices n_j x r_j, F64 or F32.
+ * rel_err (host, may be NULL): ||X - G x_j U_j|| / ||X||, which synchronises. */
+TK_API tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
+                        const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err);
+
+/* Algorithm rSTHKron: modes processed in opts->mode_order; for mode j the
+ * sketch Y = Ghat x_{k!=j} Phi_{j,k}, its thin QR Q_j, and Ghat <- Ghat x_j Q_j^T;
+ * then STHOSVD(Ghat, r) in the same order and U_j = Q_j V_j.
+ * Omega: d*d matrices, Omega[j*d+k] = Phi_{j,k}^T of size (current size of mode
+ * k when j is processed) x s_{j,k}, i.e. k_k rows for modes processed before j
+ * and n_k rows otherwise; diagonal entries are ignored.
+ * Other arguments as tucker_rhkron. */
+TK_API tk_status tucker_rsthkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
+                          const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err);
+
+/* ---- reconstruction, loss and its gradient ------------------------------- */
+
+/* Xhat = G x_1 U_1 ... x_d U_d (Section 2.2).  G: (r_1..r_d) F64/F32;
+ * U: n_j x r_j F64/F32; Xhat: (n_1..n_d) F64/F32. */
+TK_API tk_status tucker_reconstruct(tk_handle* h, const tk_tensor* G, const tk_matrix* U, tk_tensor* Xhat);
+
+/* loss = ||X - G x_1 U_1 ... x_d U_d||^2 with the residual formed explicitly
+ * and summed in FP64.  loss: host, synchronises. */
+TK_API tk_status tucker_loss(tk_handle* h, const tk_tensor* X, const tk_tensor* G, const tk_matrix* U, double* loss);
+
+/* Gradient of grad_scale * ||X - G x_j U_j||^2 (R = X - G x_j U_j, derived from
+ * the unfolding identity of Section 2.1):
+ *   dX   = 2 grad_scale R
+ *   dG   = -2 grad_scale R x_1 U_1^T ... x_d U_d^T
+ *   dU_n = -2 grad_scale (R x_{j!=n} U_j^T)_(n) G_(n)^T
+ * The products R x_{j!=n} U_j^T for all n reuse the sketch dimension tree.
+ * dG: like G; dU: d matrices like U; dX: like X or NULL (not computed). */
+TK_API tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk_tensor* G, const tk_matrix* U,
+                                      double grad_scale, tk_tensor* dG, tk_matrix* dU, tk_tensor* dX);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUCKER_H */

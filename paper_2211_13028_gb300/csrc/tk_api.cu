@@ -1,0 +1,1044 @@
+// C-ABI entry points of libtucker and the host-side orchestration of
+// Algorithms rHKron-re and rSTHKron (arXiv 2211.13028, Sections 3.2-3.3).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+
+#include "tk_internal.cuh"
+
+namespace tk {
+
+[[noreturn]] void fail(tk_status st, const std::string& msg) { throw Error{st, msg}; }
+
+cudaEvent_t Profiler::get() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    TK_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+ProfScope::ProfScope(const Ctx& ctx, const char* name, double bytes, double flops) : c(ctx) {
+    if (!c.exec || !c.prof || !c.prof->on) return;
+    ProfRec r{name, c.prof->get(), c.prof->get(), bytes, flops};
+    TK_CUDA(cudaEventRecord(r.a, c.stream));
+    c.prof->recs.push_back(r);
+    rec = &c.prof->recs.back();
+}
+
+ProfScope::~ProfScope() {
+    if (rec) cudaEventRecord(c.prof->recs.back().b, c.stream);
+}
+
+// ------------------------------------------------------------------ validation
+
+static Tens tens_in(const tk_tensor* t, const char* name, bool allow_empty = true) {
+    TK_REQUIRE(t != nullptr, TK_ERR_ARG, std::string(name) + ": null tensor");
+    TK_REQUIRE(t->d >= 1 && t->d <= TK_MAX_D, TK_ERR_SHAPE, std::string(name) + ": d out of range");
+    TK_REQUIRE(t->dtype >= TK_F64 && t->dtype <= TK_FP8_E4M3, TK_ERR_DTYPE, std::string(name) + ": bad dtype");
+    Tens T;
+    T.p = t->data;
+    T.dt = t->dtype;
+    T.d = t->d;
+    T.scale = t->scale;
+    for (int i = 0; i < t->d; ++i) {
+        TK_REQUIRE(t->dims[i] >= 0, TK_ERR_SHAPE, std::string(name) + ": negative dimension");
+        TK_REQUIRE(allow_empty || t->dims[i] > 0, TK_ERR_SHAPE, std::string(name) + ": empty dimension");
+        T.n[i] = t->dims[i];
+    }
+    if (T.numel() > 0) {
+        TK_REQUIRE(t->data != nullptr, TK_ERR_ARG, std::string(name) + ": null data");
+        TK_REQUIRE(((uintptr_t)t->data % 16) == 0, TK_ERR_ALIGN, std::string(name) + ": data not 16-byte aligned");
+    }
+    if (T.dt == TK_FP8_E4M3)
+        TK_REQUIRE(t->scale > 0.f && std::isfinite(t->scale), TK_ERR_ARG, std::string(name) + ": FP8 scale must be > 0");
+    return T;
+}
+
+static Mat mat_in(const tk_matrix* m, const char* name) {
+    TK_REQUIRE(m != nullptr, TK_ERR_ARG, std::string(name) + ": null matrix");
+    TK_REQUIRE(m->rows >= 0 && m->cols >= 0, TK_ERR_SHAPE, std::string(name) + ": negative size");
+    TK_REQUIRE(m->ld >= std::max<int64_t>(1, m->rows), TK_ERR_SHAPE, std::string(name) + ": ld < rows");
+    TK_REQUIRE(m->dtype >= TK_F64 && m->dtype <= TK_BF16, TK_ERR_DTYPE, std::string(name) + ": bad dtype");
+    if (m->rows * m->cols > 0) {
+        TK_REQUIRE(m->data != nullptr, TK_ERR_ARG, std::string(name) + ": null data");
+        TK_REQUIRE(((uintptr_t)m->data % dtype_size(m->dtype)) == 0, TK_ERR_ALIGN,
+                   std::string(name) + ": data misaligned");
+    }
+    Mat M;
+    M.p = m->data;
+    M.dt = m->dtype;
+    M.rows = m->rows;
+    M.cols = m->cols;
+    M.ld = m->ld;
+    return M;
+}
+
+static tk_dtype acc_of(tk_dtype data) { return data == TK_F64 ? TK_F64 : TK_F32; }
+
+struct Opts {
+    std::vector<int> order;
+    int qr_method = 0;
+    int refine = 0;
+    int max_sweeps = 40;
+};
+
+static Opts opts_in(const tk_opts* o, int d) {
+    Opts r;
+    r.order.resize(d);
+    std::iota(r.order.begin(), r.order.end(), 0);
+    if (!o) return r;
+    if (o->mode_order) {
+        std::vector<int> seen(d, 0);
+        for (int i = 0; i < d; ++i) {
+            int m = o->mode_order[i];
+            TK_REQUIRE(m >= 0 && m < d && !seen[m], TK_ERR_ARG, "opts.mode_order is not a permutation of 0..d-1");
+            seen[m] = 1;
+            r.order[i] = m;
+        }
+    }
+    TK_REQUIRE(o->qr_method >= 0 && o->qr_method <= 2, TK_ERR_ARG, "opts.qr_method must be 0, 1 or 2");
+    r.qr_method = o->qr_method;
+    r.refine = o->refine;
+    if (o->max_jacobi_sweeps > 0) r.max_sweeps = o->max_jacobi_sweeps;
+    else if (o->max_jacobi_sweeps == -1) r.max_sweeps = 0;
+    else TK_REQUIRE(o->max_jacobi_sweeps == 0, TK_ERR_ARG, "opts.max_jacobi_sweeps must be >= -1");
+    return r;
+}
+
+// ------------------------------------------------------------------ small helpers
+
+// Copy of a matrix into the accumulation dtype, contiguous (ld = rows).
+static Mat mat_to(Ctx& c, const Mat& M, tk_dtype dt) {
+    Mat o;
+    o.dt = dt;
+    o.rows = M.rows;
+    o.cols = M.cols;
+    o.ld = std::max<int64_t>(1, M.rows);
+    void* p = c.alloc_bytes(dtype_size(dt) * M.rows * M.cols);
+    launch_convert(c, M.p, M.dt, M.rows, M.cols, M.ld, p, dt, o.ld, 1.f);
+    o.p = p;
+    return o;
+}
+
+static Tens tens_to(Ctx& c, const Tens& T, tk_dtype dt) {
+    Tens o = T;
+    o.dt = dt;
+    o.scale = 1.f;
+    o.p = c.alloc_bytes(dtype_size(dt) * T.numel());
+    launch_convert(c, T.p, T.dt, T.numel(), 1, std::max<int64_t>(1, T.numel()), o.p, dt, std::max<int64_t>(1, T.numel()),
+                   T.scale);
+    return o;
+}
+
+// Y = T x_j M^T with M(i, a) = M[i + ld a] (mtrans = false) or M[a + ld i];
+// output allocated in the workspace unless dst is given.
+static Tens ttm_to(Ctx& c, const Tens& T, int j, const Mat& M, bool mtrans, tk_dtype acc, void* dst = nullptr) {
+    int64_t m = mtrans ? M.rows : M.cols;
+    Tens o = T;
+    o.n[j] = m;
+    o.dt = acc;
+    o.scale = 1.f;
+    o.p = dst ? dst : c.alloc_bytes(dtype_size(acc) * o.numel());
+    launch_ttm(c, T, j, M, mtrans, m, o.p, acc);
+    return o;
+}
+
+// Apply M_i to every mode in `modes`, cheapest-shrinking mode first (smallest
+// output), the last product written to dst when given.
+static Tens multi_ttm(Ctx& c, const Tens& T, std::vector<int> modes, const Mat* M, bool mtrans, tk_dtype acc,
+                      void* dst = nullptr) {
+    Tens cur = T;
+    while (!modes.empty()) {
+        size_t best = 0;
+        double bestr = 1e300;
+        for (size_t t = 0; t < modes.size(); ++t) {
+            int i = modes[t];
+            double m = (double)(mtrans ? M[i].rows : M[i].cols);
+            double ratio = m / std::max<double>(1.0, (double)cur.n[i]);
+            if (ratio < bestr - 1e-15 || (std::fabs(ratio - bestr) <= 1e-15 && i > modes[best])) {
+                bestr = ratio;
+                best = t;
+            }
+        }
+        int i = modes[best];
+        modes.erase(modes.begin() + best);
+        cur = ttm_to(c, cur, i, M[i], mtrans, acc, modes.empty() ? dst : nullptr);
+    }
+    return cur;
+}
+
+// Dimension tree of Section 4.4 (All-Modes-Multi-TTM): apply the factors of
+// `nset`, then split the modes still owed a sketch in halves and recurse.
+// Y[j] receives X x_{k != j} M_k for every j in `mset`; dst[j] (optional)
+// names the buffer for that leaf.
+static void all_modes(Ctx& c, const Tens& T, const std::vector<int>& mset, const std::vector<int>& nset, const Mat* M,
+                      tk_dtype acc, std::vector<Tens>& Y, void* const* dst) {
+    void* leaf = (mset.size() == 1 && dst) ? dst[mset[0]] : nullptr;
+    Tens cur = nset.empty() ? T : multi_ttm(c, T, nset, M, false, acc, leaf);
+    if (mset.size() == 1) {
+        if (nset.empty() && leaf) {  // d == 1 never reaches here (d >= 2 enforced)
+            launch_convert(c, cur.p, cur.dt, cur.numel(), 1, cur.numel(), leaf, acc, cur.numel(), cur.scale);
+            cur.p = leaf;
+        }
+        Y[mset[0]] = cur;
+        return;
+    }
+    size_t h = mset.size() / 2;
+    std::vector<int> m1(mset.begin(), mset.begin() + h), m2(mset.begin() + h, mset.end());
+    all_modes(c, cur, m1, m2, M, acc, Y, dst);
+    all_modes(c, cur, m2, m1, M, acc, Y, dst);
+}
+
+// Thin QR (Algorithm RRF) of several sketch unfoldings.  Y[b] is an n_b x k_b
+// view; Q[b] receives the n_b x k_b orthonormal factor in FP64 (ld n_b).
+// CholeskyQR2 (FP64 Gram, FP64 Cholesky) with a Householder fallback selected
+// on the device (no host synchronisation): a breakdown in either Cholesky
+// pass raises bad[b], which skips the remaining CholeskyQR2 kernels and lets
+// the Householder kernel run.  slots[b] is the QR-info slot to fill.
+static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<int64_t>& n,
+                       const std::vector<int64_t>& k, const std::vector<double*>& Q, const std::vector<int>& slots) {
+    const int B = (int)Y.size();
+    if (B == 0) return;
+    TK_REQUIRE(B <= TK_MAX_D, TK_ERR_ARG, "orth: too many matrices in one batch");
+    int kmax = 1;
+    KDims kd;
+    for (int b = 0; b < B; ++b) {
+        kmax = std::max<int>(kmax, (int)k[b]);
+        kd.k[b] = (int)k[b];
+    }
+    TK_REQUIRE(kmax <= 112, TK_ERR_SHAPE, "orth: sketch width above 112 is not supported");
+    int* bad = c.alloc<int>(2 * B);  // [0, B): any breakdown, [B, 2B): pass-2 breakdown
+    double* W = c.alloc<double>((int64_t)B * kmax * kmax);
+    double* Rinv = c.alloc<double>((int64_t)B * kmax * kmax);
+    std::vector<double*> Q1(B), Hsrc(B), Htau(B);
+    for (int b = 0; b < B; ++b) {
+        Q1[b] = c.alloc<double>(n[b] * k[b]);
+        Hsrc[b] = c.alloc<double>(n[b] * k[b]);
+        Htau[b] = c.alloc<double>(k[b]);
+    }
+    launch_fill_int(c, bad, 2 * B, c.qr_method == 1 ? 1 : 0);
+    if (c.qr_method != 1) {
+        // pass 1: W = Y^T Y, R1^{-1}, Q1 = Y R1^{-1}
+        for (int b = 0; b < B; ++b) {
+            const View2& A = Y[b];
+            View2 At;  // (column, row) indexing of the same data
+            At.p = A.p;
+            At.dt = A.dt;
+            At.A1 = A.T1; At.sa1 = A.st1; At.sa2 = A.st2;
+            At.T1 = A.A1; At.st1 = A.sa1; At.st2 = A.sa2;
+            gemm_nt_f64(c, k[b], k[b], n[b], At, At, 1.0, 0.0, W + (int64_t)b * kmax * kmax, kmax, bad + b);
+        }
+        launch_chol_inv(c, B, kd, kmax, W, Rinv, bad, 1e-12);
+        for (int b = 0; b < B; ++b)
+            launch_apply_rinv(c, n[b], k[b], Y[b], Rinv + (int64_t)b * kmax * kmax, kmax, Q1[b], bad + b);
+        // pass 2 on Q1
+        for (int b = 0; b < B; ++b) {
+            View2 Qt = view_cols(Q1[b], TK_F64, n[b]);
+            gemm_nt_f64(c, k[b], k[b], n[b], Qt, Qt, 1.0, 0.0, W + (int64_t)b * kmax * kmax, kmax, bad + b);
+        }
+        launch_chol_inv(c, B, kd, kmax, W, Rinv, bad, 1e-12);
+        for (int b = 0; b < B; ++b) {
+            View2 Qr = view_rows(Q1[b], TK_F64, n[b]);
+            launch_apply_rinv(c, n[b], k[b], Qr, Rinv + (int64_t)b * kmax * kmax, kmax, Q[b], bad + b);
+        }
+    }
+    for (int b = 0; b < B; ++b) {
+        if (c.qr_method != 2) {
+            launch_copy_unfold_to_matrix(c, Y[b], n[b], k[b], Hsrc[b], bad + b);
+            launch_householder(c, n[b], k[b], Hsrc[b], Q[b], Htau[b], bad + b);
+        }
+        if (slots[b] >= 0) launch_qr_info(c, c.dqr + slots[b], bad + b, c.qr_method == 2 ? 3 : 1);
+    }
+}
+
+static void orth_one(Ctx& c, const View2& Y, int64_t n, int64_t k, double* Q, int slot) {
+    orth_batch(c, {Y}, {n}, {k}, {Q}, {slot});
+}
+
+// FP64 STHOSVD of the core (Algorithm STHOSVD applied to Ghat): per mode, Gram
+// matrix of the unfolding, Jacobi eigensolver, leading r_j eigenvectors V_j,
+// Ghat <- Ghat x_j V_j^T.  Returns the truncated core; V[j] = k_j x r_j (ld k_j).
+static Tens sthosvd_core(Ctx& c, const Tens& G0, const int64_t* r, const std::vector<int>& order,
+                         std::vector<double*>& V) {
+    Tens G = G0;
+    V.assign(G0.d, nullptr);
+    for (int j : order) {
+        int64_t kj = G.n[j];
+        TK_REQUIRE(kj <= 112, TK_ERR_SHAPE, "sthosvd: core mode above 112 is not supported");
+        int64_t K = kj ? G.numel() / kj : 0;
+        double* C = c.alloc<double>(kj * kj);
+        View2 A = view_unfold_rows(G, j);
+        gemm_nt_f64(c, kj, kj, K, A, A, 1.0, 0.0, C, kj);
+        double* w = c.alloc<double>(kj);
+        double* Vf = c.alloc<double>(kj * kj);
+        launch_jacobi(c, kj, C, w, Vf, c.max_sweeps);
+        V[j] = Vf;
+        Mat Vm;
+        Vm.p = Vf;
+        Vm.dt = TK_F64;
+        Vm.rows = kj;
+        Vm.cols = r[j];
+        Vm.ld = kj;
+        G = ttm_to(c, G, j, Vm, false, TK_F64);
+    }
+    return G;
+}
+
+// Final steps shared by both algorithms: U_j = Q_j V_j, sign gauge, casts
+// into the caller's G and U, optional relative error.
+static void finish(Ctx& c, const Tens& X, const std::vector<double*>& Qd, const std::vector<int64_t>& kdim,
+                   Tens Gt, const std::vector<double*>& V, const int64_t* r, const Tens& Gout,
+                   const std::vector<Mat>& Uout, double* err_dev) {
+    const int d = X.d;
+    std::vector<double*> U(d), sg(d);
+    for (int j = 0; j < d; ++j) {
+        U[j] = c.alloc<double>(X.n[j] * r[j]);
+        sg[j] = c.alloc<double>(r[j]);
+        gemm_nt_f64(c, X.n[j], r[j], kdim[j], view_rows(Qd[j], TK_F64, X.n[j]), view_cols(V[j], TK_F64, kdim[j]), 1.0,
+                    0.0, U[j], X.n[j]);
+        launch_sign_fix(c, U[j], X.n[j], r[j], sg[j]);
+    }
+    launch_apply_signs(c, (double*)Gt.p, Gt, sg.data());
+    launch_convert(c, Gt.p, TK_F64, Gt.numel(), 1, Gt.numel(), Gout.p, Gout.dt, Gt.numel(), 1.f);
+    for (int j = 0; j < d; ++j)
+        launch_convert(c, U[j], TK_F64, X.n[j], r[j], X.n[j], (void*)Uout[j].p, Uout[j].dt, Uout[j].ld, 1.f);
+    if (!err_dev) return;
+    // ||X - G x_j U_j|| from the returned G and U, in the accumulation dtype.
+    tk_dtype acc = acc_of(X.dt);
+    Tens Ga = tens_to(c, Gout, acc);
+    std::vector<Mat> Ua(d);
+    for (int j = 0; j < d; ++j) Ua[j] = mat_to(c, Uout[j], acc);
+    std::vector<int> modes(d);
+    std::iota(modes.begin(), modes.end(), 0);
+    // expand the mode whose factor grows least first
+    Tens Xh = Ga;
+    std::vector<int> todo = modes;
+    while (!todo.empty()) {
+        size_t best = 0;
+        double bestr = 1e300;
+        for (size_t t = 0; t < todo.size(); ++t) {
+            int i = todo[t];
+            double ratio = (double)Ua[i].rows / std::max<double>(1.0, (double)Ua[i].cols);
+            if (ratio < bestr) { bestr = ratio; best = t; }
+        }
+        int i = todo[best];
+        todo.erase(todo.begin() + best);
+        Xh = ttm_to(c, Xh, i, Ua[i], true, acc);
+    }
+    launch_residual_norms(c, X, Xh.p, acc, err_dev);
+}
+
+struct Plan {
+    std::vector<int64_t> s, k;
+};
+
+}  // namespace tk
+
+using namespace tk;
+
+// ------------------------------------------------------------------ call wrapper
+
+template <typename F>
+static tk_status run_call(tk_handle* h, F&& body) {
+    if (!h) return TK_ERR_ARG;
+    h->last_error.clear();
+    try {
+        int cur = 0;
+        TK_CUDA(cudaGetDevice(&cur));
+        TK_REQUIRE(cur == h->device, TK_ERR_ARG, "handle was created on another device than the current one");
+        Ctx plan;
+        plan.stream = h->stream;
+        plan.exec = false;
+        body(plan);
+        size_t need = plan.used + 512;
+        if (need > h->ws_bytes) {
+            TK_CUDA(cudaStreamSynchronize(h->stream));
+            if (h->ws) TK_CUDA(cudaFree(h->ws));
+            h->ws = nullptr;
+            h->ws_bytes = 0;
+            size_t grow = need + need / 4;
+            if (cudaMalloc((void**)&h->ws, grow) != cudaSuccess) {
+                cudaGetLastError();
+                h->ws = nullptr;
+                fail(TK_ERR_WORKSPACE, "workspace allocation of " + std::to_string(grow) + " bytes failed");
+            }
+            h->ws_bytes = grow;
+        }
+        Ctx ex;
+        ex.stream = h->stream;
+        ex.exec = true;
+        ex.base = h->ws;
+        ex.dflags = h->dflags;
+        ex.dqr = h->dqr;
+        ex.launches = &h->launches;
+        ex.prof = &h->prof;
+        body(ex);
+        return TK_OK;
+    } catch (const Error& e) {
+        h->last_error = e.msg;
+        return e.st;
+    } catch (const std::exception& e) {
+        h->last_error = e.what();
+        return TK_ERR_ARG;
+    }
+}
+
+static void set_opts(Ctx& c, const Opts& o) {
+    c.qr_method = o.qr_method;
+    c.refine = o.refine;
+    c.max_sweeps = o.max_sweeps;
+}
+
+static void read_err(tk_handle* h, Ctx& c, const double* dev2, double* out_rel, bool squared_abs) {
+    if (!c.exec) return;
+    double host[2] = {0, 0};
+    TK_CUDA(cudaMemcpyAsync(host, dev2, sizeof(host), cudaMemcpyDeviceToHost, c.stream));
+    TK_CUDA(cudaStreamSynchronize(c.stream));
+    if (squared_abs)
+        *out_rel = host[0];
+    else
+        *out_rel = host[1] > 0 ? std::sqrt(host[0] / host[1]) : 0.0;
+    (void)h;
+}
+
+// ------------------------------------------------------------------ handle API
+
+extern "C" {
+
+tk_status tk_create(tk_handle** h, void* stream) {
+    if (!h) return TK_ERR_ARG;
+    *h = nullptr;
+    tk_handle* x = new (std::nothrow) tk_handle();
+    if (!x) return TK_ERR_WORKSPACE;
+    x->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&x->device) != cudaSuccess || cudaMalloc((void**)&x->dflags, 64) != cudaSuccess) {
+        cudaGetLastError();
+        delete x;
+        return TK_ERR_CUDA;
+    }
+    x->dqr = (int*)((char*)x->dflags + 16);
+    if (cudaMemset(x->dflags, 0, 64) != cudaSuccess) {
+        cudaFree(x->dflags);
+        delete x;
+        return TK_ERR_CUDA;
+    }
+    *h = x;
+    return TK_OK;
+}
+
+tk_status tk_destroy(tk_handle* h) {
+    if (!h) return TK_ERR_ARG;
+    cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    if (h->dflags) cudaFree(h->dflags);
+    for (auto& r : h->prof.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->prof.pool) cudaEventDestroy(e);
+    delete h;
+    return TK_OK;
+}
+
+tk_status tk_set_stream(tk_handle* h, void* stream) {
+    if (!h) return TK_ERR_ARG;
+    h->stream = (cudaStream_t)stream;
+    return TK_OK;
+}
+
+const char* tk_last_error(const tk_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
+
+tk_status tk_sync_status(tk_handle* h, int* qr_info) {
+    if (!h) return TK_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        h->last_error = cudaGetErrorString(e);
+        return TK_ERR_CUDA;
+    }
+    unsigned flags = 0;
+    int qr[TK_MAX_D];
+    if (cudaMemcpy(&flags, h->dflags, sizeof(flags), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(qr, h->dqr, sizeof(qr), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        h->last_error = "reading device status failed";
+        return TK_ERR_CUDA;
+    }
+    cudaMemset(h->dflags, 0, sizeof(unsigned));
+    if (qr_info) memcpy(qr_info, qr, sizeof(qr));
+    if (flags & FLAG_TIMEOUT) {
+        h->last_error = "a bounded device wait gave up";
+        return TK_ERR_TIMEOUT;
+    }
+    if (flags & FLAG_NOT_CONVERGED) {
+        h->last_error = "Jacobi eigensolver reached its sweep limit";
+        return TK_ERR_NOT_CONVERGED;
+    }
+    return TK_OK;
+}
+
+tk_status tk_profile(tk_handle* h, int enable) {
+    if (!h) return TK_ERR_ARG;
+    if (enable) {
+        for (auto& r : h->prof.recs) {
+            h->prof.pool.push_back(r.a);
+            h->prof.pool.push_back(r.b);
+        }
+        h->prof.recs.clear();
+    }
+    h->prof.on = enable != 0;
+    return TK_OK;
+}
+
+int tk_profile_read(tk_handle* h, tk_prof_entry* out, int max) {
+    if (!h) return -1;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return -1;
+    std::vector<tk_prof_entry> acc;
+    for (auto& r : h->prof.recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) ms = 0.f;
+        size_t i = 0;
+        for (; i < acc.size(); ++i)
+            if (strncmp(acc[i].name, r.name, sizeof(acc[i].name)) == 0) break;
+        if (i == acc.size()) {
+            tk_prof_entry e;
+            memset(&e, 0, sizeof(e));
+            strncpy(e.name, r.name, sizeof(e.name) - 1);
+            acc.push_back(e);
+        }
+        acc[i].launches += 1;
+        acc[i].ms += ms;
+        acc[i].bytes += r.bytes;
+        acc[i].flops += r.flops;
+        h->prof.pool.push_back(r.a);
+        h->prof.pool.push_back(r.b);
+    }
+    h->prof.recs.clear();
+    int n = (int)std::min<size_t>(acc.size(), (size_t)std::max(0, max));
+    for (int i = 0; i < n; ++i) out[i] = acc[i];
+    return (int)acc.size();
+}
+
+int64_t tk_workspace_bytes(const tk_handle* h) { return h ? (int64_t)h->ws_bytes : 0; }
+int64_t tk_launch_count(const tk_handle* h) { return h ? h->launches : 0; }
+
+// ------------------------------------------------------------------ subranks (host only)
+
+static __int128 sat_mul(__int128 a, __int128 b) {
+    const __int128 cap = ((__int128)1) << 100;
+    if (a == 0 || b == 0) return 0;
+    if (a > cap / b) return cap;
+    return a * b;
+}
+
+static __int128 sat_pow(__int128 a, int e) {
+    __int128 r = 1;
+    for (int i = 0; i < e; ++i) r = sat_mul(r, a);
+    return r;
+}
+
+tk_status tucker_subranks_reuse(int d, const int64_t* r, int p, int64_t* s_out, int64_t* width_out) {
+    if (d < 2 || d > TK_MAX_D || !r || !s_out || p < 0) return TK_ERR_ARG;
+    std::vector<int64_t> ell(d), s(d);
+    __int128 P = 1;
+    for (int j = 0; j < d; ++j) {
+        if (r[j] < 1) return TK_ERR_ARG;
+        ell[j] = r[j] + p;
+        P = sat_mul(P, ell[j]);
+    }
+    for (int i = 0; i < d; ++i) {
+        // smallest s with (s * l_i)^(d-1) >= P
+        double guess = std::pow((double)P, 1.0 / (d - 1)) / (double)ell[i];
+        int64_t v = std::max<int64_t>(1, (int64_t)guess);
+        while (v > 1 && sat_pow((__int128)(v - 1) * ell[i], d - 1) >= P) --v;
+        while (sat_pow((__int128)v * ell[i], d - 1) < P) ++v;
+        s[i] = v;
+    }
+    std::vector<int> idx(d);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return s[a] > s[b]; });
+    for (int i : idx) {
+        int64_t need = 1;
+        for (int j = 0; j < d; ++j) {
+            if (j == i) continue;
+            __int128 rest = 1;
+            for (int k = 0; k < d; ++k)
+                if (k != i && k != j) rest = sat_mul(rest, s[k]);
+            int64_t q = (int64_t)((ell[j] + rest - 1) / rest);
+            need = std::max(need, q);
+        }
+        s[i] = std::min(s[i], need);
+    }
+    for (int j = 0; j < d; ++j) {
+        s_out[j] = s[j];
+        if (width_out) {
+            __int128 w = 1;
+            for (int k = 0; k < d; ++k)
+                if (k != j) w = sat_mul(w, s[k]);
+            width_out[j] = (int64_t)std::min<__int128>(w, (__int128)INT64_MAX);
+        }
+    }
+    return TK_OK;
+}
+
+// Most balanced factorisation of L into m factors >= 2 (sorted descending,
+// lexicographically smallest); returns false when none exists.
+static void factor_rec(int64_t n, int m, int64_t lo, std::vector<int64_t>& cur, std::vector<int64_t>& best,
+                       bool& found) {
+    if (m == 1) {
+        if (n >= lo) {
+            cur.push_back(n);
+            std::vector<int64_t> key(cur.rbegin(), cur.rend());  // ascending build -> descending key
+            if (!found || key < best) {
+                best = key;
+                found = true;
+            }
+            cur.pop_back();
+        }
+        return;
+    }
+    for (int64_t f = lo; ; ++f) {
+        // f^m <= n
+        __int128 pw = 1;
+        for (int t = 0; t < m; ++t) pw *= f;
+        if (pw > n) break;
+        if (n % f == 0) {
+            cur.push_back(f);
+            factor_rec(n / f, m - 1, f, cur, best, found);
+            cur.pop_back();
+        }
+    }
+}
+
+tk_status tucker_subranks_matrix(int d, const int64_t* r, int p, const int* order, int64_t* S_out,
+                                 int64_t* width_out) {
+    if (d < 2 || d > TK_MAX_D || !r || !S_out || p < 0) return TK_ERR_ARG;
+    std::vector<int> ord(d);
+    std::iota(ord.begin(), ord.end(), 0);
+    if (order) {
+        std::vector<int> seen(d, 0);
+        for (int i = 0; i < d; ++i) {
+            if (order[i] < 0 || order[i] >= d || seen[order[i]]) return TK_ERR_ARG;
+            seen[order[i]] = 1;
+            ord[i] = order[i];
+        }
+    }
+    const int m = d - 1;
+    for (int j = 0; j < d; ++j) {
+        if (r[j] < 1) return TK_ERR_ARG;
+        int64_t L = std::max<int64_t>(r[j] + p, (int64_t)1 << m);
+        std::vector<int64_t> best, cur;
+        bool found = false;
+        for (;; ++L) {
+            factor_rec(L, m, 2, cur, best, found);
+            if (found) break;
+        }
+        for (int k = 0; k < d; ++k) S_out[j * d + k] = 1;
+        int t = 0;
+        for (int k : ord) {
+            if (k == j) continue;
+            S_out[j * d + k] = best[t++];
+        }
+        if (width_out) width_out[j] = L;
+    }
+    return TK_OK;
+}
+
+// ------------------------------------------------------------------ building blocks
+
+tk_status tucker_sketch(tk_handle* h, const tk_tensor* X, const tk_matrix* Omega, tk_tensor* Y) {
+    return run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X, "X");
+        c.xdata = Xt.p;
+        c.xnumel = Xt.numel();
+        const int d = Xt.d;
+        TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "sketch: d must be >= 2");
+        TK_REQUIRE(Omega && Y, TK_ERR_ARG, "sketch: null Omega or Y");
+        tk_dtype acc = acc_of(Xt.dt);
+        std::vector<Mat> Om(d);
+        std::vector<void*> dst(d);
+        for (int j = 0; j < d; ++j) {
+            Mat o = mat_in(&Omega[j], "Omega");
+            TK_REQUIRE(o.rows == Xt.n[j], TK_ERR_SHAPE, "sketch: Omega_j must have n_j rows");
+            TK_REQUIRE(acc == TK_F64 ? o.dt == TK_F64 : o.dt != TK_F64, TK_ERR_DTYPE,
+                       "sketch: Omega must be F64 for F64 data, else F32/BF16");
+            Om[j] = mat_to(c, o, acc);
+        }
+        for (int n = 0; n < d; ++n) {
+            Tens y = tens_in(&Y[n], "Y");
+            TK_REQUIRE(y.d == d && y.dt == acc, TK_ERR_DTYPE, "sketch: Y must have the data's d and F64/F32 dtype");
+            for (int j = 0; j < d; ++j)
+                TK_REQUIRE(y.n[j] == (j == n ? Xt.n[j] : Om[j].cols), TK_ERR_SHAPE, "sketch: Y[n] has wrong dims");
+            dst[n] = y.p;
+        }
+        std::vector<Tens> Ys(d);
+        std::vector<int> all(d);
+        std::iota(all.begin(), all.end(), 0);
+        all_modes(c, Xt, all, {}, Om.data(), acc, Ys, dst.data());
+    });
+}
+
+tk_status tucker_orth(tk_handle* h, const tk_matrix* Y, tk_matrix* Q, int* info, const tk_opts* opts) {
+    tk_status st = run_call(h, [&](Ctx& c) {
+        Mat y = mat_in(Y, "Y");
+        Mat q = mat_in(Q, "Q");
+        Opts o = opts_in(opts, 1);
+        set_opts(c, o);
+        TK_REQUIRE(y.dt == TK_F64 || y.dt == TK_F32, TK_ERR_DTYPE, "orth: Y must be F64 or F32");
+        TK_REQUIRE(q.dt == TK_F64 || q.dt == TK_F32, TK_ERR_DTYPE, "orth: Q must be F64 or F32");
+        int64_t k = std::min(y.rows, y.cols);
+        TK_REQUIRE(q.rows == y.rows && q.cols == k, TK_ERR_SHAPE, "orth: Q must be rows x min(rows, cols)");
+        double* Qd = c.alloc<double>(y.rows * k);
+        if (y.cols >= y.rows) {
+            launch_fill_identity(c, Qd, y.rows);
+            launch_fill_int(c, c.dqr, 1, 2);
+        } else {
+            orth_one(c, view_rows(y.p, y.dt, y.ld), y.rows, k, Qd, 0);
+        }
+        launch_convert(c, Qd, TK_F64, y.rows, k, y.rows, (void*)q.p, q.dt, q.ld, 1.f);
+    });
+    if (st == TK_OK && info) {
+        int qr[TK_MAX_D];
+        st = tk_sync_status(h, qr);
+        *info = qr[0];
+    }
+    return st;
+}
+
+tk_status tucker_core(tk_handle* h, const tk_tensor* X, const tk_matrix* Q, tk_tensor* G) {
+    return run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X, "X");
+        c.xdata = Xt.p;
+        c.xnumel = Xt.numel();
+        Tens Gt = tens_in(G, "G");
+        const int d = Xt.d;
+        TK_REQUIRE(Q != nullptr, TK_ERR_ARG, "core: null Q");
+        tk_dtype acc = acc_of(Xt.dt);
+        TK_REQUIRE(Gt.d == d && (Gt.dt == TK_F64 || Gt.dt == TK_F32), TK_ERR_DTYPE, "core: G must be F64/F32, same d");
+        std::vector<Mat> Qm(d);
+        std::vector<int> modes(d);
+        for (int j = 0; j < d; ++j) {
+            Mat q = mat_in(&Q[j], "Q");
+            TK_REQUIRE(q.rows == Xt.n[j] && q.cols == Gt.n[j], TK_ERR_SHAPE, "core: Q_j must be n_j x k_j");
+            Qm[j] = mat_to(c, q, acc);
+            modes[j] = j;
+        }
+        bool direct = Gt.dt == acc;
+        Tens out = multi_ttm(c, Xt, modes, Qm.data(), false, acc, direct ? Gt.p : nullptr);
+        if (!direct) launch_convert(c, out.p, acc, out.numel(), 1, out.numel(), Gt.p, Gt.dt, out.numel(), 1.f);
+    });
+}
+
+// ------------------------------------------------------------------ algorithms
+
+static void check_outputs(const Tens& X, const int64_t* r, const tk_tensor* G, const tk_matrix* U, Tens& Gt,
+                          std::vector<Mat>& Um) {
+    const int d = X.d;
+    Gt = tens_in(G, "G");
+    TK_REQUIRE(Gt.d == d && (Gt.dt == TK_F64 || Gt.dt == TK_F32), TK_ERR_DTYPE, "G must be F64/F32 with the data's d");
+    TK_REQUIRE(U != nullptr, TK_ERR_ARG, "null U");
+    Um.resize(d);
+    for (int j = 0; j < d; ++j) {
+        TK_REQUIRE(Gt.n[j] == r[j], TK_ERR_SHAPE, "G dims must equal the target ranks");
+        Um[j] = mat_in(&U[j], "U");
+        TK_REQUIRE(Um[j].rows == X.n[j] && Um[j].cols == r[j], TK_ERR_SHAPE, "U_j must be n_j x r_j");
+        TK_REQUIRE(Um[j].dt == TK_F64 || Um[j].dt == TK_F32, TK_ERR_DTYPE, "U must be F64/F32");
+    }
+}
+
+tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
+                        const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err) {
+    double* errd = nullptr;
+    return run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X, "X", false);
+        c.xdata = Xt.p;
+        c.xnumel = Xt.numel();
+        const int d = Xt.d;
+        TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "rhkron: d must be >= 2");
+        TK_REQUIRE(r && Omega, TK_ERR_ARG, "rhkron: null r or Omega");
+        TK_REQUIRE(p >= 0, TK_ERR_ARG, "rhkron: p must be >= 0");
+        Opts o = opts_in(opts, d);
+        set_opts(c, o);
+        tk_dtype acc = acc_of(Xt.dt);
+        Tens Gt;
+        std::vector<Mat> Um;
+        check_outputs(Xt, r, G, U, Gt, Um);
+        std::vector<Mat> Om(d);
+        std::vector<int64_t> s(d), k(d);
+        for (int j = 0; j < d; ++j) {
+            Mat om = mat_in(&Omega[j], "Omega");
+            TK_REQUIRE(om.rows == Xt.n[j] && om.cols >= 1, TK_ERR_SHAPE, "rhkron: Omega_j must be n_j x s_j");
+            TK_REQUIRE(acc == TK_F64 ? om.dt == TK_F64 : om.dt != TK_F64, TK_ERR_DTYPE,
+                       "rhkron: Omega must be F64 for F64 data, else F32/BF16");
+            s[j] = om.cols;
+            Om[j] = mat_to(c, om, acc);
+        }
+        std::vector<int> need;
+        for (int n = 0; n < d; ++n) {
+            double w = 1;
+            for (int j = 0; j < d; ++j)
+                if (j != n) w *= (double)s[j];
+            TK_REQUIRE(w >= (double)(r[n] + p), TK_ERR_SHAPE, "rhkron: prod_{j!=n} s_j must be >= r_n + p");
+            k[n] = (int64_t)std::min<double>((double)Xt.n[n], w);
+            TK_REQUIRE(r[n] >= 1 && r[n] <= k[n], TK_ERR_SHAPE, "rhkron: need 1 <= r_n <= sketch width");
+            if (k[n] < Xt.n[n]) need.push_back(n);
+        }
+        // 1. sketches (dimension tree) for the modes that need a QR
+        std::vector<Tens> Y(d);
+        if (!need.empty()) {
+            std::vector<int> rest;
+            for (int j = 0; j < d; ++j)
+                if (std::find(need.begin(), need.end(), j) == need.end()) rest.push_back(j);
+            all_modes(c, Xt, need, rest, Om.data(), acc, Y, nullptr);
+        }
+        // 2. thin QR of each sketch unfolding
+        std::vector<double*> Qd(d);
+        std::vector<View2> Yv;
+        std::vector<int64_t> nb, kb;
+        std::vector<double*> qb;
+        std::vector<int> slots;
+        for (int n = 0; n < d; ++n) {
+            Qd[n] = c.alloc<double>(Xt.n[n] * k[n]);
+            if (k[n] < Xt.n[n]) {
+                View2 v = view_unfold_rows(Y[n], n);
+                Yv.push_back(v);
+                nb.push_back(Xt.n[n]);
+                kb.push_back(k[n]);
+                qb.push_back(Qd[n]);
+                slots.push_back(n);
+            } else {
+                launch_fill_identity(c, Qd[n], Xt.n[n]);
+            }
+        }
+        launch_fill_int(c, c.dqr, TK_MAX_D, 2);
+        orth_batch(c, Yv, nb, kb, qb, slots);
+        // 3. core Ghat = X x_j Q_j^T (modes with Q = I are skipped)
+        std::vector<Mat> Qa(d);
+        std::vector<int> cm;
+        for (int j = 0; j < d; ++j) {
+            Mat qm;
+            qm.p = Qd[j];
+            qm.dt = TK_F64;
+            qm.rows = Xt.n[j];
+            qm.cols = k[j];
+            qm.ld = Xt.n[j];
+            Qa[j] = acc == TK_F64 ? qm : mat_to(c, qm, acc);
+            if (k[j] < Xt.n[j]) cm.push_back(j);
+        }
+        Tens Gh = cm.empty() ? Xt : multi_ttm(c, Xt, cm, Qa.data(), false, acc);
+        Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
+        // 4. STHOSVD of the core in FP64, U_j = Q_j V_j, gauge, casts, error
+        std::vector<double*> V;
+        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V);
+        if (rel_err) errd = c.alloc<double>(2);
+        finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, rel_err ? errd : nullptr);
+        if (rel_err) read_err(h, c, errd, rel_err, false);
+    });
+}
+
+tk_status tucker_rsthkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
+                          const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err) {
+    double* errd = nullptr;
+    return run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X, "X", false);
+        c.xdata = Xt.p;
+        c.xnumel = Xt.numel();
+        const int d = Xt.d;
+        TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "rsthkron: d must be >= 2");
+        TK_REQUIRE(r && Omega, TK_ERR_ARG, "rsthkron: null r or Omega");
+        TK_REQUIRE(p >= 0, TK_ERR_ARG, "rsthkron: p must be >= 0");
+        Opts o = opts_in(opts, d);
+        set_opts(c, o);
+        tk_dtype acc = acc_of(Xt.dt);
+        Tens Gt;
+        std::vector<Mat> Um;
+        check_outputs(Xt, r, G, U, Gt, Um);
+        launch_fill_int(c, c.dqr, TK_MAX_D, 2);
+        Tens Gh = Xt;
+        std::vector<int64_t> cur(Xt.n, Xt.n + d), k(d);
+        std::vector<double*> Qd(d);
+        for (int j : o.order) {
+            std::vector<Mat> Om(d);
+            std::vector<int> modes;
+            double w = 1;
+            for (int kk = 0; kk < d; ++kk) {
+                if (kk == j) continue;
+                Mat om = mat_in(&Omega[j * d + kk], "Omega");
+                TK_REQUIRE(om.rows == cur[kk] && om.cols >= 1, TK_ERR_SHAPE,
+                           "rsthkron: Omega[j*d+k] must be (current size of mode k) x s_{j,k}");
+                TK_REQUIRE(acc == TK_F64 ? om.dt == TK_F64 : om.dt != TK_F64, TK_ERR_DTYPE,
+                           "rsthkron: Omega must be F64 for F64 data, else F32/BF16");
+                Om[kk] = mat_to(c, om, acc);
+                modes.push_back(kk);
+                w *= (double)om.cols;
+            }
+            TK_REQUIRE(w >= (double)(r[j] + p), TK_ERR_SHAPE, "rsthkron: prod_k s_{j,k} must be >= r_j + p");
+            k[j] = (int64_t)std::min<double>((double)Xt.n[j], w);
+            TK_REQUIRE(r[j] >= 1 && r[j] <= k[j], TK_ERR_SHAPE, "rsthkron: need 1 <= r_j <= sketch width");
+            Qd[j] = c.alloc<double>(Xt.n[j] * k[j]);
+            if (k[j] < Xt.n[j]) {
+                Tens Y = multi_ttm(c, Gh, modes, Om.data(), false, acc);
+                orth_one(c, view_unfold_rows(Y, j), Xt.n[j], k[j], Qd[j], j);
+                Mat qm;
+                qm.p = Qd[j];
+                qm.dt = TK_F64;
+                qm.rows = Xt.n[j];
+                qm.cols = k[j];
+                qm.ld = Xt.n[j];
+                Mat qa = acc == TK_F64 ? qm : mat_to(c, qm, acc);
+                Gh = ttm_to(c, Gh, j, qa, false, acc);
+            } else {
+                launch_fill_identity(c, Qd[j], Xt.n[j]);
+            }
+            cur[j] = k[j];
+        }
+        Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
+        std::vector<double*> V;
+        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V);
+        if (rel_err) errd = c.alloc<double>(2);
+        finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, rel_err ? errd : nullptr);
+        if (rel_err) read_err(h, c, errd, rel_err, false);
+    });
+}
+
+// ------------------------------------------------------------------ reconstruction, loss, gradient
+
+static Tens reconstruct_acc(Ctx& c, const Tens& Gt, const std::vector<Mat>& Um, tk_dtype acc, void* dst) {
+    const int d = Gt.d;
+    Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
+    std::vector<Mat> Ua(d);
+    for (int j = 0; j < d; ++j) Ua[j] = Um[j].dt == acc ? Um[j] : mat_to(c, Um[j], acc);
+    std::vector<int> todo(d);
+    std::iota(todo.begin(), todo.end(), 0);
+    Tens cur = Ga;
+    while (!todo.empty()) {
+        size_t best = 0;
+        double bestr = 1e300;
+        for (size_t t = 0; t < todo.size(); ++t) {
+            int i = todo[t];
+            double ratio = (double)Ua[i].rows / std::max<double>(1.0, (double)Ua[i].cols);
+            if (ratio < bestr) { bestr = ratio; best = t; }
+        }
+        int i = todo[best];
+        todo.erase(todo.begin() + best);
+        cur = ttm_to(c, cur, i, Ua[i], true, acc, todo.empty() ? dst : nullptr);
+    }
+    return cur;
+}
+
+static void check_tucker(const Tens& Gt, const tk_matrix* U, std::vector<Mat>& Um, std::vector<int64_t>& n) {
+    const int d = Gt.d;
+    TK_REQUIRE(Gt.dt == TK_F64 || Gt.dt == TK_F32, TK_ERR_DTYPE, "G must be F64/F32");
+    TK_REQUIRE(U != nullptr, TK_ERR_ARG, "null U");
+    Um.resize(d);
+    n.resize(d);
+    for (int j = 0; j < d; ++j) {
+        Um[j] = mat_in(&U[j], "U");
+        TK_REQUIRE(Um[j].cols == Gt.n[j], TK_ERR_SHAPE, "U_j must have r_j columns");
+        TK_REQUIRE(Um[j].dt == TK_F64 || Um[j].dt == TK_F32, TK_ERR_DTYPE, "U must be F64/F32");
+        n[j] = Um[j].rows;
+    }
+}
+
+tk_status tucker_reconstruct(tk_handle* h, const tk_tensor* G, const tk_matrix* U, tk_tensor* Xhat) {
+    return run_call(h, [&](Ctx& c) {
+        Tens Gt = tens_in(G, "G");
+        Tens Xh = tens_in(Xhat, "Xhat");
+        std::vector<Mat> Um;
+        std::vector<int64_t> n;
+        check_tucker(Gt, U, Um, n);
+        TK_REQUIRE(Xh.d == Gt.d, TK_ERR_SHAPE, "reconstruct: Xhat must have G's d");
+        TK_REQUIRE(Xh.dt == TK_F64 || Xh.dt == TK_F32, TK_ERR_DTYPE, "reconstruct: Xhat must be F64/F32");
+        for (int j = 0; j < Gt.d; ++j) TK_REQUIRE(Xh.n[j] == n[j], TK_ERR_SHAPE, "reconstruct: Xhat dims != U rows");
+        reconstruct_acc(c, Gt, Um, Xh.dt, Xh.p);
+    });
+}
+
+tk_status tucker_loss(tk_handle* h, const tk_tensor* X, const tk_tensor* G, const tk_matrix* U, double* loss) {
+    double* dev = nullptr;
+    return run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X, "X");
+        c.xdata = Xt.p;
+        c.xnumel = Xt.numel();
+        Tens Gt = tens_in(G, "G");
+        TK_REQUIRE(loss != nullptr, TK_ERR_ARG, "loss: null output");
+        std::vector<Mat> Um;
+        std::vector<int64_t> n;
+        check_tucker(Gt, U, Um, n);
+        TK_REQUIRE(Xt.d == Gt.d, TK_ERR_SHAPE, "loss: X and G must have the same d");
+        for (int j = 0; j < Xt.d; ++j) TK_REQUIRE(Xt.n[j] == n[j], TK_ERR_SHAPE, "loss: X dims != U rows");
+        tk_dtype acc = acc_of(Xt.dt);
+        Tens Xh = reconstruct_acc(c, Gt, Um, acc, nullptr);
+        dev = c.alloc<double>(2);
+        launch_residual_norms(c, Xt, Xh.p, acc, dev);
+        read_err(h, c, dev, loss, true);
+    });
+}
+
+tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk_tensor* G, const tk_matrix* U,
+                                      double grad_scale, tk_tensor* dG, tk_matrix* dU, tk_tensor* dX) {
+    return run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X, "X");
+        c.xdata = Xt.p;
+        c.xnumel = Xt.numel();
+        Tens Gt = tens_in(G, "G");
+        const int d = Xt.d;
+        std::vector<Mat> Um;
+        std::vector<int64_t> n;
+        check_tucker(Gt, U, Um, n);
+        TK_REQUIRE(Xt.d == Gt.d && d >= 2, TK_ERR_SHAPE, "backward: X and G must have the same d >= 2");
+        for (int j = 0; j < d; ++j) TK_REQUIRE(Xt.n[j] == n[j], TK_ERR_SHAPE, "backward: X dims != U rows");
+        Tens dGt = tens_in(dG, "dG");
+        TK_REQUIRE(dGt.d == d && (dGt.dt == TK_F64 || dGt.dt == TK_F32), TK_ERR_DTYPE, "backward: dG must be F64/F32");
+        for (int j = 0; j < d; ++j) TK_REQUIRE(dGt.n[j] == Gt.n[j], TK_ERR_SHAPE, "backward: dG dims != G dims");
+        TK_REQUIRE(dU != nullptr, TK_ERR_ARG, "backward: null dU");
+        std::vector<Mat> dUm(d);
+        for (int j = 0; j < d; ++j) {
+            dUm[j] = mat_in(&dU[j], "dU");
+            TK_REQUIRE(dUm[j].rows == n[j] && dUm[j].cols == Gt.n[j], TK_ERR_SHAPE, "backward: dU_j must be n_j x r_j");
+            TK_REQUIRE(dUm[j].dt == TK_F64 || dUm[j].dt == TK_F32, TK_ERR_DTYPE, "backward: dU must be F64/F32");
+        }
+        Tens dXt;
+        if (dX) {
+            dXt = tens_in(dX, "dX");
+            TK_REQUIRE(dXt.d == d && dXt.dt == Xt.dt, TK_ERR_DTYPE, "backward: dX must have X's dims and dtype");
+            for (int j = 0; j < d; ++j) TK_REQUIRE(dXt.n[j] == Xt.n[j], TK_ERR_SHAPE, "backward: dX dims != X dims");
+        }
+        tk_dtype acc = acc_of(Xt.dt);
+        Tens Xh = reconstruct_acc(c, Gt, Um, acc, nullptr);
+        // R = X - Xhat in the accumulation dtype
+        Tens R = Xt;
+        R.dt = acc;
+        R.scale = 1.f;
+        R.p = c.alloc_bytes(dtype_size(acc) * Xt.numel());
+        launch_axpby_residual(c, Xt, Xh.p, acc, 1.0, R.p, acc);
+        if (dX) launch_axpby_residual(c, Xt, Xh.p, acc, 2.0 * grad_scale, dXt.p, dXt.dt);
+        // T_n = R x_{j != n} U_j^T for all n (dimension tree)
+        std::vector<Mat> Ua(d);
+        for (int j = 0; j < d; ++j) Ua[j] = Um[j].dt == acc ? Um[j] : mat_to(c, Um[j], acc);
+        std::vector<Tens> T(d);
+        std::vector<int> all(d);
+        std::iota(all.begin(), all.end(), 0);
+        all_modes(c, R, all, {}, Ua.data(), acc, T, nullptr);
+        // dU_n = -2 s T_n(n) G_(n)^T
+        Tens G64 = Gt.dt == TK_F64 ? Gt : tens_to(c, Gt, TK_F64);
+        for (int j = 0; j < d; ++j) {
+            int64_t K = 1;
+            for (int i = 0; i < d; ++i)
+                if (i != j) K *= Gt.n[i];
+            double* tmp = c.alloc<double>(n[j] * Gt.n[j]);
+            gemm_nt_f64(c, n[j], Gt.n[j], K, view_unfold_rows(T[j], j), view_unfold_rows(G64, j), -2.0 * grad_scale,
+                        0.0, tmp, n[j]);
+            launch_convert(c, tmp, TK_F64, n[j], Gt.n[j], n[j], (void*)dUm[j].p, dUm[j].dt, dUm[j].ld, 1.f);
+        }
+        // dG = -2 s T_0 x_0 U_0^T
+        Tens C = ttm_to(c, T[0], 0, Ua[0], false, acc);
+        launch_scale_copy(c, C.p, acc, C.numel(), -2.0 * grad_scale, dGt.p, dGt.dt);
+    });
+}
+
+}  // extern "C"

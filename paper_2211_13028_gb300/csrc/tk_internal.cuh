@@ -1,0 +1,249 @@
+// Internal declarations shared by the libtucker translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tucker.h"
+
+namespace tk {
+
+// ------------------------------------------------------------------ errors
+
+struct Error {
+    tk_status st;
+    std::string msg;
+};
+
+[[noreturn]] void fail(tk_status st, const std::string& msg);
+
+#define TK_CUDA(x)                                                                        \
+    do {                                                                                  \
+        cudaError_t e_ = (x);                                                             \
+        if (e_ != cudaSuccess) ::tk::fail(TK_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TK_REQUIRE(cond, st, msg)            \
+    do {                                     \
+        if (!(cond)) ::tk::fail((st), (msg)); \
+    } while (0)
+
+// device-side condition bits (handle flag word)
+enum : unsigned { FLAG_NOT_CONVERGED = 1u, FLAG_TIMEOUT = 2u };
+
+inline size_t dtype_size(tk_dtype t) {
+    switch (t) {
+        case TK_F64: return 8;
+        case TK_F32: return 4;
+        case TK_BF16: return 2;
+        case TK_FP8_E4M3: return 1;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------ views
+
+// Dense column-major tensor.
+struct Tens {
+    void* p = nullptr;
+    tk_dtype dt = TK_F32;
+    int d = 0;
+    int64_t n[TK_MAX_D] = {0};
+    float scale = 1.f;
+    int64_t numel() const {
+        int64_t s = 1;
+        for (int i = 0; i < d; ++i) s *= n[i];
+        return s;
+    }
+    int64_t left(int j) const {  // prod_{k<j} n_k
+        int64_t s = 1;
+        for (int i = 0; i < j; ++i) s *= n[i];
+        return s;
+    }
+    int64_t right(int j) const {  // prod_{k>j} n_k
+        int64_t s = 1;
+        for (int i = j + 1; i < d; ++i) s *= n[i];
+        return s;
+    }
+};
+
+// Column-major matrix, element (i, j) at p[i + j*ld].
+struct Mat {
+    const void* p = nullptr;
+    tk_dtype dt = TK_F64;
+    int64_t rows = 0, cols = 0, ld = 0;
+};
+
+// Strided 2-D view used by the small FP64 kernels: element (a, t) sits at
+//   (a % A1)*sa1 + (a / A1)*sa2 + (t % T1)*st1 + (t / T1)*st2.
+// It expresses plain column-major matrices, their transposes and tensor
+// unfoldings without copies.
+struct View2 {
+    const void* p = nullptr;
+    tk_dtype dt = TK_F64;
+    int64_t A1 = INT64_MAX, sa1 = 0, sa2 = 0;
+    int64_t T1 = INT64_MAX, st1 = 0, st2 = 0;
+};
+
+// (a, t) = (row, col) of a column-major matrix.
+inline View2 view_rows(const void* p, tk_dtype dt, int64_t ld) {
+    View2 v; v.p = p; v.dt = dt; v.sa1 = 1; v.st1 = ld; return v;
+}
+// (a, t) = (col, row) of a column-major matrix.
+inline View2 view_cols(const void* p, tk_dtype dt, int64_t ld) {
+    View2 v; v.p = p; v.dt = dt; v.sa1 = ld; v.st1 = 1; return v;
+}
+// (a, t) = (row, col) of the mode-j unfolding of a tensor (L, n_j, R).
+inline View2 view_unfold_rows(const Tens& T, int j) {
+    View2 v; v.p = T.p; v.dt = T.dt;
+    int64_t L = T.left(j);
+    v.sa1 = L;
+    v.T1 = L; v.st1 = 1; v.st2 = L * T.n[j];
+    return v;
+}
+// (a, t) = (col, row) of the mode-j unfolding of a tensor (L, n_j, R).
+inline View2 view_unfold_cols(const Tens& T, int j) {
+    View2 v; v.p = T.p; v.dt = T.dt;
+    int64_t L = T.left(j);
+    v.A1 = L; v.sa1 = 1; v.sa2 = L * T.n[j];
+    v.st1 = L;
+    return v;
+}
+
+// ------------------------------------------------------------------ profiler
+
+// Optional per-launch timing: when enabled on the handle, each launcher
+// records a CUDA event pair on the launching stream around its kernel and
+// tags it with a class name plus the algorithmic bytes and flops of the
+// launch.  tk_profile_read() resolves the pairs after a synchronisation.
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+    double bytes, flops;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get();
+};
+
+// ------------------------------------------------------------------ call context
+
+// Bump allocator over the handle's workspace.  Each entry point runs its
+// orchestration twice: a planning pass (exec == false) that only sums the
+// sizes, then, with the workspace grown to fit, the executing pass.  Both
+// passes make the same allocations in the same order.
+struct Ctx {
+    cudaStream_t stream = nullptr;
+    bool exec = false;
+    char* base = nullptr;
+    size_t used = 0;
+    unsigned* dflags = nullptr;  // device condition word
+    int* dqr = nullptr;          // device QR method per mode
+    int64_t* launches = nullptr;
+    int max_sweeps = 40;
+    int qr_method = 0;
+    int refine = 0;
+    Profiler* prof = nullptr;
+    const void* xdata = nullptr;   // the caller's data tensor (tags its full passes)
+    int64_t xnumel = 0;
+
+    template <typename T>
+    T* alloc(int64_t count) {
+        size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+        size_t off = (used + 255) & ~(size_t)255;
+        used = off + bytes;
+        return exec ? reinterpret_cast<T*>(base + off) : reinterpret_cast<T*>((uintptr_t)(off + 256));
+    }
+    void* alloc_bytes(size_t bytes) { return alloc<char>((int64_t)bytes); }
+    void counted(int n = 1) const {
+        if (launches) *launches += n;
+    }
+    void check_launch() const;
+};
+
+// RAII event pair around one launch (no-op unless profiling is on).
+struct ProfScope {
+    const Ctx& c;
+    ProfRec* rec = nullptr;
+    ProfScope(const Ctx& ctx, const char* name, double bytes, double flops);
+    ~ProfScope();
+};
+
+// ------------------------------------------------------------------ kernel launchers
+// Every launcher returns immediately when !c.exec.
+
+// out = X x_j M^T   (out[.., a, ..] = sum_i M(i, a) X[.., i, ..]), M(i, a) = M.p[i + a*ld]
+// or, with mtrans, M(i, a) = M.p[a + i*ld].  M must be F64 (F64 data) or F32.
+// out is dense column-major, dims of X with n_j -> m, dtype F64 or F32.
+void launch_ttm(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, void* out, tk_dtype out_dt);
+
+// C = alpha * sum_t A(a, t) B(b, t) + beta * C, FP64, C column-major m x n (ldc).
+// A, B: View2 of F64 or F32 data.  Uses split-K partials in the workspace.
+// When skip is given and *skip != 0 the kernels return without work.
+void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const View2& B, double alpha,
+                 double beta, double* C, int64_t ldc, const int* skip = nullptr);
+
+struct KDims {
+    int k[TK_MAX_D];
+};
+
+// Batched Cholesky W = R^T R and R^{-1} (FP64, one CTA per matrix).  W: batch
+// matrices k_b x k_b (ld = kmax, stride kmax*kmax).  Rinv receives R^{-1}
+// (upper).  Matrix b is skipped when bad[b] != 0; a breakdown (pivot <= tol *
+// original diagonal) sets bad[b] = 1.
+void launch_chol_inv(const Ctx& c, int batch, const KDims& kd, int kmax, const double* W, double* Rinv, int* bad,
+                     double tol);
+
+// Q(i, c) = sum_{c' <= c} Y(i, c') Rinv(c', c), FP64 out (n x k, ld n).  Skipped when *skip != 0.
+void launch_apply_rinv(const Ctx& c, int64_t n, int64_t k, const View2& Y, const double* Rinv, int64_t ldr,
+                       double* Q, const int* skip);
+
+// Householder thin QR of Y (n x k, FP64 copy in A, ld n) producing Q with R_ii >= 0,
+// run only when *run != 0.  One CTA.  tau: k doubles scratch.
+void launch_householder(const Ctx& c, int64_t n, int64_t k, double* A, double* Q, double* tau, const int* run);
+
+// Jacobi eigensolver (one CTA per matrix): A (k x k FP64 symmetric, destroyed),
+// eigenvalues descending in w, eigenvectors as columns of V (ld k).
+void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int max_sweeps);
+
+// Element-wise helpers.
+void launch_convert(const Ctx& c, const void* src, tk_dtype sdt, int64_t rows, int64_t cols, int64_t lds,
+                    void* dst, tk_dtype ddt, int64_t ldd, float src_scale);
+void launch_fill_identity(const Ctx& c, double* Q, int64_t n);
+// A (n x k, FP64, ld n) = Y; only when *run != 0 (run may be NULL = always).
+void launch_copy_unfold_to_matrix(const Ctx& c, const View2& Y, int64_t n, int64_t k, double* A,
+                                  const int* run = nullptr);
+void launch_fill_int(const Ctx& c, int* p, int count, int value);
+// *slot = *bad ? bad_value : 0
+void launch_qr_info(const Ctx& c, int* slot, const int* bad, int bad_value);
+// Sign gauge: for each column of U (n x r, F64, ld n) make the largest-|.|
+// entry positive; sign[c] = +-1.
+void launch_sign_fix(const Ctx& c, double* U, int64_t n, int64_t r, double* sign);
+void launch_apply_signs(const Ctx& c, double* G, const Tens& shape, double* const* signs_dev);
+// partial sums of (X - Y)^2 and X^2 over a tensor, reduced into out[0..1] (FP64).
+void launch_residual_norms(Ctx& c, const Tens& X, const void* Y, tk_dtype ydt, double* out2);
+// dst = alpha * (X - Y) elementwise (dst dtype = X dtype or F32/F64)
+void launch_axpby_residual(const Ctx& c, const Tens& X, const void* Y, tk_dtype ydt, double alpha, void* dst,
+                           tk_dtype ddt);
+void launch_scale_copy(const Ctx& c, const void* src, tk_dtype sdt, int64_t n, double alpha, void* dst,
+                       tk_dtype ddt);
+
+}  // namespace tk
+
+// ------------------------------------------------------------------ handle
+struct tk_handle {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    unsigned* dflags = nullptr;
+    int* dqr = nullptr;
+    std::string last_error;
+    int64_t launches = 0;
+    tk::Profiler prof;
+};

@@ -31,6 +31,7 @@ __all__ = [
     "round_to",
     "fortran",
     "from_fortran",
+    "fmat",
     "sketch_factors_reuse",
     "sketch_factors_matrix",
     "sketch_factors_noreuse",
@@ -71,6 +72,12 @@ def fortran(x: np.ndarray | torch.Tensor, dtype: str = "f32", device="cpu") -> t
         t = x.permute(*reversed(range(x.dim()))).contiguous()
     t = t.to(device=device, dtype=_TORCH_DT[dtype])
     return t.permute(*reversed(range(t.dim())))
+
+
+def fmat(a: np.ndarray, dtype: str = "f32", device="cpu") -> torch.Tensor:
+    """Column-major (stride(0) == 1) torch matrix with the values of the 2-D array ``a``."""
+    t = torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float64).T))
+    return t.to(device=device, dtype=_TORCH_DT[dtype]).t()
 
 
 def from_fortran(t: torch.Tensor) -> np.ndarray:

@@ -1,0 +1,400 @@
+"""ctypes binding of libtucker (include/tucker.h), one Python function per C
+entry point with the same name.  Argument marshalling only: every step of the
+computation runs in the library's CUDA kernels.  Torch supplies device memory
+and the current stream.
+
+Tensors are torch tensors on a CUDA device in column-major layout (mode 1
+fastest, strides ascending; see ``empty_f`` / ``synth.fortran``); a tensor in
+any other layout is rejected, never copied silently.  Matrices are 2-D torch
+tensors with stride(0) == 1 (column-major, leading dimension stride(1)).
+
+Loading fails loudly (``TuckerError``) when libtucker.so has not been built;
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import torch
+
+__all__ = [
+    "TuckerError", "load", "empty_f", "is_colmajor",
+    "tucker_subranks_reuse", "tucker_subranks_matrix",
+    "tucker_sketch", "tucker_orth", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
+    "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
+    "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
+    "library_path",
+]
+
+TK_MAX_D = 8
+TK_F64, TK_F32, TK_BF16, TK_FP8 = 0, 1, 2, 3
+_STATUS = {0: "TK_OK", 1: "TK_ERR_ARG", 2: "TK_ERR_SHAPE", 3: "TK_ERR_DTYPE", 4: "TK_ERR_ALIGN",
+           5: "TK_ERR_WORKSPACE", 6: "TK_ERR_CUDA", 7: "TK_ERR_NOT_CONVERGED", 8: "TK_ERR_TIMEOUT"}
+_DT = {torch.float64: TK_F64, torch.float32: TK_F32, torch.bfloat16: TK_BF16}
+if hasattr(torch, "float8_e4m3fn"):
+    _DT[torch.float8_e4m3fn] = TK_FP8
+
+
+class TuckerError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class TkTensor(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("dims", ctypes.c_int64 * TK_MAX_D), ("dtype", ctypes.c_int),
+                ("data", ctypes.c_void_p), ("scale", ctypes.c_float)]
+
+
+class TkMatrix(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("dtype", ctypes.c_int), ("data", ctypes.c_void_p)]
+
+
+class TkProfEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+class TkOpts(ctypes.Structure):
+    _fields_ = [("mode_order", ctypes.POINTER(ctypes.c_int)), ("qr_method", ctypes.c_int), ("refine", ctypes.c_int),
+                ("max_jacobi_sweeps", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+_lock = threading.Lock()
+_handles: Dict[int, ctypes.c_void_p] = {}
+
+
+def library_path() -> str:
+    return os.environ.get("TUCKER_LIB", os.path.join(_HERE, "_build", "libtucker.so"))
+
+
+def load():
+    """Load libtucker.so (built by paper_2211_13028_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise TuckerError(6, f"libtucker.so not found at {path}; build it with "
+                                 "`python -m paper_2211_13028_gb300.build`")
+        lib = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        vp, i64p = ctypes.c_void_p, P(ctypes.c_int64)
+        sig = {
+            "tk_create": ([P(vp), vp], ctypes.c_int),
+            "tk_destroy": ([vp], ctypes.c_int),
+            "tk_set_stream": ([vp, vp], ctypes.c_int),
+            "tk_last_error": ([vp], ctypes.c_char_p),
+            "tk_sync_status": ([vp, P(ctypes.c_int)], ctypes.c_int),
+            "tk_workspace_bytes": ([vp], ctypes.c_int64),
+            "tk_launch_count": ([vp], ctypes.c_int64),
+            "tk_profile": ([vp, ctypes.c_int], ctypes.c_int),
+            "tk_profile_read": ([vp, P(TkProfEntry), ctypes.c_int], ctypes.c_int),
+            "tucker_subranks_reuse": ([ctypes.c_int, i64p, ctypes.c_int, i64p, i64p], ctypes.c_int),
+            "tucker_subranks_matrix": ([ctypes.c_int, i64p, ctypes.c_int, P(ctypes.c_int), i64p, i64p], ctypes.c_int),
+            "tucker_sketch": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
+            "tucker_orth": ([vp, P(TkMatrix), P(TkMatrix), P(ctypes.c_int), P(TkOpts)], ctypes.c_int),
+            "tucker_core": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
+            "tucker_rhkron": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor), P(TkMatrix),
+                               P(ctypes.c_double)], ctypes.c_int),
+            "tucker_rsthkron": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor),
+                                 P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
+            "tucker_reconstruct": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
+            "tucker_loss": ([vp, P(TkTensor), P(TkTensor), P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
+            "tucker_reconstruct_backward": ([vp, P(TkTensor), P(TkTensor), P(TkMatrix), ctypes.c_double, P(TkTensor),
+                                             P(TkMatrix), P(TkTensor)], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+# ------------------------------------------------------------------ marshalling
+
+def empty_f(dims: Sequence[int], dtype=torch.float32, device="cuda") -> torch.Tensor:
+    """Uninitialised column-major tensor of shape ``dims``."""
+    t = torch.empty(tuple(int(x) for x in reversed(dims)), dtype=dtype, device=device)
+    return t.permute(*reversed(range(len(dims))))
+
+
+def is_colmajor(t: torch.Tensor) -> bool:
+    expect = 1
+    for n, s in zip(t.shape, t.stride()):
+        if n != 1 and s != expect:
+            return False
+        expect *= n
+    return True
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype not in _DT:
+        raise TuckerError(3, f"unsupported dtype {t.dtype}")
+    return _DT[t.dtype]
+
+
+def _tensor(t: torch.Tensor, scale: float = 1.0) -> TkTensor:
+    if not t.is_cuda:
+        raise TuckerError(1, "tensor must be on a CUDA device")
+    if t.dim() < 1 or t.dim() > TK_MAX_D:
+        raise TuckerError(2, "tensor order out of range")
+    if not is_colmajor(t):
+        raise TuckerError(4, "tensor must be column-major (mode 1 fastest); use empty_f / synth.fortran")
+    s = TkTensor()
+    s.d = t.dim()
+    for i, n in enumerate(t.shape):
+        s.dims[i] = int(n)
+    s.dtype = _dt(t)
+    s.data = t.data_ptr() if t.numel() else None
+    s.scale = float(scale)
+    return s
+
+
+def _matrix(m: torch.Tensor) -> TkMatrix:
+    if not m.is_cuda:
+        raise TuckerError(1, "matrix must be on a CUDA device")
+    if m.dim() != 2:
+        raise TuckerError(2, "matrix must be 2-D")
+    rows, cols = m.shape
+    if rows > 1 and cols > 0 and m.stride(0) != 1:
+        raise TuckerError(4, "matrix must be column-major (stride(0) == 1)")
+    ld = m.stride(1) if cols > 1 else max(1, rows)
+    s = TkMatrix()
+    s.rows, s.cols, s.ld = int(rows), int(cols), int(max(ld, rows, 1))
+    s.dtype = _dt(m)
+    s.data = m.data_ptr() if m.numel() else None
+    return s
+
+
+def _mats(ms: Sequence[torch.Tensor]):
+    arr = (TkMatrix * len(ms))()
+    for i, m in enumerate(ms):
+        arr[i] = _matrix(m)
+    return arr
+
+
+def _colmajor_matrix(rows: int, cols: int, dtype, device) -> torch.Tensor:
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def _handle(device: torch.device) -> ctypes.c_void_p:
+    lib = load()
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    h = _handles.get(idx)
+    if h is None:
+        with torch.cuda.device(idx):
+            h = ctypes.c_void_p()
+            st = lib.tk_create(ctypes.byref(h), ctypes.c_void_p(torch.cuda.current_stream(idx).cuda_stream))
+            if st != 0:
+                raise TuckerError(st, "tk_create failed")
+        _handles[idx] = h
+    lib.tk_set_stream(h, ctypes.c_void_p(torch.cuda.current_stream(idx).cuda_stream))
+    return h
+
+
+def _check(st: int, h) -> None:
+    if st != 0:
+        msg = load().tk_last_error(h) if h is not None else b""
+        raise TuckerError(st, (msg or b"").decode())
+
+
+def _opts(order=None, qr_method=0, refine=0, max_jacobi_sweeps=0):
+    o = TkOpts()
+    keep = None
+    if order is not None:
+        keep = (ctypes.c_int * len(order))(*[int(x) for x in order])
+        o.mode_order = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+    o.qr_method, o.refine, o.max_jacobi_sweeps = int(qr_method), int(refine), int(max_jacobi_sweeps)
+    return o, keep
+
+
+def _acc_dtype(X: torch.Tensor):
+    return torch.float64 if X.dtype == torch.float64 else torch.float32
+
+
+# ------------------------------------------------------------------ host planning
+
+def tucker_subranks_reuse(r: Sequence[int], p: int) -> Tuple[List[int], List[int]]:
+    d = len(r)
+    rr = (ctypes.c_int64 * d)(*r)
+    s = (ctypes.c_int64 * d)()
+    w = (ctypes.c_int64 * d)()
+    _check(load().tucker_subranks_reuse(d, rr, int(p), s, w), None)
+    return list(s), list(w)
+
+
+def tucker_subranks_matrix(r: Sequence[int], p: int, order: Optional[Sequence[int]] = None):
+    d = len(r)
+    rr = (ctypes.c_int64 * d)(*r)
+    S = (ctypes.c_int64 * (d * d))()
+    w = (ctypes.c_int64 * d)()
+    ordp = (ctypes.c_int * d)(*order) if order is not None else None
+    _check(load().tucker_subranks_matrix(d, rr, int(p), ordp, S, w), None)
+    return [[S[j * d + k] for k in range(d)] for j in range(d)], list(w)
+
+
+# ------------------------------------------------------------------ device entry points
+
+def tk_sync_status(device=None) -> Tuple[int, List[int]]:
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    h = _handle(dev)
+    info = (ctypes.c_int * TK_MAX_D)()
+    st = load().tk_sync_status(h, info)
+    return st, list(info)
+
+
+def tk_launch_count(device=None) -> int:
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    return int(load().tk_launch_count(_handle(dev)))
+
+
+def tk_profile(enable: bool, device=None) -> None:
+    """Start (clearing old records) or stop per-kernel-class event timing."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    h = _handle(dev)
+    _check(load().tk_profile(h, 1 if enable else 0), h)
+
+
+def tk_profile_read(device=None) -> Dict[str, dict]:
+    """Synchronise and return {class: {launches, ms, bytes, flops}} since tk_profile(True)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    h = _handle(dev)
+    buf = (TkProfEntry * 64)()
+    n = load().tk_profile_read(h, buf, 64)
+    if n < 0:
+        raise TuckerError(6, "tk_profile_read failed")
+    return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, bytes=buf[i].bytes,
+                                       flops=buf[i].flops) for i in range(min(n, 64))}
+
+
+def tk_workspace_bytes(device=None) -> int:
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    return int(load().tk_workspace_bytes(_handle(dev)))
+
+
+def tucker_sketch(X: torch.Tensor, Omega: Sequence[torch.Tensor], scale: float = 1.0) -> List[torch.Tensor]:
+    """Y_n = X x_{j != n} Phi_j for every n (Omega_j = Phi_j^T, n_j x s_j)."""
+    d = X.dim()
+    s = [int(o.shape[1]) for o in Omega]
+    acc = _acc_dtype(X)
+    Y = [empty_f([X.shape[j] if j == n else s[j] for j in range(d)], acc, X.device) for n in range(d)]
+    ys = (TkTensor * d)(*[_tensor(y) for y in Y])
+    h = _handle(X.device)
+    _check(load().tucker_sketch(h, ctypes.byref(_tensor(X, scale)), _mats(Omega), ys), h)
+    return Y
+
+
+def tucker_orth(Y: torch.Tensor, qr_method: int = 0, out_dtype=None) -> Tuple[torch.Tensor, int]:
+    """Thin QR factor Q of a tall matrix Y (Q = I when cols >= rows); returns (Q, info)."""
+    rows, cols = Y.shape
+    k = min(rows, cols)
+    Q = _colmajor_matrix(rows, k, out_dtype or Y.dtype, Y.device)
+    info = ctypes.c_int(-1)
+    o, keep = _opts(qr_method=qr_method)
+    h = _handle(Y.device)
+    _check(load().tucker_orth(h, ctypes.byref(_matrix(Y)), ctypes.byref(_matrix(Q)), ctypes.byref(info),
+                              ctypes.byref(o)), h)
+    return Q, info.value
+
+
+def tucker_core(X: torch.Tensor, Q: Sequence[torch.Tensor], out_dtype=None, scale: float = 1.0) -> torch.Tensor:
+    """Ghat = X x_1 Q_1^T ... x_d Q_d^T."""
+    G = empty_f([int(q.shape[1]) for q in Q], out_dtype or _acc_dtype(X), X.device)
+    h = _handle(X.device)
+    _check(load().tucker_core(h, ctypes.byref(_tensor(X, scale)), _mats(Q), ctypes.byref(_tensor(G))), h)
+    return G
+
+
+def _decomp(fn, X, r, p, Omega_list, order, qr_method, refine, max_jacobi_sweeps, rel_err, out_dtype, scale):
+    d = X.dim()
+    dt = out_dtype or _acc_dtype(X)
+    G = empty_f(list(r), dt, X.device)
+    U = [_colmajor_matrix(int(X.shape[j]), int(r[j]), dt, X.device) for j in range(d)]
+    rr = (ctypes.c_int64 * d)(*[int(x) for x in r])
+    o, keep = _opts(order, qr_method, refine, max_jacobi_sweeps)
+    err = ctypes.c_double(float("nan"))
+    h = _handle(X.device)
+    st = fn(h, ctypes.byref(_tensor(X, scale)), rr, int(p), _mats(Omega_list), ctypes.byref(o),
+            ctypes.byref(_tensor(G)), _mats(U), ctypes.byref(err) if rel_err else None)
+    _check(st, h)
+    return G, U, (err.value if rel_err else None)
+
+
+def tucker_rhkron(X: torch.Tensor, r: Sequence[int], p: int, Omega: Sequence[torch.Tensor], *, order=None,
+                  qr_method: int = 0, refine: int = 0, max_jacobi_sweeps: int = 0, rel_err: bool = True,
+                  out_dtype=None, scale: float = 1.0):
+    """Algorithm rHKron-re.  Omega[j] = Phi_j^T (n_j x s_j).  Returns (G, [U_j], rel_err or None)."""
+    return _decomp(load().tucker_rhkron, X, r, p, list(Omega), order, qr_method, refine, max_jacobi_sweeps, rel_err,
+                   out_dtype, scale)
+
+
+def tucker_rsthkron(X: torch.Tensor, r: Sequence[int], p: int, Omega: Dict[Tuple[int, int], torch.Tensor], *,
+                    order=None, qr_method: int = 0, refine: int = 0, max_jacobi_sweeps: int = 0,
+                    rel_err: bool = True, out_dtype=None, scale: float = 1.0):
+    """Algorithm rSTHKron.  Omega[(j, k)] = Phi_{j,k}^T sized to mode k's current size."""
+    d = X.dim()
+    dummy = torch.zeros((1, 1), dtype=next(iter(Omega.values())).dtype, device=X.device)
+    lst = [Omega.get((j, k), dummy) if j != k else dummy for j in range(d) for k in range(d)]
+    return _decomp(load().tucker_rsthkron, X, r, p, lst, order, qr_method, refine, max_jacobi_sweeps, rel_err,
+                   out_dtype, scale)
+
+
+def tucker_reconstruct(G: torch.Tensor, U: Sequence[torch.Tensor], out_dtype=None) -> torch.Tensor:
+    """Xhat = G x_1 U_1 ... x_d U_d."""
+    Xh = empty_f([int(u.shape[0]) for u in U], out_dtype or G.dtype, G.device)
+    h = _handle(G.device)
+    _check(load().tucker_reconstruct(h, ctypes.byref(_tensor(G)), _mats(U), ctypes.byref(_tensor(Xh))), h)
+    return Xh
+
+
+def tucker_loss(X: torch.Tensor, G: torch.Tensor, U: Sequence[torch.Tensor], scale: float = 1.0) -> float:
+    """||X - G x_j U_j||^2 (host float; synchronises)."""
+    out = ctypes.c_double()
+    h = _handle(X.device)
+    _check(load().tucker_loss(h, ctypes.byref(_tensor(X, scale)), ctypes.byref(_tensor(G)), _mats(U),
+                              ctypes.byref(out)), h)
+    return out.value
+
+
+def tucker_reconstruct_backward(X: torch.Tensor, G: torch.Tensor, U: Sequence[torch.Tensor], grad_scale: float = 1.0,
+                                need_dX: bool = True, scale: float = 1.0):
+    """Gradients of grad_scale * ||X - G x_j U_j||^2: returns (dG, [dU_j], dX or None)."""
+    dG = empty_f(list(G.shape), G.dtype, G.device)
+    dU = [_colmajor_matrix(int(u.shape[0]), int(u.shape[1]), u.dtype, u.device) for u in U]
+    dX = empty_f(list(X.shape), X.dtype, X.device) if need_dX else None
+    h = _handle(X.device)
+    _check(load().tucker_reconstruct_backward(h, ctypes.byref(_tensor(X, scale)), ctypes.byref(_tensor(G)), _mats(U),
+                                              float(grad_scale), ctypes.byref(_tensor(dG)), _mats(dU),
+                                              ctypes.byref(_tensor(dX)) if need_dX else None), h)
+    return dG, dU, dX
+
+
+class TuckerLoss(torch.autograd.Function):
+    """loss = ||X - G x_1 U_1 ... x_d U_d||^2 with the library's adjoint multi-TTM backward.
+
+    ``TuckerLoss.apply(X, G, U_1, ..., U_d)``.  Nothing is saved besides the
+    inputs: the backward recomputes the residual and its sketches.
+    """
+
+    @staticmethod
+    def forward(ctx, X, G, *U):
+        ctx.save_for_backward(X, G, *U)
+        return torch.tensor(tucker_loss(X, G, list(U)), dtype=torch.float64, device=X.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        X, G, *U = ctx.saved_tensors
+        scale = float(gout.item())
+        dG, dU, dX = tucker_reconstruct_backward(X, G, U, scale, need_dX=ctx.needs_input_grad[0])
+        return (dX, dG, *dU)

@@ -1,0 +1,259 @@
+"""GPU parity: every entry point of the C ABI against the FP64 oracle on the
+same seeded inputs, element by element.  Tolerances: 1e-12 (F64 path) and
+1e-5 (F32 path, and BF16/FP8 storage whose values the oracle consumes
+exactly), relative Frobenius norm unless stated."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2211_13028_gb300 import synth
+from paper_2211_13028_gb300 import tucker as T
+from tests.gpu_helpers import TOL, align, make_X, mats, rel, require_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return require_gpu()
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# ------------------------------------------------------------------ sketch (multi-TTM)
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "fp8"])
+@pytest.mark.parametrize("dims,s", [((37, 29, 41), (3, 4, 2)), ((130, 7, 66), (5, 2, 3)), ((13, 9, 11, 7), (2, 3, 2, 2))])
+def test_sketch_parity(dev, dtype, dims, s):
+    g = _rng(1)
+    X, xv, sc = make_X(g.standard_normal(dims), dtype, dev)
+    odt = "f64" if dtype == "f64" else ("bf16" if dtype == "bf16" else "f32")
+    oms = synth.sketch_factors_reuse(dims, s, seed=2, dtype=odt)
+    Y = T.tucker_sketch(X, mats(oms, odt, dev), scale=sc)
+    d = len(dims)
+    for n in range(d):
+        ref = O.multi_ttm(xv, [(j, oms[j].T) for j in range(d) if j != n])
+        assert tuple(Y[n].shape) == ref.shape
+        assert rel(to_np(Y[n]), ref) <= TOL[dtype]
+
+
+def test_sketch_matches_explicit_kronecker(dev):
+    # Y_n(n) = X_(n) Omega_n with the Kronecker product formed explicitly (Section 3.2 identity).
+    g = _rng(3)
+    dims, s = (9, 8, 7), (2, 3, 2)
+    x = g.standard_normal(dims)
+    oms = synth.sketch_factors_reuse(dims, s, seed=4)
+    Y = T.tucker_sketch(synth.fortran(x, "f64", dev), mats(oms, "f64", dev))
+    phis = [o.T for o in oms]
+    for n in range(3):
+        assert rel(O.unfold(to_np(Y[n]), n), O.unfold(x, n) @ O.kron_omega(phis, n)) <= 1e-12
+
+
+# ------------------------------------------------------------------ thin QR
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,k", [(512, 49), (97, 13), (300, 112)])
+def test_orth_cholqr2_parity(dev, dtype, n, k):
+    y = synth.round_to(_rng(5).standard_normal((n, k)), dtype)
+    Q, info = T.tucker_orth(synth.fmat(y, dtype, dev), out_dtype=torch.float64)
+    assert info == 0
+    ref = O.thin_qr(y)
+    assert np.max(np.abs(to_np(Q) - ref)) <= 1e-12
+
+
+def test_orth_householder_forced_parity(dev):
+    y = _rng(6).standard_normal((200, 30))
+    Q, info = T.tucker_orth(synth.fmat(y, "f64", dev), qr_method=1)
+    assert info == 1
+    assert np.max(np.abs(to_np(Q) - O.thin_qr(y))) <= 1e-12
+
+
+def test_orth_rank_deficient_falls_back(dev):
+    g = _rng(7)
+    y = g.standard_normal((150, 4)) @ g.standard_normal((4, 12))  # rank 4, 12 columns
+    Q, info = T.tucker_orth(synth.fmat(y, "f64", dev))
+    assert info == 1
+    q = to_np(Q)
+    assert np.max(np.abs(q.T @ q - np.eye(12))) <= 1e-13
+    assert np.linalg.norm(q @ (q.T @ y) - y) <= 1e-12 * np.linalg.norm(y)
+
+
+def test_orth_wide_is_identity(dev):
+    y = _rng(8).standard_normal((20, 25))
+    Q, info = T.tucker_orth(synth.fmat(y, "f64", dev))
+    assert info == 2
+    np.testing.assert_array_equal(to_np(Q), np.eye(20))
+
+
+# ------------------------------------------------------------------ core multi-TTM
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_core_parity(dev, dtype):
+    g = _rng(9)
+    dims, k = (70, 33, 45), (11, 9, 13)
+    X, xv, _ = make_X(g.standard_normal(dims), dtype, dev)
+    qs = [O.thin_qr(g.standard_normal((n, kk))) for n, kk in zip(dims, k)]
+    acc = "f64" if dtype == "f64" else "f32"
+    qs = [synth.round_to(q, acc) for q in qs]
+    G = T.tucker_core(X, mats(qs, acc, dev))
+    ref = O.multi_ttm(xv, [(j, qs[j].T) for j in range(3)])
+    assert rel(to_np(G), ref) <= TOL[dtype]
+
+
+# ------------------------------------------------------------------ rHKron-re end to end
+
+def _check_decomp(G, U, err, ref, xv, tol, tol_g=None):
+    ref_err = O.rel_err(xv, ref["G"], ref["U"])
+    assert abs(err - ref_err) <= tol, (err, ref_err)
+    g, u = align(to_np(G), [to_np(x) for x in U], ref["U"])
+    for j in range(len(u)):
+        assert np.max(np.abs(u[j] - ref["U"][j])) <= (tol_g or tol)
+    assert rel(g, ref["G"]) <= (tol_g or tol)
+
+
+@pytest.mark.parametrize("literal", [False, True])
+def test_rhkron_f64_tucker64(dev, literal):
+    # 64^3 FP64: Tucker core 8^3 N(0,1), orthonormal factors, 1e-3 noise; r = 8, p = 4.
+    dims, r, p = (64, 64, 64), (8, 8, 8), 4
+    x = synth.tucker_tensor(dims, (8, 8, 8), seed=0, noise_rel=1e-3)
+    s = (12, 12, 12) if literal else tuple(O.subranks_reuse(r, p)[0])
+    oms = synth.sketch_factors_reuse(dims, s, seed=1)
+    G, U, err = T.tucker_rhkron(synth.fortran(x, "f64", dev), r, p, mats(oms, "f64", dev))
+    ref = O.rhkron(x, r, oms)
+    _check_decomp(G, U, err, ref, x, 1e-12)
+    if literal:  # full-width sketches: rHKron-re reduces to STHOSVD of X
+        Gs, Us, _ = O.sthosvd(x, r)
+        assert abs(err - O.rel_err(x, Gs, Us)) <= 1e-12
+    st, info = T.tk_sync_status(dev)
+    assert st == 0 and info[:3] == ([2, 2, 2] if literal else [0, 0, 0])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_rhkron_narrow_storage(dev, dtype):
+    dims, r, p = (96, 80, 72), (10, 12, 8), 6
+    core = synth.decaying_core((16, 16, 16), 0.75, seed=11)
+    x = synth.tucker_tensor(dims, (16, 16, 16), seed=12, noise_rel=1e-4, core=core)
+    X, xv, sc = make_X(x, dtype, dev)
+    s = O.subranks_reuse(r, p)[0]
+    odt = "bf16" if dtype == "bf16" else "f32"
+    oms = synth.sketch_factors_reuse(dims, s, seed=13, dtype=odt)
+    G, U, err = T.tucker_rhkron(X, r, p, mats(oms, odt, dev), scale=sc)
+    ref = O.rhkron(xv, r, oms)
+    _check_decomp(G, U, err, ref, xv, 1e-5)
+
+
+def test_rhkron_exact_low_rank_f64(dev):
+    dims, rk = (48, 40, 36), (4, 5, 3)
+    x = synth.tucker_tensor(dims, rk, seed=21, noise_rel=0.0)
+    r, p = rk, 6
+    s = O.subranks_reuse(r, p)[0]
+    oms = synth.sketch_factors_reuse(dims, s, seed=22)
+    G, U, err = T.tucker_rhkron(synth.fortran(x, "f64", dev), r, p, mats(oms, "f64", dev))
+    assert err <= 1e-12
+    st, info = T.tk_sync_status(dev)
+    assert st == 0 and 1 in info[:3]  # rank-deficient sketches took the Householder path
+    ref = O.rhkron(x, r, oms)
+    xh = O.reconstruct(to_np(G), [to_np(u) for u in U])
+    assert rel(xh, O.reconstruct(ref["G"], ref["U"])) <= 1e-12
+
+
+# ------------------------------------------------------------------ rSTHKron end to end
+
+def test_rsthkron_f64_d3(dev):
+    dims, r, p = (50, 44, 38), (6, 5, 7), 4
+    x = synth.tucker_tensor(dims, (9, 9, 9), seed=31, noise_rel=1e-3)
+    order = [0, 1, 2]
+    S, w = O.subranks_matrix(r, p, order)
+    k = [min(n, ww) for n, ww in zip(dims, w)]
+    oms = synth.sketch_factors_matrix(dims, S, k, order, seed=32)
+    Om = {key: synth.fmat(v, "f64", dev) for key, v in oms.items()}
+    G, U, err = T.tucker_rsthkron(synth.fortran(x, "f64", dev), r, p, Om, order=order)
+    _check_decomp(G, U, err, O.rsthkron(x, r, oms, order), x, 1e-12)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rsthkron_d4_uneven_reverse_order(dev, dtype):
+    # 4-way, uneven ranks, modes processed 4 -> 1 (the shape of the 4-way workload, scaled down).
+    dims, r, p = (24, 22, 20, 26), (3, 4, 5, 6), 3
+    core = synth.decaying_core((8, 8, 8, 8), 0.7, seed=41)
+    x = synth.tucker_tensor(dims, (8, 8, 8, 8), seed=42, noise_rel=1e-3, core=core)
+    X, xv, _ = make_X(x, dtype, dev)
+    order = [3, 2, 1, 0]
+    S, w = O.subranks_matrix(r, p, order)
+    k = [min(n, ww) for n, ww in zip(dims, w)]
+    oms = synth.sketch_factors_matrix(dims, S, k, order, seed=43, dtype=dtype)
+    Om = {key: synth.fmat(v, dtype, dev) for key, v in oms.items()}
+    G, U, err = T.tucker_rsthkron(X, r, p, Om, order=order)
+    _check_decomp(G, U, err, O.rsthkron(xv, r, oms, order), xv, TOL[dtype])
+
+
+# ------------------------------------------------------------------ reconstruction, loss, gradient
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_reconstruct_loss_backward(dev, dtype):
+    g = _rng(51)
+    dims, rk = (20, 18, 16), (4, 3, 5)
+    x = synth.round_to(g.standard_normal(dims), dtype)
+    G = synth.round_to(g.standard_normal(rk), dtype)
+    U = [synth.round_to(g.standard_normal((n, k)), dtype) for n, k in zip(dims, rk)]
+    Xd, Gd, Ud = synth.fortran(x, dtype, dev), synth.fortran(G, dtype, dev), mats(U, dtype, dev)
+    tol = TOL[dtype]
+    assert rel(to_np(T.tucker_reconstruct(Gd, Ud)), O.reconstruct(G, U)) <= tol
+    ref_loss = O.loss(x, G, U)
+    assert abs(T.tucker_loss(Xd, Gd, Ud) - ref_loss) <= tol * ref_loss
+    dG, dU, dX = T.tucker_reconstruct_backward(Xd, Gd, Ud, grad_scale=0.5)
+    ref = O.loss_grads(x, G, U)
+    assert rel(to_np(dG), 0.5 * ref["dG"]) <= 10 * tol
+    for j in range(3):
+        assert rel(to_np(dU[j]), 0.5 * ref["dU"][j]) <= 10 * tol
+    assert rel(to_np(dX), 0.5 * ref["dX"]) <= tol
+
+
+def test_autograd_function_matches_oracle(dev):
+    g = _rng(52)
+    dims, rk = (12, 10, 9), (3, 2, 4)
+    x = g.standard_normal(dims)
+    G0 = g.standard_normal(rk)
+    U0 = [g.standard_normal((n, k)) for n, k in zip(dims, rk)]
+    X = synth.fortran(x, "f64", dev).requires_grad_(True)
+    G = synth.fortran(G0, "f64", dev).requires_grad_(True)
+    U = [synth.fmat(u, "f64", dev).requires_grad_(True) for u in U0]
+    loss = T.TuckerLoss.apply(X, G, *U)
+    (3.0 * loss).backward()
+    ref = O.loss_grads(x, G0, U0)
+    assert abs(loss.item() - O.loss(x, G0, U0)) <= 1e-12 * O.loss(x, G0, U0)
+    assert rel(to_np(G.grad), 3.0 * ref["dG"]) <= 1e-12
+    assert rel(to_np(X.grad), 3.0 * ref["dX"]) <= 1e-12
+    for j in range(3):
+        assert rel(U[j].grad.cpu().numpy(), 3.0 * ref["dU"][j]) <= 1e-12
+
+
+# ------------------------------------------------------------------ error paths
+
+def test_bad_shapes_are_rejected(dev):
+    x = synth.fortran(np.zeros((8, 7, 6)), "f64", dev)
+    oms = mats(synth.sketch_factors_reuse((8, 7, 6), (2, 2, 2), seed=0), "f64", dev)
+    with pytest.raises(T.TuckerError) as e:
+        T.tucker_rhkron(x, (3, 3, 3), 1, oms[:2] + [oms[0]])  # Omega_3 has the wrong row count
+    assert e.value.status == 2
+    with pytest.raises(T.TuckerError) as e:
+        T.tucker_rhkron(x, (9, 3, 3), 0, oms)  # rank above the sketch width
+    assert e.value.status == 2
+    with pytest.raises(T.TuckerError) as e:
+        T.tucker_sketch(torch.zeros((8, 7, 6), dtype=torch.float64, device=dev), oms)  # row-major
+    assert e.value.status == 4
+
+
+def test_jacobi_sweep_limit_is_reported(dev):
+    x = synth.tucker_tensor((30, 28, 26), (5, 5, 5), seed=61, noise_rel=1e-2)
+    r, p = (3, 3, 3), 2
+    oms = synth.sketch_factors_reuse(x.shape, O.subranks_reuse(r, p)[0], seed=62)
+    T.tucker_rhkron(synth.fortran(x, "f64", dev), r, p, mats(oms, "f64", dev), max_jacobi_sweeps=-1, rel_err=False)
+    st, _ = T.tk_sync_status(dev)
+    assert st == 7
+    T.tucker_rhkron(synth.fortran(x, "f64", dev), r, p, mats(oms, "f64", dev), rel_err=False)
+    st, _ = T.tk_sync_status(dev)
+    assert st == 0
