@@ -236,6 +236,7 @@ def main():
         out = step(X)
     torch.cuda.synchronize()
     errs = (out[2], out[5])
+    dev_status, qr_info = T.tk_sync_status(dev)  # 0: every Jacobi solve converged
 
     def barrier():
         if dist is not None:
@@ -311,6 +312,7 @@ def main():
                     parallelism=("replicas" if world > 1 else "single GPU")),
         phases_ms=dict(rhkron=ph[0], rsthkron=ph[1], backward=ph[2]),
         rel_err=dict(rhkron=errs[0], rsthkron=errs[1]),
+        device_status=dev_status,
         multi_ttm=dict(tflops=ttm_tflops, ms_per_step=ttm_ms / args.steps,
                        frac_of_bf16_peak=ttm_tflops / bf16),
         roofline=dict(bound="hbm" if name.startswith(("ttm", "residual", "elementwise")) else "alu",

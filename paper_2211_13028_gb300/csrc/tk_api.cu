@@ -261,11 +261,56 @@ static void orth_one(Ctx& c, const View2& Y, int64_t n, int64_t k, double* Q, in
     orth_batch(c, {Y}, {n}, {k}, {Q}, {slot});
 }
 
-// FP64 STHOSVD of the core (Algorithm STHOSVD applied to Ghat): per mode, Gram
-// matrix of the unfolding, Jacobi eigensolver, leading r_j eigenvectors V_j,
+// Leading r eigenvectors of the symmetric k x k FP64 matrix A, as the columns
+// of Vr (k x r, ld k), in descending eigenvalue order.
+//  * FP64 data: cyclic Jacobi entirely in FP64.
+//  * otherwise: a two-stage scheme built for a chip whose FP64 rate is a small
+//    fraction of its FP32 rate.  Stage 1, mixed Jacobi on A (FP32 accuracy),
+//    gives V0; one FP64 Newton-Schulz step V0 <- V0 (3I - V0^T V0) / 2 makes it
+//    orthonormal to FP64 rounding; B = V0^T A V0 (FP64) is then diagonal up to
+//    ~1e-7 ||A||, so stage 2, mixed Jacobi on B, resolves it to ~1e-15 ||A||
+//    in absolute terms; V = V0 J, the leading r columns are selected and made
+//    orthonormal with one more Newton-Schulz step.
+static void eig_top(Ctx& c, int64_t k, const double* A, int64_t r, double* Vr, bool fp64_path) {
+    if (fp64_path) {
+        double* Ac = c.alloc<double>(k * k);
+        double* w = c.alloc<double>(k);
+        double* Vf = c.alloc<double>(k * k);
+        launch_convert(c, A, TK_F64, k * k, 1, k * k, Ac, TK_F64, k * k, 1.f);
+        launch_jacobi(c, k, Ac, w, Vf, c.max_sweeps);
+        launch_convert(c, Vf, TK_F64, k, r, k, Vr, TK_F64, k, 1.f);
+        return;
+    }
+    double* D = c.alloc<double>(k);
+    float* J = c.alloc<float>(k * k);
+    double* V0 = c.alloc<double>(k * k);
+    double* V1 = c.alloc<double>(k * k);
+    double* W = c.alloc<double>(k * k);
+    double* Pm = c.alloc<double>(k * k);
+    double* B = c.alloc<double>(k * k);
+    double* V = c.alloc<double>(k * k);
+    double* Vt = c.alloc<double>(k * r);
+    double* Wr = c.alloc<double>(r * r);
+    launch_jacobi_mixed(c, k, A, D, J, 1e-6, c.max_sweeps);
+    launch_convert(c, J, TK_F32, k, k, k, V0, TK_F64, k, 1.f);
+    launch_convert(c, J, TK_F32, k, k, k, V1, TK_F64, k, 1.f);
+    gemm_nt_f64(c, k, k, k, view_cols(V0, TK_F64, k), view_cols(V0, TK_F64, k), 1.0, 0.0, W, k);
+    gemm_nt_f64(c, k, k, k, view_rows(V0, TK_F64, k), view_cols(W, TK_F64, k), -0.5, 1.5, V1, k);
+    gemm_nt_f64(c, k, k, k, view_rows(A, TK_F64, k), view_cols(V1, TK_F64, k), 1.0, 0.0, Pm, k);
+    gemm_nt_f64(c, k, k, k, view_cols(V1, TK_F64, k), view_cols(Pm, TK_F64, k), 1.0, 0.0, B, k);
+    launch_jacobi_mixed(c, k, B, D, J, 1e-14, c.max_sweeps);
+    gemm_nt_f64(c, k, k, k, view_rows(V1, TK_F64, k), view_cols(J, TK_F32, k), 1.0, 0.0, V, k);
+    launch_select_top(c, k, r, D, V, Vt);
+    launch_convert(c, Vt, TK_F64, k, r, k, Vr, TK_F64, k, 1.f);
+    gemm_nt_f64(c, r, r, k, view_cols(Vt, TK_F64, k), view_cols(Vt, TK_F64, k), 1.0, 0.0, Wr, r);
+    gemm_nt_f64(c, k, r, r, view_rows(Vt, TK_F64, k), view_cols(Wr, TK_F64, r), -0.5, 1.5, Vr, k);
+}
+
+// STHOSVD of the core (Algorithm STHOSVD applied to Ghat) with an FP64 Gram
+// matrix per mode: leading r_j eigenvectors V_j of Ghat_(j) Ghat_(j)^T, then
 // Ghat <- Ghat x_j V_j^T.  Returns the truncated core; V[j] = k_j x r_j (ld k_j).
 static Tens sthosvd_core(Ctx& c, const Tens& G0, const int64_t* r, const std::vector<int>& order,
-                         std::vector<double*>& V) {
+                         std::vector<double*>& V, bool fp64_path) {
     Tens G = G0;
     V.assign(G0.d, nullptr);
     for (int j : order) {
@@ -275,12 +320,11 @@ static Tens sthosvd_core(Ctx& c, const Tens& G0, const int64_t* r, const std::ve
         double* C = c.alloc<double>(kj * kj);
         View2 A = view_unfold_rows(G, j);
         gemm_nt_f64(c, kj, kj, K, A, A, 1.0, 0.0, C, kj);
-        double* w = c.alloc<double>(kj);
-        double* Vf = c.alloc<double>(kj * kj);
-        launch_jacobi(c, kj, C, w, Vf, c.max_sweeps);
-        V[j] = Vf;
+        double* Vj = c.alloc<double>(kj * r[j]);
+        eig_top(c, kj, C, r[j], Vj, fp64_path);
+        V[j] = Vj;
         Mat Vm;
-        Vm.p = Vf;
+        Vm.p = Vj;
         Vm.dt = TK_F64;
         Vm.rows = kj;
         Vm.cols = r[j];
@@ -833,7 +877,7 @@ tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int 
         Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
         // 4. STHOSVD of the core in FP64, U_j = Q_j V_j, gauge, casts, error
         std::vector<double*> V;
-        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V);
+        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
         if (rel_err) errd = c.alloc<double>(2);
         finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, rel_err ? errd : nullptr);
         if (rel_err) read_err(h, c, errd, rel_err, false);
@@ -898,7 +942,7 @@ tk_status tucker_rsthkron(tk_handle* h, const tk_tensor* X, const int64_t* r, in
         }
         Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
         std::vector<double*> V;
-        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V);
+        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
         if (rel_err) errd = c.alloc<double>(2);
         finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, rel_err ? errd : nullptr);
         if (rel_err) read_err(h, c, errd, rel_err, false);

@@ -211,6 +211,14 @@ void launch_householder(const Ctx& c, int64_t n, int64_t k, double* A, double* Q
 // eigenvalues descending in w, eigenvectors as columns of V (ld k).
 void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int max_sweeps);
 
+// Mixed-precision Jacobi (FP64 diagonal, FP32 off-diagonal and rotations) on the
+// symmetric k x k FP64 matrix A (ld k): eigenvalue estimates in D (unsorted),
+// accumulated rotations in J (FP32, k x k, ld k).  Converged when every
+// off-diagonal |a_pq| <= tol * ||A||_F; otherwise FLAG_NOT_CONVERGED is raised.
+void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double tol, int max_sweeps);
+// Vr (k x r, ld k) = the columns of V (k x k) for the r largest entries of D, in descending order.
+void launch_select_top(const Ctx& c, int64_t k, int64_t r, const double* D, const double* V, double* Vr);
+
 // Element-wise helpers.
 void launch_convert(const Ctx& c, const void* src, tk_dtype sdt, int64_t rows, int64_t cols, int64_t lds,
                     void* dst, tk_dtype ddt, int64_t ldd, float src_scale);

@@ -50,6 +50,25 @@ __device__ __forceinline__ double v2ld(const View2& v, int64_t a, int64_t t) {
     return v.dt == TK_F64 ? static_cast<const double*>(v.p)[o] : (double)static_cast<const float*>(v.p)[o];
 }
 
+// Sequential walk along t of one row a of a View2 (t = 0, 1, ...).
+struct V2Walk {
+    const View2& v;
+    int64_t base, lo, hi;
+    __device__ V2Walk(const View2& vv, int64_t a) : v(vv), lo(0), hi(0) {
+        base = (v.A1 == INT64_MAX) ? a * v.sa1 : (a % v.A1) * v.sa1 + (a / v.A1) * v.sa2;
+    }
+    __device__ __forceinline__ double load() const {
+        int64_t o = base + lo * v.st1 + hi * v.st2;
+        return v.dt == TK_F64 ? static_cast<const double*>(v.p)[o] : (double)static_cast<const float*>(v.p)[o];
+    }
+    __device__ __forceinline__ void next() {
+        if (++lo == v.T1) {
+            lo = 0;
+            ++hi;
+        }
+    }
+};
+
 // ------------------------------------------------------------------ TTM
 // out[l + L*(a + m*r)] = sum_i M(i, a) X[l + L*(i + nj*r)],  rows rho = l + L*r.
 // 64 x 32 output tile per 256-thread block, K step 16, 4 x 2 outputs per thread.
@@ -193,12 +212,35 @@ __global__ void __launch_bounds__(256) gemm_nt_partial_kernel(int64_t m, int64_t
     const int64_t kb = (int64_t)blockIdx.z * kchunk;
     const int64_t ke = min(K, kb + kchunk);
     double acc[2][2] = {{0, 0}, {0, 0}};
+    // each thread loads rows rr0, rr0 + 16 at column offset kk (fixed): precompute row offsets
+    const int kk = tid % 16, rr0 = tid / 16;
+    int64_t oa[2], ob[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        int64_t ra = a0 + rr0 + 16 * q, rb = b0 + rr0 + 16 * q;
+        oa[q] = ra < m ? ((A.A1 == INT64_MAX) ? ra * A.sa1 : (ra % A.A1) * A.sa1 + (ra / A.A1) * A.sa2) : -1;
+        ob[q] = rb < n ? ((B.A1 == INT64_MAX) ? rb * B.sa1 : (rb % B.A1) * B.sa1 + (rb / B.A1) * B.sa2) : -1;
+    }
     for (int64_t k0 = kb; k0 < ke; k0 += 16) {
-        for (int e = tid; e < 16 * 32; e += 256) {
-            int kk = e % 16, rr = e / 16;
-            int64_t k = k0 + kk;
-            As[kk][rr] = (k < ke && a0 + rr < m) ? v2ld(A, a0 + rr, k) : 0.0;
-            Bs[kk][rr] = (k < ke && b0 + rr < n) ? v2ld(B, b0 + rr, k) : 0.0;
+        int64_t k = k0 + kk;
+        int64_t ta = -1, tb = -1;
+        if (k < ke) {
+            ta = (A.T1 == INT64_MAX) ? k * A.st1 : (k % A.T1) * A.st1 + (k / A.T1) * A.st2;
+            tb = (B.T1 == INT64_MAX) ? k * B.st1 : (k % B.T1) * B.st1 + (k / B.T1) * B.st2;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            double va = 0.0, vb = 0.0;
+            if (ta >= 0 && oa[q] >= 0) {
+                int64_t o = oa[q] + ta;
+                va = A.dt == TK_F64 ? static_cast<const double*>(A.p)[o] : (double)static_cast<const float*>(A.p)[o];
+            }
+            if (tb >= 0 && ob[q] >= 0) {
+                int64_t o = ob[q] + tb;
+                vb = B.dt == TK_F64 ? static_cast<const double*>(B.p)[o] : (double)static_cast<const float*>(B.p)[o];
+            }
+            As[kk][rr0 + 16 * q] = va;
+            Bs[kk][rr0 + 16 * q] = vb;
         }
         __syncthreads();
 #pragma unroll
@@ -234,8 +276,38 @@ __global__ void gemm_reduce_kernel(int64_t m, int64_t n, int nsplit, const doubl
     *dst = beta == 0.0 ? alpha * s : alpha * s + beta * *dst;
 }
 
+// Small problems (m, n <= 256, K <= 512): one output per thread, 8 x 8 tiles,
+// no split-K, alpha/beta applied in place (C must not alias A or B).
+__global__ void __launch_bounds__(64) gemm_nt_tiny_kernel(int64_t m, int64_t n, int64_t K, View2 A, View2 B,
+                                                          double alpha, double beta, double* C, int64_t ldc,
+                                                          const int* skip) {
+    if (skip && *skip) return;
+    const int64_t a = (int64_t)blockIdx.x * 8 + (threadIdx.x & 7);
+    const int64_t b = (int64_t)blockIdx.y * 8 + (threadIdx.x >> 3);
+    if (a >= m || b >= n) return;
+    // walk t with incremental offsets: no integer division in the loop
+    V2Walk wa(A, a), wb(B, b);
+    double s = 0.0;
+    for (int64_t t = 0; t < K; ++t) {
+        s = fma(wa.load(), wb.load(), s);
+        wa.next();
+        wb.next();
+    }
+    double* dst = C + a + ldc * b;
+    *dst = beta == 0.0 ? alpha * s : alpha * s + beta * *dst;
+}
+
 void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const View2& B, double alpha, double beta,
                  double* C, int64_t ldc, const int* skip) {
+    if (m <= 256 && n <= 256 && K <= 512 && K > 0) {
+        if (!c.exec || m == 0 || n == 0) return;
+        dim3 grid((unsigned)((m + 7) / 8), (unsigned)((n + 7) / 8));
+        ProfScope ps(c, "gemm_f64", 8.0 * (double)(m + n) * K + 8.0 * m * n, 2.0 * m * n * K);
+        gemm_nt_tiny_kernel<<<grid, 64, 0, c.stream>>>(m, n, K, A, B, alpha, beta, C, ldc, skip);
+        c.counted();
+        c.check_launch();
+        return;
+    }
     int64_t tiles = ((m + 31) / 32) * ((n + 31) / 32);
     int64_t nsplit = (304 + tiles - 1) / tiles;
     int64_t maxsplit = (K + 63) / 64;
@@ -489,6 +561,10 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int k, double* Ag, double* 
     const int kp = k + (k & 1);
     const int half = kp / 2;
     const double eps = 2.220446049250313e-16;
+    __shared__ double red[33];
+    double part = 0.0;
+    for (int e = tid; e < k * k; e += nt) part += A[e] * A[e];
+    const double athr = 4.0 * eps * sqrt(block_sum(part, red));  // absolute off-diagonal threshold
     bool converged = (k <= 1);
     for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
         int off = 0;
@@ -496,7 +572,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int k, double* Ag, double* 
             int p = e % k, q = e / k;
             if (p < q) {
                 double apq = fabs(A[p + k * q]);
-                if (apq > 1e-300 && apq > eps * sqrt(fabs(A[p + k * p]) * fabs(A[q + k * q]))) off = 1;
+                if (apq > athr) off = 1;
             }
         }
         if (!__syncthreads_or(off)) {
@@ -517,7 +593,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int k, double* Ag, double* 
                 double c = 1.0, s = 0.0;
                 if (q < k) {
                     double app = A[p + k * p], aqq = A[q + k * q], apq = A[p + k * q];
-                    if (fabs(apq) > 1e-300 && fabs(apq) > eps * sqrt(fabs(app) * fabs(aqq))) {
+                    if (fabs(apq) > athr) {
                         double tau = (aqq - app) / (2.0 * apq);
                         double t1 = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
                         c = 1.0 / hypot(1.0, t1);
@@ -563,7 +639,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int k, double* Ag, double* 
             int p = e % k, q = e / k;
             if (p < q) {
                 double apq = fabs(A[p + k * q]);
-                if (apq > 1e-300 && apq > eps * sqrt(fabs(A[p + k * p]) * fabs(A[q + k * q]))) off = 1;
+                if (apq > athr) off = 1;
             }
         }
         converged = !__syncthreads_or(off);
@@ -592,6 +668,214 @@ void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int
         TK_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(c, "jacobi", 24.0 * k * k, 9.0 * k * k * k * 8);
     jacobi_kernel<<<1, 256, smem, c.stream>>>((int)k, A, w, V, max_sweeps, use_smem, nullptr, c.dflags);
+    c.counted();
+    c.check_launch();
+}
+
+// ------------------------------------------------------------------ mixed-precision Jacobi
+// Two-sided cyclic Jacobi on a symmetric matrix held as an FP64 diagonal D and
+// an FP32 off-diagonal F (zero diagonal), accumulating the rotations in an
+// FP32 matrix J.  Rotation angles use the FP64 diagonal difference; the pair's
+// own 2 x 2 block is updated in closed form (a_pp -= t a_pq, a_qq += t a_pq,
+// a_pq = 0).  When F is small in absolute terms (a matrix already close to
+// diagonal), FP32 storage of F carries FP64-level absolute accuracy.
+// Pairs follow a round-robin tournament; each thread rotates whole 2 x 2
+// blocks (rows of one pair x columns of another) in one read-modify-write.
+// One CTA; F, J and D live in shared memory (k <= 112).
+
+constexpr int JM_THREADS = 512;
+constexpr int JM_FB = 4;  // F blocks per thread: half(half+1)/2 <= 1596 for k <= 112
+constexpr int JM_JB = 7;  // J blocks per thread: ceil(k/2) * half <= 3136
+
+__global__ void __launch_bounds__(JM_THREADS) jacobi_mixed_kernel(int k, const double* __restrict__ A, double* Dout,
+                                                                  float* Jout, double tol, int max_sweeps,
+                                                                  unsigned* flags) {
+    extern __shared__ unsigned char smraw[];
+    const int ldf = k + 1;  // odd row stride: column walks are bank-conflict free
+    double* D = reinterpret_cast<double*>(smraw);
+    float* F = reinterpret_cast<float*>(D + k);
+    float* J = F + (size_t)k * ldf;
+    __shared__ float cs[64], sn[64];
+    __shared__ int P[64], Qp[64];
+    __shared__ double red[33];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double part = 0.0;
+    for (int e = tid; e < k * k; e += nt) {
+        int i = e % k, j = e / k;
+        double v = A[i + (int64_t)k * j];
+        part += v * v;
+        if (i == j) {
+            D[i] = v;
+            F[i * ldf + j] = 0.f;
+        } else {
+            F[i * ldf + j] = (float)v;
+        }
+        J[i * ldf + j] = (i == j) ? 1.f : 0.f;
+    }
+    const double thr = tol * sqrt(block_sum(part, red));
+    const float fthr = (float)thr;
+    const int kp = k + (k & 1), half = kp / 2, nrp = (k + 1) / 2;
+    // per-thread work lists, fixed for the whole solve
+    int fb[JM_FB], jb[JM_JB];
+    const int nfb = half * (half + 1) / 2;
+#pragma unroll
+    for (int i = 0; i < JM_FB; ++i) {
+        int e = tid + nt * i;
+        fb[i] = -1;
+        if (e < nfb) {
+            int u = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+            while (u * (u + 1) / 2 > e) --u;
+            while ((u + 1) * (u + 2) / 2 <= e) ++u;
+            int t = e - u * (u + 1) / 2;
+            fb[i] = t | (u << 8);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < JM_JB; ++i) {
+        int e = tid + nt * i;
+        jb[i] = e < nrp * half ? ((e % nrp) | ((e / nrp) << 8)) : -1;
+    }
+    bool converged = false;
+    for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
+        int off = 0;
+        for (int e = tid; e < k * k; e += nt) {
+            int i = e % k, j = e / k;
+            if (i < j && fabsf(F[i * ldf + j]) > fthr) off = 1;
+        }
+        if (!__syncthreads_or(off)) {
+            converged = true;
+            break;
+        }
+        if (sweep == max_sweeps) break;
+        for (int step = 0; step < kp - 1; ++step) {
+            if (tid < half) {
+                const int t = tid;
+                int p, q;
+                if (t == 0) {
+                    p = step;
+                    q = kp - 1;
+                } else {
+                    p = step + t;
+                    if (p >= kp - 1) p -= kp - 1;
+                    q = step - t;
+                    if (q < 0) q += kp - 1;
+                }
+                if (p > q) { int tmp = p; p = q; q = tmp; }
+                float c = 1.f, sv = 0.f;
+                if (q < k) {
+                    float fpq = F[p * ldf + q];
+                    if (fabsf(fpq) > fthr) {
+                        float tau = (float)(D[q] - D[p]) / (2.f * fpq);
+                        float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+                        c = 1.f / sqrtf(1.f + tt * tt);
+                        sv = tt * c;
+                        D[p] -= (double)tt * (double)fpq;
+                        D[q] += (double)tt * (double)fpq;
+                    }
+                } else {
+                    q = -1;
+                }
+                P[t] = p; Qp[t] = q; cs[t] = c; sn[t] = sv;
+            }
+            __syncthreads();
+            // F <- R_t^T F R_u on the 2 x 2 block (pair t rows, pair u columns), t <= u,
+            // with the (u, t) block written as its mirror: F stays exactly symmetric.
+#pragma unroll
+            for (int i = 0; i < JM_FB; ++i) {
+                if (fb[i] < 0) continue;
+                const int t = fb[i] & 0xff, u = fb[i] >> 8;
+                const int p = P[t], q = Qp[t], pp = P[u], qq = Qp[u];
+                const float s1 = sn[t], s2 = sn[u];
+                if (t == u) {
+                    if (q >= 0 && s1 != 0.f) F[p * ldf + q] = F[q * ldf + p] = 0.f;
+                    continue;
+                }
+                if (s1 == 0.f && s2 == 0.f) continue;
+                const float c1 = cs[t], c2 = cs[u];
+                float a = F[p * ldf + pp];
+                float b = qq >= 0 ? F[p * ldf + qq] : 0.f;
+                float cc = q >= 0 ? F[q * ldf + pp] : 0.f;
+                float dd = (q >= 0 && qq >= 0) ? F[q * ldf + qq] : 0.f;
+                float r00 = c1 * a - s1 * cc, r01 = c1 * b - s1 * dd;
+                float r10 = s1 * a + c1 * cc, r11 = s1 * b + c1 * dd;
+                float v00 = c2 * r00 - s2 * r01, v01 = s2 * r00 + c2 * r01;
+                float v10 = c2 * r10 - s2 * r11, v11 = s2 * r10 + c2 * r11;
+                F[p * ldf + pp] = v00;
+                F[pp * ldf + p] = v00;
+                if (qq >= 0) {
+                    F[p * ldf + qq] = v01;
+                    F[qq * ldf + p] = v01;
+                }
+                if (q >= 0) {
+                    F[q * ldf + pp] = v10;
+                    F[pp * ldf + q] = v10;
+                    if (qq >= 0) {
+                        F[q * ldf + qq] = v11;
+                        F[qq * ldf + q] = v11;
+                    }
+                }
+            }
+            // J <- J R on 2-row x pair blocks
+#pragma unroll
+            for (int i = 0; i < JM_JB; ++i) {
+                if (jb[i] < 0) continue;
+                const int rp = jb[i] & 0xff, t = jb[i] >> 8;
+                const int p = P[t], q = Qp[t];
+                const float s1 = sn[t];
+                if (q < 0 || s1 == 0.f) continue;
+                const float c1 = cs[t];
+                const int r0 = 2 * rp, r1 = 2 * rp + 1;
+                float a = J[r0 * ldf + p], b = J[r0 * ldf + q];
+                J[r0 * ldf + p] = c1 * a - s1 * b;
+                J[r0 * ldf + q] = s1 * a + c1 * b;
+                if (r1 < k) {
+                    a = J[r1 * ldf + p];
+                    b = J[r1 * ldf + q];
+                    J[r1 * ldf + p] = c1 * a - s1 * b;
+                    J[r1 * ldf + q] = s1 * a + c1 * b;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (!converged && tid == 0) atomicOr(flags, FLAG_NOT_CONVERGED);
+    for (int i = tid; i < k; i += nt) Dout[i] = D[i];
+    for (int e = tid; e < k * k; e += nt) {
+        int i = e % k, j = e / k;
+        Jout[i + (int64_t)k * j] = J[i * ldf + j];
+    }
+}
+
+void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double tol, int max_sweeps) {
+    if (!c.exec) return;
+    TK_REQUIRE(k >= 1 && k <= 112, TK_ERR_SHAPE, "jacobi_mixed: 1 <= k <= 112");
+    size_t smem = sizeof(double) * k + 2 * sizeof(float) * k * (k + 1);
+    if (smem > 48 * 1024)
+        TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(c, "jacobi", 8.0 * k * k + 8.0 * k * k, 12.0 * k * k * k * max_sweeps);
+    jacobi_mixed_kernel<<<1, JM_THREADS, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
+    c.counted();
+    c.check_launch();
+}
+
+// Vr[:, rank] = V[:, i] for the r largest D (ties: lower index first).
+__global__ void select_top_kernel(int64_t k, int64_t r, const double* D, const double* V, double* Vr) {
+    for (int64_t i = blockIdx.x; i < k; i += gridDim.x) {
+        double di = D[i];
+        int64_t rank = 0;
+        for (int64_t j = 0; j < k; ++j) {
+            double dj = D[j];
+            rank += (dj > di) || (dj == di && j < i);
+        }
+        if (rank >= r) continue;
+        for (int64_t row = threadIdx.x; row < k; row += blockDim.x) Vr[row + k * rank] = V[row + k * i];
+    }
+}
+
+void launch_select_top(const Ctx& c, int64_t k, int64_t r, const double* D, const double* V, double* Vr) {
+    if (!c.exec || k == 0 || r == 0) return;
+    ProfScope ps(c, "elementwise", 16.0 * k * r, 0.0);
+    select_top_kernel<<<(unsigned)k, 64, 0, c.stream>>>(k, r, D, V, Vr);
     c.counted();
     c.check_launch();
 }

@@ -105,13 +105,23 @@ def test_core_parity(dev, dtype):
 
 # ------------------------------------------------------------------ rHKron-re end to end
 
-def _check_decomp(G, U, err, ref, xv, tol, tol_g=None):
+def _check_decomp(G, U, err, ref, xv, tol):
+    """rel_err (absolute difference), core G (relative Frobenius, after fixing
+    the sign gauge), reconstruction, and each U_j weighted by the singular
+    values of G_(j): a column whose singular value is s_i is only determined
+    to (rounding) * s_1 / gap_i, and its effect on the reconstruction scales
+    with s_i, so || (U_j - U_j^ref) diag(s) || / || s || is the meaningful
+    per-factor error."""
     ref_err = O.rel_err(xv, ref["G"], ref["U"])
     assert abs(err - ref_err) <= tol, (err, ref_err)
     g, u = align(to_np(G), [to_np(x) for x in U], ref["U"])
+    assert rel(g, ref["G"]) <= tol
     for j in range(len(u)):
-        assert np.max(np.abs(u[j] - ref["U"][j])) <= (tol_g or tol)
-    assert rel(g, ref["G"]) <= (tol_g or tol)
+        sv = np.linalg.svd(O.unfold(ref["G"], j), compute_uv=False)
+        werr = np.linalg.norm((u[j] - ref["U"][j]) * sv[None, :]) / np.linalg.norm(sv)
+        assert werr <= tol, (j, werr)
+        assert np.max(np.abs(u[j].T @ u[j] - np.eye(u[j].shape[1]))) <= max(tol, 1e-6)
+    assert rel(O.reconstruct(g, u), O.reconstruct(ref["G"], ref["U"])) <= tol
 
 
 @pytest.mark.parametrize("literal", [False, True])
@@ -133,14 +143,21 @@ def test_rhkron_f64_tucker64(dev, literal):
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
 def test_rhkron_narrow_storage(dev, dtype):
-    dims, r, p = (96, 80, 72), (10, 12, 8), 6
-    core = synth.decaying_core((16, 16, 16), 0.75, seed=11)
+    # Core entries decay by 0.5 per index so that consecutive singular values of
+    # the unfoldings are well separated: the factors are then determined to
+    # the FP32 rounding level and can be compared column by column.  FP8
+    # quantisation noise (~2% of ||X||) hides all but the leading directions,
+    # so the FP8 case uses rank 4.
+    dims, r, p = (96, 80, 72), ((4, 4, 4) if dtype == "fp8" else (10, 12, 8)), 6
+    core = synth.decaying_core((16, 16, 16), 0.5, seed=11)
     x = synth.tucker_tensor(dims, (16, 16, 16), seed=12, noise_rel=1e-4, core=core)
     X, xv, sc = make_X(x, dtype, dev)
     s = O.subranks_reuse(r, p)[0]
     odt = "bf16" if dtype == "bf16" else "f32"
     oms = synth.sketch_factors_reuse(dims, s, seed=13, dtype=odt)
     G, U, err = T.tucker_rhkron(X, r, p, mats(oms, odt, dev), scale=sc)
+    st, info = T.tk_sync_status(dev)
+    assert st == 0 and info[:3] == [0, 0, 0]  # eigensolvers converged, CholeskyQR2 held
     ref = O.rhkron(xv, r, oms)
     _check_decomp(G, U, err, ref, xv, 1e-5)
 
