@@ -2,6 +2,7 @@
 // Algorithms rHKron-re and rSTHKron (arXiv 2211.13028, Sections 3.2-3.3).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <numeric>
@@ -145,7 +146,10 @@ static Tens ttm_to(Ctx& c, const Tens& T, int j, const Mat& M, bool mtrans, tk_d
     o.dt = acc;
     o.scale = 1.f;
     o.p = dst ? dst : c.alloc_bytes(dtype_size(acc) * o.numel());
-    launch_ttm(c, T, j, M, mtrans, m, o.p, acc);
+    if (c.use_tc && ttm_tc_eligible(T, j, m, acc))
+        launch_ttm_tc(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
+    else
+        launch_ttm(c, T, j, M, mtrans, m, o.p, acc);
     return o;
 }
 
@@ -399,6 +403,7 @@ static tk_status run_call(tk_handle* h, F&& body) {
         Ctx plan;
         plan.stream = h->stream;
         plan.exec = false;
+        plan.use_tc = h->use_tc;
         body(plan);
         size_t need = plan.used + 512;
         if (need > h->ws_bytes) {
@@ -422,6 +427,7 @@ static tk_status run_call(tk_handle* h, F&& body) {
         ex.dqr = h->dqr;
         ex.launches = &h->launches;
         ex.prof = &h->prof;
+        ex.use_tc = h->use_tc;
         body(ex);
         return TK_OK;
     } catch (const Error& e) {
@@ -461,6 +467,8 @@ tk_status tk_create(tk_handle** h, void* stream) {
     tk_handle* x = new (std::nothrow) tk_handle();
     if (!x) return TK_ERR_WORKSPACE;
     x->stream = (cudaStream_t)stream;
+    const char* ttm_env = getenv("TUCKER_TTM");
+    x->use_tc = !(ttm_env && strcmp(ttm_env, "simt") == 0);
     if (cudaGetDevice(&x->device) != cudaSuccess || cudaMalloc((void**)&x->dflags, 64) != cudaSuccess) {
         cudaGetLastError();
         delete x;

@@ -151,6 +151,7 @@ struct Ctx {
     Profiler* prof = nullptr;
     const void* xdata = nullptr;   // the caller's data tensor (tags its full passes)
     int64_t xnumel = 0;
+    bool use_tc = true;            // tensor-core TTM where eligible
 
     template <typename T>
     T* alloc(int64_t count) {
@@ -181,6 +182,11 @@ struct ProfScope {
 // or, with mtrans, M(i, a) = M.p[a + i*ld].  M must be F64 (F64 data) or F32.
 // out is dense column-major, dims of X with n_j -> m, dtype F64 or F32.
 void launch_ttm(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, void* out, tk_dtype out_dt);
+
+// Tensor-core (tcgen05, 3xTF32) version of launch_ttm for FP32 data and output,
+// m <= 96; ttm_tc_eligible says whether a TTM qualifies (shape, dtype, alignment).
+bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
+void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 
 // C = alpha * sum_t A(a, t) B(b, t) + beta * C, FP64, C column-major m x n (ldc).
 // A, B: View2 of F64 or F32 data.  Uses split-K partials in the workspace.
@@ -254,4 +260,5 @@ struct tk_handle {
     std::string last_error;
     int64_t launches = 0;
     tk::Profiler prof;
+    bool use_tc = true;  // TUCKER_TTM=simt selects the SIMT TTM kernels instead
 };

@@ -1,0 +1,573 @@
+// Tensor-core mode-j contraction (TTM) for FP32 data on sm_103a.
+//
+//   out[l + L*(a + m*r)] = sum_i M(i, a) X[l + L*(i + n_j*r)]     (X viewed as L x n_j x R)
+//
+// FP32 accuracy from TF32 tensor cores by the split-product ("3xTF32") method:
+// x = x_hi + x_lo and M = M_hi + M_lo with every part a TF32 value (round to
+// nearest), and x*M ~ x_hi*M_hi + x_hi*M_lo + x_lo*M_hi with FP32 accumulation.
+//
+// Kernel structure (persistent, one CTA of 12 warps per SM):
+//   warp 0      TMA producer: 32-deep K chunks of a 128-row tile of X (16 KB) plus the
+//               matching 32 x NPAD chunks of M_hi and M_lo, into an SMEM ring.
+//   warp 1      allocates TMEM; lane 0 issues tcgen05.mma.
+//   warps 4-7   converters: lane l of the tile reads its 32 values of the chunk from
+//               SMEM, splits them into TF32 hi / lo and writes them to TMEM with
+//               tcgen05.st.  The MMA reads A from TMEM, so X is read from SMEM
+//               exactly once, and a contraction over a non-contiguous mode
+//               (MN-major X) needs no transpose: only the element each lane reads
+//               differs.
+//   warps 8-11  epilogue: tcgen05.ld of a double-buffered accumulator, hi+lo column
+//               halves summed, rows written to global memory.
+// One MMA per 8-deep K step computes A_hi * [M_hi ; M_lo] (N = 2*NPAD, the two halves
+// land in separate TMEM columns); a second adds A_lo * M_hi into the first half.
+// Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA raises
+// FLAG_TIMEOUT, stops issuing work, drains what it issued and frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tk_internal.cuh"
+
+namespace tk {
+namespace tc {
+
+constexpr int kThreads = 384;
+constexpr int kRows = 128;    // tile rows (TMEM lanes)
+constexpr int kChunk = 32;    // K elements per pipeline stage
+constexpr int kXBytes = kRows * kChunk * 4;
+constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s per wait
+
+// ------------------------------------------------------------------ PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false when the CTA is aborting or the limit expired (which
+// also starts the abort and records FLAG_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, unsigned* flags) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (gtimer() - t0 > kTimeoutNs) {
+            *abort = 1;
+            atomicOr(flags, FLAG_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B[smem desc], kind::tf32, M = 128.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Instruction descriptor: D F32, A/B TF32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+// Shared-memory descriptor of a K-major operand in the 128-byte-swizzle layout
+// (rows of 128 B, 8-row groups 1024 B apart).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+#define TK_R32(a) "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), \
+    "r"(a[8]), "r"(a[9]), "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15]),          \
+    "r"(a[16]), "r"(a[17]), "r"(a[18]), "r"(a[19]), "r"(a[20]), "r"(a[21]), "r"(a[22]), "r"(a[23]),         \
+    "r"(a[24]), "r"(a[25]), "r"(a[26]), "r"(a[27]), "r"(a[28]), "r"(a[29]), "r"(a[30]), "r"(a[31])
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        TK_R32(v)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+    int64_t L, nj, R, m;
+    int64_t ntiles, tiles_per_r, nk;
+    float* out;
+    unsigned* flags;
+};
+
+template <int NPAD>
+struct Cfg {
+    static constexpr int kBBytes = NPAD * 128;  // one of M_hi / M_lo: NPAD rows of 128 B
+    static constexpr int kStage = kXBytes + 2 * kBBytes;
+    static constexpr int kStages = (200 * 1024) / kStage > 6 ? 6 : (200 * 1024) / kStage;
+    static constexpr int kAcc0 = 0;                // accumulators: 2 x (2*NPAD) columns
+    static constexpr int kABuf = 4 * NPAD;         // A buffers: 2 x 64 columns (hi 32 | lo 32)
+    static constexpr int kSmem = kStages * kStage + 1024 + 256;
+    static_assert(4 * NPAD + 128 <= 512, "TMEM budget");
+};
+
+template <int NPAD, bool KMAJOR>
+__global__ void __launch_bounds__(kThreads, 1)
+    ttm_tf32x3_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBhi,
+                      const __grid_constant__ CUtensorMap tmBlo, TcArgs args) {
+    using C = Cfg<NPAD>;
+    constexpr int S = C::kStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * C::kStage);
+    uint64_t* full = bars;               // [S] TMA landed
+    uint64_t* xfree = bars + S;          // [S] stage consumed (128 converter arrivals + 1 MMA commit)
+    uint64_t* afull = bars + 2 * S;      // [2] A buffer written (128 converter arrivals)
+    uint64_t* aempty = afull + 2;        // [2] A buffer consumed (MMA commit)
+    uint64_t* accfull = aempty + 2;      // [2] accumulator complete (MMA commit)
+    uint64_t* accempty = accfull + 2;    // [2] accumulator drained (128 epilogue arrivals)
+    uint64_t* done = accempty + 2;       // [1] every issued MMA complete
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&xfree[s], 129);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&afull[b], 128);
+            mbar_init(&aempty[b], 1);
+            mbar_init(&accfull[b], 1);
+            mbar_init(&accempty[b], 128);
+        }
+        mbar_init(done, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    unsigned* flags = args.flags;
+    const int64_t nk = args.nk;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+                int64_t r0 = 0, l0 = 0, rr = 0;
+                if (KMAJOR) {
+                    r0 = t * kRows;
+                } else {
+                    rr = t / args.tiles_per_r;
+                    l0 = (t % args.tiles_per_r) * kRows;
+                }
+                for (int64_t kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = (int)(it % S);
+                    const uint32_t ph = (uint32_t)((it / S) & 1);
+                    if (!mbar_wait(&xfree[s], ph ^ 1, abort, flags)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* xs = smem + s * C::kStage;
+                    uint8_t* bs = xs + kXBytes;
+                    mbar_expect_tx(&full[s], kXBytes + 2 * C::kBBytes);
+                    if (KMAJOR) {
+                        tma_load_2d(xs, &tmX, (int)(kc * kChunk), (int)r0, &full[s]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            tma_load_3d(xs + q * 4096, &tmX, (int)(l0 + 32 * q), (int)(kc * kChunk), (int)rr, &full[s]);
+                    }
+                    tma_load_2d(bs, &tmBhi, (int)(kc * kChunk), 0, &full[s]);
+                    tma_load_2d(bs + C::kBBytes, &tmBlo, (int)(kc * kChunk), 0, &full[s]);
+                }
+            }
+            // drain: every issued load has landed before the CTA can exit
+            const int64_t n_out = it < S ? it : S;
+            for (int64_t q = it - n_out; q < it; ++q) {
+                const int s = (int)(q % S);
+                const uint32_t ph = (uint32_t)((q / S) & 1);
+                const uint64_t t0 = gtimer();
+                while (!mbar_try_wait(&full[s], ph) && gtimer() - t0 < kTimeoutNs) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int64_t it = 0, ab = 0, acc = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x, ++acc) {
+                const int a = (int)(acc & 1);
+                if (!mbar_wait(&accempty[a], (uint32_t)(((acc >> 1) & 1) ^ 1), abort, flags)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tbase + C::kAcc0 + a * 2 * NPAD;
+                for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
+                    const int s = (int)(it % S);
+                    const int b = (int)(ab & 1);
+                    if (!mbar_wait(&full[s], (uint32_t)((it / S) & 1), abort, flags) ||
+                        !mbar_wait(&afull[b], (uint32_t)((ab >> 1) & 1), abort, flags)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t bs = smem_u32(smem + s * C::kStage + kXBytes);
+                    const uint32_t a_hi = tbase + C::kABuf + 64 * b;
+#pragma unroll
+                    for (int k8 = 0; k8 < kChunk / 8; ++k8) {
+                        const uint64_t bdesc = desc_sw128(bs + 32 * k8);
+                        mma_tf32_ts(d_tmem, a_hi + 8 * k8, bdesc, idesc_tf32(2 * NPAD), (kc | k8) != 0);
+                        mma_tf32_ts(d_tmem, a_hi + 32 + 8 * k8, bdesc, idesc_tf32(NPAD), 1u);
+                    }
+                    tc_commit(&aempty[b]);
+                    tc_commit(&xfree[s]);
+                }
+                if (!ok) break;
+                tc_commit(&accfull[a]);
+            }
+            tc_commit(done);
+            const uint64_t t0 = gtimer();
+            while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------ converters: X chunk -> TF32 hi / lo in TMEM
+        const int rho = threadIdx.x - 128;  // tile row == TMEM lane
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        int64_t it = 0, ab = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+            for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
+                const int s = (int)(it % S);
+                const int b = (int)(ab & 1);
+                bool got = mbar_wait(&full[s], (uint32_t)((it / S) & 1), abort, flags) &&
+                           mbar_wait(&aempty[b], (uint32_t)(((ab >> 1) & 1) ^ 1), abort, flags);
+                if (!__all_sync(0xffffffffu, got)) {  // warp-uniform: tcgen05.st below is .aligned
+                    ok = false;
+                    break;
+                }
+                const uint8_t* xs = smem + s * C::kStage;
+                float v[32];
+                if (KMAJOR) {
+                    // row rho: 128 B, 16-byte chunk j stored at chunk j ^ (rho & 7)
+                    const uint8_t* row = xs + rho * 128;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 q = *reinterpret_cast<const float4*>(row + ((j ^ (rho & 7)) << 4));
+                        v[4 * j] = q.x;
+                        v[4 * j + 1] = q.y;
+                        v[4 * j + 2] = q.z;
+                        v[4 * j + 3] = q.w;
+                    }
+                } else {
+                    // box (rho / 32): rows i of 32 floats (128 B), 128-byte swizzle
+                    const uint8_t* box = xs + (rho >> 5) * 4096;
+                    const int lc = rho & 31;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        v[i] = *reinterpret_cast<const float*>(box + i * 128 + ((((lc >> 2) ^ (i & 7)) << 4) | ((lc & 3) << 2)));
+                }
+                uint32_t hi[32], lo[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    hi[i] = tf32_rna(v[i]);
+                    lo[i] = tf32_rna(v[i] - __uint_as_float(hi[i]));
+                }
+                const uint32_t ta = tbase + lane_base + C::kABuf + 64 * b;
+                __syncwarp();
+                tmem_st32(ta, hi);
+                tmem_st32(ta + 32, lo);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                mbar_arrive(&afull[b]);
+                mbar_arrive(&xfree[s]);
+            }
+        }
+    } else if (warp >= 8) {
+        // ------------------------------------------------ epilogue
+        const int rho = threadIdx.x - 256;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        int64_t acc = 0;
+        for (int64_t t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++acc) {
+            const int a = (int)(acc & 1);
+            bool got = mbar_wait(&accfull[a], (uint32_t)((acc >> 1) & 1), abort, flags);
+            if (!__all_sync(0xffffffffu, got)) break;  // warp-uniform: tcgen05.ld below is .aligned
+            tc_fence_after();
+            int64_t base;
+            int64_t stride;
+            bool valid;
+            if (KMAJOR) {
+                const int64_t r = t * kRows + rho;
+                valid = r < args.R;
+                base = r * args.m;
+                stride = 1;
+            } else {
+                const int64_t rr = t / args.tiles_per_r;
+                const int64_t l = (t % args.tiles_per_r) * kRows + rho;
+                valid = l < args.L;
+                base = l + args.L * args.m * rr;
+                stride = args.L;
+            }
+            const uint32_t ta = tbase + lane_base + C::kAcc0 + a * 2 * NPAD;
+#pragma unroll
+            for (int c0 = 0; c0 < NPAD; c0 += 16) {
+                float h[16], g[16];
+                __syncwarp();
+                tmem_ld16(ta + c0, h);
+                tmem_ld16(ta + NPAD + c0, g);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (valid) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (c0 + i < args.m) args.out[base + (c0 + i) * stride] = h[i] + g[i];
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&accempty[a]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+static void encode(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
+                   const uint32_t* box) {
+    auto fn = encode_fn();
+    TK_REQUIRE(fn != nullptr, TK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    uint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base),
+                    reinterpret_cast<const cuuint64_t*>(dims), reinterpret_cast<const cuuint64_t*>(strides_bytes),
+                    reinterpret_cast<const cuuint32_t*>(box), estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    TK_REQUIRE(r == CUDA_SUCCESS, TK_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
+
+// hi = rn_tf32(M(i, a)), lo = rn_tf32(M(i, a) - hi), stored K-major: (i, a) at i + ldo*a,
+// a in [0, npad) with zero padding beyond m.
+__global__ void split_tf32_kernel(const void* M, tk_dtype dt, int64_t ldm, int mtrans, int64_t nj, int64_t m,
+                                  int64_t npad, int64_t ldo, float* hi, float* lo) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ldo * npad) return;
+    int64_t i = idx % ldo, a = idx / ldo;
+    double v = 0.0;
+    if (i < nj && a < m) {
+        int64_t o = mtrans ? a + ldm * i : i + ldm * a;
+        v = dt == TK_F64 ? static_cast<const double*>(M)[o] : (double)static_cast<const float*>(M)[o];
+    }
+    float h = __uint_as_float(tf32_rna((float)v));
+    float l = __uint_as_float(tf32_rna((float)(v - (double)h)));
+    hi[idx] = h;
+    lo[idx] = l;
+}
+
+static int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <int NPAD, bool KMAJOR>
+static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap& th, const CUtensorMap& tl,
+                          const TcArgs& a) {
+    using Cf = Cfg<NPAD>;
+    auto kern = ttm_tf32x3_kernel<NPAD, KMAJOR>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::kSmem));
+        attr_set = true;
+    }
+    int grid = (int)std::min<int64_t>(a.ntiles, num_sms());
+    kern<<<grid, kThreads, Cf::kSmem, c.stream>>>(tx, th, tl, a);
+}
+
+}  // namespace tc
+
+bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt) {
+    if (X.dt != TK_F32 || out_dt != TK_F32) return false;
+    if (m < 1 || m > 96) return false;
+    const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
+    if (nj < 32 || ((uintptr_t)X.p % 16) != 0) return false;
+    if (L == 1) return nj % 4 == 0 && R >= tc::kRows && R < ((int64_t)1 << 31);
+    return L % 4 == 0 && L >= 32 && L < ((int64_t)1 << 31) && R < ((int64_t)1 << 31) && nj < ((int64_t)1 << 31);
+}
+
+void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out) {
+    const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
+    const int64_t npad = (m + 15) / 16 * 16;
+    const int64_t ldo = (nj + 3) / 4 * 4;
+    float* hi = c.alloc<float>(ldo * npad);
+    float* lo = c.alloc<float>(ldo * npad);
+    if (!c.exec) return;
+    {
+        int64_t tot = ldo * npad;
+        ProfScope ps(c, "elementwise", 8.0 * tot + 8.0 * nj * m, 0.0);
+        tc::split_tf32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(M.p, M.dt, M.ld, mtrans ? 1 : 0,
+                                                                                   nj, m, npad, ldo, hi, lo);
+        c.counted();
+        c.check_launch();
+    }
+    CUtensorMap tx, th, tl;
+    const bool kmajor = (L == 1);
+    if (kmajor) {
+        uint64_t dims[2] = {(uint64_t)nj, (uint64_t)R};
+        uint64_t str[1] = {(uint64_t)nj * 4};
+        uint32_t box[2] = {tc::kChunk, tc::kRows};
+        tc::encode(&tx, X.p, 2, dims, str, box);
+    } else {
+        uint64_t dims[3] = {(uint64_t)L, (uint64_t)nj, (uint64_t)R};
+        uint64_t str[2] = {(uint64_t)L * 4, (uint64_t)L * nj * 4};
+        uint32_t box[3] = {32, tc::kChunk, 1};
+        tc::encode(&tx, X.p, 3, dims, str, box);
+    }
+    {
+        uint64_t dims[2] = {(uint64_t)nj, (uint64_t)npad};
+        uint64_t str[1] = {(uint64_t)ldo * 4};
+        uint32_t box[2] = {tc::kChunk, (uint32_t)npad};
+        tc::encode(&th, hi, 2, dims, str, box);
+        tc::encode(&tl, lo, 2, dims, str, box);
+    }
+    tc::TcArgs a;
+    a.L = L;
+    a.nj = nj;
+    a.R = R;
+    a.m = m;
+    a.nk = (nj + tc::kChunk - 1) / tc::kChunk;
+    a.tiles_per_r = kmajor ? 1 : (L + tc::kRows - 1) / tc::kRows;
+    a.ntiles = kmajor ? (R + tc::kRows - 1) / tc::kRows : R * a.tiles_per_r;
+    a.out = out;
+    a.flags = c.dflags;
+    ProfScope ps(c, (const void*)X.p == c.xdata ? "ttm_x" : (L * R * m == c.xnumel ? "ttm_full" : "ttm"),
+                 4.0 * (double)L * R * nj + 4.0 * (double)L * R * m + 8.0 * nj * m, 2.0 * (double)L * R * nj * m);
+#define TK_TC_CASE(NP)                                                   \
+    case NP:                                                             \
+        if (kmajor)                                                      \
+            tc::launch_kernel<NP, true>(c, tx, th, tl, a);               \
+        else                                                             \
+            tc::launch_kernel<NP, false>(c, tx, th, tl, a);              \
+        break;
+    switch (npad) {
+        TK_TC_CASE(16)
+        TK_TC_CASE(32)
+        TK_TC_CASE(48)
+        TK_TC_CASE(64)
+        TK_TC_CASE(80)
+        TK_TC_CASE(96)
+        default: fail(TK_ERR_SHAPE, "ttm_tc: unsupported width");
+    }
+#undef TK_TC_CASE
+    c.counted();
+    c.check_launch();
+}
+
+}  // namespace tk

@@ -1,0 +1,75 @@
+"""GPU parity of the tensor-core (tcgen05, 3xTF32) TTM path against the FP64 oracle.
+
+Shapes are chosen so that the tensor-core kernel is the one that runs (FP32
+data, 16-byte strides, contracted mode >= 32): contraction over the contiguous
+mode (K-major), over the last mode and over a middle mode (MN-major), every
+supported output width (16..96 columns after padding), several 128-row tiles
+with ragged row and K tails.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2211_13028_gb300 import synth
+from paper_2211_13028_gb300 import tucker as T
+from tests.gpu_helpers import make_X, mats, rel, require_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return require_gpu()
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+@pytest.mark.parametrize("s", [(5, 3), (17, 16), (49, 42), (96, 81), (33, 64)])
+def test_tc_two_way_both_majors(dev, s):
+    # 100 x 1665: mode 1 -> K-major (K = 100, 13 tiles + 1 ragged row), mode 2 -> MN-major (L = 100 < 128).
+    g = _rng(1)
+    dims = (100, 1665)
+    X, xv, _ = make_X(g.standard_normal(dims), "f32", dev)
+    oms = synth.sketch_factors_reuse(dims, s, seed=2, dtype="f32")
+    Y = T.tucker_sketch(X, mats(oms, "f32", dev))
+    assert rel(to_np(Y[0]), O.ttm(xv, oms[1].T, 1)) <= 1e-5
+    assert rel(to_np(Y[1]), O.ttm(xv, oms[0].T, 0)) <= 1e-5
+
+
+@pytest.mark.parametrize("dims", [(64, 70, 9), (36, 20, 300), (128, 33, 40)])
+def test_tc_three_way_middle_and_last(dev, dims):
+    g = _rng(3)
+    X, xv, _ = make_X(g.standard_normal(dims), "f32", dev)
+    s = (7, 6, 5)
+    oms = synth.sketch_factors_reuse(dims, s, seed=4, dtype="f32")
+    Y = T.tucker_sketch(X, mats(oms, "f32", dev))
+    for n in range(3):
+        ref = O.multi_ttm(xv, [(j, oms[j].T) for j in range(3) if j != n])
+        assert rel(to_np(Y[n]), ref) <= 1e-5
+
+
+def test_tc_core_wide_factors(dev):
+    # the core multi-TTM with k_j near the largest supported width
+    g = _rng(5)
+    dims, k = (160, 96, 200), (96, 81, 49)
+    X, xv, _ = make_X(g.standard_normal(dims), "f32", dev)
+    qs = [synth.round_to(O.thin_qr(g.standard_normal((n, kk))), "f32") for n, kk in zip(dims, k)]
+    G = T.tucker_core(X, mats(qs, "f32", dev))
+    assert rel(to_np(G), O.multi_ttm(xv, [(j, qs[j].T) for j in range(3)])) <= 1e-5
+
+
+def test_tc_full_size_bench_tensor(dev):
+    # the 512^3 FP32 field of the benchmark: mode-1 and mode-3 contractions as the bench runs them
+    X = synth.gaussian_bumps(512, 3, 200, 0, 1e-4, dev, "f32")
+    xv = synth.from_fortran(X)
+    s = (6, 7, 7)
+    oms = synth.sketch_factors_reuse(X.shape, s, seed=1, dtype="f32")
+    Y = T.tucker_sketch(X, mats(oms, "f32", dev))
+    for n in range(3):
+        ref = O.multi_ttm(xv, [(j, oms[j].T) for j in range(3) if j != n])
+        assert rel(to_np(Y[n]), ref) <= 1e-5
+    st, _ = T.tk_sync_status(dev)
+    assert st == 0
