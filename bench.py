@@ -166,6 +166,37 @@ class ClockSampler:
                     samples=len(sms))
 
 
+# ------------------------------------------------------------------ single building block (profiling)
+
+def profile_case(args):
+    """Three repetitions of one building block on an n^3 FP32 field of the bench generator:
+    'sketch' (tucker_sketch, s = (6,7,7)), 'core' (tucker_core, k = (49,42,42)) or
+    'residual' (tucker_loss with r = 32: the fused tensor-core residual)."""
+    import torch
+
+    from paper_2211_13028_gb300 import synth
+    from paper_2211_13028_gb300 import tucker as T
+
+    dev = torch.device("cuda", 0)
+    n = args.n
+    X = synth.gaussian_bumps(n, 3, 200, SEED, 1e-4, dev, "f32")
+    g = __import__("numpy").random.Generator(__import__("numpy").random.PCG64(SEED))
+    if args.profile_case == "sketch":
+        om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(X.shape, (6, 7, 7), SEED + 1, "f32")]
+        fn = lambda: T.tucker_sketch(X, om)  # noqa: E731
+    elif args.profile_case == "core":
+        qs = [synth.fmat(__import__("numpy").linalg.qr(g.standard_normal((n, k)))[0], "f32", dev) for k in (49, 42, 42)]
+        fn = lambda: T.tucker_core(X, qs)  # noqa: E731
+    else:
+        G = synth.fortran(g.standard_normal((32, 32, 32)), "f32", dev)
+        U = [synth.fmat(__import__("numpy").linalg.qr(g.standard_normal((n, 32)))[0], "f32", dev) for _ in range(3)]
+        fn = lambda: T.tucker_loss(X, G, U)  # noqa: E731
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    print(json.dumps(dict(profile_case=args.profile_case, n=n, status=T.tk_sync_status(dev)[0])))
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def main():
@@ -176,8 +207,14 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--sample", type=int, default=256, help="oracle sample edge (CPU legs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", choices=["sketch", "core", "residual"], default=None,
+                    help="run one building block on an n^3 FP32 field (for ncu captures) instead of the bench")
+    ap.add_argument("--n", type=int, default=384, help="edge of the --profile-case tensor")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile_case:
+        profile_case(args)
+        return
 
     if args.impl == "reference":
         run_reference(args)

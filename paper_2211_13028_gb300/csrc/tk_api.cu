@@ -338,6 +338,47 @@ static Tens sthosvd_core(Ctx& c, const Tens& G0, const int64_t* r, const std::ve
     return G;
 }
 
+// ||X - G x_1 U_1 ... x_d U_d||^2 and ||X||^2 into err2 (device, 2 doubles); with
+// dx != NULL also dx = alpha (X - Xhat).  G and U are in the accumulation
+// dtype.  All modes but one are expanded first (smallest growth first); the
+// last one is fused with the residual on tensor cores when eligible, so Xhat is
+// never written; otherwise Xhat is formed and compared by separate kernels.
+static void residual_pass(Ctx& c, const Tens& X, const Tens& G, const std::vector<Mat>& U, tk_dtype acc,
+                          double* err2, void* dx, tk_dtype dxdt, double alpha) {
+    const int d = X.d;
+    int f = d - 1;
+    std::vector<int> todo;
+    for (int j = 0; j < d; ++j)
+        if (j != f) todo.push_back(j);
+    Tens W = G;
+    while (!todo.empty()) {
+        size_t best = 0;
+        double bestr = 1e300;
+        for (size_t t = 0; t < todo.size(); ++t) {
+            int i = todo[t];
+            double ratio = (double)U[i].rows / std::max<double>(1.0, (double)U[i].cols);
+            if (ratio < bestr) { bestr = ratio; best = t; }
+        }
+        int i = todo[best];
+        todo.erase(todo.begin() + best);
+        W = ttm_to(c, W, i, U[i], true, acc);
+    }
+    const int64_t m = U[f].rows;
+    const bool fused = c.use_tc && X.dt == TK_F32 && acc == TK_F32 && (!dx || dxdt == TK_F32) &&
+                       ttm_tc_eligible(W, f, m, TK_F32);
+    if (fused) {
+        const int nb = tc_num_ctas(W, f, m);
+        double* part = c.alloc<double>(2 * nb);
+        launch_ttm_tc_residual(c, W, f, U[f], true, m, static_cast<const float*>(X.p), static_cast<float*>(dx),
+                               (float)alpha, part);
+        launch_sum_pairs(c, part, nb, err2);
+        return;
+    }
+    Tens Xh = ttm_to(c, W, f, U[f], true, acc);
+    if (dx) launch_axpby_residual(c, X, Xh.p, acc, alpha, dx, dxdt);
+    launch_residual_norms(c, X, Xh.p, acc, err2);
+}
+
 // Final steps shared by both algorithms: U_j = Q_j V_j, sign gauge, casts
 // into the caller's G and U, optional relative error.
 static void finish(Ctx& c, const Tens& X, const std::vector<double*>& Qd, const std::vector<int64_t>& kdim,
@@ -362,24 +403,7 @@ static void finish(Ctx& c, const Tens& X, const std::vector<double*>& Qd, const 
     Tens Ga = tens_to(c, Gout, acc);
     std::vector<Mat> Ua(d);
     for (int j = 0; j < d; ++j) Ua[j] = mat_to(c, Uout[j], acc);
-    std::vector<int> modes(d);
-    std::iota(modes.begin(), modes.end(), 0);
-    // expand the mode whose factor grows least first
-    Tens Xh = Ga;
-    std::vector<int> todo = modes;
-    while (!todo.empty()) {
-        size_t best = 0;
-        double bestr = 1e300;
-        for (size_t t = 0; t < todo.size(); ++t) {
-            int i = todo[t];
-            double ratio = (double)Ua[i].rows / std::max<double>(1.0, (double)Ua[i].cols);
-            if (ratio < bestr) { bestr = ratio; best = t; }
-        }
-        int i = todo[best];
-        todo.erase(todo.begin() + best);
-        Xh = ttm_to(c, Xh, i, Ua[i], true, acc);
-    }
-    launch_residual_norms(c, X, Xh.p, acc, err_dev);
+    residual_pass(c, X, Ga, Ua, acc, err_dev, nullptr, TK_F32, 0.0);
 }
 
 struct Plan {
@@ -1024,9 +1048,11 @@ tk_status tucker_loss(tk_handle* h, const tk_tensor* X, const tk_tensor* G, cons
         TK_REQUIRE(Xt.d == Gt.d, TK_ERR_SHAPE, "loss: X and G must have the same d");
         for (int j = 0; j < Xt.d; ++j) TK_REQUIRE(Xt.n[j] == n[j], TK_ERR_SHAPE, "loss: X dims != U rows");
         tk_dtype acc = acc_of(Xt.dt);
-        Tens Xh = reconstruct_acc(c, Gt, Um, acc, nullptr);
+        Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
+        std::vector<Mat> Ua(Xt.d);
+        for (int j = 0; j < Xt.d; ++j) Ua[j] = Um[j].dt == acc ? Um[j] : mat_to(c, Um[j], acc);
         dev = c.alloc<double>(2);
-        launch_residual_norms(c, Xt, Xh.p, acc, dev);
+        residual_pass(c, Xt, Ga, Ua, acc, dev, nullptr, TK_F32, 0.0);
         read_err(h, c, dev, loss, true);
     });
 }
@@ -1060,36 +1086,58 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
             TK_REQUIRE(dXt.d == d && dXt.dt == Xt.dt, TK_ERR_DTYPE, "backward: dX must have X's dims and dtype");
             for (int j = 0; j < d; ++j) TK_REQUIRE(dXt.n[j] == Xt.n[j], TK_ERR_SHAPE, "backward: dX dims != X dims");
         }
+        // With R = X - G x_j U_j and C_j = U_j^T U_j:
+        //   R x_{j!=n} U_j^T = S_n - G x_n U_n x_{j!=n} C_j,   S_n = X x_{j!=n} U_j^T,
+        // so every product with the residual comes from sketches of X (the
+        // dimension tree, recomputed, never stored across calls) plus small
+        // core-sized corrections in FP64; the residual itself is only formed,
+        // tile by tile, when dX is requested.
         tk_dtype acc = acc_of(Xt.dt);
-        Tens Xh = reconstruct_acc(c, Gt, Um, acc, nullptr);
-        // R = X - Xhat in the accumulation dtype
-        Tens R = Xt;
-        R.dt = acc;
-        R.scale = 1.f;
-        R.p = c.alloc_bytes(dtype_size(acc) * Xt.numel());
-        launch_axpby_residual(c, Xt, Xh.p, acc, 1.0, R.p, acc);
-        if (dX) launch_axpby_residual(c, Xt, Xh.p, acc, 2.0 * grad_scale, dXt.p, dXt.dt);
-        // T_n = R x_{j != n} U_j^T for all n (dimension tree)
+        const double s2 = -2.0 * grad_scale;
         std::vector<Mat> Ua(d);
         for (int j = 0; j < d; ++j) Ua[j] = Um[j].dt == acc ? Um[j] : mat_to(c, Um[j], acc);
-        std::vector<Tens> T(d);
+        std::vector<Tens> S(d);
         std::vector<int> all(d);
         std::iota(all.begin(), all.end(), 0);
-        all_modes(c, R, all, {}, Ua.data(), acc, T, nullptr);
-        // dU_n = -2 s T_n(n) G_(n)^T
+        all_modes(c, Xt, all, {}, Ua.data(), acc, S, nullptr);
         Tens G64 = Gt.dt == TK_F64 ? Gt : tens_to(c, Gt, TK_F64);
+        std::vector<double*> U64(d);
+        std::vector<Mat> Cm(d);
         for (int j = 0; j < d; ++j) {
+            const int64_t nj = n[j], rj = Gt.n[j];
+            U64[j] = c.alloc<double>(nj * rj);
+            launch_convert(c, Um[j].p, Um[j].dt, nj, rj, Um[j].ld, U64[j], TK_F64, nj, 1.f);
+            double* Cj = c.alloc<double>(rj * rj);
+            gemm_nt_f64(c, rj, rj, nj, view_cols(U64[j], TK_F64, nj), view_cols(U64[j], TK_F64, nj), 1.0, 0.0, Cj, rj);
+            Cm[j].p = Cj;
+            Cm[j].dt = TK_F64;
+            Cm[j].rows = rj;
+            Cm[j].cols = rj;
+            Cm[j].ld = rj;
+        }
+        std::vector<Tens> Pm(d);  // P_n = G x_{j != n} C_j
+        all_modes(c, G64, all, {}, Cm.data(), TK_F64, Pm, nullptr);
+        for (int j = 0; j < d; ++j) {
+            const int64_t nj = n[j], rj = Gt.n[j];
             int64_t K = 1;
             for (int i = 0; i < d; ++i)
                 if (i != j) K *= Gt.n[i];
-            double* tmp = c.alloc<double>(n[j] * Gt.n[j]);
-            gemm_nt_f64(c, n[j], Gt.n[j], K, view_unfold_rows(T[j], j), view_unfold_rows(G64, j), -2.0 * grad_scale,
-                        0.0, tmp, n[j]);
-            launch_convert(c, tmp, TK_F64, n[j], Gt.n[j], n[j], (void*)dUm[j].p, dUm[j].dt, dUm[j].ld, 1.f);
+            double* A1 = c.alloc<double>(nj * rj);
+            double* B1 = c.alloc<double>(rj * rj);
+            gemm_nt_f64(c, nj, rj, K, view_unfold_rows(S[j], j), view_unfold_rows(G64, j), s2, 0.0, A1, nj);
+            gemm_nt_f64(c, rj, rj, K, view_unfold_rows(Pm[j], j), view_unfold_rows(G64, j), 1.0, 0.0, B1, rj);
+            gemm_nt_f64(c, nj, rj, rj, view_rows(U64[j], TK_F64, nj), view_cols(B1, TK_F64, rj), -s2, 1.0, A1, nj);
+            launch_convert(c, A1, TK_F64, nj, rj, nj, (void*)dUm[j].p, dUm[j].dt, dUm[j].ld, 1.f);
         }
-        // dG = -2 s T_0 x_0 U_0^T
-        Tens C = ttm_to(c, T[0], 0, Ua[0], false, acc);
-        launch_scale_copy(c, C.p, acc, C.numel(), -2.0 * grad_scale, dGt.p, dGt.dt);
+        // dG = -2s (X x_j U_j^T - G x_j C_j) = -2s (S_0 x_0 U_0^T - P_0 x_0 C_0)
+        Tens E = ttm_to(c, S[0], 0, Ua[0], false, acc);
+        Tens F = ttm_to(c, Pm[0], 0, Cm[0], false, TK_F64);
+        launch_axpby_residual(c, E, F.p, TK_F64, s2, dGt.p, dGt.dt);
+        if (dX) {
+            Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
+            double* nrm = c.alloc<double>(2);
+            residual_pass(c, Xt, Ga, Ua, acc, nrm, dXt.p, dXt.dt, 2.0 * grad_scale);
+        }
     });
 }
 

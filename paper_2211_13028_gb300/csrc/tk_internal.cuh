@@ -187,6 +187,15 @@ void launch_ttm(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, i
 // m <= 96; ttm_tc_eligible says whether a TTM qualifies (shape, dtype, alignment).
 bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
 void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
+// Fused last step of a reconstruction: P = W x_j M^T is formed tile by tile and
+// compared with xref (P's dims, F32): per-CTA partial sums of (xref - P)^2 and
+// xref^2 go to partials[2 * cta]; with dx != NULL also dx = alpha * (xref - P).
+// P itself is never stored.  tc_num_ctas gives the number of partial pairs.
+void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const float* xref,
+                            float* dx, float alpha, double* partials);
+int tc_num_ctas(const Tens& X, int j, int64_t m);
+// out2 = {sum part[2i], sum part[2i+1]} over nb pairs
+void launch_sum_pairs(const Ctx& c, const double* part, int nb, double* out2);
 
 // C = alpha * sum_t A(a, t) B(b, t) + beta * C, FP64, C column-major m x n (ldc).
 // A, B: View2 of F64 or F32 data.  Uses split-K partials in the workspace.

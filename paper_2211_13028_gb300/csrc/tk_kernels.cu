@@ -1070,6 +1070,14 @@ __global__ void residual_final_kernel(const double* part, int nb, double* out2) 
     out2[1] = b;
 }
 
+void launch_sum_pairs(const Ctx& c, const double* part, int nb, double* out2) {
+    if (!c.exec) return;
+    ProfScope ps(c, "elementwise", 16.0 * nb, 2.0 * nb);
+    residual_final_kernel<<<1, 32, 0, c.stream>>>(part, nb, out2);
+    c.counted();
+    c.check_launch();
+}
+
 void launch_residual_norms(Ctx& c, const Tens& X, const void* Y, tk_dtype ydt, double* out2) {
     const int nb = 152 * 8;
     double* part = c.alloc<double>(2 * nb);
@@ -1109,8 +1117,8 @@ __global__ void axpby_residual_kernel(const void* X, tk_dtype xdt, float xinv, c
                                       int64_t tot, double alpha, void* dst, tk_dtype ddt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= tot) return;
-    if (xdt == TK_F64) {
-        st_any(dst, ddt, i, alpha * (ld_any(X, xdt, i) - ld_any(Y, ydt, i)));
+    if (xdt == TK_F64 || ydt == TK_F64) {  // difference formed in FP64 when either side carries it
+        st_any(dst, ddt, i, alpha * (ld_any(X, xdt, i, xinv) - ld_any(Y, ydt, i)));
     } else {
         float x = (float)ld_any(X, xdt, i, xinv), y = (float)ld_any(Y, ydt, i);
         st_any(dst, ddt, i, (double)((float)alpha * (x - y)));

@@ -169,8 +169,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 struct TcArgs {
     int64_t L, nj, R, m;
-    int64_t ntiles, tiles_per_r, nk;
-    float* out;
+    int64_t ntiles, tiles_per_r, nk, nblk;  // work item = (row tile, block of NPAD output columns)
+    float* out;                             // EPI 0: product; EPI 2: alpha * (xref - product)
+    const float* xref;                      // EPI 1, 2: tensor compared with the product (same layout)
+    float alpha;
+    double* partials;                       // EPI 1, 2: per CTA {sum (xref - product)^2, sum xref^2}
     unsigned* flags;
 };
 
@@ -185,7 +188,9 @@ struct Cfg {
     static_assert(4 * NPAD + 128 <= 512, "TMEM budget");
 };
 
-template <int NPAD, bool KMAJOR>
+// EPI 0: store the product; 1: accumulate the residual norms against xref;
+// 2: as 1 and also store alpha * (xref - product).
+template <int NPAD, bool KMAJOR, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     ttm_tf32x3_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBhi,
                       const __grid_constant__ CUtensorMap tmBlo, TcArgs args) {
@@ -237,7 +242,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int64_t it = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+            const int64_t nitems = args.ntiles * args.nblk;
+            for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+                const int64_t t = w / args.nblk, nb = w % args.nblk;
                 int64_t r0 = 0, l0 = 0, rr = 0;
                 if (KMAJOR) {
                     r0 = t * kRows;
@@ -262,8 +269,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int q = 0; q < 4; ++q)
                             tma_load_3d(xs + q * 4096, &tmX, (int)(l0 + 32 * q), (int)(kc * kChunk), (int)rr, &full[s]);
                     }
-                    tma_load_2d(bs, &tmBhi, (int)(kc * kChunk), 0, &full[s]);
-                    tma_load_2d(bs + C::kBBytes, &tmBlo, (int)(kc * kChunk), 0, &full[s]);
+                    tma_load_2d(bs, &tmBhi, (int)(kc * kChunk), (int)(nb * NPAD), &full[s]);
+                    tma_load_2d(bs + C::kBBytes, &tmBlo, (int)(kc * kChunk), (int)(nb * NPAD), &full[s]);
                 }
             }
             // drain: every issued load has landed before the CTA can exit
@@ -281,7 +288,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int64_t it = 0, ab = 0, acc = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x, ++acc) {
+            const int64_t nitems = args.ntiles * args.nblk;
+            for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++acc) {
                 const int a = (int)(acc & 1);
                 if (!mbar_wait(&accempty[a], (uint32_t)(((acc >> 1) & 1) ^ 1), abort, flags)) {
                     ok = false;
@@ -323,7 +331,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         int64_t it = 0, ab = 0;
         bool ok = true;
-        for (int64_t t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+        const int64_t nitems = args.ntiles * args.nblk;
+        for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
             for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
                 const int s = (int)(it % S);
                 const int b = (int)(ab & 1);
@@ -374,8 +383,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------ epilogue
         const int rho = threadIdx.x - 256;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        double sr = 0.0, sx = 0.0;
         int64_t acc = 0;
-        for (int64_t t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++acc) {
+        const int64_t nitems = args.ntiles * args.nblk;
+        for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x, ++acc) {
+            const int64_t t = w / args.nblk, nb = w % args.nblk;
             const int a = (int)(acc & 1);
             bool got = mbar_wait(&accfull[a], (uint32_t)((acc >> 1) & 1), abort, flags);
             if (!__all_sync(0xffffffffu, got)) break;  // warp-uniform: tcgen05.ld below is .aligned
@@ -395,6 +407,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 base = l + args.L * args.m * rr;
                 stride = args.L;
             }
+            const int64_t col0 = nb * NPAD;
+            base += col0 * stride;
+            const int64_t ncol = args.m - col0;  // valid columns in this block (may exceed NPAD)
             const uint32_t ta = tbase + lane_base + C::kAcc0 + a * 2 * NPAD;
 #pragma unroll
             for (int c0 = 0; c0 < NPAD; c0 += 16) {
@@ -404,13 +419,48 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld16(ta + NPAD + c0, g);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (valid) {
+                    if (EPI == 0) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (c0 + i < args.m) args.out[base + (c0 + i) * stride] = h[i] + g[i];
+                        for (int i = 0; i < 16; ++i)
+                            if (c0 + i < ncol) args.out[base + (c0 + i) * stride] = h[i] + g[i];
+                    } else {
+                        float fr = 0.f, fx = 0.f;
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            if (c0 + i < ncol) {
+                                const int64_t o = base + (c0 + i) * stride;
+                                const float xv = args.xref[o];
+                                const float dv = xv - (h[i] + g[i]);
+                                fr = fmaf(dv, dv, fr);
+                                fx = fmaf(xv, xv, fx);
+                                if (EPI == 2) args.out[o] = args.alpha * dv;
+                            }
+                        }
+                        sr += (double)fr;
+                        sx += (double)fx;
+                    }
                 }
             }
             tc_fence_before();
             mbar_arrive(&accempty[a]);
+        }
+        if (EPI != 0) {
+            // reduce over the 128 epilogue threads: warp shuffles, then named barrier 1
+            __shared__ double red[8];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            }
+            if (lane == 0) {
+                red[2 * (warp - 8)] = sr;
+                red[2 * (warp - 8) + 1] = sx;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (rho == 0) {
+                args.partials[2 * blockIdx.x] = red[0] + red[2] + red[4] + red[6];
+                args.partials[2 * blockIdx.x + 1] = red[1] + red[3] + red[5] + red[7];
+            }
         }
     }
     __syncthreads();
@@ -477,43 +527,60 @@ static int num_sms() {
     return n;
 }
 
-template <int NPAD, bool KMAJOR>
+template <int NPAD, bool KMAJOR, int EPI>
 static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap& th, const CUtensorMap& tl,
                           const TcArgs& a) {
     using Cf = Cfg<NPAD>;
-    auto kern = ttm_tf32x3_kernel<NPAD, KMAJOR>;
+    auto kern = ttm_tf32x3_kernel<NPAD, KMAJOR, EPI>;
     static bool attr_set = false;
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::kSmem));
         attr_set = true;
     }
-    int grid = (int)std::min<int64_t>(a.ntiles, num_sms());
+    int grid = (int)std::min<int64_t>(a.ntiles * a.nblk, num_sms());
     kern<<<grid, kThreads, Cf::kSmem, c.stream>>>(tx, th, tl, a);
 }
 
 }  // namespace tc
 
+// Output columns: up to 96 in one block (padded to 16), else blocks of 64.
+static void tc_blocks(int64_t m, int64_t& npad, int64_t& nblk) {
+    if (m <= 96) {
+        npad = (m + 15) / 16 * 16;
+        nblk = 1;
+    } else {
+        npad = 64;
+        nblk = (m + 63) / 64;
+    }
+}
+
 bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt) {
     if (X.dt != TK_F32 || out_dt != TK_F32) return false;
-    if (m < 1 || m > 96) return false;
+    if (m < 1 || m > 65535) return false;
     const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
     if (nj < 32 || ((uintptr_t)X.p % 16) != 0) return false;
     if (L == 1) return nj % 4 == 0 && R >= tc::kRows && R < ((int64_t)1 << 31);
     return L % 4 == 0 && L >= 32 && L < ((int64_t)1 << 31) && R < ((int64_t)1 << 31) && nj < ((int64_t)1 << 31);
 }
 
-void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out) {
+// Shared launcher.  epi 0: out = X x_j M^T.  epi 1/2: compare the product with
+// xref (same dims as the product): partial norms per CTA into partials, and
+// for epi 2 out = alpha * (xref - product).
+static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out, int epi,
+                       const float* xref, float alpha, double* partials, const char* prof_name) {
     const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
-    const int64_t npad = (m + 15) / 16 * 16;
+    int64_t npad, nblk;
+    tc_blocks(m, npad, nblk);
     const int64_t ldo = (nj + 3) / 4 * 4;
-    float* hi = c.alloc<float>(ldo * npad);
-    float* lo = c.alloc<float>(ldo * npad);
+    const int64_t rows_b = npad * nblk;
+    float* hi = c.alloc<float>(ldo * rows_b);
+    float* lo = c.alloc<float>(ldo * rows_b);
     if (!c.exec) return;
     {
-        int64_t tot = ldo * npad;
+        int64_t tot = ldo * rows_b;
         ProfScope ps(c, "elementwise", 8.0 * tot + 8.0 * nj * m, 0.0);
         tc::split_tf32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(M.p, M.dt, M.ld, mtrans ? 1 : 0,
-                                                                                   nj, m, npad, ldo, hi, lo);
+                                                                                   nj, m, rows_b, ldo, hi, lo);
         c.counted();
         c.check_launch();
     }
@@ -531,7 +598,7 @@ void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int6
         tc::encode(&tx, X.p, 3, dims, str, box);
     }
     {
-        uint64_t dims[2] = {(uint64_t)nj, (uint64_t)npad};
+        uint64_t dims[2] = {(uint64_t)nj, (uint64_t)rows_b};
         uint64_t str[1] = {(uint64_t)ldo * 4};
         uint32_t box[2] = {tc::kChunk, (uint32_t)npad};
         tc::encode(&th, hi, 2, dims, str, box);
@@ -543,18 +610,31 @@ void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int6
     a.R = R;
     a.m = m;
     a.nk = (nj + tc::kChunk - 1) / tc::kChunk;
+    a.nblk = nblk;
     a.tiles_per_r = kmajor ? 1 : (L + tc::kRows - 1) / tc::kRows;
     a.ntiles = kmajor ? (R + tc::kRows - 1) / tc::kRows : R * a.tiles_per_r;
     a.out = out;
+    a.xref = xref;
+    a.alpha = alpha;
+    a.partials = partials;
     a.flags = c.dflags;
-    ProfScope ps(c, (const void*)X.p == c.xdata ? "ttm_x" : (L * R * m == c.xnumel ? "ttm_full" : "ttm"),
-                 4.0 * (double)L * R * nj + 4.0 * (double)L * R * m + 8.0 * nj * m, 2.0 * (double)L * R * nj * m);
-#define TK_TC_CASE(NP)                                                   \
-    case NP:                                                             \
-        if (kmajor)                                                      \
-            tc::launch_kernel<NP, true>(c, tx, th, tl, a);               \
-        else                                                             \
-            tc::launch_kernel<NP, false>(c, tx, th, tl, a);              \
+    double bytes = 4.0 * (double)L * R * nj + 8.0 * nj * m;
+    if (epi == 0) bytes += 4.0 * (double)L * R * m;
+    if (epi >= 1) bytes += 4.0 * (double)L * R * m;
+    if (epi == 2) bytes += 4.0 * (double)L * R * m;
+    ProfScope ps(c, prof_name, bytes, 2.0 * (double)L * R * nj * m);
+#define TK_TC_CASE(NP)                                                                             \
+    case NP:                                                                                       \
+        if (epi == 0) {                                                                            \
+            if (kmajor) tc::launch_kernel<NP, true, 0>(c, tx, th, tl, a);                          \
+            else tc::launch_kernel<NP, false, 0>(c, tx, th, tl, a);                                \
+        } else if (epi == 1) {                                                                     \
+            if (kmajor) tc::launch_kernel<NP, true, 1>(c, tx, th, tl, a);                          \
+            else tc::launch_kernel<NP, false, 1>(c, tx, th, tl, a);                                \
+        } else {                                                                                   \
+            if (kmajor) tc::launch_kernel<NP, true, 2>(c, tx, th, tl, a);                          \
+            else tc::launch_kernel<NP, false, 2>(c, tx, th, tl, a);                                \
+        }                                                                                          \
         break;
     switch (npad) {
         TK_TC_CASE(16)
@@ -568,6 +648,25 @@ void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int6
 #undef TK_TC_CASE
     c.counted();
     c.check_launch();
+}
+
+void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out) {
+    const int64_t L = X.left(j), R = X.right(j);
+    const char* name = (const void*)X.p == c.xdata ? "ttm_x" : (L * R * m == c.xnumel ? "ttm_full" : "ttm");
+    ttm_tc_run(c, X, j, M, mtrans, m, out, 0, nullptr, 0.f, nullptr, name);
+}
+
+int tc_num_ctas(const Tens& X, int j, int64_t m) {
+    int64_t npad, nblk;
+    tc_blocks(m, npad, nblk);
+    const int64_t L = X.left(j), R = X.right(j);
+    const int64_t tiles = (L == 1) ? (R + tc::kRows - 1) / tc::kRows : R * ((L + tc::kRows - 1) / tc::kRows);
+    return (int)std::min<int64_t>(tiles * nblk, tc::num_sms());
+}
+
+void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const float* xref,
+                            float* dx, float alpha, double* partials) {
+    ttm_tc_run(c, W, j, M, mtrans, m, dx, dx ? 2 : 1, xref, alpha, partials, "residual_tc");
 }
 
 }  // namespace tk

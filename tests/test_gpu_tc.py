@@ -73,3 +73,41 @@ def test_tc_full_size_bench_tensor(dev):
         assert rel(to_np(Y[n]), ref) <= 1e-5
     st, _ = T.tk_sync_status(dev)
     assert st == 0
+
+
+@pytest.mark.parametrize("need_dx", [False, True])
+def test_tc_fused_residual_loss_and_gradient(dev, need_dx):
+    # last reconstruction step fused with the residual on tensor cores (r_3 >= 32), gradients from
+    # sketches of X plus FP64 core corrections
+    g = _rng(7)
+    dims, rk = (96, 80, 72), (12, 10, 36)
+    x = synth.round_to(g.standard_normal(dims), "f32")
+    G = synth.round_to(g.standard_normal(rk), "f32")
+    U = [synth.round_to(g.standard_normal((nn, k)) / np.sqrt(nn), "f32") for nn, k in zip(dims, rk)]
+    Xd, Gd, Ud = synth.fortran(x, "f32", dev), synth.fortran(G, "f32", dev), mats(U, "f32", dev)
+    ref_loss = O.loss(x, G, U)
+    assert abs(T.tucker_loss(Xd, Gd, Ud) - ref_loss) <= 1e-5 * ref_loss
+    dG, dU, dX = T.tucker_reconstruct_backward(Xd, Gd, Ud, grad_scale=0.25, need_dX=need_dx)
+    ref = O.loss_grads(x, G, U)
+    assert rel(to_np(dG), 0.25 * ref["dG"]) <= 1e-4
+    for j in range(3):
+        assert rel(to_np(dU[j]), 0.25 * ref["dU"][j]) <= 1e-4
+    if need_dx:
+        assert rel(to_np(dX), 0.25 * ref["dX"]) <= 1e-5
+    st, _ = T.tk_sync_status(dev)
+    assert st == 0
+
+
+def test_tc_rel_err_fused_matches_oracle(dev):
+    # rHKron-re with r_3 = 32 so the relative error uses the fused tensor-core residual
+    dims, r, p = (128, 96, 112), (20, 24, 32), 6
+    core = synth.decaying_core((40, 40, 40), 0.8, seed=31)
+    x = synth.tucker_tensor(dims, (40, 40, 40), seed=32, noise_rel=1e-3, core=core)
+    X, xv, _ = make_X(x, "f32", dev)
+    s = O.subranks_reuse(r, p)[0]
+    oms = synth.sketch_factors_reuse(dims, s, seed=33, dtype="f32")
+    G, U, err = T.tucker_rhkron(X, r, p, mats(oms, "f32", dev))
+    ref = O.rhkron(xv, r, oms)
+    assert abs(err - O.rel_err(xv, ref["G"], ref["U"])) <= 1e-5
+    # the error the GPU reports is the error of the factors it returned
+    assert abs(err - O.rel_err(xv, to_np(G), [to_np(u) for u in U])) <= 1e-6
