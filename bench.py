@@ -357,6 +357,7 @@ def main():
                       peak_source=f"{peak_src} hbm_gbs", bytes_per_launch=d["bytes"] / max(1, d["launches"]),
                       ms_per_launch=per_launch_ms),
         kernel_shares=shares,
+        kernel_ms_per_step=step_ms_total / args.steps,
         e2e=dict(value=e2e_ms, unit="ms", h2d_bytes_per_step=Xh.numel() * Xh.element_size(),
                  d2h_bytes_per_step=res_bytes),
         gpu_launches=launches,

@@ -365,9 +365,9 @@ static void residual_pass(Ctx& c, const Tens& X, const Tens& G, const std::vecto
     }
     const int64_t m = U[f].rows;
     const bool fused = c.use_tc && X.dt == TK_F32 && acc == TK_F32 && (!dx || dxdt == TK_F32) &&
-                       ttm_tc_eligible(W, f, m, TK_F32);
+                       ttm_tc_residual_eligible(W, f, m);
     if (fused) {
-        const int nb = tc_num_ctas(W, f, m);
+        const int nb = tc_num_ctas(W, f, m, true);
         double* part = c.alloc<double>(2 * nb);
         launch_ttm_tc_residual(c, W, f, U[f], true, m, static_cast<const float*>(X.p), static_cast<float*>(dx),
                                (float)alpha, part);

@@ -193,7 +193,8 @@ void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int6
 // P itself is never stored.  tc_num_ctas gives the number of partial pairs.
 void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const float* xref,
                             float* dx, float alpha, double* partials);
-int tc_num_ctas(const Tens& X, int j, int64_t m);
+int tc_num_ctas(const Tens& X, int j, int64_t m, bool residual);
+bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m);
 // out2 = {sum part[2i], sum part[2i+1]} over nb pairs
 void launch_sum_pairs(const Ctx& c, const double* part, int nb, double* out2);
 

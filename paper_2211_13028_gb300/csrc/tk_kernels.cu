@@ -152,10 +152,34 @@ __global__ void __launch_bounds__(256) ttm_simt_kernel(const Tx* __restrict__ X,
     }
 }
 
+// Small TTMs: one thread per output element (consecutive threads along l).
+template <typename Tx, typename Ta>
+__global__ void __launch_bounds__(256) ttm_direct_kernel(const Tx* __restrict__ X, int64_t L, int64_t nj, int64_t R,
+                                                         const Ta* __restrict__ M, int64_t ldm, int mtrans, int64_t m,
+                                                         Ta* __restrict__ out, Ta xinv) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= L * m * R) return;
+    const int64_t l = o % L, rest = o / L;
+    const int64_t a = rest % m, r = rest / m;
+    const Tx* x = X + l + L * nj * r;
+    Ta s = Ta(0);
+    for (int64_t i = 0; i < nj; ++i) s += (mtrans ? M[a + ldm * i] : M[i + ldm * a]) * ldx(x, L * i, xinv);
+    out[o] = s;
+}
+
 template <typename Tx, typename Ta>
 static void ttm_dispatch(const Ctx& c, const Tx* X, int64_t L, int64_t nj, int64_t R, const Ta* M, int64_t ldm,
                          bool mtrans, int64_t m, Ta* out, Ta xinv) {
     int64_t rows = L * R;
+    if (rows * m <= (1 << 21) && nj <= 512) {
+        const char* name = (const void*)X == c.xdata ? "ttm_x" : "ttm";
+        ProfScope ps(c, name, (double)rows * nj * sizeof(Tx) + (double)rows * m * sizeof(Ta), 2.0 * rows * nj * m);
+        ttm_direct_kernel<Tx, Ta><<<(unsigned)((rows * m + 255) / 256), 256, 0, c.stream>>>(X, L, nj, R, M, ldm,
+                                                                                           mtrans, m, out, xinv);
+        c.counted();
+        c.check_launch();
+        return;
+    }
     const char* name = (const void*)X == c.xdata ? "ttm_x" : (rows * m == c.xnumel ? "ttm_full" : "ttm");
     ProfScope ps(c, name, (double)rows * nj * sizeof(Tx) + (double)rows * m * sizeof(Ta) + (double)nj * m * sizeof(Ta),
                  2.0 * rows * nj * m);
@@ -276,34 +300,66 @@ __global__ void gemm_reduce_kernel(int64_t m, int64_t n, int nsplit, const doubl
     *dst = beta == 0.0 ? alpha * s : alpha * s + beta * *dst;
 }
 
-// Small problems (m, n <= 256, K <= 512): one output per thread, 8 x 8 tiles,
-// no split-K, alpha/beta applied in place (C must not alias A or B).
-__global__ void __launch_bounds__(64) gemm_nt_tiny_kernel(int64_t m, int64_t n, int64_t K, View2 A, View2 B,
-                                                          double alpha, double beta, double* C, int64_t ldc,
-                                                          const int* skip) {
-    if (skip && *skip) return;
-    const int64_t a = (int64_t)blockIdx.x * 8 + (threadIdx.x & 7);
-    const int64_t b = (int64_t)blockIdx.y * 8 + (threadIdx.x >> 3);
-    if (a >= m || b >= n) return;
-    // walk t with incremental offsets: no integer division in the loop
-    V2Walk wa(A, a), wb(B, b);
-    double s = 0.0;
-    for (int64_t t = 0; t < K; ++t) {
-        s = fma(wa.load(), wb.load(), s);
-        wa.next();
-        wb.next();
+// Small outputs: one warp per output element, the K terms split over the lanes
+// (a short dependent chain per lane) and combined by shuffles.
+struct V2Lane {  // walk t = lane, lane + 32, ... of row a of a View2
+    const View2& v;
+    int64_t base, lo, hi;
+    __device__ V2Lane(const View2& vv, int64_t a, int64_t t0) : v(vv) {
+        base = (v.A1 == INT64_MAX) ? a * v.sa1 : (a % v.A1) * v.sa1 + (a / v.A1) * v.sa2;
+        if (v.T1 == INT64_MAX) {
+            lo = t0;
+            hi = 0;
+        } else {
+            lo = t0 % v.T1;
+            hi = t0 / v.T1;
+        }
     }
-    double* dst = C + a + ldc * b;
-    *dst = beta == 0.0 ? alpha * s : alpha * s + beta * *dst;
+    __device__ __forceinline__ double load() const {
+        int64_t o = base + lo * v.st1 + hi * v.st2;
+        return v.dt == TK_F64 ? static_cast<const double*>(v.p)[o] : (double)static_cast<const float*>(v.p)[o];
+    }
+    __device__ __forceinline__ void next32() {
+        lo += 32;
+        if (v.T1 != INT64_MAX && lo >= v.T1) {
+            hi += lo / v.T1;
+            lo %= v.T1;
+        }
+    }
+};
+
+__global__ void __launch_bounds__(256) gemm_nt_warp_kernel(int64_t m, int64_t n, int64_t K, View2 A, View2 B,
+                                                           double alpha, double beta, double* C, int64_t ldc,
+                                                           const int* skip) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t o = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (o >= m * n) return;
+    const int64_t a = o % m, b = o / m;
+    double s = 0.0;
+    if (lane < K) {
+        V2Lane wa(A, a, lane), wb(B, b, lane);
+        for (int64_t t = lane; t < K; t += 32) {
+            s = fma(wa.load(), wb.load(), s);
+            wa.next32();
+            wb.next32();
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        double* dst = C + a + ldc * b;
+        *dst = beta == 0.0 ? alpha * s : alpha * s + beta * *dst;
+    }
 }
 
 void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const View2& B, double alpha, double beta,
                  double* C, int64_t ldc, const int* skip) {
-    if (m <= 256 && n <= 256 && K <= 512 && K > 0) {
+    if (m * n <= (1 << 17) && K > 0) {
         if (!c.exec || m == 0 || n == 0) return;
-        dim3 grid((unsigned)((m + 7) / 8), (unsigned)((n + 7) / 8));
         ProfScope ps(c, "gemm_f64", 8.0 * (double)(m + n) * K + 8.0 * m * n, 2.0 * m * n * K);
-        gemm_nt_tiny_kernel<<<grid, 64, 0, c.stream>>>(m, n, K, A, B, alpha, beta, C, ldc, skip);
+        gemm_nt_warp_kernel<<<(unsigned)((m * n + 7) / 8), 256, 0, c.stream>>>(m, n, K, A, B, alpha, beta, C, ldc,
+                                                                                skip);
         c.counted();
         c.check_launch();
         return;
@@ -362,7 +418,7 @@ __device__ double block_sum(double v, double* scratch /* >= 33 */) {
 
 // ------------------------------------------------------------------ Cholesky + inverse
 
-__global__ void __launch_bounds__(256) chol_inv_kernel(KDims kd, int kmax, const double* W, double* Rinv, int* bad,
+__global__ void __launch_bounds__(512) chol_inv_kernel(KDims kd, int kmax, const double* W, double* Rinv, int* bad,
                                                        double tol) {
     extern __shared__ double A[];  // k x k, A(i, l) = A[i + k*l]
     __shared__ double dg[256];
@@ -386,8 +442,8 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(KDims kd, int kmax, const
             if (tid == 0) s_bad = 1;
             break;  // uniform: every thread read the same pivot
         }
-        double rjj = sqrt(piv);
-        for (int l = j + 1 + tid; l < k; l += nt) A[j + k * l] /= rjj;
+        double rjj = sqrt(piv), rinv = 1.0 / rjj;
+        for (int l = j + 1 + tid; l < k; l += nt) A[j + k * l] *= rinv;
         __syncthreads();
         if (tid == 0) A[j + k * j] = rjj;
         int w = k - j - 1;
@@ -402,15 +458,23 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(KDims kd, int kmax, const
         if (tid == 0) bad[b] = 1;
         return;
     }
-    // R^{-1} by column-wise back substitution (one thread per column).
-    for (int col = tid; col < k; col += nt) {
+    // R^{-1} by back substitution, one warp per column: x_col = 1 / r_cc and
+    // x_i = -(sum_{l=i+1..col} r_il x_l) / r_ii, the sum split over the lanes.
+    for (int i = tid; i < k; i += nt) dg[i] = 1.0 / A[i + k * i];
+    __syncthreads();
+    const int lane = tid & 31, nw = nt >> 5;
+    for (int col = tid >> 5; col < k; col += nw) {
         double* X = Rb + (int64_t)kmax * col;
-        for (int i = k - 1; i > col; --i) X[i] = 0.0;
-        X[col] = 1.0 / A[col + k * col];
+        for (int i = col + 1 + lane; i < k; i += 32) X[i] = 0.0;
+        if (lane == 0) X[col] = dg[col];
+        __syncwarp();
         for (int i = col - 1; i >= 0; --i) {
             double s = 0.0;
-            for (int l = i + 1; l <= col; ++l) s = fma(A[i + k * l], X[l], s);
-            X[i] = -s / A[i + k * i];
+            for (int l = i + 1 + lane; l <= col; l += 32) s = fma(A[i + k * l], X[l], s);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) X[i] = -s * dg[i];
+            __syncwarp();
         }
     }
 }
@@ -423,7 +487,7 @@ void launch_chol_inv(const Ctx& c, int batch, const KDims& kd, int kmax, const d
     if (smem > 48 * 1024)
         TK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(c, "chol_inv", 16.0 * batch * kmax * kmax, (2.0 / 3.0) * batch * kmax * kmax * kmax);
-    chol_inv_kernel<<<batch, 256, smem, c.stream>>>(kd, kmax, W, Rinv, bad, tol);
+    chol_inv_kernel<<<batch, 512, smem, c.stream>>>(kd, kmax, W, Rinv, bad, tol);
     c.counted();
     c.check_launch();
 }

@@ -32,7 +32,7 @@
 namespace tk {
 namespace tc {
 
-constexpr int kThreads = 384;
+constexpr int kThreads = 512;
 constexpr int kRows = 128;    // tile rows (TMEM lanes)
 constexpr int kChunk = 32;    // K elements per pipeline stage
 constexpr int kXBytes = kRows * kChunk * 4;
@@ -154,6 +154,15 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
     asm volatile(
@@ -177,15 +186,20 @@ struct TcArgs {
     unsigned* flags;
 };
 
-template <int NPAD>
+template <int NPAD, int EPI>
 struct Cfg {
     static constexpr int kBBytes = NPAD * 128;  // one of M_hi / M_lo: NPAD rows of 128 B
     static constexpr int kStage = kXBytes + 2 * kBBytes;
-    static constexpr int kStages = (200 * 1024) / kStage > 6 ? 6 : (200 * 1024) / kStage;
+    static constexpr int kXrBytes = EPI ? kRows * NPAD * 4 : 0;  // X tile compared in the residual epilogue
+    static constexpr int kXrBufs = EPI ? 2 : 0;
+    static constexpr int kBudget = 200 * 1024 - kXrBufs * kXrBytes;
+    static constexpr int kStages = kBudget / kStage > 6 ? 6 : kBudget / kStage;
     static constexpr int kAcc0 = 0;                // accumulators: 2 x (2*NPAD) columns
-    static constexpr int kABuf = 4 * NPAD;         // A buffers: 2 x 64 columns (hi 32 | lo 32)
-    static constexpr int kSmem = kStages * kStage + 1024 + 256;
-    static_assert(4 * NPAD + 128 <= 512, "TMEM budget");
+    static constexpr int kABuf = 4 * NPAD;         // A buffers: NA x 64 columns (hi 32 | lo 32)
+    static constexpr int kNA = (512 - 4 * NPAD) / 64 > 6 ? 6 : (512 - 4 * NPAD) / 64;
+    static constexpr int kSmem = kStages * kStage + kXrBufs * kXrBytes + 1024 + 512;
+    static_assert(kNA >= 2, "TMEM budget");
+    static_assert(kStages >= 2, "SMEM budget");
 };
 
 // EPI 0: store the product; 1: accumulate the residual norms against xref;
@@ -193,33 +207,43 @@ struct Cfg {
 template <int NPAD, bool KMAJOR, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     ttm_tf32x3_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBhi,
-                      const __grid_constant__ CUtensorMap tmBlo, TcArgs args) {
-    using C = Cfg<NPAD>;
+                      const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmXr,
+                      TcArgs args) {
+    using C = Cfg<NPAD, EPI>;
     constexpr int S = C::kStages;
+    constexpr int NA = C::kNA;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * C::kStage);
+    float* xr_buf = reinterpret_cast<float*>(smem + S * C::kStage);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * C::kStage + C::kXrBufs * C::kXrBytes);
     uint64_t* full = bars;               // [S] TMA landed
-    uint64_t* xfree = bars + S;          // [S] stage consumed (128 converter arrivals + 1 MMA commit)
-    uint64_t* afull = bars + 2 * S;      // [2] A buffer written (128 converter arrivals)
-    uint64_t* aempty = afull + 2;        // [2] A buffer consumed (MMA commit)
-    uint64_t* accfull = aempty + 2;      // [2] accumulator complete (MMA commit)
+    uint64_t* xfree = bars + S;          // [S] stage consumed (256 converter arrivals + 1 MMA commit)
+    uint64_t* afull = bars + 2 * S;      // [NA] A buffer written (256 converter arrivals)
+    uint64_t* aempty = afull + NA;       // [NA] A buffer consumed (MMA commit)
+    uint64_t* accfull = aempty + NA;     // [2] accumulator complete (MMA commit)
     uint64_t* accempty = accfull + 2;    // [2] accumulator drained (128 epilogue arrivals)
-    uint64_t* done = accempty + 2;       // [1] every issued MMA complete
+    uint64_t* xrfull = accempty + 2;     // [2] residual X tile landed
+    uint64_t* xrempty = xrfull + 2;      // [2] residual X tile consumed (128 epilogue arrivals)
+    uint64_t* done = xrempty + 2;        // [1] every issued MMA complete
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    __shared__ double red[8];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&xfree[s], 129);
+            mbar_init(&xfree[s], 257);
+        }
+        for (int b = 0; b < NA; ++b) {
+            mbar_init(&afull[b], 256);
+            mbar_init(&aempty[b], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&afull[b], 128);
-            mbar_init(&aempty[b], 1);
             mbar_init(&accfull[b], 1);
             mbar_init(&accempty[b], 128);
+            mbar_init(&xrfull[b], 1);
+            mbar_init(&xrempty[b], 128);
         }
         mbar_init(done, 1);
         *abort = 0;
@@ -236,14 +260,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tbase = *tmem_slot;
     unsigned* flags = args.flags;
     const int64_t nk = args.nk;
+    const int64_t nitems = args.ntiles * args.nblk;
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            int64_t it = 0;
+            int64_t it = 0, item = 0;
             bool ok = true;
-            const int64_t nitems = args.ntiles * args.nblk;
-            for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+            for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++item) {
                 const int64_t t = w / args.nblk, nb = w % args.nblk;
                 int64_t r0 = 0, l0 = 0, rr = 0;
                 if (KMAJOR) {
@@ -251,6 +275,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else {
                     rr = t / args.tiles_per_r;
                     l0 = (t % args.tiles_per_r) * kRows;
+                }
+                if (EPI) {  // the X tile the epilogue compares this item's product with
+                    const int xb = (int)(item & 1);
+                    if (!mbar_wait(&xrempty[xb], (uint32_t)(((item >> 1) & 1) ^ 1), abort, flags)) break;
+                    mbar_expect_tx(&xrfull[xb], C::kXrBytes);
+                    tma_load_3d(xr_buf + xb * (C::kXrBytes / 4), &tmXr, (int)l0, (int)(nb * NPAD), (int)rr,
+                                &xrfull[xb]);
                 }
                 for (int64_t kc = 0; kc < nk; ++kc, ++it) {
                     const int s = (int)(it % S);
@@ -276,10 +307,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             // drain: every issued load has landed before the CTA can exit
             const int64_t n_out = it < S ? it : S;
             for (int64_t q = it - n_out; q < it; ++q) {
-                const int s = (int)(q % S);
-                const uint32_t ph = (uint32_t)((q / S) & 1);
                 const uint64_t t0 = gtimer();
-                while (!mbar_try_wait(&full[s], ph) && gtimer() - t0 < kTimeoutNs) {
+                while (!mbar_try_wait(&full[q % S], (uint32_t)((q / S) & 1)) && gtimer() - t0 < kTimeoutNs) {
+                }
+            }
+            if (EPI) {
+                const int64_t n_xr = item < 2 ? item : 2;
+                for (int64_t q = item - n_xr; q < item; ++q) {
+                    const uint64_t t0 = gtimer();
+                    while (!mbar_try_wait(&xrfull[q & 1], (uint32_t)((q >> 1) & 1)) && gtimer() - t0 < kTimeoutNs) {
+                    }
                 }
             }
         }
@@ -288,7 +325,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int64_t it = 0, ab = 0, acc = 0;
             bool ok = true;
-            const int64_t nitems = args.ntiles * args.nblk;
             for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++acc) {
                 const int a = (int)(acc & 1);
                 if (!mbar_wait(&accempty[a], (uint32_t)(((acc >> 1) & 1) ^ 1), abort, flags)) {
@@ -299,9 +335,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t d_tmem = tbase + C::kAcc0 + a * 2 * NPAD;
                 for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
                     const int s = (int)(it % S);
-                    const int b = (int)(ab & 1);
+                    const int b = (int)(ab % NA);
                     if (!mbar_wait(&full[s], (uint32_t)((it / S) & 1), abort, flags) ||
-                        !mbar_wait(&afull[b], (uint32_t)((ab >> 1) & 1), abort, flags)) {
+                        !mbar_wait(&afull[b], (uint32_t)((ab / NA) & 1), abort, flags)) {
                         ok = false;
                         break;
                     }
@@ -325,71 +361,77 @@ __global__ void __launch_bounds__(kThreads, 1)
             while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
             }
         }
-    } else if (warp >= 4 && warp < 8) {
+    } else if (warp >= 4 && warp < 12) {
         // ------------------------------------------------ converters: X chunk -> TF32 hi / lo in TMEM
-        const int rho = threadIdx.x - 128;  // tile row == TMEM lane
-        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        // two warps per TMEM lane quarter; warp half hs converts K columns [16 hs, 16 hs + 16)
+        const int q = warp & 3, hs = (warp - 4) >> 2;
+        const int rho = 32 * q + lane;  // tile row == TMEM lane
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         int64_t it = 0, ab = 0;
         bool ok = true;
-        const int64_t nitems = args.ntiles * args.nblk;
         for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
             for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
                 const int s = (int)(it % S);
-                const int b = (int)(ab & 1);
+                const int b = (int)(ab % NA);
                 bool got = mbar_wait(&full[s], (uint32_t)((it / S) & 1), abort, flags) &&
-                           mbar_wait(&aempty[b], (uint32_t)(((ab >> 1) & 1) ^ 1), abort, flags);
+                           mbar_wait(&aempty[b], (uint32_t)(((ab / NA) & 1) ^ 1), abort, flags);
                 if (!__all_sync(0xffffffffu, got)) {  // warp-uniform: tcgen05.st below is .aligned
                     ok = false;
                     break;
                 }
                 const uint8_t* xs = smem + s * C::kStage;
-                float v[32];
+                float v[16];
                 if (KMAJOR) {
                     // row rho: 128 B, 16-byte chunk j stored at chunk j ^ (rho & 7)
                     const uint8_t* row = xs + rho * 128;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float4 q = *reinterpret_cast<const float4*>(row + ((j ^ (rho & 7)) << 4));
-                        v[4 * j] = q.x;
-                        v[4 * j + 1] = q.y;
-                        v[4 * j + 2] = q.z;
-                        v[4 * j + 3] = q.w;
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * hs + jj;
+                        const float4 f = *reinterpret_cast<const float4*>(row + ((j ^ (rho & 7)) << 4));
+                        v[4 * jj] = f.x;
+                        v[4 * jj + 1] = f.y;
+                        v[4 * jj + 2] = f.z;
+                        v[4 * jj + 3] = f.w;
                     }
                 } else {
                     // box (rho / 32): rows i of 32 floats (128 B), 128-byte swizzle
                     const uint8_t* box = xs + (rho >> 5) * 4096;
                     const int lc = rho & 31;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        v[i] = *reinterpret_cast<const float*>(box + i * 128 + ((((lc >> 2) ^ (i & 7)) << 4) | ((lc & 3) << 2)));
+                    for (int ii = 0; ii < 16; ++ii) {
+                        const int i = 16 * hs + ii;
+                        v[ii] = *reinterpret_cast<const float*>(box + i * 128 +
+                                                                ((((lc >> 2) ^ (i & 7)) << 4) | ((lc & 3) << 2)));
+                    }
                 }
-                uint32_t hi[32], lo[32];
+                uint32_t hi[16], lo[16];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < 16; ++i) {
                     hi[i] = tf32_rna(v[i]);
                     lo[i] = tf32_rna(v[i] - __uint_as_float(hi[i]));
                 }
-                const uint32_t ta = tbase + lane_base + C::kABuf + 64 * b;
+                const uint32_t ta = tbase + lane_base + C::kABuf + 64 * b + 16 * hs;
                 __syncwarp();
-                tmem_st32(ta, hi);
-                tmem_st32(ta + 32, lo);
+                tmem_st16(ta, hi);
+                tmem_st16(ta + 32, lo);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(&afull[b]);
                 mbar_arrive(&xfree[s]);
             }
         }
-    } else if (warp >= 8) {
+    } else if (warp >= 12) {
         // ------------------------------------------------ epilogue
-        const int rho = threadIdx.x - 256;
-        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const int q = warp & 3;
+        const int rho = 32 * q + lane;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         double sr = 0.0, sx = 0.0;
         int64_t acc = 0;
-        const int64_t nitems = args.ntiles * args.nblk;
         for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x, ++acc) {
             const int64_t t = w / args.nblk, nb = w % args.nblk;
             const int a = (int)(acc & 1);
             bool got = mbar_wait(&accfull[a], (uint32_t)((acc >> 1) & 1), abort, flags);
+            if (EPI) got = got && mbar_wait(&xrfull[a], (uint32_t)((acc >> 1) & 1), abort, flags);
             if (!__all_sync(0xffffffffu, got)) break;  // warp-uniform: tcgen05.ld below is .aligned
             tc_fence_after();
             int64_t base;
@@ -411,6 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             base += col0 * stride;
             const int64_t ncol = args.m - col0;  // valid columns in this block (may exceed NPAD)
             const uint32_t ta = tbase + lane_base + C::kAcc0 + a * 2 * NPAD;
+            const float* xt = xr_buf + a * (C::kXrBytes / 4);  // [column][row] of the residual X tile
 #pragma unroll
             for (int c0 = 0; c0 < NPAD; c0 += 16) {
                 float h[16], g[16];
@@ -428,12 +471,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             if (c0 + i < ncol) {
-                                const int64_t o = base + (c0 + i) * stride;
-                                const float xv = args.xref[o];
+                                const float xv = xt[(c0 + i) * kRows + rho];
                                 const float dv = xv - (h[i] + g[i]);
                                 fr = fmaf(dv, dv, fr);
                                 fx = fmaf(xv, xv, fx);
-                                if (EPI == 2) args.out[o] = args.alpha * dv;
+                                if (EPI == 2) args.out[base + (c0 + i) * stride] = args.alpha * dv;
                             }
                         }
                         sr += (double)fr;
@@ -443,18 +485,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_before();
             mbar_arrive(&accempty[a]);
+            if (EPI) mbar_arrive(&xrempty[a]);
         }
         if (EPI != 0) {
             // reduce over the 128 epilogue threads: warp shuffles, then named barrier 1
-            __shared__ double red[8];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
                 sx += __shfl_xor_sync(0xffffffffu, sx, o);
             }
             if (lane == 0) {
-                red[2 * (warp - 8)] = sr;
-                red[2 * (warp - 8) + 1] = sx;
+                red[2 * q] = sr;
+                red[2 * q + 1] = sx;
             }
             asm volatile("bar.sync 1, 128;" ::: "memory");
             if (rho == 0) {
@@ -487,14 +529,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 static void encode(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
-                   const uint32_t* box) {
+                   const uint32_t* box, bool swizzle = true) {
     auto fn = encode_fn();
     TK_REQUIRE(fn != nullptr, TK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     uint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base),
                     reinterpret_cast<const cuuint64_t*>(dims), reinterpret_cast<const cuuint64_t*>(strides_bytes),
                     reinterpret_cast<const cuuint32_t*>(box), estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     TK_REQUIRE(r == CUDA_SUCCESS, TK_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
@@ -529,8 +572,8 @@ static int num_sms() {
 
 template <int NPAD, bool KMAJOR, int EPI>
 static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap& th, const CUtensorMap& tl,
-                          const TcArgs& a) {
-    using Cf = Cfg<NPAD>;
+                          const CUtensorMap& txr, const TcArgs& a) {
+    using Cf = Cfg<NPAD, EPI>;
     auto kern = ttm_tf32x3_kernel<NPAD, KMAJOR, EPI>;
     static bool attr_set = false;
     if (!attr_set) {
@@ -538,14 +581,15 @@ static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap
         attr_set = true;
     }
     int grid = (int)std::min<int64_t>(a.ntiles * a.nblk, num_sms());
-    kern<<<grid, kThreads, Cf::kSmem, c.stream>>>(tx, th, tl, a);
+    kern<<<grid, kThreads, Cf::kSmem, c.stream>>>(tx, th, tl, txr, a);
 }
 
 }  // namespace tc
 
-// Output columns: up to 96 in one block (padded to 16), else blocks of 64.
-static void tc_blocks(int64_t m, int64_t& npad, int64_t& nblk) {
-    if (m <= 96) {
+// Output columns: up to 96 (64 for the residual epilogue, whose X tiles share
+// shared memory with the pipeline) in one block padded to 16, else blocks of 64.
+static void tc_blocks(int64_t m, int64_t& npad, int64_t& nblk, bool residual = false) {
+    if (m <= (residual ? 64 : 96)) {
         npad = (m + 15) / 16 * 16;
         nblk = 1;
     } else {
@@ -570,7 +614,7 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
                        const float* xref, float alpha, double* partials, const char* prof_name) {
     const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
     int64_t npad, nblk;
-    tc_blocks(m, npad, nblk);
+    tc_blocks(m, npad, nblk, epi != 0);
     const int64_t ldo = (nj + 3) / 4 * 4;
     const int64_t rows_b = npad * nblk;
     float* hi = c.alloc<float>(ldo * rows_b);
@@ -604,6 +648,14 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
         tc::encode(&th, hi, 2, dims, str, box);
         tc::encode(&tl, lo, 2, dims, str, box);
     }
+    CUtensorMap txr = tx;  // unused when epi == 0
+    if (epi != 0) {
+        TK_REQUIRE(!kmajor, TK_ERR_SHAPE, "ttm_tc: the fused residual needs a non-leading mode");
+        uint64_t dims[3] = {(uint64_t)L, (uint64_t)m, (uint64_t)R};
+        uint64_t str[2] = {(uint64_t)L * 4, (uint64_t)L * m * 4};
+        uint32_t box[3] = {tc::kRows, (uint32_t)npad, 1};
+        tc::encode(&txr, xref, 3, dims, str, box, false);
+    }
     tc::TcArgs a;
     a.L = L;
     a.nj = nj;
@@ -626,14 +678,14 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
 #define TK_TC_CASE(NP)                                                                             \
     case NP:                                                                                       \
         if (epi == 0) {                                                                            \
-            if (kmajor) tc::launch_kernel<NP, true, 0>(c, tx, th, tl, a);                          \
-            else tc::launch_kernel<NP, false, 0>(c, tx, th, tl, a);                                \
+            if (kmajor) tc::launch_kernel<NP, true, 0>(c, tx, th, tl, txr, a);                          \
+            else tc::launch_kernel<NP, false, 0>(c, tx, th, tl, txr, a);                                \
         } else if (epi == 1) {                                                                     \
-            if (kmajor) tc::launch_kernel<NP, true, 1>(c, tx, th, tl, a);                          \
-            else tc::launch_kernel<NP, false, 1>(c, tx, th, tl, a);                                \
+            if (kmajor) tc::launch_kernel<NP, true, 1>(c, tx, th, tl, txr, a);                          \
+            else tc::launch_kernel<NP, false, 1>(c, tx, th, tl, txr, a);                                \
         } else {                                                                                   \
-            if (kmajor) tc::launch_kernel<NP, true, 2>(c, tx, th, tl, a);                          \
-            else tc::launch_kernel<NP, false, 2>(c, tx, th, tl, a);                                \
+            if (kmajor) tc::launch_kernel<NP, true, 2>(c, tx, th, tl, txr, a);                          \
+            else tc::launch_kernel<NP, false, 2>(c, tx, th, tl, txr, a);                                \
         }                                                                                          \
         break;
     switch (npad) {
@@ -656,12 +708,19 @@ void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int6
     ttm_tc_run(c, X, j, M, mtrans, m, out, 0, nullptr, 0.f, nullptr, name);
 }
 
-int tc_num_ctas(const Tens& X, int j, int64_t m) {
+int tc_num_ctas(const Tens& X, int j, int64_t m, bool residual) {
     int64_t npad, nblk;
-    tc_blocks(m, npad, nblk);
+    tc_blocks(m, npad, nblk, residual);
     const int64_t L = X.left(j), R = X.right(j);
     const int64_t tiles = (L == 1) ? (R + tc::kRows - 1) / tc::kRows : R * ((L + tc::kRows - 1) / tc::kRows);
     return (int)std::min<int64_t>(tiles * nblk, tc::num_sms());
+}
+
+bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m) {
+    int64_t npad, nblk;
+    tc_blocks(m, npad, nblk, true);
+    // the residual X tile is a (128 rows x npad columns) TMA box: keep it inside the tensor
+    return W.left(j) >= tc::kRows && m >= npad && ttm_tc_eligible(W, j, m, TK_F32);
 }
 
 void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const float* xref,
