@@ -295,14 +295,14 @@ static void eig_top(Ctx& c, int64_t k, const double* A, int64_t r, double* Vr, b
     double* V = c.alloc<double>(k * k);
     double* Vt = c.alloc<double>(k * r);
     double* Wr = c.alloc<double>(r * r);
-    launch_jacobi_mixed(c, k, A, D, J, 1e-6, c.max_sweeps);
+    launch_jacobi_mixed(c, k, A, D, J, 1e-6, c.max_sweeps, false);
     launch_convert(c, J, TK_F32, k, k, k, V0, TK_F64, k, 1.f);
     launch_convert(c, J, TK_F32, k, k, k, V1, TK_F64, k, 1.f);
     gemm_nt_f64(c, k, k, k, view_cols(V0, TK_F64, k), view_cols(V0, TK_F64, k), 1.0, 0.0, W, k);
     gemm_nt_f64(c, k, k, k, view_rows(V0, TK_F64, k), view_cols(W, TK_F64, k), -0.5, 1.5, V1, k);
     gemm_nt_f64(c, k, k, k, view_rows(A, TK_F64, k), view_cols(V1, TK_F64, k), 1.0, 0.0, Pm, k);
     gemm_nt_f64(c, k, k, k, view_cols(V1, TK_F64, k), view_cols(Pm, TK_F64, k), 1.0, 0.0, B, k);
-    launch_jacobi_mixed(c, k, B, D, J, 1e-14, c.max_sweeps);
+    launch_jacobi_mixed(c, k, B, D, J, 1e-14, c.max_sweeps, true);
     gemm_nt_f64(c, k, k, k, view_rows(V1, TK_F64, k), view_cols(J, TK_F32, k), 1.0, 0.0, V, k);
     launch_select_top(c, k, r, D, V, Vt);
     launch_convert(c, Vt, TK_F64, k, r, k, Vr, TK_F64, k, 1.f);

@@ -436,19 +436,27 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(KDims kd, int kmax, const
     for (int i = tid; i < k; i += nt) dg[i] = Wb[i + (int64_t)kmax * i];
     if (tid == 0) s_bad = 0;
     __syncthreads();
+    __shared__ double s_rinv;
     for (int j = 0; j < k; ++j) {
-        double piv = A[j + k * j];
-        if (!(piv > tol * dg[j]) || !(piv > 0.0)) {
-            if (tid == 0) s_bad = 1;
-            break;  // uniform: every thread read the same pivot
+        // one thread takes the FP64 square root and reciprocal (FP64 throughput is scarce)
+        if (tid == 0) {
+            const double piv = A[j + k * j];
+            if (!(piv > tol * dg[j]) || !(piv > 0.0)) {
+                s_bad = 1;
+            } else {
+                const double rjj = sqrt(piv);
+                A[j + k * j] = rjj;
+                s_rinv = 1.0 / rjj;
+            }
         }
-        double rjj = sqrt(piv), rinv = 1.0 / rjj;
+        __syncthreads();
+        if (s_bad) break;  // uniform
+        const double rinv = s_rinv;
         for (int l = j + 1 + tid; l < k; l += nt) A[j + k * l] *= rinv;
         __syncthreads();
-        if (tid == 0) A[j + k * j] = rjj;
-        int w = k - j - 1;
+        const int w = k - j - 1;
         for (int e = tid; e < w * w; e += nt) {
-            int i = j + 1 + e % w, l = j + 1 + e / w;
+            const int i = j + 1 + e % w, l = j + 1 + e / w;
             if (i <= l) A[i + k * l] -= A[j + k * i] * A[j + k * l];
         }
         __syncthreads();
@@ -751,13 +759,16 @@ constexpr int JM_THREADS = 512;
 constexpr int JM_FB = 4;  // F blocks per thread: half(half+1)/2 <= 1596 for k <= 112
 constexpr int JM_JB = 7;  // J blocks per thread: ceil(k/2) * half <= 3136
 
+// TD: type of the diagonal.  float for the first stage (whose result only
+// seeds the second), double for the stage that resolves the eigenvalues.
+template <typename TD>
 __global__ void __launch_bounds__(JM_THREADS) jacobi_mixed_kernel(int k, const double* __restrict__ A, double* Dout,
                                                                   float* Jout, double tol, int max_sweeps,
                                                                   unsigned* flags) {
     extern __shared__ unsigned char smraw[];
     const int ldf = k + 1;  // odd row stride: column walks are bank-conflict free
-    double* D = reinterpret_cast<double*>(smraw);
-    float* F = reinterpret_cast<float*>(D + k);
+    TD* D = reinterpret_cast<TD*>(smraw);
+    float* F = reinterpret_cast<float*>(reinterpret_cast<double*>(smraw) + k);
     float* J = F + (size_t)k * ldf;
     __shared__ float cs[64], sn[64];
     __shared__ int P[64], Qp[64];
@@ -769,7 +780,7 @@ __global__ void __launch_bounds__(JM_THREADS) jacobi_mixed_kernel(int k, const d
         double v = A[i + (int64_t)k * j];
         part += v * v;
         if (i == j) {
-            D[i] = v;
+            D[i] = (TD)v;
             F[i * ldf + j] = 0.f;
         } else {
             F[i * ldf + j] = (float)v;
@@ -829,12 +840,15 @@ __global__ void __launch_bounds__(JM_THREADS) jacobi_mixed_kernel(int k, const d
                 if (q < k) {
                     float fpq = F[p * ldf + q];
                     if (fabsf(fpq) > fthr) {
-                        float tau = (float)(D[q] - D[p]) / (2.f * fpq);
-                        float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-                        c = 1.f / sqrtf(1.f + tt * tt);
+                        // rotation angle from the diagonal difference; fast FP32 reciprocals suffice
+                        // (the off-diagonal is zeroed explicitly and convergence is measured)
+                        float tau = __fdividef((float)(D[q] - D[p]), 2.f * fpq);
+                        float tt = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+                        c = rsqrtf(fmaf(tt, tt, 1.f));
                         sv = tt * c;
-                        D[p] -= (double)tt * (double)fpq;
-                        D[q] += (double)tt * (double)fpq;
+                        const TD dt = (TD)tt * (TD)fpq;
+                        D[p] -= dt;
+                        D[q] += dt;
                     }
                 } else {
                     q = -1;
@@ -903,21 +917,30 @@ __global__ void __launch_bounds__(JM_THREADS) jacobi_mixed_kernel(int k, const d
         }
     }
     if (!converged && tid == 0) atomicOr(flags, FLAG_NOT_CONVERGED);
-    for (int i = tid; i < k; i += nt) Dout[i] = D[i];
+    for (int i = tid; i < k; i += nt) Dout[i] = (double)D[i];
     for (int e = tid; e < k * k; e += nt) {
         int i = e % k, j = e / k;
         Jout[i + (int64_t)k * j] = J[i * ldf + j];
     }
 }
 
-void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double tol, int max_sweeps) {
+void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double tol, int max_sweeps,
+                         bool fp64_diag) {
     if (!c.exec) return;
     TK_REQUIRE(k >= 1 && k <= 112, TK_ERR_SHAPE, "jacobi_mixed: 1 <= k <= 112");
     size_t smem = sizeof(double) * k + 2 * sizeof(float) * k * (k + 1);
-    if (smem > 48 * 1024)
-        TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(c, "jacobi", 8.0 * k * k + 8.0 * k * k, 12.0 * k * k * k * max_sweeps);
-    jacobi_mixed_kernel<<<1, JM_THREADS, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
+    if (fp64_diag) {
+        if (smem > 48 * 1024)
+            TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        jacobi_mixed_kernel<double><<<1, JM_THREADS, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
+    } else {
+        if (smem > 48 * 1024)
+            TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        jacobi_mixed_kernel<float><<<1, JM_THREADS, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
+    }
     c.counted();
     c.check_launch();
 }
