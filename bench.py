@@ -194,7 +194,19 @@ def profile_case(args):
     for _ in range(3):
         fn()
     torch.cuda.synchronize()
-    print(json.dumps(dict(profile_case=args.profile_case, n=n, status=T.tk_sync_status(dev)[0])))
+    T.tk_profile(True, dev)
+    for _ in range(5):
+        fn()
+    prof = T.tk_profile_read(dev)
+    T.tk_profile(False, dev)
+    hbm = _peaks()[0]
+    out = dict(profile_case=args.profile_case, n=n, status=T.tk_sync_status(dev)[0], kernels={})
+    for name, v in prof.items():
+        ms = v["ms"] / v["launches"]
+        out["kernels"][name] = dict(launches=v["launches"] // 5, us_per_launch=1e3 * ms,
+                                    gbs=(v["bytes"] / v["launches"]) / (ms * 1e-3) / 1e9 if ms > 0 else 0.0,
+                                    frac_hbm=((v["bytes"] / v["launches"]) / (ms * 1e-3) / 1e9) / hbm if ms > 0 else 0.0)
+    print(json.dumps(out))
 
 
 # ------------------------------------------------------------------ GPU leg

@@ -100,6 +100,17 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(c0),
+                 "r"(c1)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)map), "r"(c0),
+                 "r"(c1), "r"(c2)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -192,8 +203,8 @@ struct Cfg {
     static constexpr int kStage = kXBytes + 2 * kBBytes;
     static constexpr int kXrBytes = EPI ? kRows * NPAD * 4 : 0;  // X tile compared in the residual epilogue
     static constexpr int kXrBufs = EPI ? 2 : 0;
-    static constexpr int kBudget = 200 * 1024 - kXrBufs * kXrBytes;
-    static constexpr int kStages = kBudget / kStage > 6 ? 6 : kBudget / kStage;
+    static constexpr int kBudget = 210 * 1024 - kXrBufs * kXrBytes;
+    static constexpr int kStages = kBudget / kStage > 12 ? 12 : kBudget / kStage;
     static constexpr int kAcc0 = 0;                // accumulators: 2 x (2*NPAD) columns
     static constexpr int kABuf = 4 * NPAD;         // A buffers: NA x 64 columns (hi 32 | lo 32)
     static constexpr int kNA = (512 - 4 * NPAD) / 64 > 6 ? 6 : (512 - 4 * NPAD) / 64;
@@ -265,6 +276,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
+            // L2 prefetch of the X chunk kPf chunks ahead of the one being loaded, so that
+            // more DRAM requests are in flight than the shared-memory ring can hold
+            constexpr int64_t kPf = 8;
+            const int64_t nchunks_cta = (nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0) * nk;
+            auto prefetch = [&](int64_t q) {
+                if (q >= nchunks_cta) return;
+                const int64_t wq = blockIdx.x + (q / nk) * gridDim.x, kq = q % nk;
+                const int64_t tq = wq / args.nblk;
+                if (args.nblk > 1 && wq % args.nblk != 0) return;  // same X tile as the previous column block
+                if (KMAJOR) {
+                    tma_prefetch_2d(&tmX, (int)(kq * kChunk), (int)(tq * kRows));
+                } else {
+                    const int64_t rq = tq / args.tiles_per_r, lq = (tq % args.tiles_per_r) * kRows;
+#pragma unroll
+                    for (int b4 = 0; b4 < 4; ++b4) tma_prefetch_3d(&tmX, (int)(lq + 32 * b4), (int)(kq * kChunk), (int)rq);
+                }
+            };
+            for (int64_t q = 0; q < kPf; ++q) prefetch(q);
             int64_t it = 0, item = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++item) {
@@ -290,6 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
+                    prefetch(it + kPf);
                     uint8_t* xs = smem + s * C::kStage;
                     uint8_t* bs = xs + kXBytes;
                     mbar_expect_tx(&full[s], kXBytes + 2 * C::kBBytes);
