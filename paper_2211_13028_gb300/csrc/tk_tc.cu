@@ -100,17 +100,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(c0),
-                 "r"(c1)
-                 : "memory");
-}
-__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int c0, int c1, int c2) {
-    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)map), "r"(c0),
-                 "r"(c1), "r"(c2)
-                 : "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -228,13 +217,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* xr_buf = reinterpret_cast<float*>(smem + S * C::kStage);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * C::kStage + C::kXrBufs * C::kXrBytes);
     uint64_t* full = bars;               // [S] TMA landed
-    uint64_t* xfree = bars + S;          // [S] stage consumed (256 converter arrivals + 1 MMA commit)
-    uint64_t* afull = bars + 2 * S;      // [NA] A buffer written (256 converter arrivals)
+    uint64_t* xfree = bars + S;          // [S] stage consumed (one arrival per converter warp + 1 MMA commit)
+    uint64_t* afull = bars + 2 * S;      // [NA] A buffer written (one arrival per converter warp)
     uint64_t* aempty = afull + NA;       // [NA] A buffer consumed (MMA commit)
     uint64_t* accfull = aempty + NA;     // [2] accumulator complete (MMA commit)
-    uint64_t* accempty = accfull + 2;    // [2] accumulator drained (128 epilogue arrivals)
+    uint64_t* accempty = accfull + 2;    // [2] accumulator drained (one arrival per epilogue warp)
     uint64_t* xrfull = accempty + 2;     // [2] residual X tile landed
-    uint64_t* xrempty = xrfull + 2;      // [2] residual X tile consumed (128 epilogue arrivals)
+    uint64_t* xrempty = xrfull + 2;      // [2] residual X tile consumed (one arrival per epilogue warp)
     uint64_t* done = xrempty + 2;        // [1] every issued MMA complete
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -244,17 +233,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&xfree[s], 257);
+            mbar_init(&xfree[s], 9);   // 8 converter warps + 1 MMA commit
         }
         for (int b = 0; b < NA; ++b) {
-            mbar_init(&afull[b], 256);
+            mbar_init(&afull[b], 8);   // 8 converter warps
             mbar_init(&aempty[b], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accfull[b], 1);
-            mbar_init(&accempty[b], 128);
+            mbar_init(&accempty[b], 4);   // 4 epilogue warps
             mbar_init(&xrfull[b], 1);
-            mbar_init(&xrempty[b], 128);
+            mbar_init(&xrempty[b], 4);
         }
         mbar_init(done, 1);
         *abort = 0;
@@ -276,24 +265,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            // L2 prefetch of the X chunk kPf chunks ahead of the one being loaded, so that
-            // more DRAM requests are in flight than the shared-memory ring can hold
-            constexpr int64_t kPf = 8;
-            const int64_t nchunks_cta = (nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0) * nk;
-            auto prefetch = [&](int64_t q) {
-                if (q >= nchunks_cta) return;
-                const int64_t wq = blockIdx.x + (q / nk) * gridDim.x, kq = q % nk;
-                const int64_t tq = wq / args.nblk;
-                if (args.nblk > 1 && wq % args.nblk != 0) return;  // same X tile as the previous column block
-                if (KMAJOR) {
-                    tma_prefetch_2d(&tmX, (int)(kq * kChunk), (int)(tq * kRows));
-                } else {
-                    const int64_t rq = tq / args.tiles_per_r, lq = (tq % args.tiles_per_r) * kRows;
-#pragma unroll
-                    for (int b4 = 0; b4 < 4; ++b4) tma_prefetch_3d(&tmX, (int)(lq + 32 * b4), (int)(kq * kChunk), (int)rq);
-                }
-            };
-            for (int64_t q = 0; q < kPf; ++q) prefetch(q);
             int64_t it = 0, item = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++item) {
@@ -319,7 +290,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    prefetch(it + kPf);
                     uint8_t* xs = smem + s * C::kStage;
                     uint8_t* bs = xs + kXBytes;
                     mbar_expect_tx(&full[s], kXBytes + 2 * C::kBBytes);
@@ -446,8 +416,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_st16(ta + 32, lo);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
-                mbar_arrive(&afull[b]);
-                mbar_arrive(&xfree[s]);
+                __syncwarp();  // the warp's TMEM stores and SMEM reads are ordered before lane 0's arrivals
+                if (lane == 0) {
+                    mbar_arrive(&afull[b]);
+                    mbar_arrive(&xfree[s]);
+                }
             }
         }
     } else if (warp >= 12) {
@@ -514,8 +487,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             tc_fence_before();
-            mbar_arrive(&accempty[a]);
-            if (EPI) mbar_arrive(&xrempty[a]);
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&accempty[a]);
+                if (EPI) mbar_arrive(&xrempty[a]);
+            }
         }
         if (EPI != 0) {
             // reduce over the 128 epilogue threads: warp shuffles, then named barrier 1
