@@ -32,7 +32,7 @@
 namespace tk {
 namespace tc {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 768;
 constexpr int kRows = 128;    // tile rows (TMEM lanes)
 constexpr int kChunk = 32;    // K elements per pipeline stage
 constexpr int kXBytes = kRows * kChunk * 4;
@@ -196,7 +196,7 @@ struct Cfg {
     static constexpr int kStages = kBudget / kStage > 12 ? 12 : kBudget / kStage;
     static constexpr int kAcc0 = 0;                // accumulators: 2 x (2*NPAD) columns
     static constexpr int kABuf = 4 * NPAD;         // A buffers: NA x 64 columns (hi 32 | lo 32)
-    static constexpr int kNA = (512 - 4 * NPAD) / 64 > 6 ? 6 : (512 - 4 * NPAD) / 64;
+    static constexpr int kNA = (512 - 4 * NPAD) / 64 > 6 ? 6 : (512 - 4 * NPAD) / 64;  // >= 2
     static constexpr int kSmem = kStages * kStage + kXrBufs * kXrBytes + 1024 + 512;
     static_assert(kNA >= 2, "TMEM budget");
     static_assert(kStages >= 2, "SMEM budget");
@@ -361,16 +361,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
             }
         }
-    } else if (warp >= 4 && warp < 12) {
+    } else if (warp >= 4 && warp < 20) {
         // ------------------------------------------------ converters: X chunk -> TF32 hi / lo in TMEM
-        // two warps per TMEM lane quarter; warp half hs converts K columns [16 hs, 16 hs + 16)
-        const int q = warp & 3, hs = (warp - 4) >> 2;
+        // 16 warps: group g = 0/1 takes the even/odd chunks, so two chunks are converted at
+        // once; within a group two warps per TMEM lane quarter, half hs converting K columns
+        // [16 hs, 16 hs + 16).
+        const int cw = warp - 4;
+        const int q = warp & 3, hs = (cw >> 2) & 1, grp = cw >> 3;
         const int rho = 32 * q + lane;  // tile row == TMEM lane
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         int64_t it = 0, ab = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
             for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
+                if ((it & 1) != grp) continue;
                 const int s = (int)(it % S);
                 const int b = (int)(ab % NA);
                 bool got = mbar_wait(&full[s], (uint32_t)((it / S) & 1), abort, flags) &&
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-    } else if (warp >= 12) {
+    } else if (warp >= 20) {
         // ------------------------------------------------ epilogue
         const int q = warp & 3;
         const int rho = 32 * q + lane;
