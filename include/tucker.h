@@ -1,8 +1,8 @@
 /*
  * tucker.h -- C ABI of libtucker, a GB300 (sm_103a) implementation of the
  * randomized Tucker decompositions of "Parallel Randomized Tucker
- * Decomposition Algorithms" (arXiv 2211.13028): rHKron-re (Section 3.3,
- * Algorithm rHKron-re) and rSTHKron (Section 3.2, Algorithm rSTHKron), their
+ * Decomposition Algorithms" (arXiv 2211.13028): rHKron-re (Section 4.3,
+ * Algorithm rHKron-re) and rSTHKron (Section 4.2, Algorithm rSTHKron), their
  * building blocks (Kronecker sketch multi-TTM, thin QR of a sketch, core
  * multi-TTM, core truncation) and the reconstruction loss with its gradient.
  *
@@ -137,7 +137,7 @@ TK_API int tk_profile_read(tk_handle* h, tk_prof_entry* out, int max);
 
 /* ---- host-side integer planning (no device work; h may be NULL) -------- */
 
-/* Subrank vector of Algorithm rHKron-re (Section 3.3, the formula
+/* Subrank vector of Algorithm rHKron-re (Section 4.3, the formula
  * s_i = ceil((prod_j l_j)^(1/(d-1)) / l_i) with l_j = r_j + p), followed by a
  * reduction: entries taken largest first (ties: lowest mode) are each lowered
  * to the smallest value that keeps prod_{k!=j} s_k >= l_j for every mode j.
@@ -146,7 +146,7 @@ TK_API int tk_profile_read(tk_handle* h, tk_prof_entry* out, int max);
  * r_j < 1 or p < 0. */
 TK_API tk_status tucker_subranks_reuse(int d, const int64_t* r, int p, int64_t* s_out, int64_t* width_out);
 
-/* Subrank matrix of Algorithm rSTHKron (Section 3.2, "Choosing subranks"):
+/* Subrank matrix of Algorithm rSTHKron (Section 4.2, "Choosing subranks"):
  * row j holds d-1 integer factors >= 2 of the smallest l_j' >= r_j + p that
  * has such a factorisation, the most balanced one (smallest largest factor).
  * The factors are given in descending order to the other modes taken in
@@ -160,7 +160,7 @@ TK_API tk_status tucker_subranks_matrix(int d, const int64_t* r, int p, const in
 /* Kronecker-structured sketches of Algorithm rHKron-re (sketch line):
  * for every mode n, Y_n = X x_1 Phi_1 ... x_{n-1} Phi_{n-1} x_{n+1} Phi_{n+1} ... x_d Phi_d,
  * equivalently Y_n(n) = X_(n) (Phi_d kron ... kron Phi_1, skipping n)^T
- * (Section 3.2), computed with the dimension tree of Section 4.4 and never
+ * (Section 4.2), computed with the dimension tree of Section 4.4 and never
  * forming the Kronecker product.
  * X: d-way tensor (F64, F32, BF16 or FP8_E4M3).  Omega: d matrices
  * Omega_j = Phi_j^T, n_j x s_j, dtype F64 for F64 data else F32 or BF16.
@@ -188,7 +188,7 @@ TK_API tk_status tucker_core(tk_handle* h, const tk_tensor* X, const tk_matrix* 
  * (n_j x s_j), thin QR of each sketch unfolding into Q_n (n_n x k_n,
  * k_n = min(n_n, prod_{j!=n} s_j)), core Ghat = X x_j Q_j^T, STHOSVD of Ghat to
  * ranks r in FP64 (Gram matrix + Jacobi eigensolver per mode), U_j = Q_j V_j
- * (Section 3, holistic truncation).  Each column of U_j is signed so that its
+ * (Section 4, holistic truncation).  Each column of U_j is signed so that its
  * largest-magnitude entry is positive; G's slices follow.
  * X: F64, F32, BF16 or FP8_E4M3.  r: d host ranks, 1 <= r_j <= k_j.
  * p: oversampling, only checked against the Omega widths (prod_{j!=n} s_j >= r_n + p).

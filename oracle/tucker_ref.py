@@ -16,14 +16,14 @@ Pins (tests/test_oracle_*.py):
     Kronecker unfolding identity of Section 2.1, round trips.
   * thin_qr: Q^T Q = I, Q R = Y, R upper triangular with positive diagonal
     (which fixes Q uniquely), classical Gram-Schmidt on tiny inputs.
-  * sthosvd: closed-form error 0.4^r on the Section 6.1 tensor, the STHOSVD
+  * sthosvd: closed-form error 0.4^r on the Section 7.1 tensor, the STHOSVD
     error identity (sum of discarded squared singular values).
   * rhkron / rsthkron / rhkron_noreuse: exact recovery of exactly low-rank
     tensors, the Section 5 invariants (core singular values bounded by those
     of X, the core error bound Eq. core_svals, Pythagoras for orthonormal
-    factors), the Section 6.1 medians (statistical).
+    factors), the Section 7.1 medians (statistical).
   * subranks_reuse / subranks_matrix: the vectors and matrices printed for
-    the Miranda and SP runs (Sections 6.5-6.6).
+    the Miranda and SP runs (Sections 7.5-7.6).
   * loss_grads: central finite differences in FP64.
 """
 from __future__ import annotations
@@ -109,7 +109,7 @@ def kron_unfolded_multi_ttm(X: np.ndarray, A: Sequence[np.ndarray], j: int) -> n
 
 
 def kron_omega(phis: Sequence[np.ndarray], j: int) -> np.ndarray:
-    """Omega_j = (Phi_d kron ... kron Phi_{j+1} kron Phi_{j-1} kron ... kron Phi_1)^T (Section 3.2)."""
+    """Omega_j = (Phi_d kron ... kron Phi_{j+1} kron Phi_{j-1} kron ... kron Phi_1)^T (Section 4.2)."""
     K = np.ones((1, 1))
     for k in range(len(phis) - 1, -1, -1):
         if k != j:
@@ -188,7 +188,7 @@ def _ceil_root_ratio(P: int, ell: int, d: int) -> int:
 
 
 def subranks_reuse(r: Sequence[int], p: int):
-    """Subrank vector of Algorithm rHKron-re (Section 3.3).
+    """Subrank vector of Algorithm rHKron-re (Section 4.3).
 
     The paper's formula s_i = ceil((prod_j l_j)^(1/(d-1)) / l_i), then (reading)
     each entry, largest first (ties: lowest mode), is lowered to the smallest
@@ -225,7 +225,7 @@ def subranks_reuse(r: Sequence[int], p: int):
 def balanced_factors(ell: int, m: int):
     """Smallest L >= ell that is a product of m integers >= 2, and its most balanced
     such factorisation (smallest largest factor, compared as sorted-descending
-    tuples).  Reading of Section 3.2's subrank heuristic."""
+    tuples).  Reading of Section 4.2's subrank heuristic."""
     def facts(n, m, lo):
         if m == 1:
             if n >= lo:
@@ -251,7 +251,7 @@ def balanced_factors(ell: int, m: int):
 
 
 def subranks_matrix(r: Sequence[int], p: int, order: Sequence[int] | None = None):
-    """Subrank matrix S of Algorithm rSTHKron (Section 3.2).
+    """Subrank matrix S of Algorithm rSTHKron (Section 4.2).
 
     Row j holds d-1 integer factors (each >= 2) of l_j' >= l_j = r_j + p, l_j' the
     smallest such value, most balanced factorisation.  Reading: the factors

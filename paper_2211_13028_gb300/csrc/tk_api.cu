@@ -1,5 +1,5 @@
 // C-ABI entry points of libtucker and the host-side orchestration of
-// Algorithms rHKron-re and rSTHKron (arXiv 2211.13028, Sections 3.2-3.3).
+// Algorithms rHKron-re and rSTHKron (arXiv 2211.13028, Sections 4.2-4.3).
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -264,6 +264,7 @@ static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<in
 static void orth_one(Ctx& c, const View2& Y, int64_t n, int64_t k, double* Q, int slot) {
     orth_batch(c, {Y}, {n}, {k}, {Q}, {slot});
 }
+
 
 // Leading r eigenvectors of the symmetric k x k FP64 matrix A, as the columns
 // of Vr (k x r, ld k), in descending eigenvalue order.

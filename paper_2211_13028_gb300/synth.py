@@ -12,7 +12,7 @@ Conventions
   (values already rounded to the working dtype when one is given) or as torch
   tensors in column-major layout (mode 1 fastest, strides ascending), which is
   the layout the C-ABI expects.
-* Sketch factors follow Section 3.2: Phi_j is s_j x n_j with i.i.d. N(0,1)
+* Sketch factors follow Section 4.2: Phi_j is s_j x n_j with i.i.d. N(0,1)
   entries.  They are handed around as Omega_j = Phi_j^T (n_j x s_j), the
   orientation the C-ABI takes.
 * ``dtype`` names are the C-ABI's: "f64", "f32", "bf16", "fp8".  A value drawn
@@ -175,7 +175,7 @@ def tucker_tensor(dims: Sequence[int], core_dims: Sequence[int], seed: int, nois
 
 
 def e1_tensor(n: int, ratio: float = 0.4, seed: int = 0, d: int = 3) -> np.ndarray:
-    """Section 6.1 test tensor: superdiagonal core ratio^(i-1), random orthogonal factors."""
+    """Section 7.1 test tensor: superdiagonal core ratio^(i-1), random orthogonal factors."""
     g = _gen(seed)
     core = np.zeros((n,) * d)
     for i in range(n):

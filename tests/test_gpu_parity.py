@@ -41,7 +41,7 @@ def test_sketch_parity(dev, dtype, dims, s):
 
 
 def test_sketch_matches_explicit_kronecker(dev):
-    # Y_n(n) = X_(n) Omega_n with the Kronecker product formed explicitly (Section 3.2 identity).
+    # Y_n(n) = X_(n) Omega_n with the Kronecker product formed explicitly (Section 4.2 identity).
     g = _rng(3)
     dims, s = (9, 8, 7), (2, 3, 2)
     x = g.standard_normal(dims)

@@ -61,7 +61,7 @@ def test_multi_ttm_kronecker_unfolding_identity():
 
 
 def test_kronecker_sketch_identity():
-    # X_(n) Omega_n = (X x_{j != n} Phi_j)_(n) with Omega_n the explicit Kronecker product (Section 3.2).
+    # X_(n) Omega_n = (X x_{j != n} Phi_j)_(n) with Omega_n the explicit Kronecker product (Section 4.2).
     g = _rng(4)
     X = g.standard_normal((5, 4, 6))
     phis = [g.standard_normal((2, 5)), g.standard_normal((3, 4)), g.standard_normal((2, 6))]
@@ -116,7 +116,7 @@ def test_thin_qr_full_width_is_identity():
 # ------------------------------------------------------------------ STHOSVD
 
 def test_sthosvd_closed_form_on_section61_tensor():
-    # Superdiagonal core 0.4^(i-1): truncating to rank 10 leaves error exactly 0.4^10 (Section 6.1).
+    # Superdiagonal core 0.4^(i-1): truncating to rank 10 leaves error exactly 0.4^10 (Section 7.1).
     X = synth.e1_tensor(40, 0.4, seed=0)
     G, U, _ = O.sthosvd(X, (10, 10, 10))
     err = O.rel_err(X, G, U)
@@ -261,7 +261,7 @@ def test_section5_invariants():
 
 
 def test_section61_medians_statistical():
-    # 100 trials on a 64^3 copy of the Section 6.1 tensor: medians within 1% of 0.4^10 and upper
+    # 100 trials on a 64^3 copy of the Section 7.1 tensor: medians within 1% of 0.4^10 and upper
     # quartiles within 2% (the printed quartiles reach 1.65%).
     golden = json.load(open(os.path.join(GOLDEN, "e1_accuracy.json")))
     X = synth.e1_tensor(64, golden["ratio"], seed=0)
