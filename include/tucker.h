@@ -177,6 +177,26 @@ TK_API tk_status tucker_sketch(tk_handle* h, const tk_tensor* X, const tk_matrix
  * 2 identity; a non-NULL info synchronises. */
 TK_API tk_status tucker_orth(tk_handle* h, const tk_matrix* Y, tk_matrix* Q, int* info, const tk_opts* opts);
 
+/* Thin QR that allocates nothing (the paper has no counterpart; it is a
+ * service for callers that cannot allocate device memory where they need the
+ * factorisation: inside a CUDA-graph capture, under an allocator that owns all
+ * device memory, or on a path that must not trigger an allocation's implicit
+ * synchronisation).  Same result as tucker_orth with default options
+ * (CholeskyQR2, Householder fallback, identity for cols >= rows), but it takes
+ * no handle: work is queued on cuda_stream (void* cudaStream_t, NULL = legacy
+ * default stream) and its scratch is a fixed 6 MiB device array inside the
+ * library, present on every GPU that loads it until the process exits.
+ * Limits: rows <= 4096 and min(rows, cols) <= 64, else TK_ERR_SHAPE.
+ * The first call on a device looks up that array's device address, so make
+ * it before any stream capture on that device.  Every call shares the array:
+ * calls that overlap on the GPU (different streams, or several threads) race
+ * and must be serialised by the caller.  Y: rows x cols, F64 or F32; Q: rows x
+ * min(rows, cols), F64 or F32, both device pointers.  info (host, may be
+ * NULL; non-NULL synchronises the stream): 0 CholeskyQR2, 1 Householder,
+ * 2 identity.  Other errors: TK_ERR_ARG, TK_ERR_DTYPE, TK_ERR_ALIGN,
+ * TK_ERR_CUDA. */
+TK_API tk_status tucker_orth_noalloc(void* cuda_stream, const tk_matrix* Y, tk_matrix* Q, int* info);
+
 /* Core multi-TTM Ghat = X x_1 Q_1^T x_2 Q_2^T ... x_d Q_d^T (Algorithm
  * rHKron-re, core line).  Q: d matrices n_j x k_j (F64 for F64 data, else F32).
  * G: tensor (k_1,...,k_d), F64 or F32. */

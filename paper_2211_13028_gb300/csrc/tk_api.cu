@@ -61,7 +61,7 @@ static Tens tens_in(const tk_tensor* t, const char* name, bool allow_empty = tru
     return T;
 }
 
-static Mat mat_in(const tk_matrix* m, const char* name) {
+Mat mat_in(const tk_matrix* m, const char* name) {
     TK_REQUIRE(m != nullptr, TK_ERR_ARG, std::string(name) + ": null matrix");
     TK_REQUIRE(m->rows >= 0 && m->cols >= 0, TK_ERR_SHAPE, std::string(name) + ": negative size");
     TK_REQUIRE(m->ld >= std::max<int64_t>(1, m->rows), TK_ERR_SHAPE, std::string(name) + ": ld < rows");
@@ -265,6 +265,18 @@ static void orth_one(Ctx& c, const View2& Y, int64_t n, int64_t k, double* Q, in
     orth_batch(c, {Y}, {n}, {k}, {Q}, {slot});
 }
 
+// Same steps as tucker_orth's body, for the allocation-free entry point.
+void orth_matrix(Ctx& c, const Mat& y, const Mat& q) {
+    const int64_t k = std::min(y.rows, y.cols);
+    double* Qd = c.alloc<double>(y.rows * k);
+    if (y.cols >= y.rows) {
+        launch_fill_identity(c, Qd, y.rows);
+        launch_fill_int(c, c.dqr, 1, 2);
+    } else {
+        orth_one(c, view_rows(y.p, y.dt, y.ld), y.rows, k, Qd, 0);
+    }
+    launch_convert(c, Qd, TK_F64, y.rows, k, y.rows, (void*)q.p, q.dt, q.ld, 1.f);
+}
 
 // Leading r eigenvectors of the symmetric k x k FP64 matrix A, as the columns
 // of Vr (k x r, ld k), in descending eigenvalue order.

@@ -236,6 +236,12 @@ void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, fl
 // Vr (k x r, ld k) = the columns of V (k x k) for the r largest entries of D, in descending order.
 void launch_select_top(const Ctx& c, int64_t k, int64_t r, const double* D, const double* V, double* Vr);
 
+// Thin QR of the plain matrix y (rows x cols) into q (rows x min(rows, cols)):
+// CholeskyQR2 with the Householder fallback, identity when cols >= rows; the
+// method used goes to c.dqr[0].  All scratch comes from c.alloc.
+void orth_matrix(Ctx& c, const Mat& y, const Mat& q);
+Mat mat_in(const tk_matrix* m, const char* name);
+
 // Element-wise helpers.
 void launch_convert(const Ctx& c, const void* src, tk_dtype sdt, int64_t rows, int64_t cols, int64_t lds,
                     void* dst, tk_dtype ddt, int64_t ldd, float src_scale);

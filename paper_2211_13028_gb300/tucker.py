@@ -23,7 +23,7 @@ import torch
 __all__ = [
     "TuckerError", "load", "empty_f", "is_colmajor",
     "tucker_subranks_reuse", "tucker_subranks_matrix",
-    "tucker_sketch", "tucker_orth", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
+    "tucker_sketch", "tucker_orth", "tucker_orth_noalloc", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
     "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
     "library_path",
@@ -104,6 +104,7 @@ def load():
             "tucker_sketch": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
             "tucker_orth": ([vp, P(TkMatrix), P(TkMatrix), P(ctypes.c_int), P(TkOpts)], ctypes.c_int),
             "tucker_core": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
+            "tucker_orth_noalloc": ([vp, P(TkMatrix), P(TkMatrix), P(ctypes.c_int)], ctypes.c_int),
             "tucker_rhkron": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor), P(TkMatrix),
                                P(ctypes.c_double)], ctypes.c_int),
             "tucker_rsthkron": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor),
@@ -305,6 +306,21 @@ def tucker_orth(Y: torch.Tensor, qr_method: int = 0, out_dtype=None) -> Tuple[to
     h = _handle(Y.device)
     _check(load().tucker_orth(h, ctypes.byref(_matrix(Y)), ctypes.byref(_matrix(Q)), ctypes.byref(info),
                               ctypes.byref(o)), h)
+    return Q, info.value
+
+
+def tucker_orth_noalloc(Y: torch.Tensor, out_dtype=None) -> Tuple[torch.Tensor, int]:
+    """Thin QR like tucker_orth, computed without any device allocation by the
+    library (fixed internal scratch; rows <= 4096, min(rows, cols) <= 64).
+    For callers that cannot allocate at the call site (graph capture, external
+    allocators).  Calls must not overlap on the GPU.  Returns (Q, info)."""
+    rows, cols = Y.shape
+    Q = _colmajor_matrix(rows, min(rows, cols), out_dtype or Y.dtype, Y.device)
+    info = ctypes.c_int(-1)
+    st = load().tucker_orth_noalloc(ctypes.c_void_p(torch.cuda.current_stream(Y.device).cuda_stream),
+                                    ctypes.byref(_matrix(Y)), ctypes.byref(_matrix(Q)), ctypes.byref(info))
+    if st != 0:
+        raise TuckerError(st, "tucker_orth_noalloc failed")
     return Q, info.value
 
 
