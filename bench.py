@@ -169,9 +169,10 @@ class ClockSampler:
 # ------------------------------------------------------------------ single building block (profiling)
 
 def profile_case(args):
-    """Three repetitions of one building block on an n^3 FP32 field of the bench generator:
-    'sketch' (tucker_sketch, s = (6,7,7)), 'core' (tucker_core, k = (49,42,42)) or
-    'residual' (tucker_loss with r = 32: the fused tensor-core residual)."""
+    """Repetitions of one building block on an n^3 FP32 field of the bench generator:
+    'sketch' (tucker_sketch, s = (6,7,7)), 'core' (tucker_core, k = (49,42,42)),
+    'residual' (tucker_loss with r = 32: the fused tensor-core residual) or
+    'rhkron' (all of rHKron-re, r = 32, p = 8)."""
     import torch
 
     from paper_2211_13028_gb300 import synth
@@ -187,6 +188,11 @@ def profile_case(args):
     elif args.profile_case == "core":
         qs = [synth.fmat(__import__("numpy").linalg.qr(g.standard_normal((n, k)))[0], "f32", dev) for k in (49, 42, 42)]
         fn = lambda: T.tucker_core(X, qs)  # noqa: E731
+    elif args.profile_case == "rhkron":
+        # the whole of rHKron-re at r = 32, p = 8: the core sizes (49,42,42) do not depend on n
+        s, _ = T.tucker_subranks_reuse(RANKS, P_OVER)
+        om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(X.shape, s, SEED + 1, "f32")]
+        fn = lambda: T.tucker_rhkron(X, RANKS, P_OVER, om)  # noqa: E731
     else:
         G = synth.fortran(g.standard_normal((32, 32, 32)), "f32", dev)
         U = [synth.fmat(__import__("numpy").linalg.qr(g.standard_normal((n, 32)))[0], "f32", dev) for _ in range(3)]
@@ -219,7 +225,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--sample", type=int, default=256, help="oracle sample edge (CPU legs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=["sketch", "core", "residual"], default=None,
+    ap.add_argument("--serial", action="store_true", help="run both algorithms on one stream")
+    ap.add_argument("--profile-case", choices=["sketch", "core", "residual", "rhkron"], default=None,
                     help="run one building block on an n^3 FP32 field (for ncu captures) instead of the bench")
     ap.add_argument("--n", type=int, default=384, help="edge of the --profile-case tensor")
     args = ap.parse_args()
@@ -266,25 +273,40 @@ def main():
     torch.cuda.synchronize()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # The two algorithms are independent: rHKron-re and its gradient run on one stream, rSTHKron on a
+    # second, so the latency-bound small kernels of one overlap the other (--serial: one stream).
+    main_s = torch.cuda.current_stream(dev)
+    sa = torch.cuda.Stream(dev) if not args.serial else main_s
+    sb = torch.cuda.Stream(dev) if not args.serial else main_s
 
     def step(Xin, marks=None):
-        if marks:
-            marks[0].record()
-        G1, U1, e1 = T.tucker_rhkron(Xin, r, p, om)
-        if marks:
-            marks[1].record()
-        G2, U2, e2 = T.tucker_rsthkron(Xin, r, p, oms)
-        if marks:
-            marks[2].record()
-        dG, dU, dX = T.tucker_reconstruct_backward(Xin, G1, U1, 1.0)
-        if marks:
-            marks[3].record()
+        if sa is not main_s:
+            sa.wait_stream(main_s)
+            sb.wait_stream(main_s)
+        with torch.cuda.stream(sa):
+            if marks:
+                marks[0].record(sa)
+            G1, U1, e1 = T.tucker_rhkron(Xin, r, p, om, async_outputs=True)
+            if marks:
+                marks[1].record(sa)
+            dG, dU, dX = T.tucker_reconstruct_backward(Xin, G1, U1, 1.0)
+            if marks:
+                marks[2].record(sa)
+        with torch.cuda.stream(sb):
+            if marks:
+                marks[3].record(sb)
+            G2, U2, e2 = T.tucker_rsthkron(Xin, r, p, oms, async_outputs=True)
+            if marks:
+                marks[4].record(sb)
+        if sa is not main_s:
+            main_s.wait_stream(sa)
+            main_s.wait_stream(sb)
         return (G1, U1, e1, G2, U2, e2, dG, dU)
 
     for _ in range(args.warmup):
         out = step(X)
     torch.cuda.synchronize()
-    errs = (out[2], out[5])
+    errs = (out[2].value, out[5].value)
     dev_status, qr_info = T.tk_sync_status(dev)  # 0: every Jacobi solve converged
 
     def barrier():
@@ -292,7 +314,7 @@ def main():
             dist.barrier()
 
     # ---- device-timed region (inputs resident in HBM; X = 512 MiB > L2)
-    marks = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    marks = [[ev() for _ in range(5)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -312,7 +334,8 @@ def main():
     barrier()
     clk = clocks.stop()
     ms = t0.elapsed_time(t1) / args.steps
-    ph = [sum(marks[i][a].elapsed_time(marks[i][a + 1]) for i in range(args.steps)) / args.steps for a in range(3)]
+    ph = [sum(marks[i][a].elapsed_time(marks[i][b]) for i in range(args.steps)) / args.steps
+          for a, b in ((0, 1), (3, 4), (1, 2))]
     if dist is not None:
         tt = torch.tensor([ms], dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -330,7 +353,7 @@ def main():
         Xd.copy_(Xh, non_blocking=True)
         out = step(Xd.permute(2, 1, 0))
         host = [t.detach().to("cpu", non_blocking=True) for t in [out[0], *out[1], out[3], *out[4], out[6], *out[7]]]
-        torch.cuda.current_stream().synchronize()
+        main_s.synchronize()
         res_bytes = sum(t.numel() * t.element_size() for t in host) + 16
     e1.record()
     torch.cuda.synchronize()
@@ -358,8 +381,11 @@ def main():
         metric=METRIC, value=ms, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
         higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
         config=dict(workload=WORKLOAD, l2="X is 512 MiB, larger than the 129 MB L2: no flush between steps",
-                    parallelism=("replicas" if world > 1 else "single GPU")),
-        phases_ms=dict(rhkron=ph[0], rsthkron=ph[1], backward=ph[2]),
+                    parallelism=("replicas" if world > 1 else "single GPU"),
+                    streams=("one stream" if args.serial else
+                             "rHKron-re + gradient on one stream, rSTHKron on a second, concurrently")),
+        phases_ms=dict(rhkron=ph[0], rsthkron=ph[1], backward=ph[2],
+                       note=("sequential" if args.serial else "rsthkron overlaps rhkron + backward")),
         rel_err=dict(rhkron=errs[0], rsthkron=errs[1]),
         device_status=dev_status,
         multi_ttm=dict(tflops=ttm_tflops, ms_per_step=ttm_ms / args.steps,

@@ -85,13 +85,23 @@ typedef struct {
  *  refine            bulk TTMs on BF16/FP8 data: 0 = apply Q as a BF16 hi+lo
  *                    pair (refinement pass), -1 = BF16 Q only.
  *  max_jacobi_sweeps 0 = default (40); > 0 = limit; -1 = zero sweeps (makes the
- *                    solver report non-convergence, for testing).          */
+ *                    solver report non-convergence, for testing).
+ *  async_outputs     0 = a host scalar output (rel_err) is written before the
+ *                    call returns (the call synchronises its stream);
+ *                    1 = it is written by a stream-ordered host callback, so
+ *                    the call returns without synchronising and several
+ *                    decompositions can be in flight on different streams;
+ *                    read it only after synchronising the stream (or an
+ *                    event recorded after the call).  The output pointer
+ *                    must stay valid until then.  A handle keeps 64 pending
+ *                    outputs at most; the 65th call waits for the stream.   */
 typedef struct {
     const int* mode_order;
     int qr_method;
     int refine;
     int max_jacobi_sweeps;
-    int reserved[5];
+    int async_outputs;
+    int reserved[4];
 } tk_opts;
 
 typedef struct tk_handle tk_handle;

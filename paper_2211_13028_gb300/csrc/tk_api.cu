@@ -87,6 +87,7 @@ struct Opts {
     int qr_method = 0;
     int refine = 0;
     int max_sweeps = 40;
+    bool async_outputs = false;
 };
 
 static Opts opts_in(const tk_opts* o, int d) {
@@ -106,6 +107,8 @@ static Opts opts_in(const tk_opts* o, int d) {
     TK_REQUIRE(o->qr_method >= 0 && o->qr_method <= 2, TK_ERR_ARG, "opts.qr_method must be 0, 1 or 2");
     r.qr_method = o->qr_method;
     r.refine = o->refine;
+    TK_REQUIRE(o->async_outputs == 0 || o->async_outputs == 1, TK_ERR_ARG, "opts.async_outputs must be 0 or 1");
+    r.async_outputs = o->async_outputs != 0;
     if (o->max_jacobi_sweeps > 0) r.max_sweeps = o->max_jacobi_sweeps;
     else if (o->max_jacobi_sweeps == -1) r.max_sweeps = 0;
     else TK_REQUIRE(o->max_jacobi_sweeps == 0, TK_ERR_ARG, "opts.max_jacobi_sweeps must be >= -1");
@@ -482,8 +485,33 @@ static void set_opts(Ctx& c, const Opts& o) {
     c.max_sweeps = o.max_sweeps;
 }
 
-static void read_err(tk_handle* h, Ctx& c, const double* dev2, double* out_rel, bool squared_abs) {
+static void CUDART_CB deliver_slot(void* arg) {
+    auto* sl = static_cast<tk_handle::HostSlot*>(arg);
+    if (sl->mode == 1)
+        *sl->dst = sl->vals[0];
+    else
+        *sl->dst = sl->vals[1] > 0 ? std::sqrt(sl->vals[0] / sl->vals[1]) : 0.0;
+    __atomic_store_n(&sl->pending, 0, __ATOMIC_RELEASE);
+}
+
+// Host scalar from the device pair dev2 = {a, b}: sqrt(a / b) or a.  With
+// async, a D2H copy into the handle's pinned ring and a host callback that
+// writes *out after the stream reaches it; otherwise a synchronising copy.
+static void read_err(tk_handle* h, Ctx& c, const double* dev2, double* out_rel, bool squared_abs,
+                     bool async = false) {
     if (!c.exec) return;
+    if (async) {
+        tk_handle::HostSlot* sl = &h->slots[h->next_slot];
+        h->next_slot = (h->next_slot + 1) % tk_handle::kHostSlots;
+        // a slot is reused only after its callback has run
+        if (__atomic_load_n(&sl->pending, __ATOMIC_ACQUIRE)) TK_CUDA(cudaStreamSynchronize(c.stream));
+        sl->pending = 1;
+        sl->dst = out_rel;
+        sl->mode = squared_abs ? 1 : 0;
+        TK_CUDA(cudaMemcpyAsync(sl->vals, dev2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        TK_CUDA(cudaLaunchHostFunc(c.stream, deliver_slot, sl));
+        return;
+    }
     double host[2] = {0, 0};
     TK_CUDA(cudaMemcpyAsync(host, dev2, sizeof(host), cudaMemcpyDeviceToHost, c.stream));
     TK_CUDA(cudaStreamSynchronize(c.stream));
@@ -512,6 +540,14 @@ tk_status tk_create(tk_handle** h, void* stream) {
         return TK_ERR_CUDA;
     }
     x->dqr = (int*)((char*)x->dflags + 16);
+    if (cudaHostAlloc((void**)&x->slots, sizeof(tk_handle::HostSlot) * tk_handle::kHostSlots, cudaHostAllocDefault) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(x->dflags);
+        delete x;
+        return TK_ERR_CUDA;
+    }
+    std::memset((void*)x->slots, 0, sizeof(tk_handle::HostSlot) * tk_handle::kHostSlots);
     if (cudaMemset(x->dflags, 0, 64) != cudaSuccess) {
         cudaFree(x->dflags);
         delete x;
@@ -526,6 +562,7 @@ tk_status tk_destroy(tk_handle* h) {
     cudaStreamSynchronize(h->stream);
     if (h->ws) cudaFree(h->ws);
     if (h->dflags) cudaFree(h->dflags);
+    if (h->slots) cudaFreeHost(h->slots);
     for (auto& r : h->prof.recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -925,7 +962,7 @@ tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int 
         Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
         if (rel_err) errd = c.alloc<double>(2);
         finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, rel_err ? errd : nullptr);
-        if (rel_err) read_err(h, c, errd, rel_err, false);
+        if (rel_err) read_err(h, c, errd, rel_err, false, o.async_outputs);
     });
 }
 
@@ -990,7 +1027,7 @@ tk_status tucker_rsthkron(tk_handle* h, const tk_tensor* X, const int64_t* r, in
         Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
         if (rel_err) errd = c.alloc<double>(2);
         finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, rel_err ? errd : nullptr);
-        if (rel_err) read_err(h, c, errd, rel_err, false);
+        if (rel_err) read_err(h, c, errd, rel_err, false, o.async_outputs);
     });
 }
 

@@ -278,4 +278,14 @@ struct tk_handle {
     int64_t launches = 0;
     tk::Profiler prof;
     bool use_tc = true;  // TUCKER_TTM=simt selects the SIMT TTM kernels instead
+    // pinned ring for host scalar outputs delivered by stream-ordered callbacks
+    static constexpr int kHostSlots = 64;
+    struct HostSlot {
+        double vals[2];
+        double* dst;
+        int mode;              // 0: sqrt(a / b) (relative error), 1: a (squared norm)
+        volatile int pending;  // set when queued, cleared by the host callback
+    };
+    HostSlot* slots = nullptr;
+    int next_slot = 0;
 };

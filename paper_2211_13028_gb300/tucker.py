@@ -13,6 +13,7 @@ there is no fallback path.
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import os
 import threading
@@ -26,7 +27,7 @@ __all__ = [
     "tucker_sketch", "tucker_orth", "tucker_orth_noalloc", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
     "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
-    "library_path",
+    "library_path", "PendingScalar",
 ]
 
 TK_MAX_D = 8
@@ -61,13 +62,16 @@ class TkProfEntry(ctypes.Structure):
 
 class TkOpts(ctypes.Structure):
     _fields_ = [("mode_order", ctypes.POINTER(ctypes.c_int)), ("qr_method", ctypes.c_int), ("refine", ctypes.c_int),
-                ("max_jacobi_sweeps", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("max_jacobi_sweeps", ctypes.c_int), ("async_outputs", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
 _lock = threading.Lock()
-_handles: Dict[int, ctypes.c_void_p] = {}
+_handles: Dict[Tuple[int, int], ctypes.c_void_p] = {}  # one handle (and workspace) per (device, stream)
+# Host doubles that a handle's stream-ordered callbacks may still write: the library reuses one of
+# its 64 callback slots only after that slot's callback ran, so the 64 most recent stay referenced.
+_pending: Dict[int, "collections.deque"] = {}
 
 
 def library_path() -> str:
@@ -190,17 +194,19 @@ def _colmajor_matrix(rows: int, cols: int, dtype, device) -> torch.Tensor:
 
 
 def _handle(device: torch.device) -> ctypes.c_void_p:
+    """Handle bound to the current torch stream of ``device``.  Streams never
+    share a handle, so calls queued on different streams never share workspace."""
     lib = load()
     idx = device.index if device.index is not None else torch.cuda.current_device()
-    h = _handles.get(idx)
+    stream = torch.cuda.current_stream(idx).cuda_stream
+    h = _handles.get((idx, stream))
     if h is None:
         with torch.cuda.device(idx):
             h = ctypes.c_void_p()
-            st = lib.tk_create(ctypes.byref(h), ctypes.c_void_p(torch.cuda.current_stream(idx).cuda_stream))
+            st = lib.tk_create(ctypes.byref(h), ctypes.c_void_p(stream))
             if st != 0:
                 raise TuckerError(st, "tk_create failed")
-        _handles[idx] = h
-    lib.tk_set_stream(h, ctypes.c_void_p(torch.cuda.current_stream(idx).cuda_stream))
+        _handles[(idx, stream)] = h
     return h
 
 
@@ -210,8 +216,9 @@ def _check(st: int, h) -> None:
         raise TuckerError(st, (msg or b"").decode())
 
 
-def _opts(order=None, qr_method=0, refine=0, max_jacobi_sweeps=0):
+def _opts(order=None, qr_method=0, refine=0, max_jacobi_sweeps=0, async_outputs=False):
     o = TkOpts()
+    o.async_outputs = 1 if async_outputs else 0
     keep = None
     if order is not None:
         keep = (ctypes.c_int * len(order))(*[int(x) for x in order])
@@ -256,27 +263,38 @@ def tk_sync_status(device=None) -> Tuple[int, List[int]]:
 
 
 def tk_launch_count(device=None) -> int:
+    """Kernel launches queued through every handle of the device."""
+    return int(sum(load().tk_launch_count(h) for h in _device_handles(device)))
+
+
+def _device_handles(device):
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-    return int(load().tk_launch_count(_handle(dev)))
+    _handle(dev)
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    return [h for (i, _), h in _handles.items() if i == idx]
 
 
 def tk_profile(enable: bool, device=None) -> None:
-    """Start (clearing old records) or stop per-kernel-class event timing."""
-    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-    h = _handle(dev)
-    _check(load().tk_profile(h, 1 if enable else 0), h)
+    """Start (clearing old records) or stop per-kernel-class event timing on every handle of the device."""
+    for h in _device_handles(device):
+        _check(load().tk_profile(h, 1 if enable else 0), h)
 
 
 def tk_profile_read(device=None) -> Dict[str, dict]:
-    """Synchronise and return {class: {launches, ms, bytes, flops}} since tk_profile(True)."""
-    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-    h = _handle(dev)
-    buf = (TkProfEntry * 64)()
-    n = load().tk_profile_read(h, buf, 64)
-    if n < 0:
-        raise TuckerError(6, "tk_profile_read failed")
-    return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, bytes=buf[i].bytes,
-                                       flops=buf[i].flops) for i in range(min(n, 64))}
+    """Synchronise and return {class: {launches, ms, bytes, flops}} since tk_profile(True), summed over handles."""
+    out: Dict[str, dict] = {}
+    for h in _device_handles(device):
+        buf = (TkProfEntry * 64)()
+        n = load().tk_profile_read(h, buf, 64)
+        if n < 0:
+            raise TuckerError(6, "tk_profile_read failed")
+        for i in range(min(n, 64)):
+            e = out.setdefault(buf[i].name.decode(), dict(launches=0, ms=0.0, bytes=0.0, flops=0.0))
+            e["launches"] += buf[i].launches
+            e["ms"] += buf[i].ms
+            e["bytes"] += buf[i].bytes
+            e["flops"] += buf[i].flops
+    return out
 
 
 def tk_workspace_bytes(device=None) -> int:
@@ -332,38 +350,57 @@ def tucker_core(X: torch.Tensor, Q: Sequence[torch.Tensor], out_dtype=None, scal
     return G
 
 
-def _decomp(fn, X, r, p, Omega_list, order, qr_method, refine, max_jacobi_sweeps, rel_err, out_dtype, scale):
+class PendingScalar:
+    """Host scalar written by a stream-ordered callback (``async_outputs=True``);
+    ``value`` is valid once the stream has been synchronised."""
+
+    def __init__(self):
+        self._c = ctypes.c_double(float("nan"))
+
+    @property
+    def value(self) -> float:
+        return self._c.value
+
+
+def _decomp(fn, X, r, p, Omega_list, order, qr_method, refine, max_jacobi_sweeps, rel_err, out_dtype, scale,
+            async_outputs=False):
     d = X.dim()
     dt = out_dtype or _acc_dtype(X)
     G = empty_f(list(r), dt, X.device)
     U = [_colmajor_matrix(int(X.shape[j]), int(r[j]), dt, X.device) for j in range(d)]
     rr = (ctypes.c_int64 * d)(*[int(x) for x in r])
-    o, keep = _opts(order, qr_method, refine, max_jacobi_sweeps)
-    err = ctypes.c_double(float("nan"))
+    o, keep = _opts(order, qr_method, refine, max_jacobi_sweeps, async_outputs)
+    pend = PendingScalar()
     h = _handle(X.device)
     st = fn(h, ctypes.byref(_tensor(X, scale)), rr, int(p), _mats(Omega_list), ctypes.byref(o),
-            ctypes.byref(_tensor(G)), _mats(U), ctypes.byref(err) if rel_err else None)
+            ctypes.byref(_tensor(G)), _mats(U), ctypes.byref(pend._c) if rel_err else None)
     _check(st, h)
-    return G, U, (err.value if rel_err else None)
+    if not rel_err:
+        return G, U, None
+    if async_outputs:
+        _pending.setdefault(h.value, collections.deque(maxlen=64)).append(pend)
+        return G, U, pend
+    return G, U, pend.value
 
 
 def tucker_rhkron(X: torch.Tensor, r: Sequence[int], p: int, Omega: Sequence[torch.Tensor], *, order=None,
                   qr_method: int = 0, refine: int = 0, max_jacobi_sweeps: int = 0, rel_err: bool = True,
-                  out_dtype=None, scale: float = 1.0):
-    """Algorithm rHKron-re.  Omega[j] = Phi_j^T (n_j x s_j).  Returns (G, [U_j], rel_err or None)."""
+                  out_dtype=None, scale: float = 1.0, async_outputs: bool = False):
+    """Algorithm rHKron-re.  Omega[j] = Phi_j^T (n_j x s_j).  Returns (G, [U_j], rel_err or None);
+    with async_outputs the relative error is a PendingScalar and the call does not synchronise."""
     return _decomp(load().tucker_rhkron, X, r, p, list(Omega), order, qr_method, refine, max_jacobi_sweeps, rel_err,
-                   out_dtype, scale)
+                   out_dtype, scale, async_outputs)
 
 
 def tucker_rsthkron(X: torch.Tensor, r: Sequence[int], p: int, Omega: Dict[Tuple[int, int], torch.Tensor], *,
                     order=None, qr_method: int = 0, refine: int = 0, max_jacobi_sweeps: int = 0,
-                    rel_err: bool = True, out_dtype=None, scale: float = 1.0):
+                    rel_err: bool = True, out_dtype=None, scale: float = 1.0, async_outputs: bool = False):
     """Algorithm rSTHKron.  Omega[(j, k)] = Phi_{j,k}^T sized to mode k's current size."""
     d = X.dim()
     dummy = torch.zeros((1, 1), dtype=next(iter(Omega.values())).dtype, device=X.device)
     lst = [Omega.get((j, k), dummy) if j != k else dummy for j in range(d) for k in range(d)]
     return _decomp(load().tucker_rsthkron, X, r, p, lst, order, qr_method, refine, max_jacobi_sweeps, rel_err,
-                   out_dtype, scale)
+                   out_dtype, scale, async_outputs)
 
 
 def tucker_reconstruct(G: torch.Tensor, U: Sequence[torch.Tensor], out_dtype=None) -> torch.Tensor:

@@ -1,0 +1,73 @@
+"""Concurrent decompositions on two streams with stream-ordered host outputs.
+
+rHKron-re on one stream and rSTHKron on another, both reading the same X, must
+give exactly what the same calls give one after the other on one stream (each
+stream has its own handle and workspace, and every kernel is deterministic for
+a given shape).  More pending outputs than the handle's callback slots must
+still all be delivered.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2211_13028_gb300 import synth
+from paper_2211_13028_gb300 import tucker as T
+from tests.gpu_helpers import make_X, mats, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return require_gpu()
+
+
+def _setup(dev):
+    dims, r, p = (96, 80, 72), (12, 10, 9), 5
+    core = synth.decaying_core((20, 20, 20), 0.7, seed=41)
+    x = synth.tucker_tensor(dims, (20, 20, 20), seed=42, noise_rel=1e-3, core=core)
+    X, xv, _ = make_X(x, "f32", dev)
+    s, _ = O.subranks_reuse(r, p)
+    om = mats(synth.sketch_factors_reuse(dims, s, seed=43, dtype="f32"), "f32", dev)
+    S, w = O.subranks_matrix(r, p)
+    k = [min(n, ww) for n, ww in zip(dims, w)]
+    oms = {key: synth.fmat(v, "f32", dev)
+           for key, v in synth.sketch_factors_matrix(dims, S, k, [0, 1, 2], 44, "f32").items()}
+    return X, r, p, om, oms
+
+
+def test_two_streams_match_one_stream(dev):
+    X, r, p, om, oms = _setup(dev)
+    G1, U1, e1 = T.tucker_rhkron(X, r, p, om)
+    G2, U2, e2 = T.tucker_rsthkron(X, r, p, oms)
+    torch.cuda.synchronize()
+    sa, sb = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    sa.wait_stream(torch.cuda.current_stream(dev))
+    sb.wait_stream(torch.cuda.current_stream(dev))
+    res = []
+    for _ in range(3):
+        with torch.cuda.stream(sa):
+            a = T.tucker_rhkron(X, r, p, om, async_outputs=True)
+        with torch.cuda.stream(sb):
+            b = T.tucker_rsthkron(X, r, p, oms, async_outputs=True)
+        res.append((a, b))
+    torch.cuda.synchronize()
+    for (Ga, Ua, ea), (Gb, Ub, eb) in res:
+        assert torch.equal(Ga, G1) and torch.equal(Gb, G2)
+        assert all(torch.equal(u, v) for u, v in zip(Ua, U1))
+        assert all(torch.equal(u, v) for u, v in zip(Ub, U2))
+        assert ea.value == e1 and eb.value == e2
+    assert T.tk_sync_status(dev)[0] == 0
+
+
+def test_more_pending_outputs_than_slots(dev):
+    X, r, p, om, _ = _setup(dev)
+    _, _, e_ref = T.tucker_rhkron(X, r, p, om)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        outs = [T.tucker_rhkron(X, r, p, om, async_outputs=True)[2] for _ in range(70)]
+    s.synchronize()
+    vals = np.array([o.value for o in outs])
+    assert np.all(vals == e_ref)
