@@ -225,69 +225,6 @@ void launch_ttm(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, i
 
 // ------------------------------------------------------------------ FP64 GEMM (NT) with split-K
 
-__global__ void __launch_bounds__(256) gemm_nt_partial_kernel(int64_t m, int64_t n, int64_t K, int64_t kchunk,
-                                                              View2 A, View2 B, double* P, const int* skip) {
-    if (skip && *skip) return;
-    __shared__ double As[16][33];
-    __shared__ double Bs[16][33];
-    const int tid = threadIdx.x;
-    const int tx = tid % 16, ty = tid / 16;
-    const int64_t a0 = (int64_t)blockIdx.x * 32, b0 = (int64_t)blockIdx.y * 32;
-    const int64_t kb = (int64_t)blockIdx.z * kchunk;
-    const int64_t ke = min(K, kb + kchunk);
-    double acc[2][2] = {{0, 0}, {0, 0}};
-    // each thread loads rows rr0, rr0 + 16 at column offset kk (fixed): precompute row offsets
-    const int kk = tid % 16, rr0 = tid / 16;
-    int64_t oa[2], ob[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        int64_t ra = a0 + rr0 + 16 * q, rb = b0 + rr0 + 16 * q;
-        oa[q] = ra < m ? ((A.A1 == INT64_MAX) ? ra * A.sa1 : (ra % A.A1) * A.sa1 + (ra / A.A1) * A.sa2) : -1;
-        ob[q] = rb < n ? ((B.A1 == INT64_MAX) ? rb * B.sa1 : (rb % B.A1) * B.sa1 + (rb / B.A1) * B.sa2) : -1;
-    }
-    for (int64_t k0 = kb; k0 < ke; k0 += 16) {
-        int64_t k = k0 + kk;
-        int64_t ta = -1, tb = -1;
-        if (k < ke) {
-            ta = (A.T1 == INT64_MAX) ? k * A.st1 : (k % A.T1) * A.st1 + (k / A.T1) * A.st2;
-            tb = (B.T1 == INT64_MAX) ? k * B.st1 : (k % B.T1) * B.st1 + (k / B.T1) * B.st2;
-        }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            double va = 0.0, vb = 0.0;
-            if (ta >= 0 && oa[q] >= 0) {
-                int64_t o = oa[q] + ta;
-                va = A.dt == TK_F64 ? static_cast<const double*>(A.p)[o] : (double)static_cast<const float*>(A.p)[o];
-            }
-            if (tb >= 0 && ob[q] >= 0) {
-                int64_t o = ob[q] + tb;
-                vb = B.dt == TK_F64 ? static_cast<const double*>(B.p)[o] : (double)static_cast<const float*>(B.p)[o];
-            }
-            As[kk][rr0 + 16 * q] = va;
-            Bs[kk][rr0 + 16 * q] = vb;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            double av[2] = {As[kk][tx], As[kk][tx + 16]};
-            double bv[2] = {Bs[kk][ty], Bs[kk][ty + 16]};
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 2; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-    double* Pz = P + (int64_t)blockIdx.z * m * n;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            int64_t a = a0 + tx + 16 * i, b = b0 + ty + 16 * j;
-            if (a < m && b < n) Pz[a + m * b] = acc[i][j];
-        }
-}
-
 __global__ void gemm_reduce_kernel(int64_t m, int64_t n, int nsplit, const double* P, double alpha, double beta,
                                    double* C, int64_t ldc, const int* skip) {
     if (skip && *skip) return;
@@ -300,96 +237,121 @@ __global__ void gemm_reduce_kernel(int64_t m, int64_t n, int nsplit, const doubl
     *dst = beta == 0.0 ? alpha * s : alpha * s + beta * *dst;
 }
 
-// Small outputs: one warp per output element, the K terms split over the lanes
-// (a short dependent chain per lane) and combined by shuffles.
-struct V2Lane {  // walk t = lane, lane + 32, ... of row a of a View2
-    const View2& v;
-    int64_t base, lo, hi;
-    __device__ V2Lane(const View2& vv, int64_t a, int64_t t0) : v(vv) {
-        base = (v.A1 == INT64_MAX) ? a * v.sa1 : (a % v.A1) * v.sa1 + (a / v.A1) * v.sa2;
-        if (v.T1 == INT64_MAX) {
-            lo = t0;
-            hi = 0;
-        } else {
-            lo = t0 % v.T1;
-            hi = t0 / v.T1;
-        }
-    }
-    __device__ __forceinline__ double load() const {
-        int64_t o = base + lo * v.st1 + hi * v.st2;
-        return v.dt == TK_F64 ? static_cast<const double*>(v.p)[o] : (double)static_cast<const float*>(v.p)[o];
-    }
-    __device__ __forceinline__ void next32() {
-        lo += 32;
-        if (v.T1 != INT64_MAX && lo >= v.T1) {
-            hi += lo / v.T1;
-            lo %= v.T1;
-        }
+// 16 x 16 output tile per 256-thread CTA (one output per thread), K staged
+// through shared memory 32 at a time for both operands (converted to FP64 on
+// load).  Each operand is loaded with lanes running along whichever of its two
+// indices is contiguous in memory.  Split-K: CTA z covers [z kchunk, (z+1)
+// kchunk) and, with P != NULL, writes its partial tile to P[z] for a
+// deterministic reduction; otherwise it applies alpha/beta to C directly.
+struct TileLoader {
+    // element e in [0, 512) of a 16 x 32 (row x k) tile -> (row, k)
+    bool kfast;
+    __device__ TileLoader(const View2& v) { kfast = (v.T1 == INT64_MAX && v.st1 == 1); }
+    __device__ __forceinline__ void rk(int e, int& r, int& kk) const {
+        if (kfast) { r = e >> 5; kk = e & 31; }
+        else { r = e & 15; kk = e >> 4; }
     }
 };
 
-__global__ void __launch_bounds__(256) gemm_nt_warp_kernel(int64_t m, int64_t n, int64_t K, View2 A, View2 B,
-                                                           double alpha, double beta, double* C, int64_t ldc,
-                                                           const int* skip) {
-    if (skip && *skip) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t o = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (o >= m * n) return;
-    const int64_t a = o % m, b = o / m;
-    double s = 0.0;
-    if (lane < K) {
-        V2Lane wa(A, a, lane), wb(B, b, lane);
-        for (int64_t t = lane; t < K; t += 32) {
-            s = fma(wa.load(), wb.load(), s);
-            wa.next32();
-            wb.next32();
-        }
+__device__ __forceinline__ int64_t v2row(const View2& v, int64_t a) {
+    if (v.A1 == INT64_MAX) return a * v.sa1;
+    if (a < 0x7fffffff && v.A1 < 0x7fffffff) {
+        const uint32_t q = (uint32_t)a / (uint32_t)v.A1;
+        return (int64_t)((uint32_t)a - q * (uint32_t)v.A1) * v.sa1 + (int64_t)q * v.sa2;
     }
+    return (a % v.A1) * v.sa1 + (a / v.A1) * v.sa2;
+}
+__device__ __forceinline__ int64_t v2col(const View2& v, int64_t t) {
+    if (v.T1 == INT64_MAX) return t * v.st1;
+    if (t < 0x7fffffff && v.T1 < 0x7fffffff) {
+        const uint32_t q = (uint32_t)t / (uint32_t)v.T1;
+        return (int64_t)((uint32_t)t - q * (uint32_t)v.T1) * v.st1 + (int64_t)q * v.st2;
+    }
+    return (t % v.T1) * v.st1 + (t / v.T1) * v.st2;
+}
+__device__ __forceinline__ double v2get(const View2& v, int64_t o) {
+    return v.dt == TK_F64 ? static_cast<const double*>(v.p)[o] : (double)static_cast<const float*>(v.p)[o];
+}
+
+__global__ void __launch_bounds__(256) gemm_tile16_kernel(int64_t m, int64_t n, int64_t K, int64_t kchunk, View2 A,
+                                                          View2 B, double alpha, double beta, double* C, int64_t ldc,
+                                                          double* P, const int* skip) {
+    if (skip && *skip) return;
+    __shared__ double As[32][17];
+    __shared__ double Bs[32][17];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t a0 = (int64_t)blockIdx.x * 16, b0 = (int64_t)blockIdx.y * 16;
+    const int64_t kb = (int64_t)blockIdx.z * kchunk;
+    const int64_t ke = min(K, kb + kchunk);
+    const TileLoader la(A), lb(B);
+    int ra[2], ka[2], rb[2], kb2[2];
+    int64_t oa[2], ob[2];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
+    for (int q = 0; q < 2; ++q) {
+        la.rk(tid + 256 * q, ra[q], ka[q]);
+        lb.rk(tid + 256 * q, rb[q], kb2[q]);
+        oa[q] = a0 + ra[q] < m ? v2row(A, a0 + ra[q]) : -1;
+        ob[q] = b0 + rb[q] < n ? v2row(B, b0 + rb[q]) : -1;
+    }
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int64_t k0 = kb; k0 < ke; k0 += 32) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int64_t k1 = k0 + ka[q], k2 = k0 + kb2[q];
+            As[ka[q]][ra[q]] = (oa[q] >= 0 && k1 < ke) ? v2get(A, oa[q] + v2col(A, k1)) : 0.0;
+            Bs[kb2[q]][rb[q]] = (ob[q] >= 0 && k2 < ke) ? v2get(B, ob[q] + v2col(B, k2)) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 2) {
+            acc0 = fma(As[kk][tx], Bs[kk][ty], acc0);
+            acc1 = fma(As[kk + 1][tx], Bs[kk + 1][ty], acc1);
+        }
+        __syncthreads();
+    }
+    const int64_t a = a0 + tx, b = b0 + ty;
+    if (a >= m || b >= n) return;
+    const double sum = acc0 + acc1;
+    if (P) {
+        P[(int64_t)blockIdx.z * m * n + a + m * b] = sum;
+    } else {
         double* dst = C + a + ldc * b;
-        *dst = beta == 0.0 ? alpha * s : alpha * s + beta * *dst;
+        *dst = beta == 0.0 ? alpha * sum : alpha * sum + beta * *dst;
     }
 }
 
 void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const View2& B, double alpha, double beta,
                  double* C, int64_t ldc, const int* skip) {
-    if (m * n <= (1 << 17) && K > 0) {
-        if (!c.exec || m == 0 || n == 0) return;
-        ProfScope ps(c, "gemm_f64", 8.0 * (double)(m + n) * K + 8.0 * m * n, 2.0 * m * n * K);
-        gemm_nt_warp_kernel<<<(unsigned)((m * n + 7) / 8), 256, 0, c.stream>>>(m, n, K, A, B, alpha, beta, C, ldc,
-                                                                                skip);
-        c.counted();
-        c.check_launch();
-        return;
+    // 16 x 16 tiles; split K only when the tiles alone leave most SMs idle and
+    // each split still has at least 64 terms.
+    const int64_t tiles = ((m + 15) / 16) * ((n + 15) / 16);
+    int64_t nsplit = 1;
+    if (K >= 128 && tiles < 2 * 152) {
+        nsplit = std::min<int64_t>((2 * 152 + tiles - 1) / tiles, K / 64);
+        nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, 512));
     }
-    int64_t tiles = ((m + 31) / 32) * ((n + 31) / 32);
-    int64_t nsplit = (304 + tiles - 1) / tiles;
-    int64_t maxsplit = (K + 63) / 64;
-    if (nsplit > maxsplit) nsplit = maxsplit;
-    if (nsplit < 1) nsplit = 1;
-    if (nsplit > 1024) nsplit = 1024;
-    int64_t kchunk = (K + nsplit - 1) / nsplit;
-    kchunk = (kchunk + 15) / 16 * 16;
+    int64_t kchunk = K > 0 ? (K + nsplit - 1) / nsplit : 1;
+    kchunk = (kchunk + 31) / 32 * 32;
     nsplit = K > 0 ? (K + kchunk - 1) / kchunk : 1;
-    double* P = c.alloc<double>(nsplit * m * n);
+    double* P = nsplit > 1 ? c.alloc<double>(nsplit * m * n) : nullptr;
     if (!c.exec || m == 0 || n == 0) return;
-    if (K == 0) {
-        cudaMemsetAsync(P, 0, sizeof(double) * m * n, c.stream);
-    } else {
-        dim3 grid((unsigned)((m + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)nsplit);
-        ProfScope ps(c, "gemm_f64", 8.0 * (double)(m + n) * K + 8.0 * m * n * nsplit, 2.0 * m * n * K);
-        gemm_nt_partial_kernel<<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, P, skip);
+    dim3 grid((unsigned)((m + 15) / 16), (unsigned)((n + 15) / 16), (unsigned)nsplit);
+    {
+        ProfScope ps(c, "gemm_f64", 8.0 * (double)(m * ((n + 15) / 16) + n * ((m + 15) / 16)) * K + 8.0 * m * n * nsplit,
+                     2.0 * m * n * K);
+        gemm_tile16_kernel<<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, skip);
         c.counted();
         c.check_launch();
     }
-    int64_t tot = m * n;
-    ProfScope ps(c, "gemm_f64", 8.0 * m * n * (nsplit + 1), (double)m * n * nsplit);
-    gemm_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(m, n, (int)nsplit, P, alpha, beta, C,
-                                                                              ldc, skip);
-    c.counted();
-    c.check_launch();
+    if (nsplit > 1) {
+        const int64_t tot = m * n;
+        ProfScope ps(c, "gemm_f64", 8.0 * m * n * (nsplit + 1), (double)m * n * nsplit);
+        gemm_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(m, n, (int)nsplit, P, alpha, beta, C,
+                                                                                  ldc, skip);
+        c.counted();
+        c.check_launch();
+    }
 }
 
 // ------------------------------------------------------------------ block reductions
@@ -418,72 +380,101 @@ __device__ double block_sum(double v, double* scratch /* >= 33 */) {
 
 // ------------------------------------------------------------------ Cholesky + inverse
 
-__global__ void __launch_bounds__(512) chol_inv_kernel(KDims kd, int kmax, const double* W, double* Rinv, int* bad,
-                                                       double tol) {
-    extern __shared__ double A[];  // k x k, A(i, l) = A[i + k*l]
+// Cholesky W = R^T R with R^{-1} formed in the same column loop.  With
+// L = R^T, step j computes row j of R (r_jj = sqrt(pivot), r_jl = a_jl / r_jj),
+// applies the rank-1 trailing update, and advances a Gauss-Jordan forward
+// elimination M <- L^{-1} started from M = I: row j of M is scaled by 1/r_jj and
+// M(i, 0..j) -= r_ji M(j, 0..j) for i > j.  Both updates are enumerated as one
+// packed index space, so every FP64 lane does useful work (the FP64 pipe is the
+// bottleneck of this kernel).  The pivot's 1/sqrt is an FP32 seed refined by
+// two FP64 Newton steps (error below one FP64 ulp-scale), and it is taken one
+// column ahead by the thread that updates the next diagonal entry, which leaves
+// two barriers per column.  R^{-1} = M^T.
+__device__ __forceinline__ double chol_rsqrt(double a) {
+    double y = (double)rsqrtf((float)a);
+    const double h = 0.5 * a;
+    y = y * fma(-h * y, y, 1.5);
+    y = y * fma(-h * y, y, 1.5);
+    return y;
+}
+
+constexpr int CHOL_THREADS = 256;
+
+__global__ void __launch_bounds__(CHOL_THREADS) chol_inv_kernel(KDims kd, int kmax, const double* W, double* Rinv,
+                                                                int* bad, double tol) {
+    extern __shared__ double sm[];  // A: k x k (upper part becomes R), M: k x k lower (L^{-1})
     __shared__ double dg[256];
+    __shared__ double s_y;
     __shared__ int s_bad;
     const int b = blockIdx.x;
     if (bad[b]) return;
     const int k = kd.k[b];
+    double* A = sm;
+    double* M = sm + (size_t)k * k;
     const double* Wb = W + (int64_t)b * kmax * kmax;
     double* Rb = Rinv + (int64_t)b * kmax * kmax;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < k * k; e += nt) {
-        int i = e % k, l = e / k;
+        const int i = e % k, l = e / k;
         A[e] = Wb[i + (int64_t)kmax * l];
+        M[e] = (i == l) ? 1.0 : 0.0;
     }
     for (int i = tid; i < k; i += nt) dg[i] = Wb[i + (int64_t)kmax * i];
-    if (tid == 0) s_bad = 0;
     __syncthreads();
-    __shared__ double s_rinv;
+    if (tid == 0) {
+        const double piv = A[0];
+        s_bad = !(piv > tol * dg[0]) || !(piv > 0.0);
+        s_y = s_bad ? 0.0 : chol_rsqrt(piv);
+    }
+    __syncthreads();
     for (int j = 0; j < k; ++j) {
-        // one thread takes the FP64 square root and reciprocal (FP64 throughput is scarce)
-        if (tid == 0) {
-            const double piv = A[j + k * j];
-            if (!(piv > tol * dg[j]) || !(piv > 0.0)) {
-                s_bad = 1;
+        if (s_bad) break;  // uniform: written before the last barrier
+        const double y = s_y;
+        // row j of R and row j of M, one packed loop over the k columns
+        for (int l = tid; l < k; l += nt) {
+            if (l < j)
+                M[j + k * l] *= y;
+            else if (l == j) {
+                M[j + k * j] *= y;
+                A[j + k * j] *= y;  // pivot * (1/sqrt(pivot)) = r_jj
+            } else
+                A[j + k * l] *= y;
+        }
+        __syncthreads();
+        // trailing update (j < i <= l) followed by the inverse update (i > j, l <= j)
+        const int w = k - j - 1;
+        const int ntri = w * (w + 1) / 2;
+        const int ntot = ntri + w * (j + 1);
+        for (int e = tid; e < ntot; e += nt) {
+            if (e < ntri) {
+                // column-packed triangle: l' = floor((sqrt(8e+1)-1)/2), i' = e - l'(l'+1)/2
+                int lp = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                while (lp * (lp + 1) / 2 > e) --lp;
+                while ((lp + 1) * (lp + 2) / 2 <= e) ++lp;
+                const int ip = e - lp * (lp + 1) / 2;
+                const int i = j + 1 + ip, l = j + 1 + lp;
+                const double v = A[i + k * l] - A[j + k * i] * A[j + k * l];
+                A[i + k * l] = v;
+                if (e == 0) {  // the next pivot: this thread updated A(j+1, j+1)
+                    const bool fail = !(v > tol * dg[j + 1]) || !(v > 0.0);
+                    s_bad = fail;
+                    s_y = fail ? 0.0 : chol_rsqrt(v);
+                }
             } else {
-                const double rjj = sqrt(piv);
-                A[j + k * j] = rjj;
-                s_rinv = 1.0 / rjj;
+                const int e2 = e - ntri;
+                const int i = j + 1 + e2 % w, l = e2 / w;
+                M[i + k * l] -= A[j + k * i] * M[j + k * l];
             }
         }
         __syncthreads();
-        if (s_bad) break;  // uniform
-        const double rinv = s_rinv;
-        for (int l = j + 1 + tid; l < k; l += nt) A[j + k * l] *= rinv;
-        __syncthreads();
-        const int w = k - j - 1;
-        for (int e = tid; e < w * w; e += nt) {
-            const int i = j + 1 + e % w, l = j + 1 + e / w;
-            if (i <= l) A[i + k * l] -= A[j + k * i] * A[j + k * l];
-        }
-        __syncthreads();
     }
-    __syncthreads();
     if (s_bad) {
         if (tid == 0) bad[b] = 1;
         return;
     }
-    // R^{-1} by back substitution, one warp per column: x_col = 1 / r_cc and
-    // x_i = -(sum_{l=i+1..col} r_il x_l) / r_ii, the sum split over the lanes.
-    for (int i = tid; i < k; i += nt) dg[i] = 1.0 / A[i + k * i];
-    __syncthreads();
-    const int lane = tid & 31, nw = nt >> 5;
-    for (int col = tid >> 5; col < k; col += nw) {
-        double* X = Rb + (int64_t)kmax * col;
-        for (int i = col + 1 + lane; i < k; i += 32) X[i] = 0.0;
-        if (lane == 0) X[col] = dg[col];
-        __syncwarp();
-        for (int i = col - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int l = i + 1 + lane; l <= col; l += 32) s = fma(A[i + k * l], X[l], s);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == 0) X[i] = -s * dg[i];
-            __syncwarp();
-        }
+    for (int e = tid; e < k * k; e += nt) {
+        const int i = e % k, l = e / k;
+        Rb[i + (int64_t)kmax * l] = (i <= l) ? M[l + k * i] : 0.0;
     }
 }
 
@@ -491,11 +482,11 @@ void launch_chol_inv(const Ctx& c, int batch, const KDims& kd, int kmax, const d
                      double tol) {
     if (!c.exec) return;
     TK_REQUIRE(kmax <= 112, TK_ERR_SHAPE, "chol_inv: at most 112 columns");
-    size_t smem = sizeof(double) * kmax * kmax;
+    size_t smem = 2 * sizeof(double) * kmax * kmax;
     if (smem > 48 * 1024)
         TK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(c, "chol_inv", 16.0 * batch * kmax * kmax, (2.0 / 3.0) * batch * kmax * kmax * kmax);
-    chol_inv_kernel<<<batch, 512, smem, c.stream>>>(kd, kmax, W, Rinv, bad, tol);
+    chol_inv_kernel<<<batch, CHOL_THREADS, smem, c.stream>>>(kd, kmax, W, Rinv, bad, tol);
     c.counted();
     c.check_launch();
 }
@@ -745,84 +736,85 @@ void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int
 }
 
 // ------------------------------------------------------------------ mixed-precision Jacobi
-// Two-sided cyclic Jacobi on a symmetric matrix held as an FP64 diagonal D and
-// an FP32 off-diagonal F (zero diagonal), accumulating the rotations in an
-// FP32 matrix J.  Rotation angles use the FP64 diagonal difference; the pair's
-// own 2 x 2 block is updated in closed form (a_pp -= t a_pq, a_qq += t a_pq,
-// a_pq = 0).  When F is small in absolute terms (a matrix already close to
-// diagonal), FP32 storage of F carries FP64-level absolute accuracy.
-// Pairs follow a round-robin tournament; each thread rotates whole 2 x 2
-// blocks (rows of one pair x columns of another) in one read-modify-write.
-// One CTA; F, J and D live in shared memory (k <= 112).
+// Two-sided cyclic Jacobi on a symmetric matrix held as a diagonal D and an
+// FP32 off-diagonal F (zero diagonal), accumulating the rotations in an FP32
+// matrix J.  Rotation angles use the diagonal difference; the pair's own 2 x 2
+// block is updated in closed form (a_pp -= t a_pq, a_qq += t a_pq, a_pq = 0).
+// When F is small in absolute terms (a matrix already close to diagonal), FP32
+// storage of F carries FP64-level absolute accuracy, provided D accumulates the
+// tiny updates t a_pq without loss: the resolving stage keeps D as an unevaluated
+// sum of two floats (hi + lo, about 48 significant bits) updated with an exact
+// two-product and two-sum (Dekker; Knuth), so no FP64 instruction (1/64 of the
+// FP32 rate on this GPU) sits on the per-round critical path.
+// Pairs follow a round-robin tournament over k rounded up to even (an odd k
+// gets a zero row and column that never rotates).  A round has two phases: one
+// thread per pair computes its rotation; then each (pair t, pair u) block of
+// F' = R^T F R and of J' = J R is produced by one thread from the four entries
+// it replaces (F is double-buffered, J is updated in place), with no
+// mirrored writes and no per-entry branching.  One CTA of up to 1024 threads;
+// F, F', J and D live in shared memory.
 
-constexpr int JM_THREADS = 512;
-constexpr int JM_FB = 4;  // F blocks per thread: half(half+1)/2 <= 1596 for k <= 112
-constexpr int JM_JB = 7;  // J blocks per thread: ceil(k/2) * half <= 3136
+constexpr int JM_MAX_THREADS = 1024;
 
-// TD: type of the diagonal.  float for the first stage (whose result only
-// seeds the second), double for the stage that resolves the eigenvalues.
-template <typename TD>
-__global__ void __launch_bounds__(JM_THREADS) jacobi_mixed_kernel(int k, const double* __restrict__ A, double* Dout,
-                                                                  float* Jout, double tol, int max_sweeps,
-                                                                  unsigned* flags) {
-    extern __shared__ unsigned char smraw[];
-    const int ldf = k + 1;  // odd row stride: column walks are bank-conflict free
-    TD* D = reinterpret_cast<TD*>(smraw);
-    float* F = reinterpret_cast<float*>(reinterpret_cast<double*>(smraw) + k);
-    float* J = F + (size_t)k * ldf;
-    __shared__ float cs[64], sn[64];
-    __shared__ int P[64], Qp[64];
+// (hi, lo) += (bh, bl) for normalised double-float pairs.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+    const float s = __fadd_rn(hi, bh);
+    const float v = __fadd_rn(s, -hi);
+    const float e0 = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -v)), __fadd_rn(bh, -v));  // hi + bh = s + e0 exactly
+    const float e = __fadd_rn(e0, __fadd_rn(lo, bl));
+    const float h2 = __fadd_rn(s, e);
+    lo = __fadd_rn(e, -__fadd_rn(h2, -s));
+    hi = h2;
+}
+
+// DF: the diagonal is a double-float pair (the stage that resolves the
+// eigenvalues); otherwise a plain float (the first stage, which only seeds the
+// second).
+template <bool DF>
+__global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_mixed_kernel(int k, const double* __restrict__ A,
+                                                                      double* Dout, float* Jout, double tol,
+                                                                      int max_sweeps, unsigned* flags) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int kp = k + (k & 1), half = kp / 2;
+    const int ld = kp + 1;  // odd strides: walks along either index are bank-conflict free
+    float* Dh = reinterpret_cast<float*>(smraw);
+    float* Dl = Dh + kp;
+    float* F = Dl + kp;                 // F(i, j) = F[i * ld + j], kp x kp with a zero diagonal
+    float* Fn = F + (size_t)kp * ld;    // the next round's F
+    float* J = Fn + (size_t)kp * ld;    // column-major: J(i, j) = J[j * ld + i]
+    __shared__ float4 meta[64];         // per pair: (p, q as int bits, c, s)
     __shared__ double red[33];
     const int tid = threadIdx.x, nt = blockDim.x;
     double part = 0.0;
-    for (int e = tid; e < k * k; e += nt) {
-        int i = e % k, j = e / k;
-        double v = A[i + (int64_t)k * j];
+    for (int e = tid; e < kp * kp; e += nt) {
+        const int i = e % kp, j = e / kp;
+        const double v = (i < k && j < k) ? A[i + (int64_t)k * j] : 0.0;
         part += v * v;
         if (i == j) {
-            D[i] = (TD)v;
-            F[i * ldf + j] = 0.f;
+            const float h = (float)v;
+            Dh[i] = h;
+            Dl[i] = DF ? (float)(v - (double)h) : 0.f;
+            F[i * ld + j] = 0.f;
         } else {
-            F[i * ldf + j] = (float)v;
+            F[i * ld + j] = (float)v;
         }
-        J[i * ldf + j] = (i == j) ? 1.f : 0.f;
+        J[j * ld + i] = (i == j) ? 1.f : 0.f;
     }
     const double thr = tol * sqrt(block_sum(part, red));
     const float fthr = (float)thr;
-    const int kp = k + (k & 1), half = kp / 2, nrp = (k + 1) / 2;
-    // per-thread work lists, fixed for the whole solve
-    int fb[JM_FB], jb[JM_JB];
-    const int nfb = half * (half + 1) / 2;
-#pragma unroll
-    for (int i = 0; i < JM_FB; ++i) {
-        int e = tid + nt * i;
-        fb[i] = -1;
-        if (e < nfb) {
-            int u = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
-            while (u * (u + 1) / 2 > e) --u;
-            while ((u + 1) * (u + 2) / 2 <= e) ++u;
-            int t = e - u * (u + 1) / 2;
-            fb[i] = t | (u << 8);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < JM_JB; ++i) {
-        int e = tid + nt * i;
-        jb[i] = e < nrp * half ? ((e % nrp) | ((e / nrp) << 8)) : -1;
-    }
+    const int nblk = half * half;
     bool converged = false;
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
         int off = 0;
-        for (int e = tid; e < k * k; e += nt) {
-            int i = e % k, j = e / k;
-            if (i < j && fabsf(F[i * ldf + j]) > fthr) off = 1;
-        }
+        for (int i = tid >> 5; i < k; i += nt >> 5)
+            for (int j = i + 1 + (tid & 31); j < k; j += 32) off |= fabsf(F[i * ld + j]) > fthr;
         if (!__syncthreads_or(off)) {
             converged = true;
             break;
         }
         if (sweep == max_sweeps) break;
         for (int step = 0; step < kp - 1; ++step) {
+            int rotated = 0;
             if (tid < half) {
                 const int t = tid;
                 int p, q;
@@ -837,90 +829,76 @@ __global__ void __launch_bounds__(JM_THREADS) jacobi_mixed_kernel(int k, const d
                 }
                 if (p > q) { int tmp = p; p = q; q = tmp; }
                 float c = 1.f, sv = 0.f;
-                if (q < k) {
-                    float fpq = F[p * ldf + q];
-                    if (fabsf(fpq) > fthr) {
-                        // rotation angle from the diagonal difference; fast FP32 reciprocals suffice
-                        // (the off-diagonal is zeroed explicitly and convergence is measured)
-                        float tau = __fdividef((float)(D[q] - D[p]), 2.f * fpq);
-                        float tt = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
-                        c = rsqrtf(fmaf(tt, tt, 1.f));
-                        sv = tt * c;
-                        const TD dt = (TD)tt * (TD)fpq;
-                        D[p] -= dt;
-                        D[q] += dt;
-                    }
-                } else {
-                    q = -1;
-                }
-                P[t] = p; Qp[t] = q; cs[t] = c; sn[t] = sv;
-            }
-            __syncthreads();
-            // F <- R_t^T F R_u on the 2 x 2 block (pair t rows, pair u columns), t <= u,
-            // with the (u, t) block written as its mirror: F stays exactly symmetric.
-#pragma unroll
-            for (int i = 0; i < JM_FB; ++i) {
-                if (fb[i] < 0) continue;
-                const int t = fb[i] & 0xff, u = fb[i] >> 8;
-                const int p = P[t], q = Qp[t], pp = P[u], qq = Qp[u];
-                const float s1 = sn[t], s2 = sn[u];
-                if (t == u) {
-                    if (q >= 0 && s1 != 0.f) F[p * ldf + q] = F[q * ldf + p] = 0.f;
-                    continue;
-                }
-                if (s1 == 0.f && s2 == 0.f) continue;
-                const float c1 = cs[t], c2 = cs[u];
-                float a = F[p * ldf + pp];
-                float b = qq >= 0 ? F[p * ldf + qq] : 0.f;
-                float cc = q >= 0 ? F[q * ldf + pp] : 0.f;
-                float dd = (q >= 0 && qq >= 0) ? F[q * ldf + qq] : 0.f;
-                float r00 = c1 * a - s1 * cc, r01 = c1 * b - s1 * dd;
-                float r10 = s1 * a + c1 * cc, r11 = s1 * b + c1 * dd;
-                float v00 = c2 * r00 - s2 * r01, v01 = s2 * r00 + c2 * r01;
-                float v10 = c2 * r10 - s2 * r11, v11 = s2 * r10 + c2 * r11;
-                F[p * ldf + pp] = v00;
-                F[pp * ldf + p] = v00;
-                if (qq >= 0) {
-                    F[p * ldf + qq] = v01;
-                    F[qq * ldf + p] = v01;
-                }
-                if (q >= 0) {
-                    F[q * ldf + pp] = v10;
-                    F[pp * ldf + q] = v10;
-                    if (qq >= 0) {
-                        F[q * ldf + qq] = v11;
-                        F[qq * ldf + q] = v11;
+                const float fpq = F[p * ld + q];
+                if (fabsf(fpq) > fthr) {
+                    // rotation angle from the diagonal difference; fast FP32 reciprocals and
+                    // square roots suffice (the off-diagonal is zeroed explicitly and
+                    // convergence is measured)
+                    float diff = Dh[q] - Dh[p];
+                    if (DF) diff += Dl[q] - Dl[p];
+                    const float tau = __fdividef(diff, 2.f * fpq);
+                    float sq = fmaf(tau, tau, 1.f);
+                    sq = sq * rsqrtf(sq);
+                    const float tt = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + sq);
+                    c = rsqrtf(fmaf(tt, tt, 1.f));
+                    sv = tt * c;
+                    rotated = 1;
+                    if (DF) {
+                        const float ph = __fmul_rn(tt, fpq);
+                        const float pl = fmaf(tt, fpq, -ph);  // tt * fpq = ph + pl exactly
+                        float hp = Dh[p], lp = Dl[p], hq = Dh[q], lq = Dl[q];
+                        df_add(hp, lp, -ph, -pl);
+                        df_add(hq, lq, ph, pl);
+                        Dh[p] = hp; Dl[p] = lp; Dh[q] = hq; Dl[q] = lq;
+                    } else {
+                        const float dt = tt * fpq;
+                        Dh[p] -= dt;
+                        Dh[q] += dt;
                     }
                 }
+                meta[t] = make_float4(__int_as_float(p), __int_as_float(q), c, sv);
             }
-            // J <- J R on 2-row x pair blocks
-#pragma unroll
-            for (int i = 0; i < JM_JB; ++i) {
-                if (jb[i] < 0) continue;
-                const int rp = jb[i] & 0xff, t = jb[i] >> 8;
-                const int p = P[t], q = Qp[t];
-                const float s1 = sn[t];
-                if (q < 0 || s1 == 0.f) continue;
-                const float c1 = cs[t];
-                const int r0 = 2 * rp, r1 = 2 * rp + 1;
-                float a = J[r0 * ldf + p], b = J[r0 * ldf + q];
-                J[r0 * ldf + p] = c1 * a - s1 * b;
-                J[r0 * ldf + q] = s1 * a + c1 * b;
-                if (r1 < k) {
-                    a = J[r1 * ldf + p];
-                    b = J[r1 * ldf + q];
-                    J[r1 * ldf + p] = c1 * a - s1 * b;
-                    J[r1 * ldf + q] = s1 * a + c1 * b;
+            if (!__syncthreads_or(rotated)) continue;  // nothing rotates: F and J stay as they are
+            for (int e = tid; e < nblk; e += nt) {
+                const int t = e % half, u = e / half;
+                const float4 mt = meta[t], mu = meta[u];
+                const int pt = __float_as_int(mt.x), qt = __float_as_int(mt.y);
+                const int pu = __float_as_int(mu.x), qu = __float_as_int(mu.y);
+                const float ct = mt.z, st = mt.w, cu = mu.z, su = mu.w;
+                const float a = F[pt * ld + pu], b = F[pt * ld + qu];
+                const float cc = F[qt * ld + pu], dd = F[qt * ld + qu];
+                const float ja = J[pu * ld + pt], jb = J[qu * ld + pt];
+                const float jc = J[pu * ld + qt], jd = J[qu * ld + qt];
+                const float r00 = fmaf(ct, a, -st * cc), r01 = fmaf(ct, b, -st * dd);
+                const float r10 = fmaf(st, a, ct * cc), r11 = fmaf(st, b, ct * dd);
+                float v00 = fmaf(cu, r00, -su * r01), v01 = fmaf(su, r00, cu * r01);
+                float v10 = fmaf(cu, r10, -su * r11), v11 = fmaf(su, r10, cu * r11);
+                if (t == u) {  // the pair's own block: zero diagonal, a_pq annihilated when rotated
+                    v00 = 0.f;
+                    v11 = 0.f;
+                    v01 = su != 0.f ? 0.f : b;
+                    v10 = v01;
                 }
+                Fn[pt * ld + pu] = v00;
+                Fn[pt * ld + qu] = v01;
+                Fn[qt * ld + pu] = v10;
+                Fn[qt * ld + qu] = v11;
+                J[pu * ld + pt] = fmaf(cu, ja, -su * jb);
+                J[qu * ld + pt] = fmaf(su, ja, cu * jb);
+                J[pu * ld + qt] = fmaf(cu, jc, -su * jd);
+                J[qu * ld + qt] = fmaf(su, jc, cu * jd);
             }
             __syncthreads();
+            float* tmp = F;
+            F = Fn;
+            Fn = tmp;
         }
     }
     if (!converged && tid == 0) atomicOr(flags, FLAG_NOT_CONVERGED);
-    for (int i = tid; i < k; i += nt) Dout[i] = (double)D[i];
+    for (int i = tid; i < k; i += nt) Dout[i] = (double)Dh[i] + (double)Dl[i];
     for (int e = tid; e < k * k; e += nt) {
-        int i = e % k, j = e / k;
-        Jout[i + (int64_t)k * j] = J[i * ldf + j];
+        const int i = e % k, j = e / k;
+        Jout[i + (int64_t)k * j] = J[j * ld + i];
     }
 }
 
@@ -928,18 +906,21 @@ void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, fl
                          bool fp64_diag) {
     if (!c.exec) return;
     TK_REQUIRE(k >= 1 && k <= 112, TK_ERR_SHAPE, "jacobi_mixed: 1 <= k <= 112");
-    size_t smem = sizeof(double) * k + 2 * sizeof(float) * k * (k + 1);
+    const int64_t kp = k + (k & 1), half = kp / 2;
+    const size_t smem = 2 * sizeof(float) * kp + 3 * sizeof(float) * kp * (kp + 1);
+    int nt = (int)std::min<int64_t>(JM_MAX_THREADS, (half * half + 31) / 32 * 32);
+    nt = std::max(nt, 64);
     ProfScope ps(c, "jacobi", 8.0 * k * k + 8.0 * k * k, 12.0 * k * k * k * max_sweeps);
     if (fp64_diag) {
         if (smem > 48 * 1024)
-            TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
-        jacobi_mixed_kernel<double><<<1, JM_THREADS, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
+        jacobi_mixed_kernel<true><<<1, nt, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
     } else {
         if (smem > 48 * 1024)
-            TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
-        jacobi_mixed_kernel<float><<<1, JM_THREADS, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
+        jacobi_mixed_kernel<false><<<1, nt, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
     }
     c.counted();
     c.check_launch();
