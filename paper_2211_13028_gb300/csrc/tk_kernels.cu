@@ -172,7 +172,7 @@ static void ttm_dispatch(const Ctx& c, const Tx* X, int64_t L, int64_t nj, int64
                          bool mtrans, int64_t m, Ta* out, Ta xinv) {
     int64_t rows = L * R;
     if (rows * m <= (1 << 21) && nj <= 512) {
-        const char* name = (const void*)X == c.xdata ? "ttm_x" : "ttm";
+        const char* name = (const void*)X == c.xdata ? "xpass_simt" : "ttm_simt";
         ProfScope ps(c, name, (double)rows * nj * sizeof(Tx) + (double)rows * m * sizeof(Ta), 2.0 * rows * nj * m);
         ttm_direct_kernel<Tx, Ta><<<(unsigned)((rows * m + 255) / 256), 256, 0, c.stream>>>(X, L, nj, R, M, ldm,
                                                                                            mtrans, m, out, xinv);
@@ -180,7 +180,7 @@ static void ttm_dispatch(const Ctx& c, const Tx* X, int64_t L, int64_t nj, int64
         c.check_launch();
         return;
     }
-    const char* name = (const void*)X == c.xdata ? "ttm_x" : (rows * m == c.xnumel ? "ttm_full" : "ttm");
+    const char* name = ((const void*)X == c.xdata || rows * m == c.xnumel) ? "xpass_simt" : "ttm_simt";
     ProfScope ps(c, name, (double)rows * nj * sizeof(Tx) + (double)rows * m * sizeof(Ta) + (double)nj * m * sizeof(Ta),
                  2.0 * rows * nj * m);
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((m + 31) / 32));

@@ -714,7 +714,9 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
 
 void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out) {
     const int64_t L = X.left(j), R = X.right(j);
-    const char* name = (const void*)X.p == c.xdata ? "ttm_x" : (L * R * m == c.xnumel ? "ttm_full" : "ttm");
+    // kernel classes: "xpass_tc" streams all of X (a pass over the input),
+    // "ttm_tc" contracts an intermediate
+    const char* name = ((const void*)X.p == c.xdata || L * R * m == c.xnumel) ? "xpass_tc" : "ttm_tc";
     ttm_tc_run(c, X, j, M, mtrans, m, out, 0, nullptr, 0.f, nullptr, name);
 }
 
@@ -735,7 +737,7 @@ bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m) {
 
 void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const float* xref,
                             float* dx, float alpha, double* partials) {
-    ttm_tc_run(c, W, j, M, mtrans, m, dx, dx ? 2 : 1, xref, alpha, partials, "residual_tc");
+    ttm_tc_run(c, W, j, M, mtrans, m, dx, dx ? 2 : 1, xref, alpha, partials, "xpass_tc");
 }
 
 }  // namespace tk
