@@ -187,6 +187,10 @@ void launch_ttm(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, i
 // m <= 96; ttm_tc_eligible says whether a TTM qualifies (shape, dtype, alignment).
 bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
 void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
+// BF16 data: tcgen05 kind::f16 with A straight from shared memory and the
+// factor split into BF16 hi + lo (FP32 output).
+bool ttm_bf16_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
+void launch_ttm_bf16(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 // Fused last step of a reconstruction: P = W x_j M^T is formed tile by tile and
 // compared with xref (P's dims, F32): per-CTA partial sums of (xref - P)^2 and
 // xref^2 go to partials[2 * cta]; with dx != NULL also dx = alpha * (xref - P).
