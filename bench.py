@@ -226,6 +226,89 @@ def profile_case(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ BF16 storage form (1024^3)
+
+def run_bf16_workload(args):
+    """rHKron-re at r = 64, p = 16 (s = (9,9,9)) on the 1024^3 Gaussian-bump field stored in BF16
+    (X rounded once; the core pass applies Q as a BF16 hi + lo pair), timed beside the same
+    decomposition of the FP32 field.  Relative errors are reported against the data each form
+    consumed and against the FP32 field; the FP64 oracle is run on a 256^3 field of the same
+    generator and ranks (the whole 1024^3 oracle would take minutes on the host)."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_2211_13028_gb300 import synth
+    from paper_2211_13028_gb300 import tucker as T
+
+    n, r, p = 1024, (64, 64, 64), 16
+    # oracle leg first, before any CUDA work in this process
+    n_or = args.oracle_n
+    xo = synth.from_fortran(synth.gaussian_bumps(n_or, 3, 200, SEED, 1e-4, "cpu", "f32"))
+    xo16 = synth.round_to(xo, "bf16")
+    s, _ = O.subranks_reuse(r, p)
+    om_o = synth.sketch_factors_reuse(xo.shape, s, SEED + 1, "bf16")
+    t_or = time.perf_counter()
+    ref = O.rhkron(xo16, r, om_o)
+    t_or = time.perf_counter() - t_or
+    err_or = O.rel_err(xo16, ref["G"], ref["U"])
+
+    dev = torch.device("cuda", 0)
+    T.load()
+    Xo = synth.fortran(xo16, "bf16", dev)
+    _, _, err_gpu_small = T.tucker_rhkron(Xo, r, p, [synth.fmat(o, "f32", dev) for o in om_o])
+    del Xo
+    X32 = synth.gaussian_bumps(n, 3, 200, SEED, 1e-4, dev, "f32")
+    X16 = X32.to(torch.bfloat16)
+    assert T.is_colmajor(X16)
+    om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(tuple(X32.shape), s, SEED + 1, "bf16")]
+    nrm32 = float(torch.linalg.vector_norm(X32.double()))
+    hbm = _peaks()[0]
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    forms = {}
+    for name, X in (("bf16", X16), ("f32", X32)):
+        for _ in range(args.warmup):
+            out = T.tucker_rhkron(X, r, p, om)
+        torch.cuda.synchronize()
+        T.tk_profile(True, dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            out = T.tucker_rhkron(X, r, p, om, async_outputs=True)
+        e1.record()
+        torch.cuda.synchronize()
+        prof = T.tk_profile_read(dev)
+        T.tk_profile(False, dev)
+        G, U, err = out
+        loss32 = T.tucker_loss(X32, G, U)
+        xp = prof.get("xpass_tc", dict(ms=0.0, launches=1, bytes=0.0))
+        gbs = (xp["bytes"] / max(1, xp["launches"])) / (xp["ms"] / max(1, xp["launches"]) * 1e-3) / 1e9 \
+            if xp["ms"] > 0 else 0.0
+        forms[name] = dict(ms=e0.elapsed_time(e1) / args.steps, rel_err_vs_own_data=err.value,
+                           rel_err_vs_f32_field=float(np.sqrt(max(loss32, 0.0))) / nrm32,
+                           xpass_gbs=gbs, xpass_frac=gbs / hbm,
+                           xpass_launches=xp["launches"] // args.steps,
+                           xpass_bytes_per_step=xp["bytes"] / args.steps)
+    clk = clocks.stop()
+    st, _ = T.tk_sync_status(dev)
+    line = dict(
+        metric="rHKron-re wall time, 1024^3 field, r=64, p=16: BF16 storage (Q hi+lo refinement) vs FP32",
+        value=forms["bf16"]["ms"], unit="ms", n_gpus=1, steps=args.steps, warmup=args.warmup,
+        ms_per_step=forms["bf16"]["ms"], higher_is_better=False, scaling="weak", vs_baseline=None,
+        dtype="bf16", data="synthetic",
+        config=dict(workload=("bumps1024_bf16: 1024^3 Gaussian-bump field (the 512^3 generator at n=1024), "
+                              "stored BF16 (rounded once) and FP32; rHKron-re r=(64,64,64), p=16, s=(9,9,9)"),
+                    l2="X is 2 GiB (BF16) / 4 GiB (FP32), larger than L2: no flush"),
+        forms=forms, speedup_bf16_over_f32=forms["f32"]["ms"] / forms["bf16"]["ms"],
+        oracle_check=dict(n=n_or, oracle_rel_err=err_or, gpu_rel_err=err_gpu_small,
+                          abs_diff=abs(err_or - err_gpu_small), oracle_seconds=t_or,
+                          note="FP64 oracle on the BF16-rounded %d^3 field of the same generator" % n_or),
+        device_status=st, clocks=clk)
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def main():
@@ -240,10 +323,16 @@ def main():
     ap.add_argument("--profile-case", choices=["sketch", "core", "residual", "rhkron"], default=None,
                     help="run one building block on an n^3 FP32 field (for ncu captures) instead of the bench")
     ap.add_argument("--n", type=int, default=384, help="edge of the --profile-case tensor")
+    ap.add_argument("--workload", choices=["bumps512_f32", "bumps1024_bf16"], default="bumps512_f32",
+                    help="bumps512_f32: the default step; bumps1024_bf16: the BF16 storage form vs FP32")
+    ap.add_argument("--oracle-n", type=int, default=256, help="edge of the oracle check of --workload bumps1024_bf16")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.profile_case:
         profile_case(args)
+        return
+    if args.workload == "bumps1024_bf16" and args.impl == "native":
+        run_bf16_workload(args)
         return
 
     if args.impl == "reference":

@@ -382,13 +382,13 @@ static void residual_pass(Ctx& c, const Tens& X, const Tens& G, const std::vecto
         W = ttm_to(c, W, i, U[i], true, acc);
     }
     const int64_t m = U[f].rows;
-    const bool fused = c.use_tc && X.dt == TK_F32 && acc == TK_F32 && (!dx || dxdt == TK_F32) &&
-                       ttm_tc_residual_eligible(W, f, m);
+    // BF16 data: the epilogue reads the BF16 X tile (and writes a BF16 dX) itself
+    const bool fused = c.use_tc && (X.dt == TK_F32 || (X.dt == TK_BF16 && X.left(f) % 8 == 0)) &&
+                       acc == TK_F32 && (!dx || dxdt == X.dt) && ttm_tc_residual_eligible(W, f, m);
     if (fused) {
         const int nb = tc_num_ctas(W, f, m, true);
         double* part = c.alloc<double>(2 * nb);
-        launch_ttm_tc_residual(c, W, f, U[f], true, m, static_cast<const float*>(X.p), static_cast<float*>(dx),
-                               (float)alpha, part);
+        launch_ttm_tc_residual(c, W, f, U[f], true, m, X.p, X.dt, dx, (float)alpha, part);
         launch_sum_pairs(c, part, nb, err2);
         return;
     }

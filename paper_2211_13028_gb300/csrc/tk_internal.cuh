@@ -195,8 +195,8 @@ void launch_ttm_bf16(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, in
 // compared with xref (P's dims, F32): per-CTA partial sums of (xref - P)^2 and
 // xref^2 go to partials[2 * cta]; with dx != NULL also dx = alpha * (xref - P).
 // P itself is never stored.  tc_num_ctas gives the number of partial pairs.
-void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const float* xref,
-                            float* dx, float alpha, double* partials);
+void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const void* xref,
+                            tk_dtype xrdt, void* dx, float alpha, double* partials);
 int tc_num_ctas(const Tens& X, int j, int64_t m, bool residual);
 bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m);
 // out2 = {sum part[2i], sum part[2i+1]} over nb pairs

@@ -22,6 +22,8 @@
 // land in separate TMEM columns); a second adds A_lo * M_hi into the first half.
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA raises
 // FLAG_TIMEOUT, stops issuing work, drains what it issued and frees its TMEM.
+#include <cuda_bf16.h>
+
 #include "tk_tc_common.cuh"
 
 namespace tk {
@@ -78,18 +80,18 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
 struct TcArgs {
     int64_t L, nj, R, m;
     int64_t ntiles, tiles_per_r, nk, nblk;  // work item = (row tile, block of NPAD output columns)
-    float* out;                             // EPI 0: product; EPI 2: alpha * (xref - product)
-    const float* xref;                      // EPI 1, 2: tensor compared with the product (same layout)
+    void* out;                              // EPI 0: product (FP32); EPI 2: alpha * (xref - product) (XR)
+    const void* xref;                       // EPI 1, 2: tensor compared with the product (same layout, XR)
     float alpha;
     double* partials;                       // EPI 1, 2: per CTA {sum (xref - product)^2, sum xref^2}
     unsigned* flags;
 };
 
-template <int NPAD, int EPI>
+template <int NPAD, int EPI, typename XR = float>
 struct Cfg {
     static constexpr int kBBytes = NPAD * 128;  // one of M_hi / M_lo: NPAD rows of 128 B
     static constexpr int kStage = kXBytes + 2 * kBBytes;
-    static constexpr int kXrBytes = EPI ? kRows * NPAD * 4 : 0;  // X tile compared in the residual epilogue
+    static constexpr int kXrBytes = EPI ? kRows * NPAD * (int)sizeof(XR) : 0;  // X tile compared in the residual epilogue
     static constexpr int kXrBufs = EPI ? 2 : 0;
     static constexpr int kBudget = 210 * 1024 - kXrBufs * kXrBytes;
     static constexpr int kStages = kBudget / kStage > 12 ? 12 : kBudget / kStage;
@@ -101,14 +103,20 @@ struct Cfg {
     static_assert(kStages >= 2, "SMEM budget");
 };
 
+__device__ __forceinline__ float xr_to_f32(float v) { return v; }
+__device__ __forceinline__ float xr_to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ void xr_store(float* p, float v) { *p = v; }
+__device__ __forceinline__ void xr_store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
 // EPI 0: store the product; 1: accumulate the residual norms against xref;
-// 2: as 1 and also store alpha * (xref - product).
-template <int NPAD, bool KMAJOR, int EPI>
+// 2: as 1 and also store alpha * (xref - product).  XR: element type of xref
+// and of the EPI 2 output (FP32, or BF16 for BF16 data).
+template <int NPAD, bool KMAJOR, int EPI, typename XR = float>
 __global__ void __launch_bounds__(kThreads, 1)
     ttm_tf32x3_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBhi,
                       const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmXr,
                       TcArgs args) {
-    using C = Cfg<NPAD, EPI>;
+    using C = Cfg<NPAD, EPI, XR>;
     constexpr int S = C::kStages;
     constexpr int NA = C::kNA;
     extern __shared__ uint8_t smem_raw[];
@@ -179,8 +187,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int xb = (int)(item & 1);
                     if (!mbar_wait(&xrempty[xb], (uint32_t)(((item >> 1) & 1) ^ 1), abort, flags)) break;
                     mbar_expect_tx(&xrfull[xb], C::kXrBytes);
-                    tma_load_3d(xr_buf + xb * (C::kXrBytes / 4), &tmXr, (int)l0, (int)(nb * NPAD), (int)rr,
-                                &xrfull[xb]);
+                    tma_load_3d(reinterpret_cast<uint8_t*>(xr_buf) + xb * C::kXrBytes, &tmXr, (int)l0, (int)(nb * NPAD),
+                                (int)rr, &xrfull[xb]);
                 }
                 for (int64_t kc = 0; kc < nk; ++kc, ++it) {
                     const int s = (int)(it % S);
@@ -359,7 +367,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             base += col0 * stride;
             const int64_t ncol = args.m - col0;  // valid columns in this block (may exceed NPAD)
             const uint32_t ta = tbase + lane_base + C::kAcc0 + a * 2 * NPAD;
-            const float* xt = xr_buf + a * (C::kXrBytes / 4);  // [column][row] of the residual X tile
+            // [column][row] of the residual X tile
+            const XR* xt = reinterpret_cast<const XR*>(reinterpret_cast<const uint8_t*>(xr_buf) + a * C::kXrBytes);
 #pragma unroll
             for (int c0 = 0; c0 < NPAD; c0 += 16) {
                 float h[16], g[16];
@@ -371,17 +380,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (EPI == 0) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (c0 + i < ncol) args.out[base + (c0 + i) * stride] = h[i] + g[i];
+                            if (c0 + i < ncol) static_cast<float*>(args.out)[base + (c0 + i) * stride] = h[i] + g[i];
                     } else {
                         float fr = 0.f, fx = 0.f;
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             if (c0 + i < ncol) {
-                                const float xv = xt[(c0 + i) * kRows + rho];
+                                const float xv = xr_to_f32(xt[(c0 + i) * kRows + rho]);
                                 const float dv = xv - (h[i] + g[i]);
                                 fr = fmaf(dv, dv, fr);
                                 fx = fmaf(xv, xv, fx);
-                                if (EPI == 2) args.out[base + (c0 + i) * stride] = args.alpha * dv;
+                                if (EPI == 2) xr_store(static_cast<XR*>(args.out) + base + (c0 + i) * stride, args.alpha * dv);
                             }
                         }
                         sr += (double)fr;
@@ -441,11 +450,11 @@ __global__ void split_tf32_kernel(const void* M, tk_dtype dt, int64_t ldm, int m
     lo[idx] = l;
 }
 
-template <int NPAD, bool KMAJOR, int EPI>
+template <int NPAD, bool KMAJOR, int EPI, typename XR = float>
 static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap& th, const CUtensorMap& tl,
                           const CUtensorMap& txr, const TcArgs& a) {
-    using Cf = Cfg<NPAD, EPI>;
-    auto kern = ttm_tf32x3_kernel<NPAD, KMAJOR, EPI>;
+    using Cf = Cfg<NPAD, EPI, XR>;
+    auto kern = ttm_tf32x3_kernel<NPAD, KMAJOR, EPI, XR>;
     static bool attr_set = false;
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::kSmem));
@@ -481,8 +490,8 @@ bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt) {
 // Shared launcher.  epi 0: out = X x_j M^T.  epi 1/2: compare the product with
 // xref (same dims as the product): partial norms per CTA into partials, and
 // for epi 2 out = alpha * (xref - product).
-static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out, int epi,
-                       const float* xref, float alpha, double* partials, const char* prof_name) {
+static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, void* out, int epi,
+                       const void* xref, tk_dtype xrdt, float alpha, double* partials, const char* prof_name) {
     const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
     int64_t npad, nblk;
     tc_blocks(m, npad, nblk, epi != 0);
@@ -520,12 +529,16 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
         tc::encode(&tl, lo, 2, dims, str, box);
     }
     CUtensorMap txr = tx;  // unused when epi == 0
+    const bool xr_bf16 = epi != 0 && xrdt == TK_BF16;
     if (epi != 0) {
         TK_REQUIRE(!kmajor, TK_ERR_SHAPE, "ttm_tc: the fused residual needs a non-leading mode");
+        TK_REQUIRE(xrdt == TK_F32 || xrdt == TK_BF16, TK_ERR_DTYPE, "ttm_tc: residual reference must be F32/BF16");
+        const uint64_t es = xr_bf16 ? 2 : 4;
         uint64_t dims[3] = {(uint64_t)L, (uint64_t)m, (uint64_t)R};
-        uint64_t str[2] = {(uint64_t)L * 4, (uint64_t)L * m * 4};
+        uint64_t str[2] = {(uint64_t)L * es, (uint64_t)L * m * es};
         uint32_t box[3] = {tc::kRows, (uint32_t)npad, 1};
-        tc::encode(&txr, xref, 3, dims, str, box, false);
+        tc::encode(&txr, xref, 3, dims, str, box, false,
+                   xr_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
     }
     tc::TcArgs a;
     a.L = L;
@@ -541,22 +554,24 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
     a.alpha = alpha;
     a.partials = partials;
     a.flags = c.dflags;
+    const double xres = xr_bf16 ? 2.0 : 4.0;
     double bytes = 4.0 * (double)L * R * nj + 8.0 * nj * m;
     if (epi == 0) bytes += 4.0 * (double)L * R * m;
-    if (epi >= 1) bytes += 4.0 * (double)L * R * m;
-    if (epi == 2) bytes += 4.0 * (double)L * R * m;
+    if (epi >= 1) bytes += xres * (double)L * R * m;
+    if (epi == 2) bytes += xres * (double)L * R * m;
     ProfScope ps(c, prof_name, bytes, 2.0 * (double)L * R * nj * m);
 #define TK_TC_CASE(NP)                                                                             \
     case NP:                                                                                       \
         if (epi == 0) {                                                                            \
             if (kmajor) tc::launch_kernel<NP, true, 0>(c, tx, th, tl, txr, a);                          \
             else tc::launch_kernel<NP, false, 0>(c, tx, th, tl, txr, a);                                \
+        } else if (xr_bf16) {                                                                      \
+            if (epi == 1) tc::launch_kernel<NP, false, 1, __nv_bfloat16>(c, tx, th, tl, txr, a);         \
+            else tc::launch_kernel<NP, false, 2, __nv_bfloat16>(c, tx, th, tl, txr, a);                  \
         } else if (epi == 1) {                                                                     \
-            if (kmajor) tc::launch_kernel<NP, true, 1>(c, tx, th, tl, txr, a);                          \
-            else tc::launch_kernel<NP, false, 1>(c, tx, th, tl, txr, a);                                \
+            tc::launch_kernel<NP, false, 1>(c, tx, th, tl, txr, a);                                     \
         } else {                                                                                   \
-            if (kmajor) tc::launch_kernel<NP, true, 2>(c, tx, th, tl, txr, a);                          \
-            else tc::launch_kernel<NP, false, 2>(c, tx, th, tl, txr, a);                                \
+            tc::launch_kernel<NP, false, 2>(c, tx, th, tl, txr, a);                                     \
         }                                                                                          \
         break;
     switch (npad) {
@@ -578,7 +593,7 @@ void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int6
     // kernel classes: "xpass_tc" streams all of X (a pass over the input),
     // "ttm_tc" contracts an intermediate
     const char* name = ((const void*)X.p == c.xdata || L * R * m == c.xnumel) ? "xpass_tc" : "ttm_tc";
-    ttm_tc_run(c, X, j, M, mtrans, m, out, 0, nullptr, 0.f, nullptr, name);
+    ttm_tc_run(c, X, j, M, mtrans, m, out, 0, nullptr, TK_F32, 0.f, nullptr, name);
 }
 
 int tc_num_ctas(const Tens& X, int j, int64_t m, bool residual) {
@@ -596,9 +611,9 @@ bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m) {
     return W.left(j) >= tc::kRows && m >= npad && ttm_tc_eligible(W, j, m, TK_F32);
 }
 
-void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const float* xref,
-                            float* dx, float alpha, double* partials) {
-    ttm_tc_run(c, W, j, M, mtrans, m, dx, dx ? 2 : 1, xref, alpha, partials, "xpass_tc");
+void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const void* xref,
+                            tk_dtype xrdt, void* dx, float alpha, double* partials) {
+    ttm_tc_run(c, W, j, M, mtrans, m, dx, dx ? 2 : 1, xref, xrdt, alpha, partials, "xpass_tc");
 }
 
 }  // namespace tk

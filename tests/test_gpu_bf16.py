@@ -79,3 +79,25 @@ def test_bf16_refinement_pass_matters(dev):
     e_refined, e_single = core_err(), core_err(refine=-1)
     assert e_refined <= 2e-5
     assert e_single >= 10 * e_refined
+
+
+def test_bf16_fused_residual_loss_and_gradient(dev):
+    # the last reconstruction TTM fused with the residual against the BF16 tensor (no
+    # FP32 Xhat); dX is returned in X's dtype, so it carries one BF16 rounding
+    g = _rng(8)
+    dims, rk = (96, 80, 72), (12, 10, 36)
+    x = synth.round_to(g.standard_normal(dims), "bf16")
+    G = synth.round_to(g.standard_normal(rk), "f32")
+    U = [synth.round_to(g.standard_normal((nn, k)) / np.sqrt(nn), "f32") for nn, k in zip(dims, rk)]
+    Xd, Gd, Ud = synth.fortran(x, "bf16", dev), synth.fortran(G, "f32", dev), mats(U, "f32", dev)
+    ref_loss = O.loss(x, G, U)
+    assert abs(T.tucker_loss(Xd, Gd, Ud) - ref_loss) <= 1e-5 * ref_loss
+    dG, dU, dX = T.tucker_reconstruct_backward(Xd, Gd, Ud, grad_scale=0.25, need_dX=True)
+    ref = O.loss_grads(x, G, U)
+    assert dX.dtype == torch.bfloat16
+    assert rel(to_np(dG), 0.25 * ref["dG"]) <= 1e-4
+    for j in range(3):
+        assert rel(to_np(dU[j]), 0.25 * ref["dU"][j]) <= 1e-4
+    assert rel(to_np(dX), 0.25 * ref["dX"]) <= 4e-3
+    st, _ = T.tk_sync_status(dev)
+    assert st == 0
