@@ -192,6 +192,8 @@ def profile_case(args):
     dev = torch.device("cuda", 0)
     n = args.n
     X = synth.gaussian_bumps(n, 3, 200, SEED, 1e-4, dev, "f32")
+    if args.dtype == "bf16":
+        X = X.to(torch.bfloat16)
     g = __import__("numpy").random.Generator(__import__("numpy").random.PCG64(SEED))
     if args.profile_case == "sketch":
         om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(X.shape, (6, 7, 7), SEED + 1, "f32")]
@@ -217,7 +219,7 @@ def profile_case(args):
     prof = T.tk_profile_read(dev)
     T.tk_profile(False, dev)
     hbm = _peaks()[0]
-    out = dict(profile_case=args.profile_case, n=n, status=T.tk_sync_status(dev)[0], kernels={})
+    out = dict(profile_case=args.profile_case, n=n, dtype=args.dtype, status=T.tk_sync_status(dev)[0], kernels={})
     for name, v in prof.items():
         ms = v["ms"] / v["launches"]
         out["kernels"][name] = dict(launches=v["launches"] // 5, us_per_launch=1e3 * ms,
@@ -309,6 +311,147 @@ def run_bf16_workload(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ 4-way rSTHKron (160^4)
+
+def run_tucker4_workload(args):
+    """rSTHKron on the 160^4 FP32 four-way tensor (core 40^4 with entries N(0,1) 0.9^(index sum),
+    random orthonormal factors, 1e-3 noise), uneven ranks (10,20,30,40), p = 6, modes processed
+    4 -> 1; the FP64 oracle checks the same generator at a reduced edge."""
+    import torch
+
+    import oracle as O
+    from paper_2211_13028_gb300 import synth
+    from paper_2211_13028_gb300 import tucker as T
+
+    r, p, order = (10, 20, 30, 40), 6, [3, 2, 1, 0]
+    n_or = args.oracle_n4
+    xo = synth.from_fortran(synth.tucker4_device(n_or, 40, 0.9, 1e-3, SEED, "cpu", "f32"))
+    S, w = O.subranks_matrix(r, p, order)
+    ko = [min(n_or, ww) for ww in w]
+    oms_o = synth.sketch_factors_matrix(xo.shape, S, ko, order, SEED + 2, "f32")
+    t_or = time.perf_counter()
+    ref = O.rsthkron(xo, r, oms_o, order)
+    t_or = time.perf_counter() - t_or
+    err_or = O.rel_err(xo, ref["G"], ref["U"])
+
+    dev = torch.device("cuda", 0)
+    T.load()
+    Xo = synth.fortran(xo, "f32", dev)
+    _, _, err_gpu_small = T.tucker_rsthkron(Xo, r, p, {kk: synth.fmat(v, "f32", dev) for kk, v in oms_o.items()},
+                                            order=order)
+    del Xo
+    n = 160
+    X = synth.tucker4_device(n, 40, 0.9, 1e-3, SEED, dev, "f32")
+    k = [min(n, ww) for ww in w]
+    oms = {kk: synth.fmat(v, "f32", dev)
+           for kk, v in synth.sketch_factors_matrix(tuple(X.shape), S, k, order, SEED + 2, "f32").items()}
+    for _ in range(args.warmup):
+        out = T.tucker_rsthkron(X, r, p, oms, order=order)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    T.tk_profile(True, dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        out = T.tucker_rsthkron(X, r, p, oms, order=order, async_outputs=True)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = T.tk_profile_read(dev)
+    T.tk_profile(False, dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    hbm = _peaks()[0]
+    xp = prof.get("xpass_tc", dict(ms=0.0, launches=1, bytes=0.0))
+    gbs = (xp["bytes"] / max(1, xp["launches"])) / (xp["ms"] / max(1, xp["launches"]) * 1e-3) / 1e9 \
+        if xp["ms"] > 0 else 0.0
+    tot = sum(v["ms"] for v in prof.values())
+    line = dict(
+        metric="rSTHKron wall time, 160^4 FP32, r=(10,20,30,40), p=6, order 4->1", value=ms, unit="ms",
+        n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=ms, higher_is_better=False,
+        scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload=("tucker160x4_f32: 160^4 FP32, core 40^4 N(0,1)*0.9^(index sum), orthonormal "
+                              "factors, 1e-3 noise; rSTHKron r=(10,20,30,40), p=6 (l'=16,27,36,48), order 4->1"),
+                    l2="X is 2.6 GB, larger than L2: no flush"),
+        rel_err=out[2].value,
+        xpass=dict(gbs=gbs, frac=gbs / hbm, launches_per_step=xp["launches"] / args.steps,
+                   bytes_per_step=xp["bytes"] / args.steps),
+        kernel_shares={kk: round(v["ms"] / tot, 4) for kk, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+        oracle_check=dict(n=n_or, oracle_rel_err=err_or, gpu_rel_err=err_gpu_small,
+                          abs_diff=abs(err_or - err_gpu_small), oracle_seconds=t_or,
+                          note="FP64 oracle on the %d^4 tensor of the same generator" % n_or),
+        device_status=T.tk_sync_status(dev)[0], clocks=clk)
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ gradient descent on the loss (256^3)
+
+def run_descent_workload(args):
+    """Tucker fitting by gradient descent: rHKron-re initialisation (r = 16, p = 8) of the 256^3
+    FP32 tensor (core 16^3 N(0,1), orthonormal factors, 1e-2 noise), then 50 Adam steps
+    (lr 1e-3, betas (0.9, 0.999), eps 1e-8) on ||X - G x_j U_j||^2 through TuckerLoss: each step
+    is one loss plus its adjoint (dG, dU; X is a constant) on the GPU and torch's Adam update."""
+    import numpy as np
+    import torch
+
+    from paper_2211_13028_gb300 import synth
+    from paper_2211_13028_gb300 import tucker as T
+
+    dev = torch.device("cuda", 0)
+    T.load()
+    n, r, p, nsteps = 256, (16, 16, 16), 8, 50
+    x = synth.tucker_tensor((n, n, n), r, seed=SEED, noise_rel=1e-2)
+    X = synth.fortran(x, "f32", dev)
+    nrm = float(np.linalg.norm(x))
+    s, _ = T.tucker_subranks_reuse(r, p)
+    om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(x.shape, s, SEED + 1, "f32")]
+
+    def fit():
+        G0, U0, e0 = T.tucker_rhkron(X, r, p, om)
+        G = G0.clone().requires_grad_(True)
+        U = [u.clone().requires_grad_(True) for u in U0]
+        opt = torch.optim.Adam([G] + U, lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+        for _ in range(nsteps):
+            opt.zero_grad(set_to_none=False)
+            loss = T.TuckerLoss.apply(X, G, *U)
+            loss.backward()
+            opt.step()
+        return e0, loss
+
+    for _ in range(args.warmup):
+        fit()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_init = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    G0, U0, err0 = T.tucker_rhkron(X, r, p, om)
+    t_init.record()
+    G = G0.clone().requires_grad_(True)
+    U = [u.clone().requires_grad_(True) for u in U0]
+    opt = torch.optim.Adam([G] + U, lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    for _ in range(nsteps):
+        opt.zero_grad(set_to_none=False)
+        loss = T.TuckerLoss.apply(X, G, *U)
+        loss.backward()
+        opt.step()
+    e1.record()
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    init = e0.elapsed_time(t_init)
+    final = float(np.sqrt(T.tucker_loss(X, G.detach(), [u.detach() for u in U]))) / nrm
+    line = dict(
+        metric="Tucker fit: rHKron-re init + 50 Adam steps on ||X - G x U||^2, 256^3 FP32, r=16", value=total,
+        unit="ms", n_gpus=1, steps=1, warmup=args.warmup, ms_per_step=(total - init) / nsteps,
+        higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload=("descent256_f32: 256^3 FP32, core 16^3 N(0,1), orthonormal factors, 1e-2 noise; "
+                              "rHKron-re r=16 p=8 (s=(5,5,5)); Adam lr=1e-3 betas=(0.9,0.999) eps=1e-8, 50 steps"),
+                    l2="X is 64 MiB, inside L2 after the first pass of a step"),
+        init_ms=init, adam_step_ms=(total - init) / nsteps, rel_err_init=err0, rel_err_final=final,
+        device_status=T.tk_sync_status(dev)[0])
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def main():
@@ -323,9 +466,13 @@ def main():
     ap.add_argument("--profile-case", choices=["sketch", "core", "residual", "rhkron"], default=None,
                     help="run one building block on an n^3 FP32 field (for ncu captures) instead of the bench")
     ap.add_argument("--n", type=int, default=384, help="edge of the --profile-case tensor")
-    ap.add_argument("--workload", choices=["bumps512_f32", "bumps1024_bf16"], default="bumps512_f32",
-                    help="bumps512_f32: the default step; bumps1024_bf16: the BF16 storage form vs FP32")
+    ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32", help="storage of the --profile-case tensor")
+    ap.add_argument("--workload", choices=["bumps512_f32", "bumps1024_bf16", "tucker160x4_f32", "descent256_f32"],
+                    default="bumps512_f32",
+                    help="bumps512_f32: the default step; bumps1024_bf16: the BF16 storage form vs FP32; "
+                         "tucker160x4_f32: 4-way rSTHKron; descent256_f32: rHKron-re init + 50 Adam steps")
     ap.add_argument("--oracle-n", type=int, default=256, help="edge of the oracle check of --workload bumps1024_bf16")
+    ap.add_argument("--oracle-n4", type=int, default=48, help="edge of the oracle check of --workload tucker160x4_f32")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.profile_case:
@@ -333,6 +480,12 @@ def main():
         return
     if args.workload == "bumps1024_bf16" and args.impl == "native":
         run_bf16_workload(args)
+        return
+    if args.workload == "tucker160x4_f32" and args.impl == "native":
+        run_tucker4_workload(args)
+        return
+    if args.workload == "descent256_f32" and args.impl == "native":
+        run_descent_workload(args)
         return
 
     if args.impl == "reference":

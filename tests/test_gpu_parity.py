@@ -248,6 +248,43 @@ def test_autograd_function_matches_oracle(dev):
         assert rel(U[j].grad.cpu().numpy(), 3.0 * ref["dU"][j]) <= 1e-12
 
 
+def test_gradient_matches_fp64_finite_differences(dev):
+    # Central differences (h = 1e-6) of the GPU loss itself on a 24^3 FP64 problem, along
+    # random directions in (X, G, U) and at 20 individual entries, against the GPU gradient.
+    g = _rng(53)
+    dims, rk = (24, 24, 24), (4, 3, 5)
+    G0 = g.standard_normal(rk)
+    U0 = [g.standard_normal((n, k)) / np.sqrt(n) for n, k in zip(dims, rk)]
+    # X near the model keeps the loss O(1), so the differences are not lost to cancellation
+    x = O.reconstruct(G0, U0) + 0.05 * g.standard_normal(dims)
+    X = synth.fortran(x, "f64", dev).requires_grad_(True)
+    G = synth.fortran(G0, "f64", dev).requires_grad_(True)
+    U = [synth.fmat(u, "f64", dev).requires_grad_(True) for u in U0]
+    params = [X, G] + U
+    T.TuckerLoss.apply(*params).backward()
+    grads = [p.grad.detach().clone() for p in params]
+
+    def loss_at(shift):
+        with torch.no_grad():
+            return T.tucker_loss(X + shift[0], G + shift[1], [u + d for u, d in zip(U, shift[2:])])
+
+    h = 1e-6
+    for trial in range(6):
+        dirs = [torch.randn(p.shape, dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(trial))
+                for p in params]
+        fd = (loss_at([h * d for d in dirs]) - loss_at([-h * d for d in dirs])) / (2 * h)
+        an = sum(float((gr * d).sum()) for gr, d in zip(grads, dirs))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), trial
+    for e in range(20):
+        which = e % len(params)
+        idx = tuple(int(i) for i in np.unravel_index(int(g.integers(params[which].numel())), params[which].shape))
+        shift = [torch.zeros_like(p) for p in params]
+        shift[which][idx] = h
+        fd = (loss_at(shift) - loss_at([-s for s in shift])) / (2 * h)
+        an = float(grads[which][idx])
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (which, idx)
+
+
 # ------------------------------------------------------------------ error paths
 
 def test_bad_shapes_are_rejected(dev):
