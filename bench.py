@@ -50,6 +50,39 @@ TRAFFIC_RATIO = {"xpass_tc": 231.4 / 230.0}
 TRAFFIC_NOTE = {"xpass_tc": "algorithmic bytes per launch x 1.006, the DRAM/algorithmic ratio of a 384^3 capture"}
 
 
+# ------------------------------------------------------------------ ranks (one process per GPU)
+
+def rank_env():
+    """(rank, world size, local rank) from the torchrun environment (1 process when absent)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def init_ranks(world: int):
+    """A gloo process group for the barrier and the timing reduction when world > 1 (the data
+    path has no collective: every rank decomposes its own tensor), else None."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("gloo")
+    return dist
+
+
+def barrier(dist) -> None:
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(x: float, dist) -> float:
+    """The slowest rank's value: the job's time is set by its last replica."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ CPU oracle leg
 
 def oracle_step(n: int):
@@ -102,8 +135,8 @@ def cpu_baseline(n_sample: int, budget_s: float = 20.0):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    rank = rank_env()[0]
+    if rank != 0:  # the oracle runs once, on rank 0; the other ranks exit without work
         return
     n_sample = args.sample
     for _ in range(args.warmup):
@@ -492,9 +525,7 @@ def main():
         run_reference(args)
         return
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
 
     # CPU baseline first (before any CUDA work in this process), rank 0 at N=1 only.
     cpu = None
@@ -506,10 +537,7 @@ def main():
     from paper_2211_13028_gb300 import synth
     from paper_2211_13028_gb300 import tucker as T
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
+    dist = init_ranks(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     T.load()
@@ -562,16 +590,13 @@ def main():
     errs = (out[2].value, out[5].value)
     dev_status, qr_info = T.tk_sync_status(dev)  # 0: every Jacobi solve converged
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
 
     # ---- device-timed region (inputs resident in HBM; X = 512 MiB > L2)
     marks = [[ev() for _ in range(5)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    barrier()
+    barrier(dist)
     torch.cuda.synchronize()
     l0 = T.tk_launch_count(dev)
     T.tk_profile(True, dev)
@@ -586,22 +611,19 @@ def main():
     prof = T.tk_profile_read(dev)
     T.tk_profile(False, dev)
     launches = T.tk_launch_count(dev) - l0
-    barrier()
+    barrier(dist)
     clk = clocks.stop()
     ms = t0.elapsed_time(t1) / args.steps
     ph = [sum(marks[i][a].elapsed_time(marks[i][b]) for i in range(args.steps)) / args.steps
           for a, b in ((0, 1), (3, 4), (1, 2))]
-    if dist is not None:
-        tt = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist)
 
     # ---- end to end through the public API with host buffers
     Xh = X.detach().permute(2, 1, 0).contiguous().cpu().pin_memory()
     Xd = torch.empty_like(X.permute(2, 1, 0).contiguous())
     res_bytes = 0
     e0, e1 = ev(), ev()
-    barrier()
+    barrier(dist)
     torch.cuda.synchronize()
     e0.record()
     for i in range(args.steps):
@@ -613,10 +635,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist)
 
     # ---- roofline of the dominant kernel class
     hbm, bf16, peak_src = _peaks()
