@@ -29,7 +29,21 @@
 namespace tk {
 namespace tc {
 
-constexpr int kThreads = 768;
+// Warp roles: 0 TMA producer, 1 TMEM allocation + MMA issue, 2-3 idle, then
+// the converters, then the epilogue.  The plain-store kernels (EPI 0) need many
+// converters (X streams through them) and a light epilogue; the residual
+// kernels (EPI 1, 2) convert only the small reconstruction operand but compare
+// every element of X in the epilogue, so they trade converters for epilogue warps.
+template <int EPI>
+struct Warps {
+    static constexpr int kConv = EPI ? 8 : 16;   // converter warps: (1 or 2 chunk groups) x 2 K halves x 4 lane quarters
+    static constexpr int kGroups = kConv / 8;
+    static constexpr int kEpi = EPI ? 16 : 4;    // epilogue warps: 4 lane quarters x column groups
+    static constexpr int kColGroups = kEpi / 4;
+    static constexpr int kFirstConv = 4;
+    static constexpr int kFirstEpi = 4 + kConv;
+    static constexpr int kThreads = 32 * (4 + kConv + kEpi);
+};
 constexpr int kRows = 128;    // tile rows (TMEM lanes)
 constexpr int kChunk = 32;    // K elements per pipeline stage
 constexpr int kXBytes = kRows * kChunk * 4;
@@ -92,7 +106,10 @@ struct Cfg {
     static constexpr int kBBytes = NPAD * 128;  // one of M_hi / M_lo: NPAD rows of 128 B
     static constexpr int kStage = kXBytes + 2 * kBBytes;
     static constexpr int kXrBytes = EPI ? kRows * NPAD * (int)sizeof(XR) : 0;  // X tile compared in the residual epilogue
-    static constexpr int kXrBufs = EPI ? 2 : 0;
+    // X tiles in flight: about 128 KB, enough to cover HBM latency at one SM's share of
+    // the bandwidth (2 to 8 tiles)
+    static constexpr int kXrFit = EPI ? (128 * 1024) / (kRows * NPAD * (int)sizeof(XR)) : 0;
+    static constexpr int kXrBufs = EPI ? (kXrFit > 8 ? 8 : (kXrFit < 2 ? 2 : kXrFit)) : 0;
     static constexpr int kBudget = 210 * 1024 - kXrBufs * kXrBytes;
     static constexpr int kStages = kBudget / kStage > 12 ? 12 : kBudget / kStage;
     static constexpr int kAcc0 = 0;                // accumulators: 2 x (2*NPAD) columns
@@ -112,7 +129,7 @@ __device__ __forceinline__ void xr_store(__nv_bfloat16* p, float v) { *p = __flo
 // 2: as 1 and also store alpha * (xref - product).  XR: element type of xref
 // and of the EPI 2 output (FP32, or BF16 for BF16 data).
 template <int NPAD, bool KMAJOR, int EPI, typename XR = float>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
     ttm_tf32x3_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBhi,
                       const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmXr,
                       TcArgs args) {
@@ -129,12 +146,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* aempty = afull + NA;       // [NA] A buffer consumed (MMA commit)
     uint64_t* accfull = aempty + NA;     // [2] accumulator complete (MMA commit)
     uint64_t* accempty = accfull + 2;    // [2] accumulator drained (one arrival per epilogue warp)
-    uint64_t* xrfull = accempty + 2;     // [2] residual X tile landed
-    uint64_t* xrempty = xrfull + 2;      // [2] residual X tile consumed (one arrival per epilogue warp)
-    uint64_t* done = xrempty + 2;        // [1] every issued MMA complete
+    constexpr int XB = C::kXrBufs > 0 ? C::kXrBufs : 1;
+    uint64_t* xrfull = accempty + 2;     // [XB] residual X tile landed
+    uint64_t* xrempty = xrfull + XB;     // [XB] residual X tile consumed (one arrival per epilogue warp)
+    uint64_t* done = xrempty + XB;       // [1] every issued MMA complete
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    __shared__ double red[8];
+    using W = Warps<EPI>;
+    __shared__ double red[2 * W::kEpi];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -148,9 +167,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accfull[b], 1);
-            mbar_init(&accempty[b], 4);   // 4 epilogue warps
+            mbar_init(&accempty[b], W::kEpi);   // one arrival per epilogue warp
+        }
+        for (int b = 0; b < XB; ++b) {
             mbar_init(&xrfull[b], 1);
-            mbar_init(&xrempty[b], 4);
+            mbar_init(&xrempty[b], W::kEpi);
         }
         mbar_init(done, 1);
         *abort = 0;
@@ -184,8 +205,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     l0 = (t % args.tiles_per_r) * kRows;
                 }
                 if (EPI) {  // the X tile the epilogue compares this item's product with
-                    const int xb = (int)(item & 1);
-                    if (!mbar_wait(&xrempty[xb], (uint32_t)(((item >> 1) & 1) ^ 1), abort, flags)) break;
+                    const int xb = (int)(item % XB);
+                    if (!mbar_wait(&xrempty[xb], (uint32_t)(((item / XB) & 1) ^ 1), abort, flags)) break;
                     mbar_expect_tx(&xrfull[xb], C::kXrBytes);
                     tma_load_3d(reinterpret_cast<uint8_t*>(xr_buf) + xb * C::kXrBytes, &tmXr, (int)l0, (int)(nb * NPAD),
                                 (int)rr, &xrfull[xb]);
@@ -219,10 +240,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (EPI) {
-                const int64_t n_xr = item < 2 ? item : 2;
+                const int64_t n_xr = item < XB ? item : XB;
                 for (int64_t q = item - n_xr; q < item; ++q) {
                     const uint64_t t0 = gtimer();
-                    while (!mbar_try_wait(&xrfull[q & 1], (uint32_t)((q >> 1) & 1)) && gtimer() - t0 < kTimeoutNs) {
+                    while (!mbar_try_wait(&xrfull[q % XB], (uint32_t)((q / XB) & 1)) && gtimer() - t0 < kTimeoutNs) {
                     }
                 }
             }
@@ -268,12 +289,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             while (!mbar_try_wait(done, 0) && gtimer() - t0 < kTimeoutNs) {
             }
         }
-    } else if (warp >= 4 && warp < 20) {
+    } else if (warp >= W::kFirstConv && warp < W::kFirstEpi) {
         // ------------------------------------------------ converters: X chunk -> TF32 hi / lo in TMEM
-        // 16 warps: group g = 0/1 takes the even/odd chunks, so two chunks are converted at
-        // once; within a group two warps per TMEM lane quarter, half hs converting K columns
-        // [16 hs, 16 hs + 16).
-        const int cw = warp - 4;
+        // groups of 8 warps (with 2 groups, group g takes the even / odd chunks, so two chunks
+        // are converted at once); within a group two warps per TMEM lane quarter, half hs
+        // converting K columns [16 hs, 16 hs + 16).
+        const int cw = warp - W::kFirstConv;
         const int q = warp & 3, hs = (cw >> 2) & 1, grp = cw >> 3;
         const int rho = 32 * q + lane;  // tile row == TMEM lane
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
@@ -281,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
             for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
-                if ((it & 1) != grp) continue;
+                if (W::kGroups == 2 && (it & 1) != grp) continue;
                 const int s = (int)(it % S);
                 const int b = (int)(ab % NA);
                 bool got = mbar_wait(&full[s], (uint32_t)((it / S) & 1), abort, flags) &&
@@ -334,9 +355,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-    } else if (warp >= 20) {
+    } else if (warp >= W::kFirstEpi) {
         // ------------------------------------------------ epilogue
+        // warp e drains TMEM lane quarter warp % 4 (the quarter a warp may access) and the
+        // 16-column slices cg, cg + kColGroups, ... of the accumulator
         const int q = warp & 3;
+        const int cg = (warp - W::kFirstEpi) >> 2;
         const int rho = 32 * q + lane;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         double sr = 0.0, sx = 0.0;
@@ -344,8 +368,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x, ++acc) {
             const int64_t t = w / args.nblk, nb = w % args.nblk;
             const int a = (int)(acc & 1);
+            const int xb = (int)(acc % XB);
             bool got = mbar_wait(&accfull[a], (uint32_t)((acc >> 1) & 1), abort, flags);
-            if (EPI) got = got && mbar_wait(&xrfull[a], (uint32_t)((acc >> 1) & 1), abort, flags);
+            if (EPI) got = got && mbar_wait(&xrfull[xb], (uint32_t)((acc / XB) & 1), abort, flags);
             if (!__all_sync(0xffffffffu, got)) break;  // warp-uniform: tcgen05.ld below is .aligned
             tc_fence_after();
             int64_t base;
@@ -368,9 +393,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t ncol = args.m - col0;  // valid columns in this block (may exceed NPAD)
             const uint32_t ta = tbase + lane_base + C::kAcc0 + a * 2 * NPAD;
             // [column][row] of the residual X tile
-            const XR* xt = reinterpret_cast<const XR*>(reinterpret_cast<const uint8_t*>(xr_buf) + a * C::kXrBytes);
+            const XR* xt = reinterpret_cast<const XR*>(reinterpret_cast<const uint8_t*>(xr_buf) + xb * C::kXrBytes);
 #pragma unroll
-            for (int c0 = 0; c0 < NPAD; c0 += 16) {
+            for (int c0 = 16 * cg; c0 < NPAD; c0 += 16 * W::kColGroups) {
                 float h[16], g[16];
                 __syncwarp();
                 tmem_ld16(ta + c0, h);
@@ -402,24 +427,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&accempty[a]);
-                if (EPI) mbar_arrive(&xrempty[a]);
+                if (EPI) mbar_arrive(&xrempty[xb]);
             }
         }
         if (EPI != 0) {
-            // reduce over the 128 epilogue threads: warp shuffles, then named barrier 1
+            // reduce over the epilogue threads: warp shuffles, then named barrier 1, then one
+            // thread sums the warps in a fixed order
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
                 sx += __shfl_xor_sync(0xffffffffu, sx, o);
             }
+            const int e = warp - W::kFirstEpi;
             if (lane == 0) {
-                red[2 * q] = sr;
-                red[2 * q + 1] = sx;
+                red[2 * e] = sr;
+                red[2 * e + 1] = sx;
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (rho == 0) {
-                args.partials[2 * blockIdx.x] = red[0] + red[2] + red[4] + red[6];
-                args.partials[2 * blockIdx.x + 1] = red[1] + red[3] + red[5] + red[7];
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * W::kEpi) : "memory");
+            if (e == 0 && lane == 0) {
+                double a0 = 0.0, a1 = 0.0;
+                for (int i = 0; i < W::kEpi; ++i) {
+                    a0 += red[2 * i];
+                    a1 += red[2 * i + 1];
+                }
+                args.partials[2 * blockIdx.x] = a0;
+                args.partials[2 * blockIdx.x + 1] = a1;
             }
         }
     }
@@ -461,7 +493,7 @@ static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap
         attr_set = true;
     }
     int grid = (int)std::min<int64_t>(a.ntiles * a.nblk, num_sms());
-    kern<<<grid, kThreads, Cf::kSmem, c.stream>>>(tx, th, tl, txr, a);
+    kern<<<grid, Warps<EPI>::kThreads, Cf::kSmem, c.stream>>>(tx, th, tl, txr, a);
 }
 
 }  // namespace tc
