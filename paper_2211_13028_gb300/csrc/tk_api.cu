@@ -188,6 +188,13 @@ static Tens multi_ttm(Ctx& c, const Tens& T, std::vector<int> modes, const Mat* 
 // names the buffer for that leaf.
 static void all_modes(Ctx& c, const Tens& T, const std::vector<int>& mset, const std::vector<int>& nset, const Mat* M,
                       tk_dtype acc, std::vector<Tens>& Y, void* const* dst) {
+    // the tree applies each factor more than once: keep their tensor-core splits
+    struct CacheOn {
+        Ctx& c;
+        bool was;
+        explicit CacheOn(Ctx& cc) : c(cc), was(cc.split_cache) { c.split_cache = true; }
+        ~CacheOn() { c.split_cache = was; }
+    } cache_on(c);
     void* leaf = (mset.size() == 1 && dst) ? dst[mset[0]] : nullptr;
     Tens cur = nset.empty() ? T : multi_ttm(c, T, nset, M, false, acc, leaf);
     if (mset.size() == 1) {
@@ -313,17 +320,14 @@ static void eig_top(Ctx& c, int64_t k, const double* A, int64_t r, double* Vr, b
     double* V = c.alloc<double>(k * k);
     double* Vt = c.alloc<double>(k * r);
     double* Wr = c.alloc<double>(r * r);
-    launch_jacobi_mixed(c, k, A, D, J, 1e-6, c.max_sweeps, false);
-    launch_convert(c, J, TK_F32, k, k, k, V0, TK_F64, k, 1.f);
-    launch_convert(c, J, TK_F32, k, k, k, V1, TK_F64, k, 1.f);
+    launch_jacobi_mixed(c, k, A, D, nullptr, V0, V1, 1e-6, c.max_sweeps, false);  // V0 = V1 = J in FP64
     gemm_nt_f64(c, k, k, k, view_cols(V0, TK_F64, k), view_cols(V0, TK_F64, k), 1.0, 0.0, W, k);
     gemm_nt_f64(c, k, k, k, view_rows(V0, TK_F64, k), view_cols(W, TK_F64, k), -0.5, 1.5, V1, k);
     gemm_nt_f64(c, k, k, k, view_rows(A, TK_F64, k), view_cols(V1, TK_F64, k), 1.0, 0.0, Pm, k);
     gemm_nt_f64(c, k, k, k, view_cols(V1, TK_F64, k), view_cols(Pm, TK_F64, k), 1.0, 0.0, B, k);
-    launch_jacobi_mixed(c, k, B, D, J, 1e-14, c.max_sweeps, true);
+    launch_jacobi_mixed(c, k, B, D, J, nullptr, nullptr, 1e-14, c.max_sweeps, true);
     gemm_nt_f64(c, k, k, k, view_rows(V1, TK_F64, k), view_cols(J, TK_F32, k), 1.0, 0.0, V, k);
-    launch_select_top(c, k, r, D, V, Vt);
-    launch_convert(c, Vt, TK_F64, k, r, k, Vr, TK_F64, k, 1.f);
+    launch_select_top(c, k, r, D, V, Vt, Vr);  // Vr starts as a copy of Vt for the Newton-Schulz step
     gemm_nt_f64(c, r, r, k, view_cols(Vt, TK_F64, k), view_cols(Vt, TK_F64, k), 1.0, 0.0, Wr, r);
     gemm_nt_f64(c, k, r, r, view_rows(Vt, TK_F64, k), view_cols(Wr, TK_F64, r), -0.5, 1.5, Vr, k);
 }

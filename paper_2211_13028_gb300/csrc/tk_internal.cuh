@@ -152,6 +152,17 @@ struct Ctx {
     const void* xdata = nullptr;   // the caller's data tensor (tags its full passes)
     int64_t xnumel = 0;
     bool use_tc = true;            // tensor-core TTM where eligible
+    // Factor splits (TF32 hi / lo) made in this pass, reused while split_cache is
+    // on: only inside a dimension tree, whose factors are not modified.
+    struct Split {
+        const void* p;
+        int64_t ld, nj, m, npad, rows;
+        int dt, mtrans;
+        float* hi;
+        float* lo;
+    };
+    std::vector<Split> splits;
+    bool split_cache = false;
 
     template <typename T>
     T* alloc(int64_t count) {
@@ -233,12 +244,14 @@ void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int
 
 // Mixed-precision Jacobi (FP64 diagonal, FP32 off-diagonal and rotations) on the
 // symmetric k x k FP64 matrix A (ld k): eigenvalue estimates in D (unsorted),
-// accumulated rotations in J (FP32, k x k, ld k).  Converged when every
+// accumulated rotations in J (FP32, k x k, ld k; may be NULL) and, when
+// non-NULL, as FP64 copies in J64a and J64b.  Converged when every
 // off-diagonal |a_pq| <= tol * ||A||_F; otherwise FLAG_NOT_CONVERGED is raised.
-void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double tol, int max_sweeps,
-                         bool fp64_diag);
+void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
+                         double tol, int max_sweeps, bool fp64_diag);
 // Vr (k x r, ld k) = the columns of V (k x k) for the r largest entries of D, in descending order.
-void launch_select_top(const Ctx& c, int64_t k, int64_t r, const double* D, const double* V, double* Vr);
+void launch_select_top(const Ctx& c, int64_t k, int64_t r, const double* D, const double* V, double* Vr,
+                       double* Vr2 = nullptr);
 
 // Thin QR of the plain matrix y (rows x cols) into q (rows x min(rows, cols)):
 // CholeskyQR2 with the Householder fallback, identity when cols >= rows; the

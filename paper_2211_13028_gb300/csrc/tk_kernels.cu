@@ -772,8 +772,9 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
 // second).
 template <bool DF>
 __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_mixed_kernel(int k, const double* __restrict__ A,
-                                                                      double* Dout, float* Jout, double tol,
-                                                                      int max_sweeps, unsigned* flags) {
+                                                                      double* Dout, float* Jout, double* J64a,
+                                                                      double* J64b, double tol, int max_sweeps,
+                                                                      unsigned* flags) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int kp = k + (k & 1), half = kp / 2;
     const int ld = kp + 1;  // odd strides: walks along either index are bank-conflict free
@@ -898,12 +899,15 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_mixed_kernel(int k, con
     for (int i = tid; i < k; i += nt) Dout[i] = (double)Dh[i] + (double)Dl[i];
     for (int e = tid; e < k * k; e += nt) {
         const int i = e % k, j = e / k;
-        Jout[i + (int64_t)k * j] = J[j * ld + i];
+        const float v = J[j * ld + i];
+        if (Jout) Jout[i + (int64_t)k * j] = v;
+        if (J64a) J64a[i + (int64_t)k * j] = (double)v;
+        if (J64b) J64b[i + (int64_t)k * j] = (double)v;
     }
 }
 
-void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double tol, int max_sweeps,
-                         bool fp64_diag) {
+void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
+                         double tol, int max_sweeps, bool fp64_diag) {
     if (!c.exec) return;
     TK_REQUIRE(k >= 1 && k <= 112, TK_ERR_SHAPE, "jacobi_mixed: 1 <= k <= 112");
     const int64_t kp = k + (k & 1), half = kp / 2;
@@ -915,19 +919,19 @@ void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, fl
         if (smem > 48 * 1024)
             TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
-        jacobi_mixed_kernel<true><<<1, nt, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
+        jacobi_mixed_kernel<true><<<1, nt, smem, c.stream>>>((int)k, A, D, J, J64a, J64b, tol, max_sweeps, c.dflags);
     } else {
         if (smem > 48 * 1024)
             TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
-        jacobi_mixed_kernel<false><<<1, nt, smem, c.stream>>>((int)k, A, D, J, tol, max_sweeps, c.dflags);
+        jacobi_mixed_kernel<false><<<1, nt, smem, c.stream>>>((int)k, A, D, J, J64a, J64b, tol, max_sweeps, c.dflags);
     }
     c.counted();
     c.check_launch();
 }
 
 // Vr[:, rank] = V[:, i] for the r largest D (ties: lower index first).
-__global__ void select_top_kernel(int64_t k, int64_t r, const double* D, const double* V, double* Vr) {
+__global__ void select_top_kernel(int64_t k, int64_t r, const double* D, const double* V, double* Vr, double* Vr2) {
     for (int64_t i = blockIdx.x; i < k; i += gridDim.x) {
         double di = D[i];
         int64_t rank = 0;
@@ -936,14 +940,19 @@ __global__ void select_top_kernel(int64_t k, int64_t r, const double* D, const d
             rank += (dj > di) || (dj == di && j < i);
         }
         if (rank >= r) continue;
-        for (int64_t row = threadIdx.x; row < k; row += blockDim.x) Vr[row + k * rank] = V[row + k * i];
+        for (int64_t row = threadIdx.x; row < k; row += blockDim.x) {
+            const double v = V[row + k * i];
+            Vr[row + k * rank] = v;
+            if (Vr2) Vr2[row + k * rank] = v;
+        }
     }
 }
 
-void launch_select_top(const Ctx& c, int64_t k, int64_t r, const double* D, const double* V, double* Vr) {
+void launch_select_top(const Ctx& c, int64_t k, int64_t r, const double* D, const double* V, double* Vr,
+                       double* Vr2) {
     if (!c.exec || k == 0 || r == 0) return;
     ProfScope ps(c, "elementwise", 16.0 * k * r, 0.0);
-    select_top_kernel<<<(unsigned)k, 64, 0, c.stream>>>(k, r, D, V, Vr);
+    select_top_kernel<<<(unsigned)k, 64, 0, c.stream>>>(k, r, D, V, Vr, Vr2);
     c.counted();
     c.check_launch();
 }
@@ -1127,21 +1136,41 @@ __global__ void __launch_bounds__(256) residual_partial_kernel(const Tx* X, cons
     }
 }
 
-__global__ void residual_final_kernel(const double* part, int nb, double* out2) {
-    if (threadIdx.x != 0) return;
+// Sum of nb (a, b) pairs: fixed strided per-thread sums, then warp and block
+// trees in a fixed order (deterministic for a given nb).
+__global__ void __launch_bounds__(256) residual_final_kernel(const double* part, int nb, double* out2) {
+    __shared__ double sa[8], sb[8];
     double a = 0.0, b = 0.0;
-    for (int i = 0; i < nb; ++i) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         a += part[2 * i];
         b += part[2 * i + 1];
     }
-    out2[0] = a;
-    out2[1] = b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            ta += sa[i];
+            tb += sb[i];
+        }
+        out2[0] = ta;
+        out2[1] = tb;
+    }
 }
 
 void launch_sum_pairs(const Ctx& c, const double* part, int nb, double* out2) {
     if (!c.exec) return;
     ProfScope ps(c, "elementwise", 16.0 * nb, 2.0 * nb);
-    residual_final_kernel<<<1, 32, 0, c.stream>>>(part, nb, out2);
+    residual_final_kernel<<<1, 256, 0, c.stream>>>(part, nb, out2);
     c.counted();
     c.check_launch();
 }

@@ -529,10 +529,27 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
     tc_blocks(m, npad, nblk, epi != 0);
     const int64_t ldo = (nj + 3) / 4 * 4;
     const int64_t rows_b = npad * nblk;
-    float* hi = c.alloc<float>(ldo * rows_b);
-    float* lo = c.alloc<float>(ldo * rows_b);
+    float* hi = nullptr;
+    float* lo = nullptr;
+    bool have = false;
+    if (c.split_cache) {
+        for (const Ctx::Split& e : c.splits)
+            if (e.p == M.p && e.dt == (int)M.dt && e.ld == M.ld && e.mtrans == (mtrans ? 1 : 0) && e.nj == nj &&
+                e.m == m && e.npad == npad && e.rows == rows_b) {
+                hi = e.hi;
+                lo = e.lo;
+                have = true;
+                break;
+            }
+    }
+    if (!have) {
+        hi = c.alloc<float>(ldo * rows_b);
+        lo = c.alloc<float>(ldo * rows_b);
+        if (c.split_cache)
+            c.splits.push_back({M.p, M.ld, nj, m, npad, rows_b, (int)M.dt, mtrans ? 1 : 0, hi, lo});
+    }
     if (!c.exec) return;
-    {
+    if (!have) {
         int64_t tot = ldo * rows_b;
         ProfScope ps(c, "elementwise", 8.0 * tot + 8.0 * nj * m, 0.0);
         tc::split_tf32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(M.p, M.dt, M.ld, mtrans ? 1 : 0,
