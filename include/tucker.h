@@ -253,7 +253,10 @@ TK_API tk_status tucker_loss(tk_handle* h, const tk_tensor* X, const tk_tensor* 
  *   dG   = -2 grad_scale R x_1 U_1^T ... x_d U_d^T
  *   dU_n = -2 grad_scale (R x_{j!=n} U_j^T)_(n) G_(n)^T
  * The products R x_{j!=n} U_j^T for all n reuse the sketch dimension tree.
- * dG: like G; dU: d matrices like U; dX: like X or NULL (not computed). */
+ * dG: like G; dU: d matrices like U; dX: like X.  Each output may be NULL
+ * (not computed; dU is all d matrices or NULL), so the dX pass and the dG / dU
+ * part can be queued separately, e.g. on two streams.  At least one output
+ * must be given (TK_ERR_ARG otherwise). */
 TK_API tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk_tensor* G, const tk_matrix* U,
                                       double grad_scale, tk_tensor* dG, tk_matrix* dU, tk_tensor* dX);
 

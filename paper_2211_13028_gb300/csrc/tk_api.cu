@@ -1126,15 +1126,22 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
         check_tucker(Gt, U, Um, n);
         TK_REQUIRE(Xt.d == Gt.d && d >= 2, TK_ERR_SHAPE, "backward: X and G must have the same d >= 2");
         for (int j = 0; j < d; ++j) TK_REQUIRE(Xt.n[j] == n[j], TK_ERR_SHAPE, "backward: X dims != U rows");
-        Tens dGt = tens_in(dG, "dG");
-        TK_REQUIRE(dGt.d == d && (dGt.dt == TK_F64 || dGt.dt == TK_F32), TK_ERR_DTYPE, "backward: dG must be F64/F32");
-        for (int j = 0; j < d; ++j) TK_REQUIRE(dGt.n[j] == Gt.n[j], TK_ERR_SHAPE, "backward: dG dims != G dims");
-        TK_REQUIRE(dU != nullptr, TK_ERR_ARG, "backward: null dU");
+        TK_REQUIRE(dG || dU || dX, TK_ERR_ARG, "backward: no output requested");
+        Tens dGt;
+        if (dG) {
+            dGt = tens_in(dG, "dG");
+            TK_REQUIRE(dGt.d == d && (dGt.dt == TK_F64 || dGt.dt == TK_F32), TK_ERR_DTYPE,
+                       "backward: dG must be F64/F32");
+            for (int j = 0; j < d; ++j) TK_REQUIRE(dGt.n[j] == Gt.n[j], TK_ERR_SHAPE, "backward: dG dims != G dims");
+        }
         std::vector<Mat> dUm(d);
-        for (int j = 0; j < d; ++j) {
-            dUm[j] = mat_in(&dU[j], "dU");
-            TK_REQUIRE(dUm[j].rows == n[j] && dUm[j].cols == Gt.n[j], TK_ERR_SHAPE, "backward: dU_j must be n_j x r_j");
-            TK_REQUIRE(dUm[j].dt == TK_F64 || dUm[j].dt == TK_F32, TK_ERR_DTYPE, "backward: dU must be F64/F32");
+        if (dU) {
+            for (int j = 0; j < d; ++j) {
+                dUm[j] = mat_in(&dU[j], "dU");
+                TK_REQUIRE(dUm[j].rows == n[j] && dUm[j].cols == Gt.n[j], TK_ERR_SHAPE,
+                           "backward: dU_j must be n_j x r_j");
+                TK_REQUIRE(dUm[j].dt == TK_F64 || dUm[j].dt == TK_F32, TK_ERR_DTYPE, "backward: dU must be F64/F32");
+            }
         }
         Tens dXt;
         if (dX) {
@@ -1152,6 +1159,12 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
         const double s2 = -2.0 * grad_scale;
         std::vector<Mat> Ua(d);
         for (int j = 0; j < d; ++j) Ua[j] = Um[j].dt == acc ? Um[j] : mat_to(c, Um[j], acc);
+        if (!dG && !dU) {  // dX only: one fused residual pass
+            Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
+            double* nrm = c.alloc<double>(2);
+            residual_pass(c, Xt, Ga, Ua, acc, nrm, dXt.p, dXt.dt, 2.0 * grad_scale);
+            return;
+        }
         std::vector<Tens> S(d);
         std::vector<int> all(d);
         std::iota(all.begin(), all.end(), 0);
@@ -1173,7 +1186,7 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
         }
         std::vector<Tens> Pm(d);  // P_n = G x_{j != n} C_j
         all_modes(c, G64, all, {}, Cm.data(), TK_F64, Pm, nullptr);
-        for (int j = 0; j < d; ++j) {
+        for (int j = 0; j < d && dU; ++j) {
             const int64_t nj = n[j], rj = Gt.n[j];
             int64_t K = 1;
             for (int i = 0; i < d; ++i)
@@ -1186,9 +1199,11 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
             launch_convert(c, A1, TK_F64, nj, rj, nj, (void*)dUm[j].p, dUm[j].dt, dUm[j].ld, 1.f);
         }
         // dG = -2s (X x_j U_j^T - G x_j C_j) = -2s (S_0 x_0 U_0^T - P_0 x_0 C_0)
-        Tens E = ttm_to(c, S[0], 0, Ua[0], false, acc);
-        Tens F = ttm_to(c, Pm[0], 0, Cm[0], false, TK_F64);
-        launch_axpby_residual(c, E, F.p, TK_F64, s2, dGt.p, dGt.dt);
+        if (dG) {
+            Tens E = ttm_to(c, S[0], 0, Ua[0], false, acc);
+            Tens F = ttm_to(c, Pm[0], 0, Cm[0], false, TK_F64);
+            launch_axpby_residual(c, E, F.p, TK_F64, s2, dGt.p, dGt.dt);
+        }
         if (dX) {
             Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
             double* nrm = c.alloc<double>(2);

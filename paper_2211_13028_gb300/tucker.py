@@ -421,14 +421,15 @@ def tucker_loss(X: torch.Tensor, G: torch.Tensor, U: Sequence[torch.Tensor], sca
 
 
 def tucker_reconstruct_backward(X: torch.Tensor, G: torch.Tensor, U: Sequence[torch.Tensor], grad_scale: float = 1.0,
-                                need_dX: bool = True, scale: float = 1.0):
-    """Gradients of grad_scale * ||X - G x_j U_j||^2: returns (dG, [dU_j], dX or None)."""
-    dG = empty_f(list(G.shape), G.dtype, G.device)
-    dU = [_colmajor_matrix(int(u.shape[0]), int(u.shape[1]), u.dtype, u.device) for u in U]
+                                need_dX: bool = True, scale: float = 1.0, need_dG: bool = True, need_dU: bool = True):
+    """Gradients of grad_scale * ||X - G x_j U_j||^2: returns (dG, [dU_j], dX), each None when not requested."""
+    dG = empty_f(list(G.shape), G.dtype, G.device) if need_dG else None
+    dU = [_colmajor_matrix(int(u.shape[0]), int(u.shape[1]), u.dtype, u.device) for u in U] if need_dU else None
     dX = empty_f(list(X.shape), X.dtype, X.device) if need_dX else None
     h = _handle(X.device)
     _check(load().tucker_reconstruct_backward(h, ctypes.byref(_tensor(X, scale)), ctypes.byref(_tensor(G)), _mats(U),
-                                              float(grad_scale), ctypes.byref(_tensor(dG)), _mats(dU),
+                                              float(grad_scale), ctypes.byref(_tensor(dG)) if need_dG else None,
+                                              _mats(dU) if need_dU else None,
                                               ctypes.byref(_tensor(dX)) if need_dX else None), h)
     return dG, dU, dX
 
@@ -449,5 +450,7 @@ class TuckerLoss(torch.autograd.Function):
     def backward(ctx, gout):
         X, G, *U = ctx.saved_tensors
         scale = float(gout.item())
-        dG, dU, dX = tucker_reconstruct_backward(X, G, U, scale, need_dX=ctx.needs_input_grad[0])
-        return (dX, dG, *dU)
+        need_u = any(ctx.needs_input_grad[2:])
+        dG, dU, dX = tucker_reconstruct_backward(X, G, U, scale, need_dX=ctx.needs_input_grad[0],
+                                                 need_dG=ctx.needs_input_grad[1], need_dU=need_u)
+        return (dX, dG, *(dU if dU is not None else [None] * len(U)))

@@ -71,3 +71,22 @@ def test_more_pending_outputs_than_slots(dev):
     s.synchronize()
     vals = np.array([o.value for o in outs])
     assert np.all(vals == e_ref)
+
+
+def test_backward_outputs_can_be_requested_separately(dev):
+    # dX alone (one fused residual pass) and (dG, dU) alone give what one call gives
+    g = np.random.Generator(np.random.PCG64(61))
+    dims, rk = (96, 80, 72), (12, 10, 36)
+    x = synth.round_to(g.standard_normal(dims), "f32")
+    G = synth.round_to(g.standard_normal(rk), "f32")
+    U = [synth.round_to(g.standard_normal((nn, k)) / np.sqrt(nn), "f32") for nn, k in zip(dims, rk)]
+    Xd, Gd, Ud = synth.fortran(x, "f32", dev), synth.fortran(G, "f32", dev), mats(U, "f32", dev)
+    dG, dU, dX = T.tucker_reconstruct_backward(Xd, Gd, Ud, 0.5)
+    _, _, dX2 = T.tucker_reconstruct_backward(Xd, Gd, Ud, 0.5, need_dG=False, need_dU=False)
+    dG2, dU2, none = T.tucker_reconstruct_backward(Xd, Gd, Ud, 0.5, need_dX=False)
+    dG3, none2, none3 = T.tucker_reconstruct_backward(Xd, Gd, Ud, 0.5, need_dX=False, need_dU=False)
+    assert none is None and none2 is None and none3 is None
+    assert torch.equal(dX, dX2) and torch.equal(dG, dG2) and torch.equal(dG, dG3)
+    assert all(torch.equal(a, b) for a, b in zip(dU, dU2))
+    with pytest.raises(T.TuckerError):
+        T.tucker_reconstruct_backward(Xd, Gd, Ud, 0.5, need_dX=False, need_dG=False, need_dU=False)
