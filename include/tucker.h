@@ -134,7 +134,12 @@ TK_API int64_t tk_launch_count(const tk_handle* h);
  * and fills up to max entries (one per class, in first-seen order) with the
  * launch count, summed device milliseconds and summed algorithmic bytes
  * (inputs read once + outputs written once) and flops; it returns the number
- * of classes (or -1 on error) and clears the records. */
+ * of classes (or -1 on error) and clears the records.  Each recorded launch
+ * costs two cudaEventRecord calls on the host, so tk_profile_only restricts
+ * recording to the classes whose name starts with `prefix` (NULL or "" = all
+ * classes; the filter persists until changed).  Class names: "xpass_tc",
+ * "ttm_tc", "xpass_simt", "ttm_simt", "gemm_f64", "chol_inv", "apply_rinv",
+ * "householder", "jacobi", "residual", "elementwise". */
 typedef struct {
     char name[32];
     int64_t launches;
@@ -143,6 +148,7 @@ typedef struct {
     double flops;
 } tk_prof_entry;
 TK_API tk_status tk_profile(tk_handle* h, int enable);
+TK_API tk_status tk_profile_only(tk_handle* h, const char* prefix);
 TK_API int tk_profile_read(tk_handle* h, tk_prof_entry* out, int max);
 
 /* ---- host-side integer planning (no device work; h may be NULL) -------- */

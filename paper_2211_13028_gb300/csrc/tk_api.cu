@@ -26,6 +26,7 @@ cudaEvent_t Profiler::get() {
 
 ProfScope::ProfScope(const Ctx& ctx, const char* name, double bytes, double flops) : c(ctx) {
     if (!c.exec || !c.prof || !c.prof->on) return;
+    if (!c.prof->only.empty() && strncmp(name, c.prof->only.c_str(), c.prof->only.size()) != 0) return;
     ProfRec r{name, c.prof->get(), c.prof->get(), bytes, flops};
     TK_CUDA(cudaEventRecord(r.a, c.stream));
     c.prof->recs.push_back(r);
@@ -621,8 +622,25 @@ tk_status tk_profile(tk_handle* h, int enable) {
             h->prof.pool.push_back(r.b);
         }
         h->prof.recs.clear();
+        // Create the events now: cudaEventCreate inside the profiled region would cost the
+        // host far more than the launches being timed.
+        h->prof.recs.reserve(4096);
+        while (h->prof.pool.size() < 8192) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                break;
+            }
+            h->prof.pool.push_back(e);
+        }
     }
     h->prof.on = enable != 0;
+    return TK_OK;
+}
+
+tk_status tk_profile_only(tk_handle* h, const char* prefix) {
+    if (!h) return TK_ERR_ARG;
+    h->prof.only = prefix ? prefix : "";
     return TK_OK;
 }
 

@@ -126,6 +126,7 @@ struct ProfRec {
 };
 struct Profiler {
     bool on = false;
+    std::string only;  // record only classes whose name starts with this ("" = all)
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> pool;
     cudaEvent_t get();

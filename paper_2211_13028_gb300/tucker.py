@@ -102,6 +102,7 @@ def load():
             "tk_workspace_bytes": ([vp], ctypes.c_int64),
             "tk_launch_count": ([vp], ctypes.c_int64),
             "tk_profile": ([vp, ctypes.c_int], ctypes.c_int),
+            "tk_profile_only": ([vp, ctypes.c_char_p], ctypes.c_int),
             "tk_profile_read": ([vp, P(TkProfEntry), ctypes.c_int], ctypes.c_int),
             "tucker_subranks_reuse": ([ctypes.c_int, i64p, ctypes.c_int, i64p, i64p], ctypes.c_int),
             "tucker_subranks_matrix": ([ctypes.c_int, i64p, ctypes.c_int, P(ctypes.c_int), i64p, i64p], ctypes.c_int),
@@ -274,9 +275,13 @@ def _device_handles(device):
     return [h for (i, _), h in _handles.items() if i == idx]
 
 
-def tk_profile(enable: bool, device=None) -> None:
-    """Start (clearing old records) or stop per-kernel-class event timing on every handle of the device."""
+def tk_profile(enable: bool, device=None, only: Optional[str] = None) -> None:
+    """Start (clearing old records) or stop per-kernel-class event timing on every handle of the device;
+    ``only`` restricts the recording to classes whose name starts with it (each timed launch costs
+    the host two event records)."""
     for h in _device_handles(device):
+        if enable:
+            _check(load().tk_profile_only(h, (only or "").encode()), h)
         _check(load().tk_profile(h, 1 if enable else 0), h)
 
 
