@@ -234,6 +234,12 @@ def profile_case(args):
     elif args.profile_case == "core":
         qs = [synth.fmat(__import__("numpy").linalg.qr(g.standard_normal((n, k)))[0], "f32", dev) for k in (49, 42, 42)]
         fn = lambda: T.tucker_core(X, qs)  # noqa: E731
+    elif args.profile_case == "backward":
+        # dG and dU at an rHKron-re result (r = 32, p = 8)
+        s, _ = T.tucker_subranks_reuse(RANKS, P_OVER)
+        om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(X.shape, s, SEED + 1, "f32")]
+        G, U, _ = T.tucker_rhkron(X, RANKS, P_OVER, om)
+        fn = lambda: T.tucker_reconstruct_backward(X, G, U, 1.0, need_dX=False)  # noqa: E731
     elif args.profile_case == "rhkron":
         # the whole of rHKron-re at r = 32, p = 8: the core sizes (49,42,42) do not depend on n
         s, _ = T.tucker_subranks_reuse(RANKS, P_OVER)
@@ -500,7 +506,7 @@ def main():
     ap.add_argument("--sample", type=int, default=256, help="oracle sample edge (CPU legs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serial", action="store_true", help="run both algorithms on one stream")
-    ap.add_argument("--profile-case", choices=["sketch", "core", "residual", "rhkron"], default=None,
+    ap.add_argument("--profile-case", choices=["sketch", "core", "residual", "rhkron", "backward"], default=None,
                     help="run one building block on an n^3 FP32 field (for ncu captures) instead of the bench")
     ap.add_argument("--n", type=int, default=384, help="edge of the --profile-case tensor")
     ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32", help="storage of the --profile-case tensor")

@@ -112,9 +112,10 @@ struct Cfg {
     static constexpr int kXrBufs = EPI ? (kXrFit > 8 ? 8 : (kXrFit < 2 ? 2 : kXrFit)) : 0;
     static constexpr int kBudget = 210 * 1024 - kXrBufs * kXrBytes;
     static constexpr int kStages = kBudget / kStage > 12 ? 12 : kBudget / kStage;
-    static constexpr int kAcc0 = 0;                // accumulators: 2 x (2*NPAD) columns
-    static constexpr int kABuf = 4 * NPAD;         // A buffers: NA x 64 columns (hi 32 | lo 32)
-    static constexpr int kNA = (512 - 4 * NPAD) / 64 > 6 ? 6 : (512 - 4 * NPAD) / 64;  // >= 2
+    static constexpr int kAccCols = 2 * NPAD;      // accumulators: 2 x (2*NPAD) columns
+    static constexpr int kAcc0 = 0;
+    static constexpr int kABuf = 2 * kAccCols;     // A buffers: NA x 64 columns (hi 32 | lo 32)
+    static constexpr int kNA = (512 - kABuf) / 64 > 6 ? 6 : (512 - kABuf) / 64;  // >= 2
     static constexpr int kSmem = kStages * kStage + kXrBufs * kXrBytes + 1024 + 512;
     static_assert(kNA >= 2, "TMEM budget");
     static_assert(kStages >= 2, "SMEM budget");
@@ -224,9 +225,8 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                     if (KMAJOR) {
                         tma_load_2d(xs, &tmX, (int)(kc * kChunk), (int)r0, &full[s]);
                     } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            tma_load_3d(xs + q * 4096, &tmX, (int)(l0 + 32 * q), (int)(kc * kChunk), (int)rr, &full[s]);
+                        // one unswizzled 128 x 32 box: rows i of 128 floats (512 B)
+                        tma_load_3d(xs, &tmX, (int)l0, (int)(kc * kChunk), (int)rr, &full[s]);
                     }
                     tma_load_2d(bs, &tmBhi, (int)(kc * kChunk), (int)(nb * NPAD), &full[s]);
                     tma_load_2d(bs + C::kBBytes, &tmBlo, (int)(kc * kChunk), (int)(nb * NPAD), &full[s]);
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tbase + C::kAcc0 + a * 2 * NPAD;
+                const uint32_t d_tmem = tbase + C::kAcc0 + a * C::kAccCols;
                 for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
                     const int s = (int)(it % S);
                     const int b = (int)(ab % NA);
@@ -326,14 +326,11 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                         v[4 * jj + 3] = f.w;
                     }
                 } else {
-                    // box (rho / 32): rows i of 32 floats (128 B), 128-byte swizzle
-                    const uint8_t* box = xs + (rho >> 5) * 4096;
-                    const int lc = rho & 31;
+                    // rows i of 128 floats (512 B, no swizzle): lanes read consecutive words
 #pragma unroll
                     for (int ii = 0; ii < 16; ++ii) {
                         const int i = 16 * hs + ii;
-                        v[ii] = *reinterpret_cast<const float*>(box + i * 128 +
-                                                                ((((lc >> 2) ^ (i & 7)) << 4) | ((lc & 3) << 2)));
+                        v[ii] = *reinterpret_cast<const float*>(xs + i * 512 + rho * 4);
                     }
                 }
                 uint32_t hi[16], lo[16];
@@ -391,7 +388,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
             const int64_t col0 = nb * NPAD;
             base += col0 * stride;
             const int64_t ncol = args.m - col0;  // valid columns in this block (may exceed NPAD)
-            const uint32_t ta = tbase + lane_base + C::kAcc0 + a * 2 * NPAD;
+            const uint32_t ta = tbase + lane_base + C::kAcc0 + a * C::kAccCols;
             // [column][row] of the residual X tile
             const XR* xt = reinterpret_cast<const XR*>(reinterpret_cast<const uint8_t*>(xr_buf) + xb * C::kXrBytes);
 #pragma unroll
@@ -567,8 +564,8 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
     } else {
         uint64_t dims[3] = {(uint64_t)L, (uint64_t)nj, (uint64_t)R};
         uint64_t str[2] = {(uint64_t)L * 4, (uint64_t)L * nj * 4};
-        uint32_t box[3] = {32, tc::kChunk, 1};
-        tc::encode(&tx, X.p, 3, dims, str, box);
+        uint32_t box[3] = {tc::kRows, tc::kChunk, 1};
+        tc::encode(&tx, X.p, 3, dims, str, box, false);
     }
     {
         uint64_t dims[2] = {(uint64_t)nj, (uint64_t)rows_b};
