@@ -233,6 +233,16 @@ TK_API tk_status tucker_core(tk_handle* h, const tk_tensor* X, const tk_matrix* 
 TK_API tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
                         const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err);
 
+/* Appendix Alg. rHKron (without factor reuse): like tucker_rhkron, but each
+ * mode n has its own sketch factors, Y_n = X x_{j!=n} Phi_{n,j}, so the
+ * sketches share no products.  Omega: d*d matrices, Omega[n*d + j] =
+ * Phi_{n,j}^T (n_j x s_{n,j}); the diagonal entries are not read.  Needs
+ * prod_{j!=n} s_{n,j} >= r_n + p for every n.  Other arguments as
+ * tucker_rhkron. */
+TK_API tk_status tucker_rhkron_noreuse(tk_handle* h, const tk_tensor* X, const int64_t* r, int p,
+                                       const tk_matrix* Omega, const tk_opts* opts, tk_tensor* G, tk_matrix* U,
+                                       double* rel_err);
+
 /* Algorithm rSTHKron: modes processed in opts->mode_order; for mode j the
  * sketch Y = Ghat x_{k!=j} Phi_{j,k}, its thin QR Q_j, and Ghat <- Ghat x_j Q_j^T;
  * then STHOSVD(Ghat, r) in the same order and U_j = Q_j V_j.

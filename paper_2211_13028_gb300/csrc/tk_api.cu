@@ -900,6 +900,61 @@ static void check_outputs(const Tens& X, const int64_t* r, const tk_tensor* G, c
     }
 }
 
+}  // extern "C"
+
+// Steps 2-4 of Alg. rHKron-re (and of the appendix Alg. rHKron, which differs
+// only in its sketches): thin QR of each sketch unfolding (Q = I where the
+// sketch is at least as wide as the mode), the core Ghat = X x_j Q_j^T, the FP64
+// STHOSVD of the core, U_j = Q_j V_j, and the relative error into errd.
+static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, const std::vector<int64_t>& k,
+                                 const int64_t* r, const Opts& o, const Tens& Gt, const std::vector<Mat>& Um,
+                                 double* errd) {
+    const int d = Xt.d;
+    const tk_dtype acc = acc_of(Xt.dt);
+    // 2. thin QR of each sketch unfolding
+    std::vector<double*> Qd(d);
+    std::vector<View2> Yv;
+    std::vector<int64_t> nb, kb;
+    std::vector<double*> qb;
+    std::vector<int> slots;
+    for (int n = 0; n < d; ++n) {
+        Qd[n] = c.alloc<double>(Xt.n[n] * k[n]);
+        if (k[n] < Xt.n[n]) {
+            View2 v = view_unfold_rows(Y[n], n);
+            Yv.push_back(v);
+            nb.push_back(Xt.n[n]);
+            kb.push_back(k[n]);
+            qb.push_back(Qd[n]);
+            slots.push_back(n);
+        } else {
+            launch_fill_identity(c, Qd[n], Xt.n[n]);
+        }
+    }
+    launch_fill_int(c, c.dqr, TK_MAX_D, 2);
+    orth_batch(c, Yv, nb, kb, qb, slots);
+    // 3. core Ghat = X x_j Q_j^T (modes with Q = I are skipped)
+    std::vector<Mat> Qa(d);
+    std::vector<int> cm;
+    for (int j = 0; j < d; ++j) {
+        Mat qm;
+        qm.p = Qd[j];
+        qm.dt = TK_F64;
+        qm.rows = Xt.n[j];
+        qm.cols = k[j];
+        qm.ld = Xt.n[j];
+        Qa[j] = acc == TK_F64 ? qm : mat_to(c, qm, acc);
+        if (k[j] < Xt.n[j]) cm.push_back(j);
+    }
+    Tens Gh = cm.empty() ? Xt : multi_ttm(c, Xt, cm, Qa.data(), false, acc);
+    Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
+    // 4. STHOSVD of the core in FP64, U_j = Q_j V_j, gauge, casts, error
+    std::vector<double*> V;
+    Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
+    finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, errd);
+}
+
+extern "C" {
+
 tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
                         const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err) {
     double* errd = nullptr;
@@ -945,47 +1000,55 @@ tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int 
                 if (std::find(need.begin(), need.end(), j) == need.end()) rest.push_back(j);
             all_modes(c, Xt, need, rest, Om.data(), acc, Y, nullptr);
         }
-        // 2. thin QR of each sketch unfolding
-        std::vector<double*> Qd(d);
-        std::vector<View2> Yv;
-        std::vector<int64_t> nb, kb;
-        std::vector<double*> qb;
-        std::vector<int> slots;
-        for (int n = 0; n < d; ++n) {
-            Qd[n] = c.alloc<double>(Xt.n[n] * k[n]);
-            if (k[n] < Xt.n[n]) {
-                View2 v = view_unfold_rows(Y[n], n);
-                Yv.push_back(v);
-                nb.push_back(Xt.n[n]);
-                kb.push_back(k[n]);
-                qb.push_back(Qd[n]);
-                slots.push_back(n);
-            } else {
-                launch_fill_identity(c, Qd[n], Xt.n[n]);
-            }
-        }
-        launch_fill_int(c, c.dqr, TK_MAX_D, 2);
-        orth_batch(c, Yv, nb, kb, qb, slots);
-        // 3. core Ghat = X x_j Q_j^T (modes with Q = I are skipped)
-        std::vector<Mat> Qa(d);
-        std::vector<int> cm;
-        for (int j = 0; j < d; ++j) {
-            Mat qm;
-            qm.p = Qd[j];
-            qm.dt = TK_F64;
-            qm.rows = Xt.n[j];
-            qm.cols = k[j];
-            qm.ld = Xt.n[j];
-            Qa[j] = acc == TK_F64 ? qm : mat_to(c, qm, acc);
-            if (k[j] < Xt.n[j]) cm.push_back(j);
-        }
-        Tens Gh = cm.empty() ? Xt : multi_ttm(c, Xt, cm, Qa.data(), false, acc);
-        Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
-        // 4. STHOSVD of the core in FP64, U_j = Q_j V_j, gauge, casts, error
-        std::vector<double*> V;
-        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
         if (rel_err) errd = c.alloc<double>(2);
-        finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, rel_err ? errd : nullptr);
+        rhkron_from_sketches(c, Xt, Y, k, r, o, Gt, Um, errd);
+        if (rel_err) read_err(h, c, errd, rel_err, false, o.async_outputs);
+    });
+}
+
+tk_status tucker_rhkron_noreuse(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
+                                const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err) {
+    double* errd = nullptr;
+    return run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X, "X", false);
+        c.xdata = Xt.p;
+        c.xnumel = Xt.numel();
+        const int d = Xt.d;
+        TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "rhkron_noreuse: d must be >= 2");
+        TK_REQUIRE(r && Omega, TK_ERR_ARG, "rhkron_noreuse: null r or Omega");
+        TK_REQUIRE(p >= 0, TK_ERR_ARG, "rhkron_noreuse: p must be >= 0");
+        Opts o = opts_in(opts, d);
+        set_opts(c, o);
+        tk_dtype acc = acc_of(Xt.dt);
+        Tens Gt;
+        std::vector<Mat> Um;
+        check_outputs(Xt, r, G, U, Gt, Um);
+        std::vector<int64_t> k(d);
+        std::vector<Tens> Y(d);
+        for (int n = 0; n < d; ++n) {
+            // Y_n = X x_{j != n} Phi_{n,j} with fresh factors per mode (no shared tree)
+            std::vector<Mat> Om(d);
+            std::vector<int> modes;
+            double w = 1;
+            for (int j = 0; j < d; ++j) {
+                if (j == n) continue;
+                Mat om = mat_in(&Omega[n * d + j], "Omega");
+                TK_REQUIRE(om.rows == Xt.n[j] && om.cols >= 1, TK_ERR_SHAPE,
+                           "rhkron_noreuse: Omega_{n,j} must be n_j x s_{n,j}");
+                TK_REQUIRE(acc == TK_F64 ? om.dt == TK_F64 : om.dt != TK_F64, TK_ERR_DTYPE,
+                           "rhkron_noreuse: Omega must be F64 for F64 data, else F32/BF16");
+                w *= (double)om.cols;
+                Om[j] = mat_to(c, om, acc);
+                modes.push_back(j);
+            }
+            TK_REQUIRE(w >= (double)(r[n] + p), TK_ERR_SHAPE,
+                       "rhkron_noreuse: prod_{j!=n} s_{n,j} must be >= r_n + p");
+            k[n] = (int64_t)std::min<double>((double)Xt.n[n], w);
+            TK_REQUIRE(r[n] >= 1 && r[n] <= k[n], TK_ERR_SHAPE, "rhkron_noreuse: need 1 <= r_n <= sketch width");
+            if (k[n] < Xt.n[n]) Y[n] = multi_ttm(c, Xt, modes, Om.data(), false, acc);
+        }
+        if (rel_err) errd = c.alloc<double>(2);
+        rhkron_from_sketches(c, Xt, Y, k, r, o, Gt, Um, errd);
         if (rel_err) read_err(h, c, errd, rel_err, false, o.async_outputs);
     });
 }

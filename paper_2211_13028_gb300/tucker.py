@@ -27,7 +27,7 @@ __all__ = [
     "tucker_sketch", "tucker_orth", "tucker_orth_noalloc", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
     "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
-    "library_path", "PendingScalar",
+    "library_path", "PendingScalar", "tucker_rhkron_noreuse",
 ]
 
 TK_MAX_D = 8
@@ -113,6 +113,8 @@ def load():
             "tucker_rhkron": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor), P(TkMatrix),
                                P(ctypes.c_double)], ctypes.c_int),
             "tucker_rsthkron": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor),
+                                 P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
+            "tucker_rhkron_noreuse": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor),
                                  P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
             "tucker_reconstruct": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
             "tucker_loss": ([vp, P(TkTensor), P(TkTensor), P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
@@ -405,6 +407,17 @@ def tucker_rsthkron(X: torch.Tensor, r: Sequence[int], p: int, Omega: Dict[Tuple
     dummy = torch.zeros((1, 1), dtype=next(iter(Omega.values())).dtype, device=X.device)
     lst = [Omega.get((j, k), dummy) if j != k else dummy for j in range(d) for k in range(d)]
     return _decomp(load().tucker_rsthkron, X, r, p, lst, order, qr_method, refine, max_jacobi_sweeps, rel_err,
+                   out_dtype, scale, async_outputs)
+
+
+def tucker_rhkron_noreuse(X: torch.Tensor, r: Sequence[int], p: int, Omega: Dict[Tuple[int, int], torch.Tensor], *,
+                          order=None, qr_method: int = 0, refine: int = 0, max_jacobi_sweeps: int = 0,
+                          rel_err: bool = True, out_dtype=None, scale: float = 1.0, async_outputs: bool = False):
+    """Appendix Algorithm rHKron (no factor reuse).  Omega[(n, j)] = Phi_{n,j}^T (n_j x s_{n,j})."""
+    d = X.dim()
+    dummy = torch.zeros((1, 1), dtype=next(iter(Omega.values())).dtype, device=X.device)
+    lst = [Omega.get((n, j), dummy) if n != j else dummy for n in range(d) for j in range(d)]
+    return _decomp(load().tucker_rhkron_noreuse, X, r, p, lst, order, qr_method, refine, max_jacobi_sweeps, rel_err,
                    out_dtype, scale, async_outputs)
 
 

@@ -311,3 +311,80 @@ def test_jacobi_sweep_limit_is_reported(dev):
     T.tucker_rhkron(synth.fortran(x, "f64", dev), r, p, mats(oms, "f64", dev), rel_err=False)
     st, _ = T.tk_sync_status(dev)
     assert st == 0
+
+
+# ------------------------------------------------------------------ appendix rHKron (no reuse), 4-way, edge cases
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rhkron_noreuse_parity(dev, dtype):
+    # appendix Algorithm rHKron: fresh factors per mode (rows of the subrank matrix)
+    dims, r, p = (40, 36, 32), (5, 4, 6), 5
+    core = synth.decaying_core((10, 10, 10), 0.6, seed=71)
+    x = synth.tucker_tensor(dims, (10, 10, 10), seed=72, noise_rel=1e-3, core=core)
+    X, xv, _ = make_X(x, dtype, dev)
+    S, _ = O.subranks_matrix(r, p)
+    oms = synth.sketch_factors_noreuse(dims, S, seed=73, dtype=dtype)
+    Om = {key: synth.fmat(v, dtype, dev) for key, v in oms.items()}
+    G, U, err = T.tucker_rhkron_noreuse(X, r, p, Om)
+    _check_decomp(G, U, err, O.rhkron_noreuse(xv, r, oms), xv, TOL[dtype])
+
+
+def test_rhkron_noreuse_exact_low_rank(dev):
+    dims, rk = (24, 20, 18, 16), (3, 2, 4, 2)
+    x = synth.tucker_tensor(dims, rk, seed=74, noise_rel=0.0)
+    S, _ = O.subranks_matrix(rk, 2)
+    oms = synth.sketch_factors_noreuse(dims, S, seed=75)
+    Om = {key: synth.fmat(v, "f64", dev) for key, v in oms.items()}
+    _, _, err = T.tucker_rhkron_noreuse(synth.fortran(x, "f64", dev), rk, 2, Om)
+    assert err <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rhkron_four_way(dev, dtype):
+    # rHKron-re on a 4-way tensor: the dimension tree over four modes (Sec. 4.4)
+    dims, r, p = (20, 18, 16, 22), (3, 4, 2, 5), 3
+    core = synth.decaying_core((6, 6, 6, 6), 0.6, seed=76)
+    x = synth.tucker_tensor(dims, (6, 6, 6, 6), seed=77, noise_rel=1e-3, core=core)
+    X, xv, _ = make_X(x, dtype, dev)
+    s = O.subranks_reuse(r, p)[0]
+    oms = synth.sketch_factors_reuse(dims, s, seed=78, dtype=dtype)
+    G, U, err = T.tucker_rhkron(X, r, p, mats(oms, dtype, dev))
+    _check_decomp(G, U, err, O.rhkron(xv, r, oms), xv, TOL[dtype])
+
+
+def test_rhkron_full_rank_and_no_oversampling(dev):
+    # r = n on one mode (its factor is a rotation of the whole space) and p = 0
+    dims = (12, 30, 26)
+    x = synth.round_to(np.random.Generator(np.random.PCG64(79)).standard_normal(dims), "f64")
+    r, p = (12, 5, 4), 0
+    s = O.subranks_reuse(r, p)[0]
+    oms = synth.sketch_factors_reuse(dims, s, seed=80)
+    G, U, err = T.tucker_rhkron(synth.fortran(x, "f64", dev), r, p, mats(oms, "f64", dev))
+    ref = O.rhkron(x, r, oms)
+    assert abs(err - O.rel_err(x, ref["G"], ref["U"])) <= 1e-12
+    assert rel(O.reconstruct(*align(to_np(G), [to_np(u) for u in U], ref["U"])), O.reconstruct(ref["G"], ref["U"])) <= 1e-12
+
+
+def test_core_truncation_at_the_maximum_width(dev):
+    # sketch widths of 112 (the largest the core eigensolver and Cholesky take) on FP32 data
+    dims, r, p = (200, 150, 130), (104, 56, 104), 8
+    core = synth.decaying_core((112, 112, 112), 0.97, seed=81)
+    x = synth.tucker_tensor(dims, (112, 112, 112), seed=82, noise_rel=1e-3, core=core)
+    X, xv, _ = make_X(x, "f32", dev)
+    s = (8, 14, 8)  # sketch widths prod_{j!=n} s_j = 112, 64, 112
+    oms = synth.sketch_factors_reuse(dims, s, seed=83, dtype="f32")
+    G, U, err = T.tucker_rhkron(X, r, p, mats(oms, "f32", dev))
+    ref = O.rhkron(xv, r, oms)
+    assert abs(err - O.rel_err(xv, ref["G"], ref["U"])) <= 1e-5
+    st, _ = T.tk_sync_status(dev)
+    assert st == 0
+
+
+def test_empty_dimension_is_rejected_before_launch(dev):
+    x = torch.zeros((0, 4, 5), dtype=torch.float64, device=dev).permute(2, 1, 0).contiguous().permute(2, 1, 0)
+    oms = [torch.zeros((0, 2), dtype=torch.float64, device=dev).t().contiguous().t(),
+           synth.fmat(np.ones((4, 2)), "f64", dev), synth.fmat(np.ones((5, 2)), "f64", dev)]
+    l0 = T.tk_launch_count(dev)
+    with pytest.raises(T.TuckerError):
+        T.tucker_rhkron(x, (1, 1, 1), 1, oms)
+    assert T.tk_launch_count(dev) == l0
