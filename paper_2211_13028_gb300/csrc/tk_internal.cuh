@@ -248,7 +248,7 @@ void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int
 // accumulated rotations in J (FP32, k x k, ld k; may be NULL) and, when
 // non-NULL, as FP64 copies in J64a and J64b.  Converged when every
 // off-diagonal |a_pq| <= tol * ||A||_F; otherwise FLAG_NOT_CONVERGED is raised.
-void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
+void launch_jacobi_mixed(Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
                          double tol, int max_sweeps, bool fp64_diag);
 // Vr (k x r, ld k) = the columns of V (k x k) for the r largest entries of D, in descending order.
 void launch_select_top(const Ctx& c, int64_t k, int64_t r, const double* D, const double* V, double* Vr,

@@ -746,15 +746,31 @@ void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int
 // sum of two floats (hi + lo, about 48 significant bits) updated with an exact
 // two-product and two-sum (Dekker; Knuth), so no FP64 instruction (1/64 of the
 // FP32 rate on this GPU) sits on the per-round critical path.
-// Pairs follow a round-robin tournament over k rounded up to even (an odd k
-// gets a zero row and column that never rotates).  A round has two phases: one
-// thread per pair computes its rotation; then each (pair t, pair u) block of
-// F' = R^T F R and of J' = J R is produced by one thread from the four entries
-// it replaces (F is double-buffered, J is updated in place), with no
-// mirrored writes and no per-entry branching.  One CTA of up to 1024 threads;
-// F, F', J and D live in shared memory.
+// Pairs follow the circle method on kp = k rounded up to even (an odd k gets
+// a zero row and column that never rotates).  The indices sit in kp slots;
+// slot pair t = (2t, 2t + 1) is rotated at every step, after which every entry
+// moves by one fixed slot permutation pi (slot 0 stays, the other kp - 1 slots
+// advance one place around a cycle), so over kp - 1 consecutive steps every
+// pair of indices meets once.  Because the pairing is fixed in slot
+// coordinates, a thread updates the same 2 x 2 block (pair t, pair u >= t) of
+// F' = R^T F R at every step and writes it straight to the permuted positions
+// of the next step: every shared-memory address is computed once, before the
+// sweeps.  F keeps its upper triangle only (it stays exactly symmetric) and is
+// double-buffered.  Warp 0 computes the rotations: at each step, lane t forms
+// the next step's pivot of pair t itself (one entry of the block update, from
+// the same inputs) and its rotation, and carries the pair's diagonal entries
+// and index labels to their new slots, while the other warps update F; one
+// barrier per step.  Rotations (c, s per pair and step) are logged to global
+// memory and J = R_1 R_2 ... is formed by a second kernel that replays the log
+// on every row of J independently (one warp per row, several CTAs) with the
+// same permutation, so J's work is off the per-step critical path.  The matrix
+// is scaled by a power of two to about unit Frobenius norm on entry (exact),
+// which keeps its FP32 entries and the rotation arithmetic clear of overflow
+// and underflow.  Converged: a sweep boundary at which no off-diagonal entry
+// exceeds the threshold, or kp - 1 consecutive steps without a rotation.
 
 constexpr int JM_MAX_THREADS = 1024;
+constexpr int JM_BPT = 2;  // blocks per update thread: h (h + 1) / 2 <= 2 * 992 for h <= 56
 
 // (hi, lo) += (bh, bl) for normalised double-float pairs.
 __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
@@ -767,165 +783,397 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
     hi = h2;
 }
 
+// The slot an entry at slot x moves to after a step (h = kp / 2 pairs).
+__device__ __forceinline__ int jm_pi(int x, int h) {
+    if (h == 1 || x == 0) return x;
+    if (x == 1) return 2;
+    if (x & 1) return x - 2;
+    return x == 2 * h - 2 ? 2 * h - 1 : x + 2;
+}
+
+// The slot whose entry moves to slot y.
+__device__ __forceinline__ int jm_pi_inv(int y, int h) {
+    if (h == 1 || y == 0) return y;
+    if (y == 2) return 1;
+    if (y & 1) return y == 2 * h - 1 ? 2 * h - 2 : y + 2;
+    return y - 2;
+}
+
+__device__ __forceinline__ int jm_tri(int i, int j, int ld) { return i < j ? i * ld + j : j * ld + i; }
+
+// Rotation annihilating the (p, q) entry f against the diagonal (p: hp + lp,
+// q: hq + lq): the smaller root t = sgn(phi) psi / (|phi| + sqrt(phi^2 +
+// psi^2)) of t^2 + 2 t phi / psi - 1 = 0 (phi = a_qq - a_pp, psi = 2 a_pq),
+// c = 1 / sqrt(1 + t^2), s = t c; the diagonal moves by -+ t f.  Fast FP32
+// reciprocals and square roots suffice (the off-diagonal is zeroed explicitly
+// and convergence is measured).  Returns whether it rotates.
+template <bool DF>
+__device__ __forceinline__ int jm_rotate(float f, float fthr, bool allow, float& hp, float& lp, float& hq, float& lq,
+                                         float2& cs) {
+    cs = make_float2(1.f, 0.f);
+    if (!(allow && fabsf(f) > fthr)) return 0;
+    float phi = hq - hp;
+    if (DF) phi += lq - lp;
+    const float psi = 2.f * f;
+    const float r2 = fmaxf(fmaf(phi, phi, psi * psi), 1e-37f);
+    const float t = __fdividef(phi >= 0.f ? psi : -psi, fabsf(phi) + r2 * rsqrtf(r2));
+    const float c = rsqrtf(fmaf(t, t, 1.f));
+    cs = make_float2(c, t * c);
+    if (DF) {
+        const float ph = __fmul_rn(t, f);
+        const float pl = fmaf(t, f, -ph);  // t f = ph + pl exactly
+        df_add(hp, lp, -ph, -pl);
+        df_add(hq, lq, ph, pl);
+    } else {
+        const float dt = t * f;
+        hp -= dt;
+        hq += dt;
+    }
+    return 1;
+}
+
+// What warp 0's lane needs to form the next-step pivot of one pair: the
+// source block's read base and pairs, which of its four outputs, the source
+// slots of the pair's two entries.
+struct JmPivot {
+    int rd, t, u, sp, sq;
+    bool diag, row1, col1;
+};
+
+__device__ __forceinline__ JmPivot jm_pivot_source(int tp, int h, int ld) {
+    JmPivot pv;
+    pv.sp = jm_pi_inv(2 * tp, h);
+    pv.sq = jm_pi_inv(2 * tp + 1, h);
+    const int ta = pv.sp >> 1, tb = pv.sq >> 1;
+    pv.diag = (ta == tb);  // only with a single pair
+    pv.t = min(ta, tb);
+    pv.u = max(ta, tb);
+    const int rs = (ta <= tb) ? pv.sp : pv.sq, cs = (ta <= tb) ? pv.sq : pv.sp;  // row slot in pair t, column slot in u
+    pv.row1 = rs & 1;
+    pv.col1 = cs & 1;
+    pv.rd = pv.diag ? (2 * pv.t) * ld + 2 * pv.t + 1 : (2 * pv.t) * ld + 2 * pv.u;
+    return pv;
+}
+
+// The next-step pivot of a pair: one output of its source block's update.
+__device__ __forceinline__ float jm_pivot_value(const JmPivot& pv, const float* F, const float2* mc, int ld) {
+    const float2 rt = mc[pv.t];
+    if (pv.diag) return rt.y != 0.f ? 0.f : F[pv.rd];
+    const float2 ru = mc[pv.u];
+    const float a = F[pv.rd], b = F[pv.rd + 1], c = F[pv.rd + ld], d = F[pv.rd + ld + 1];
+    const float al = pv.row1 ? rt.y : rt.x, be = pv.row1 ? rt.x : -rt.y;  // row (2t or 2t + 1) of R_t^T
+    const float x0 = fmaf(al, a, be * c), x1 = fmaf(al, b, be * d);
+    const float ga = pv.col1 ? ru.y : ru.x, de = pv.col1 ? ru.x : -ru.y;  // column (2u or 2u + 1) of R_u
+    return fmaf(ga, x0, de * x1);
+}
+
 // DF: the diagonal is a double-float pair (the stage that resolves the
 // eigenvalues); otherwise a plain float (the first stage, which only seeds the
-// second).
+// second).  rlog: (max_sweeps * (kp - 1) + 1) * (kp / 2) entries; ginfo:
+// 1 + kp ints (steps taken, then the final slot -> index labels).
 template <bool DF>
-__global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_mixed_kernel(int k, const double* __restrict__ A,
-                                                                      double* Dout, float* Jout, double* J64a,
-                                                                      double* J64b, double tol, int max_sweeps,
-                                                                      unsigned* flags) {
+__global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, const double* __restrict__ A,
+                                                                      double* Dout, double tol, int max_sweeps,
+                                                                      float2* __restrict__ rlog,
+                                                                      int* __restrict__ ginfo, unsigned* flags) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int kp = k + (k & 1), half = kp / 2;
-    const int ld = kp + 1;  // odd strides: walks along either index are bank-conflict free
-    float* Dh = reinterpret_cast<float*>(smraw);
-    float* Dl = Dh + kp;
-    float* F = Dl + kp;                 // F(i, j) = F[i * ld + j], kp x kp with a zero diagonal
-    float* Fn = F + (size_t)kp * ld;    // the next round's F
-    float* J = Fn + (size_t)kp * ld;    // column-major: J(i, j) = J[j * ld + i]
-    __shared__ float4 meta[64];         // per pair: (p, q as int bits, c, s)
+    const int kp = k + (k & 1), h = kp / 2, m = kp - 1;
+    const int ld = kp + 1;  // odd stride: walks along either index are bank-conflict free
+    float* Fc = reinterpret_cast<float*>(smraw);  // upper triangle in slot coordinates: F(a, b) = Fc[a * ld + b], a < b
+    float* Fx = Fc + (size_t)kp * ld;             // the next step's
+    float* Hc = Fx + (size_t)kp * ld;             // diagonal (high part) per slot
+    float* Hx = Hc + kp;
+    float* Lc = Hx + kp;                          // diagonal (low part) per slot
+    float* Lx = Lc + kp;
+    int* Ic = reinterpret_cast<int*>(Lx + kp);    // index label per slot
+    int* Ix = Ic + kp;
+    __shared__ float2 meta[2][64];  // (c, s) per pair of the current / next step
     __shared__ double red[33];
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const bool rwarp = tid < 32;
     double part = 0.0;
+    for (int e = tid; e < k * k; e += nt) part += A[e] * A[e];
+    const double nrm = sqrt(block_sum(part, red));
+    int ex = 0;
+    if (nrm > 0.0 && nrm < INFINITY) frexp(nrm, &ex);
+    const double sc = ldexp(1.0, -ex);  // nrm * sc in [0.5, 1)
     for (int e = tid; e < kp * kp; e += nt) {
         const int i = e % kp, j = e / kp;
-        const double v = (i < k && j < k) ? A[i + (int64_t)k * j] : 0.0;
-        part += v * v;
-        if (i == j) {
-            const float h = (float)v;
-            Dh[i] = h;
-            Dl[i] = DF ? (float)(v - (double)h) : 0.f;
-            F[i * ld + j] = 0.f;
-        } else {
-            F[i * ld + j] = (float)v;
+        if (i < j) {
+            Fc[i * ld + j] = (j < k) ? (float)(A[i + (int64_t)k * j] * sc) : 0.f;
+        } else if (i == j) {
+            const double v = (i < k) ? A[i + (int64_t)k * i] * sc : 0.0;
+            const float hv = (float)v;
+            Hc[i] = hv;
+            Lc[i] = DF ? (float)(v - (double)hv) : 0.f;
+            Ic[i] = i;
         }
-        J[j * ld + i] = (i == j) ? 1.f : 0.f;
     }
-    const double thr = tol * sqrt(block_sum(part, red));
-    const float fthr = (float)thr;
-    const int nblk = half * half;
+    const float fthr = (float)(tol * nrm * sc);
+    // update threads (warps 1..): their blocks' read bases and write addresses
+    const int nblk = h * (h + 1) / 2, nu = nt - 32, ut = tid - 32;
+    int bt[JM_BPT], rd[JM_BPT], w0[JM_BPT], w1[JM_BPT], w2[JM_BPT], w3[JM_BPT];
+#pragma unroll
+    for (int b = 0; b < JM_BPT; ++b) {
+        bt[b] = -1;
+        rd[b] = w0[b] = w1[b] = w2[b] = w3[b] = 0;
+        const int e = ut + b * nu;
+        if (rwarp || e >= nblk) continue;
+        int t = 0, rem = e;
+        while (rem >= h - t) {
+            rem -= h - t;
+            ++t;
+        }
+        const int u = t + rem;
+        bt[b] = t | (u << 8);
+        if (t == u) {
+            rd[b] = 2 * t * ld + 2 * t + 1;
+            w0[b] = jm_tri(jm_pi(2 * t, h), jm_pi(2 * t + 1, h), ld);
+        } else {
+            rd[b] = 2 * t * ld + 2 * u;
+            const int pr0 = jm_pi(2 * t, h), pr1 = jm_pi(2 * t + 1, h), pc0 = jm_pi(2 * u, h), pc1 = jm_pi(2 * u + 1, h);
+            w0[b] = jm_tri(pr0, pc0, ld);
+            w1[b] = jm_tri(pr0, pc1, ld);
+            w2[b] = jm_tri(pr1, pc0, ld);
+            w3[b] = jm_tri(pr1, pc1, ld);
+        }
+    }
+    // warp 0: the pairs lane and lane + 32
+    const bool has0 = rwarp && lane < h, has1 = rwarp && lane + 32 < h;
+    JmPivot pv0 = jm_pivot_source(has0 ? lane : 0, h, ld), pv1 = jm_pivot_source(has1 ? lane + 32 : 0, h, ld);
+    __syncthreads();
+    const int64_t total = (int64_t)max_sweeps * m;  // steps allowed
+    int any = 0;
+    if (total > 0 && rwarp) {  // the first step's rotations, in place
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            const int tp = lane + 32 * o;
+            if (tp >= h) continue;
+            const int p = 2 * tp, q = p + 1;
+            float hp = Hc[p], lp = Lc[p], hq = Hc[q], lq = Lc[q];
+            float2 cs;
+            any |= jm_rotate<DF>(Fc[p * ld + q], fthr, true, hp, lp, hq, lq, cs);
+            Hc[p] = hp;
+            Lc[p] = lp;
+            Hc[q] = hq;
+            Lc[q] = lq;
+            meta[0][tp] = cs;
+            rlog[tp] = cs;
+        }
+    }
+    int active = __syncthreads_or(any);  // whether the current step rotates anything
+    int cur = 0, steps = 0, s = 0, idle = 0;
     bool converged = false;
-    for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
-        int off = 0;
-        for (int i = tid >> 5; i < k; i += nt >> 5)
-            for (int j = i + 1 + (tid & 31); j < k; j += 32) off |= fabsf(F[i * ld + j]) > fthr;
-        if (!__syncthreads_or(off)) {
+    for (int64_t g = 0; g < total; ++g) {
+        if (s == 0) {
+            int off = 0;
+            for (int a = tid >> 5; a < kp; a += nt >> 5)
+                for (int b = a + 1 + lane; b < kp; b += 32) off |= fabsf(Fc[a * ld + b]) > fthr;
+            if (!__syncthreads_or(off)) {
+                converged = true;
+                break;
+            }
+        }
+        idle = active ? 0 : idle + 1;
+        if (idle >= m) {
             converged = true;
             break;
         }
-        if (sweep == max_sweeps) break;
-        for (int step = 0; step < kp - 1; ++step) {
-            int rotated = 0;
-            if (tid < half) {
-                const int t = tid;
-                int p, q;
-                if (t == 0) {
-                    p = step;
-                    q = kp - 1;
-                } else {
-                    p = step + t;
-                    if (p >= kp - 1) p -= kp - 1;
-                    q = step - t;
-                    if (q < 0) q += kp - 1;
+        const float2* mc = meta[cur];
+        any = 0;
+        if (rwarp) {
+            const bool want = g + 1 < total;
+            float2* mn = meta[cur ^ 1];
+            float2* lg = rlog + (g + 1) * h;
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                if (!(o ? has1 : has0)) continue;
+                const JmPivot& pv = o ? pv1 : pv0;
+                const int tp = lane + 32 * o;
+                float hp = Hc[pv.sp], hq = Hc[pv.sq], lp = 0.f, lq = 0.f;
+                if (DF) {
+                    lp = Lc[pv.sp];
+                    lq = Lc[pv.sq];
                 }
-                if (p > q) { int tmp = p; p = q; q = tmp; }
-                float c = 1.f, sv = 0.f;
-                const float fpq = F[p * ld + q];
-                if (fabsf(fpq) > fthr) {
-                    // rotation angle from the diagonal difference; fast FP32 reciprocals and
-                    // square roots suffice (the off-diagonal is zeroed explicitly and
-                    // convergence is measured)
-                    float diff = Dh[q] - Dh[p];
-                    if (DF) diff += Dl[q] - Dl[p];
-                    const float tau = __fdividef(diff, 2.f * fpq);
-                    float sq = fmaf(tau, tau, 1.f);
-                    sq = sq * rsqrtf(sq);
-                    const float tt = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + sq);
-                    c = rsqrtf(fmaf(tt, tt, 1.f));
-                    sv = tt * c;
-                    rotated = 1;
-                    if (DF) {
-                        const float ph = __fmul_rn(tt, fpq);
-                        const float pl = fmaf(tt, fpq, -ph);  // tt * fpq = ph + pl exactly
-                        float hp = Dh[p], lp = Dl[p], hq = Dh[q], lq = Dl[q];
-                        df_add(hp, lp, -ph, -pl);
-                        df_add(hq, lq, ph, pl);
-                        Dh[p] = hp; Dl[p] = lp; Dh[q] = hq; Dl[q] = lq;
-                    } else {
-                        const float dt = tt * fpq;
-                        Dh[p] -= dt;
-                        Dh[q] += dt;
-                    }
+                const int ip = Ic[pv.sp], iq = Ic[pv.sq];
+                const float f = jm_pivot_value(pv, Fc, mc, ld);
+                float2 cs;
+                any |= jm_rotate<DF>(f, fthr, want, hp, lp, hq, lq, cs);
+                Hx[2 * tp] = hp;
+                Hx[2 * tp + 1] = hq;
+                if (DF) {
+                    Lx[2 * tp] = lp;
+                    Lx[2 * tp + 1] = lq;
                 }
-                meta[t] = make_float4(__int_as_float(p), __int_as_float(q), c, sv);
+                Ix[2 * tp] = ip;
+                Ix[2 * tp + 1] = iq;
+                mn[tp] = cs;
+                lg[tp] = cs;
             }
-            if (!__syncthreads_or(rotated)) continue;  // nothing rotates: F and J stay as they are
-            for (int e = tid; e < nblk; e += nt) {
-                const int t = e % half, u = e / half;
-                const float4 mt = meta[t], mu = meta[u];
-                const int pt = __float_as_int(mt.x), qt = __float_as_int(mt.y);
-                const int pu = __float_as_int(mu.x), qu = __float_as_int(mu.y);
-                const float ct = mt.z, st = mt.w, cu = mu.z, su = mu.w;
-                const float a = F[pt * ld + pu], b = F[pt * ld + qu];
-                const float cc = F[qt * ld + pu], dd = F[qt * ld + qu];
-                const float ja = J[pu * ld + pt], jb = J[qu * ld + pt];
-                const float jc = J[pu * ld + qt], jd = J[qu * ld + qt];
-                const float r00 = fmaf(ct, a, -st * cc), r01 = fmaf(ct, b, -st * dd);
-                const float r10 = fmaf(st, a, ct * cc), r11 = fmaf(st, b, ct * dd);
-                float v00 = fmaf(cu, r00, -su * r01), v01 = fmaf(su, r00, cu * r01);
-                float v10 = fmaf(cu, r10, -su * r11), v11 = fmaf(su, r10, cu * r11);
-                if (t == u) {  // the pair's own block: zero diagonal, a_pq annihilated when rotated
-                    v00 = 0.f;
-                    v11 = 0.f;
-                    v01 = su != 0.f ? 0.f : b;
-                    v10 = v01;
+        } else {
+#pragma unroll
+            for (int b = 0; b < JM_BPT; ++b) {
+                if (bt[b] < 0) continue;
+                const int t = bt[b] & 255, u = bt[b] >> 8;
+                const float2 rt = mc[t];
+                if (t == u) {  // the pair's own entry: annihilated when it rotates
+                    Fx[w0[b]] = rt.y != 0.f ? 0.f : Fc[rd[b]];
+                    continue;
                 }
-                Fn[pt * ld + pu] = v00;
-                Fn[pt * ld + qu] = v01;
-                Fn[qt * ld + pu] = v10;
-                Fn[qt * ld + qu] = v11;
-                J[pu * ld + pt] = fmaf(cu, ja, -su * jb);
-                J[qu * ld + pt] = fmaf(su, ja, cu * jb);
-                J[pu * ld + qt] = fmaf(cu, jc, -su * jd);
-                J[qu * ld + qt] = fmaf(su, jc, cu * jd);
+                const float2 ru = mc[u];
+                const int r = rd[b];
+                const float a = Fc[r], bb = Fc[r + 1], cc = Fc[r + ld], dd = Fc[r + ld + 1];
+                const float r00 = fmaf(rt.x, a, -rt.y * cc), r01 = fmaf(rt.x, bb, -rt.y * dd);
+                const float r10 = fmaf(rt.y, a, rt.x * cc), r11 = fmaf(rt.y, bb, rt.x * dd);
+                Fx[w0[b]] = fmaf(ru.x, r00, -ru.y * r01);
+                Fx[w1[b]] = fmaf(ru.y, r00, ru.x * r01);
+                Fx[w2[b]] = fmaf(ru.x, r10, -ru.y * r11);
+                Fx[w3[b]] = fmaf(ru.y, r10, ru.x * r11);
             }
-            __syncthreads();
-            float* tmp = F;
-            F = Fn;
-            Fn = tmp;
         }
+        const int nxt = __syncthreads_or(any);
+        float* x;
+        x = Fc; Fc = Fx; Fx = x;
+        x = Hc; Hc = Hx; Hx = x;
+        x = Lc; Lc = Lx; Lx = x;
+        int* y = Ic; Ic = Ix; Ix = y;
+        cur ^= 1;
+        ++steps;
+        s = (s + 1 == m) ? 0 : s + 1;
+        active = nxt;
+    }
+    if (!converged) {  // the allowed sweeps ran out: measure once more
+        int off = 0;
+        for (int a = tid >> 5; a < kp; a += nt >> 5)
+            for (int b = a + 1 + lane; b < kp; b += 32) off |= fabsf(Fc[a * ld + b]) > fthr;
+        converged = !__syncthreads_or(off);
     }
     if (!converged && tid == 0) atomicOr(flags, FLAG_NOT_CONVERGED);
-    for (int i = tid; i < k; i += nt) Dout[i] = (double)Dh[i] + (double)Dl[i];
-    for (int e = tid; e < k * k; e += nt) {
-        const int i = e % k, j = e / k;
-        const float v = J[j * ld + i];
+    for (int x = tid; x < kp; x += nt) {
+        const int i = Ic[x];
+        if (i < k) Dout[i] = ((double)Hc[x] + (DF ? (double)Lc[x] : 0.0)) / sc;
+        ginfo[1 + x] = i;
+    }
+    if (tid == 0) ginfo[0] = steps;
+}
+
+// J = R_1 R_2 ... R_steps from the log, one warp per row of J: lane t holds
+// pair t (and t + 32), rotates it and writes it to the permuted slots of the
+// next step; the final slot labels say which column each slot is.  The log is
+// staged through shared memory in chunks, the next chunk fetched into
+// registers while the current one is applied.
+constexpr int JR_WARPS = 4;
+constexpr int JR_STAGE = 8;  // log entries a thread carries while staging
+
+__global__ void __launch_bounds__(JR_WARPS * 32) jacobi_replay_kernel(int k, const float2* __restrict__ rlog,
+                                                                      const int* __restrict__ ginfo, float* Jout,
+                                                                      double* J64a, double* J64b) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int kp = k + (k & 1), h = kp / 2;
+    const int nt = JR_WARPS * 32, cr = JR_STAGE * nt / h;  // steps per chunk
+    float2* stage = reinterpret_cast<float2*>(smraw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float* ra = reinterpret_cast<float*>(stage + (size_t)cr * h) + (size_t)warp * 2 * kp;  // this warp's row
+    float* rb = ra + kp;
+    const int i = blockIdx.x * JR_WARPS + warp;
+    const int steps = ginfo[0];
+    for (int x = lane; x < kp; x += 32) ra[x] = (x == i) ? 1.f : 0.f;
+    const int t0 = lane, t1 = lane + 32;
+    const int d00 = jm_pi(2 * t0, h), d01 = jm_pi(2 * t0 + 1, h);
+    const int d10 = jm_pi(2 * t1, h), d11 = jm_pi(2 * t1 + 1, h);
+    float2 pre[JR_STAGE];
+    int cn = min(cr, steps);
+#pragma unroll
+    for (int w = 0; w < JR_STAGE; ++w) {
+        const int e = tid + w * nt;
+        if (e < cn * h) pre[w] = rlog[e];
+    }
+    for (int c0 = 0; c0 < steps;) {
+        __syncthreads();  // the previous chunk is no longer read
+#pragma unroll
+        for (int w = 0; w < JR_STAGE; ++w) {
+            const int e = tid + w * nt;
+            if (e < cn * h) stage[e] = pre[w];
+        }
+        __syncthreads();
+        const int c1 = c0 + cn, nn = min(cr, steps - c1);
+#pragma unroll
+        for (int w = 0; w < JR_STAGE; ++w) {
+            const int e = tid + w * nt;
+            if (e < nn * h) pre[w] = rlog[(int64_t)c1 * h + e];
+        }
+        if (i < k) {
+            for (int rr = 0; rr < cn; ++rr) {
+                const float2* cs = stage + rr * h;
+                if (t0 < h) {
+                    const float2 q = cs[t0];
+                    const float a = ra[2 * t0], b = ra[2 * t0 + 1];
+                    rb[d00] = fmaf(q.x, a, -q.y * b);
+                    rb[d01] = fmaf(q.y, a, q.x * b);
+                }
+                if (t1 < h) {
+                    const float2 q = cs[t1];
+                    const float a = ra[2 * t1], b = ra[2 * t1 + 1];
+                    rb[d10] = fmaf(q.x, a, -q.y * b);
+                    rb[d11] = fmaf(q.y, a, q.x * b);
+                }
+                __syncwarp();  // the next step reads slots other lanes wrote
+                float* x = ra;
+                ra = rb;
+                rb = x;
+            }
+        }
+        c0 = c1;
+        cn = nn;
+    }
+    __syncwarp();
+    if (i >= k) return;
+    for (int x = lane; x < kp; x += 32) {
+        const int j = ginfo[1 + x];
+        if (j >= k) continue;
+        const float v = ra[x];
         if (Jout) Jout[i + (int64_t)k * j] = v;
         if (J64a) J64a[i + (int64_t)k * j] = (double)v;
         if (J64b) J64b[i + (int64_t)k * j] = (double)v;
     }
 }
 
-void launch_jacobi_mixed(const Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
+void launch_jacobi_mixed(Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
                          double tol, int max_sweeps, bool fp64_diag) {
-    if (!c.exec) return;
     TK_REQUIRE(k >= 1 && k <= 112, TK_ERR_SHAPE, "jacobi_mixed: 1 <= k <= 112");
-    const int64_t kp = k + (k & 1), half = kp / 2;
-    const size_t smem = 2 * sizeof(float) * kp + 3 * sizeof(float) * kp * (kp + 1);
-    int nt = (int)std::min<int64_t>(JM_MAX_THREADS, (half * half + 31) / 32 * 32);
-    nt = std::max(nt, 64);
-    ProfScope ps(c, "jacobi", 8.0 * k * k + 8.0 * k * k, 12.0 * k * k * k * max_sweeps);
-    if (fp64_diag) {
-        if (smem > 48 * 1024)
-            TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        jacobi_mixed_kernel<true><<<1, nt, smem, c.stream>>>((int)k, A, D, J, J64a, J64b, tol, max_sweeps, c.dflags);
-    } else {
-        if (smem > 48 * 1024)
-            TK_CUDA(cudaFuncSetAttribute(jacobi_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        jacobi_mixed_kernel<false><<<1, nt, smem, c.stream>>>((int)k, A, D, J, J64a, J64b, tol, max_sweeps, c.dflags);
+    TK_REQUIRE(max_sweeps >= 0, TK_ERR_ARG, "jacobi_mixed: max_sweeps >= 0");
+    const int64_t kp = k + (k & 1), h = kp / 2, nblk = h * (h + 1) / 2;
+    float2* rlog = c.alloc<float2>(((int64_t)max_sweeps * (kp - 1) + 1) * h);
+    int* ginfo = c.alloc<int>(1 + kp);
+    if (!c.exec) return;
+    const size_t smem = sizeof(float) * (2 * kp * (kp + 1) + 4 * kp) + sizeof(int) * 2 * kp;
+    // warp 0 computes rotations; the rest update blocks (at most JM_BPT each)
+    const int64_t nu = std::min<int64_t>(JM_MAX_THREADS - 32, (nblk + 31) / 32 * 32);
+    const int nt = (int)(32 + nu);
+    {
+        ProfScope ps(c, "jacobi", 8.0 * k * k + 8.0 * k, 12.0 * k * k * k * max_sweeps);
+        if (fp64_diag) {
+            if (smem > 48 * 1024)
+                TK_CUDA(cudaFuncSetAttribute(jacobi_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            jacobi_sweep_kernel<true>
+                <<<1, nt, smem, c.stream>>>((int)k, A, D, tol, max_sweeps, rlog, ginfo, c.dflags);
+        } else {
+            if (smem > 48 * 1024)
+                TK_CUDA(cudaFuncSetAttribute(jacobi_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            jacobi_sweep_kernel<false>
+                <<<1, nt, smem, c.stream>>>((int)k, A, D, tol, max_sweeps, rlog, ginfo, c.dflags);
+        }
+        c.counted();
+        c.check_launch();
     }
+    if (!J && !J64a && !J64b) return;
+    const int cr = JR_STAGE * JR_WARPS * 32 / (int)h;
+    const size_t rsmem = sizeof(float2) * cr * h + sizeof(float) * JR_WARPS * 2 * kp;
+    ProfScope ps(c, "jacobi", 8.0 * h * (max_sweeps * (kp - 1) + 1) + 8.0 * k * k, 6.0 * k * k * k * max_sweeps);
+    jacobi_replay_kernel<<<(unsigned)((k + JR_WARPS - 1) / JR_WARPS), JR_WARPS * 32, rsmem, c.stream>>>(
+        (int)k, rlog, ginfo, J, J64a, J64b);
     c.counted();
     c.check_launch();
 }
