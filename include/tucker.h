@@ -106,6 +106,25 @@ typedef struct {
 
 typedef struct tk_handle tk_handle;
 
+/* CUDA graphs.  The decompositions, the reconstruction and its gradient can
+ * be recorded into a CUDA graph by stream capture of the handle's stream
+ * (cudaStreamBeginCapture, or any framework built on it) and replayed many
+ * times; nothing in them synchronises.  Rules while recording:
+ *  - each recorded call must have run once on the handle with the same sizes
+ *    beforehand, so that the workspace is large enough (TK_ERR_WORKSPACE
+ *    otherwise); all calls recorded from one handle share its workspace, so
+ *    replay them on that handle's stream (or in stream order with it);
+ *  - a host scalar output (rel_err) needs async_outputs = 1 (TK_ERR_ARG
+ *    otherwise); it is written to the pointer given when recording, at every
+ *    replay, once the stream reaches it;
+ *  - the profiler records nothing.
+ * The workspace block and the host-output slots that a graph recorded stay
+ * reserved (a later workspace growth retires the block instead of freeing it)
+ * until tk_graph_release, which the caller may call only when no graph
+ * recorded from this handle will run again, or tk_destroy.  Neither the
+ * handle nor the recorded tensors may be freed while a graph can still run. */
+TK_API tk_status tk_graph_release(tk_handle* h);
+
 /* Create a handle bound to a CUDA stream (cudaStream_t passed as void*, NULL =
  * legacy default stream) on the current device.  *h receives the handle. */
 TK_API tk_status tk_create(tk_handle** h, void* cuda_stream);

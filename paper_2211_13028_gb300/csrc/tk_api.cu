@@ -25,7 +25,7 @@ cudaEvent_t Profiler::get() {
 }
 
 ProfScope::ProfScope(const Ctx& ctx, const char* name, double bytes, double flops) : c(ctx) {
-    if (!c.exec || !c.prof || !c.prof->on) return;
+    if (!c.exec || c.capturing || !c.prof || !c.prof->on) return;
     if (!c.prof->only.empty() && strncmp(name, c.prof->only.c_str(), c.prof->only.size()) != 0) return;
     ProfRec r{name, c.prof->get(), c.prof->get(), bytes, flops};
     TK_CUDA(cudaEventRecord(r.a, c.stream));
@@ -447,15 +447,27 @@ static tk_status run_call(tk_handle* h, F&& body) {
         int cur = 0;
         TK_CUDA(cudaGetDevice(&cur));
         TK_REQUIRE(cur == h->device, TK_ERR_ARG, "handle was created on another device than the current one");
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        TK_CUDA(cudaStreamIsCapturing(h->stream, &cst));
+        const bool capturing = cst != cudaStreamCaptureStatusNone;
         Ctx plan;
         plan.stream = h->stream;
         plan.exec = false;
         plan.use_tc = h->use_tc;
+        plan.capturing = capturing;
         body(plan);
         size_t need = plan.used + 512;
         if (need > h->ws_bytes) {
+            TK_REQUIRE(!capturing, TK_ERR_WORKSPACE,
+                       "recording into a CUDA graph needs a large enough workspace: run the call once first");
             TK_CUDA(cudaStreamSynchronize(h->stream));
-            if (h->ws) TK_CUDA(cudaFree(h->ws));
+            if (h->ws) {
+                if (h->ws_held)
+                    h->retired.push_back(h->ws);
+                else
+                    TK_CUDA(cudaFree(h->ws));
+            }
+            h->ws_held = false;
             h->ws = nullptr;
             h->ws_bytes = 0;
             size_t grow = need + need / 4;
@@ -466,9 +478,11 @@ static tk_status run_call(tk_handle* h, F&& body) {
             }
             h->ws_bytes = grow;
         }
+        if (capturing) h->ws_held = true;
         Ctx ex;
         ex.stream = h->stream;
         ex.exec = true;
+        ex.capturing = capturing;
         ex.base = h->ws;
         ex.dflags = h->dflags;
         ex.dqr = h->dqr;
@@ -507,12 +521,22 @@ static void CUDART_CB deliver_slot(void* arg) {
 static void read_err(tk_handle* h, Ctx& c, const double* dev2, double* out_rel, bool squared_abs,
                      bool async = false) {
     if (!c.exec) return;
+    TK_REQUIRE(async || !c.capturing, TK_ERR_ARG, "a host output recorded into a CUDA graph needs async_outputs");
     if (async) {
-        tk_handle::HostSlot* sl = &h->slots[h->next_slot];
-        h->next_slot = (h->next_slot + 1) % tk_handle::kHostSlots;
-        // a slot is reused only after its callback has run
-        if (__atomic_load_n(&sl->pending, __ATOMIC_ACQUIRE)) TK_CUDA(cudaStreamSynchronize(c.stream));
-        sl->pending = 1;
+        // next slot not recorded by a graph; a slot is reused only after its callback has run
+        tk_handle::HostSlot* sl = nullptr;
+        for (int n = 0; n < tk_handle::kHostSlots && !sl; ++n) {
+            tk_handle::HostSlot* x = &h->slots[h->next_slot];
+            h->next_slot = (h->next_slot + 1) % tk_handle::kHostSlots;
+            if (!x->reserved && !(c.capturing && __atomic_load_n(&x->pending, __ATOMIC_ACQUIRE))) sl = x;
+        }
+        TK_REQUIRE(sl, TK_ERR_ARG, "every host-output slot is held by a recorded CUDA graph (tk_graph_release)");
+        if (c.capturing) {
+            sl->reserved = 1;  // delivered at every replay of the graph
+        } else {
+            if (__atomic_load_n(&sl->pending, __ATOMIC_ACQUIRE)) TK_CUDA(cudaStreamSynchronize(c.stream));
+            sl->pending = 1;
+        }
         sl->dst = out_rel;
         sl->mode = squared_abs ? 1 : 0;
         TK_CUDA(cudaMemcpyAsync(sl->vals, dev2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -568,6 +592,7 @@ tk_status tk_destroy(tk_handle* h) {
     if (!h) return TK_ERR_ARG;
     cudaStreamSynchronize(h->stream);
     if (h->ws) cudaFree(h->ws);
+    for (char* p : h->retired) cudaFree(p);
     if (h->dflags) cudaFree(h->dflags);
     if (h->slots) cudaFreeHost(h->slots);
     for (auto& r : h->prof.recs) {
@@ -576,6 +601,19 @@ tk_status tk_destroy(tk_handle* h) {
     }
     for (auto e : h->prof.pool) cudaEventDestroy(e);
     delete h;
+    return TK_OK;
+}
+
+tk_status tk_graph_release(tk_handle* h) {
+    if (!h) return TK_ERR_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        h->last_error = "tk_graph_release: stream synchronisation failed";
+        return TK_ERR_CUDA;
+    }
+    for (char* p : h->retired) cudaFree(p);
+    h->retired.clear();
+    h->ws_held = false;
+    for (int i = 0; i < tk_handle::kHostSlots; ++i) h->slots[i].reserved = 0;
     return TK_OK;
 }
 

@@ -153,6 +153,7 @@ struct Ctx {
     const void* xdata = nullptr;   // the caller's data tensor (tags its full passes)
     int64_t xnumel = 0;
     bool use_tc = true;            // tensor-core TTM where eligible
+    bool capturing = false;        // the stream is recording a CUDA graph (launches are not run now)
     // Factor splits (TF32 hi / lo) made in this pass, reused while split_cache is
     // on: only inside a dimension tree, whose factors are not modified.
     struct Split {
@@ -303,7 +304,13 @@ struct tk_handle {
         double* dst;
         int mode;              // 0: sqrt(a / b) (relative error), 1: a (squared norm)
         volatile int pending;  // set when queued, cleared by the host callback
+        int reserved;          // recorded into a CUDA graph: delivered at every replay, never reused
     };
     HostSlot* slots = nullptr;
     int next_slot = 0;
+    // CUDA graph recording: the workspace block a graph recorded must outlive it,
+    // so a block that was in use while recording is retired, not freed, when
+    // the workspace grows (freed by tk_graph_release or tk_destroy)
+    bool ws_held = false;
+    std::vector<char*> retired;
 };

@@ -27,7 +27,7 @@ __all__ = [
     "tucker_sketch", "tucker_orth", "tucker_orth_noalloc", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
     "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
-    "library_path", "PendingScalar", "tucker_rhkron_noreuse",
+    "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tk_graph_release", "TuckerGraph",
 ]
 
 TK_MAX_D = 8
@@ -104,6 +104,7 @@ def load():
             "tk_profile": ([vp, ctypes.c_int], ctypes.c_int),
             "tk_profile_only": ([vp, ctypes.c_char_p], ctypes.c_int),
             "tk_profile_read": ([vp, P(TkProfEntry), ctypes.c_int], ctypes.c_int),
+            "tk_graph_release": ([vp], ctypes.c_int),
             "tucker_subranks_reuse": ([ctypes.c_int, i64p, ctypes.c_int, i64p, i64p], ctypes.c_int),
             "tucker_subranks_matrix": ([ctypes.c_int, i64p, ctypes.c_int, P(ctypes.c_int), i64p, i64p], ctypes.c_int),
             "tucker_sketch": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
@@ -275,6 +276,35 @@ def _device_handles(device):
     _handle(dev)
     idx = dev.index if dev.index is not None else torch.cuda.current_device()
     return [h for (i, _), h in _handles.items() if i == idx]
+
+
+def tk_graph_release(device=None) -> None:
+    """Free the workspace blocks and host-output slots that CUDA graphs recorded from this device's
+    handles; call it only when none of those graphs will be replayed again."""
+    for h in _device_handles(device):
+        _check(load().tk_graph_release(h), h)
+
+
+class TuckerGraph:
+    """``fn`` (a sequence of this module's calls, on the current stream or streams forked from it)
+    recorded once into a CUDA graph and replayed.  ``fn`` runs ``warmup`` times first on a private
+    stream, which sizes the workspaces of the handles it uses; its return value from the recording
+    run is ``outputs`` (tensors and PendingScalar objects that every replay rewrites).  Host scalars
+    need ``async_outputs=True``.  ``replay()`` queues the graph on the current stream."""
+
+    def __init__(self, fn, warmup: int = 1):
+        self.stream = torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            for _ in range(max(1, warmup)):
+                fn()
+        self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            self.outputs = fn()
+
+    def replay(self) -> None:
+        self.graph.replay()
 
 
 def tk_profile(enable: bool, device=None, only: Optional[str] = None) -> None:
