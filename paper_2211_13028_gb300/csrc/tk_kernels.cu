@@ -321,8 +321,73 @@ __global__ void __launch_bounds__(256) gemm_tile16_kernel(int64_t m, int64_t n, 
     }
 }
 
+// Small FP64 products (FP64 runs at 2 FMA per clock per SM here, so a
+// 16 x 16 tile over 16 CTAs leaves the GPU idle): a CTA takes a T x T tile and
+// splits K over G = 256 / T^2 thread groups, which are summed in shared memory
+// at the end, so a k x k x k product with k ~ 50 spreads over ~170 SMs.
+template <int T>
+__global__ void __launch_bounds__(256) gemm_small_kernel(int64_t m, int64_t n, int64_t K, View2 A, View2 B,
+                                                         double alpha, double beta, double* C, int64_t ldc,
+                                                         const int* skip) {
+    if (skip && *skip) return;
+    constexpr int G = 256 / (T * T);
+    __shared__ double As[32][T + 1];
+    __shared__ double Bs[32][T + 1];
+    __shared__ double red[G][T * T];
+    const int tid = threadIdx.x, o = tid % (T * T), g = tid / (T * T);
+    const int tx = o % T, ty = o / T;
+    const int64_t a0 = (int64_t)blockIdx.x * T, b0 = (int64_t)blockIdx.y * T;
+    const bool akf = (A.T1 == INT64_MAX && A.st1 == 1), bkf = (B.T1 == INT64_MAX && B.st1 == 1);
+    double acc = 0.0;
+    for (int64_t k0 = 0; k0 < K; k0 += 32) {
+        for (int e = tid; e < 64 * T; e += 256) {
+            const bool isb = e >= 32 * T;
+            const int f = isb ? e - 32 * T : e;
+            const bool kf = isb ? bkf : akf;
+            const int r = kf ? f >> 5 : f % T, kk = kf ? f & 31 : f / T;
+            const View2& V = isb ? B : A;
+            const int64_t row = (isb ? b0 : a0) + r, k = k0 + kk;
+            const double v = (row < (isb ? n : m) && k < K) ? v2get(V, v2row(V, row) + v2col(V, k)) : 0.0;
+            if (isb)
+                Bs[kk][r] = v;
+            else
+                As[kk][r] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = g; kk < 32; kk += G) acc = fma(As[kk][tx], Bs[kk][ty], acc);
+        __syncthreads();
+    }
+    red[g][o] = acc;
+    __syncthreads();
+    if (g != 0) return;
+    double sum = 0.0;
+#pragma unroll
+    for (int q = 0; q < G; ++q) sum += red[q][o];
+    const int64_t a = a0 + tx, b = b0 + ty;
+    if (a >= m || b >= n) return;
+    double* dst = C + a + ldc * b;
+    *dst = beta == 0.0 ? alpha * sum : alpha * sum + beta * *dst;
+}
+
 void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const View2& B, double alpha, double beta,
                  double* C, int64_t ldc, const int* skip) {
+    // short K and few 16 x 16 tiles: smaller tiles with K split inside the CTA
+    if (K < 128 && ((m + 15) / 16) * ((n + 15) / 16) < 152) {
+        if (!c.exec || m == 0 || n == 0) return;
+        const bool t8 = ((m + 7) / 8) * ((n + 7) / 8) >= 152;
+        const int T = t8 ? 8 : 4;
+        dim3 grid((unsigned)((m + T - 1) / T), (unsigned)((n + T - 1) / T));
+        ProfScope ps(c, "gemm_f64", 8.0 * (double)(m * ((n + T - 1) / T) + n * ((m + T - 1) / T)) * K + 8.0 * m * n,
+                     2.0 * m * n * K);
+        if (t8)
+            gemm_small_kernel<8><<<grid, 256, 0, c.stream>>>(m, n, K, A, B, alpha, beta, C, ldc, skip);
+        else
+            gemm_small_kernel<4><<<grid, 256, 0, c.stream>>>(m, n, K, A, B, alpha, beta, C, ldc, skip);
+        c.counted();
+        c.check_launch();
+        return;
+    }
     // 16 x 16 tiles; split K only when the tiles alone leave most SMs idle and
     // each split still has at least 64 terms.
     const int64_t tiles = ((m + 15) / 16) * ((n + 15) / 16);
