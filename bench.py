@@ -253,8 +253,10 @@ def profile_case(args):
         fn()
     torch.cuda.synchronize()
     T.tk_profile(True, dev)
+    torch.cuda.nvtx.range_push("profile_reps")  # lets ncu select exactly these repetitions
     for _ in range(5):
         fn()
+    torch.cuda.nvtx.range_pop()
     prof = T.tk_profile_read(dev)
     T.tk_profile(False, dev)
     hbm = _peaks()[0]

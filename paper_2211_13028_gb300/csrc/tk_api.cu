@@ -1312,7 +1312,10 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
                 if (i != j) K *= Gt.n[i];
             double* A1 = c.alloc<double>(nj * rj);
             double* B1 = c.alloc<double>(rj * rj);
-            gemm_nt_f64(c, nj, rj, K, view_unfold_rows(S[j], j), view_unfold_rows(G64, j), s2, 0.0, A1, nj);
+            // S_n carries the FP32 rounding of the sketch pass, far above double-float accumulation error,
+            // so for FP32 data this product (the largest of the gradient) runs on the FP32 pipe
+            gemm_nt_f64(c, nj, rj, K, view_unfold_rows(S[j], j), view_unfold_rows(Gt.dt == TK_F32 ? Gt : G64, j), s2,
+                        0.0, A1, nj, nullptr, true);
             gemm_nt_f64(c, rj, rj, K, view_unfold_rows(Pm[j], j), view_unfold_rows(G64, j), 1.0, 0.0, B1, rj);
             gemm_nt_f64(c, nj, rj, rj, view_rows(U64[j], TK_F64, nj), view_cols(B1, TK_F64, rj), -s2, 1.0, A1, nj);
             launch_convert(c, A1, TK_F64, nj, rj, nj, (void*)dUm[j].p, dUm[j].dt, dUm[j].ld, 1.f);

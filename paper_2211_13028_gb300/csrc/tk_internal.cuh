@@ -217,9 +217,11 @@ void launch_sum_pairs(const Ctx& c, const double* part, int nb, double* out2);
 
 // C = alpha * sum_t A(a, t) B(b, t) + beta * C, FP64, C column-major m x n (ldc).
 // A, B: View2 of F64 or F32 data.  Uses split-K partials in the workspace.
-// When skip is given and *skip != 0 the kernels return without work.
+// When skip is given and *skip != 0 the kernels return without work.  With
+// df_ok and both operands F32, products are accumulated as double-float pairs
+// on the FP32 pipe (~48 significant bits) instead of in FP64.
 void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const View2& B, double alpha,
-                 double beta, double* C, int64_t ldc, const int* skip = nullptr);
+                 double beta, double* C, int64_t ldc, const int* skip = nullptr, bool df_ok = false);
 
 struct KDims {
     int k[TK_MAX_D];

@@ -5,6 +5,8 @@
 #include <cuda_fp8.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "tk_internal.cuh"
 
 namespace tk {
@@ -246,7 +248,9 @@ __global__ void gemm_reduce_kernel(int64_t m, int64_t n, int nsplit, const doubl
 struct TileLoader {
     // element e in [0, 512) of a 16 x 32 (row x k) tile -> (row, k)
     bool kfast;
-    __device__ TileLoader(const View2& v) { kfast = (v.T1 == INT64_MAX && v.st1 == 1); }
+    // k contiguous within 32-aligned runs (plain columns, or an unfolding whose
+    // fastest contracted mode is a multiple of 32 long): warps read along k
+    __device__ TileLoader(const View2& v) { kfast = v.st1 == 1 && (v.T1 == INT64_MAX || v.T1 % 32 == 0); }
     __device__ __forceinline__ void rk(int e, int& r, int& kk) const {
         if (kfast) { r = e >> 5; kk = e & 31; }
         else { r = e & 15; kk = e >> 4; }
@@ -273,12 +277,45 @@ __device__ __forceinline__ double v2get(const View2& v, int64_t o) {
     return v.dt == TK_F64 ? static_cast<const double*>(v.p)[o] : (double)static_cast<const float*>(v.p)[o];
 }
 
+// (hi, lo) += (bh, bl) for normalised double-float pairs (Knuth two-sum on
+// the high parts, the low parts added into the error).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+    const float s = __fadd_rn(hi, bh);
+    const float v = __fadd_rn(s, -hi);
+    const float e0 = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -v)), __fadd_rn(bh, -v));  // hi + bh = s + e0 exactly
+    const float e = __fadd_rn(e0, __fadd_rn(lo, bl));
+    const float h2 = __fadd_rn(s, e);
+    lo = __fadd_rn(e, -__fadd_rn(h2, -s));
+    hi = h2;
+}
+
+// One step of the compensated dot product Dot2 (Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005): the product is split exactly
+// (p + e, e = fma(a, b, -p)), p is added to the running sum s with Knuth's
+// two-sum, and both rounding errors go into the correction c.  Only s + p is
+// on the loop-carried path; the result s + c is as accurate as a dot product
+// carried out in twice the working precision.
+__device__ __forceinline__ void dot2_step(float& s, float& c, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fadd_rn(t, -s);
+    const float q = __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -z)), __fadd_rn(p, -z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
+// DFACC: both operands hold FP32 values (FP32 data), and the products are
+// accumulated on the FP32 pipe with Dot2 (as accurate as about 48 significant
+// bits, several times the FP64 rate here); otherwise FP64 fma.
+template <bool DFACC>
 __global__ void __launch_bounds__(256) gemm_tile16_kernel(int64_t m, int64_t n, int64_t K, int64_t kchunk, View2 A,
                                                           View2 B, double alpha, double beta, double* C, int64_t ldc,
                                                           double* P, const int* skip) {
+    using E = typename std::conditional<DFACC, float, double>::type;
     if (skip && *skip) return;
-    __shared__ double As[32][17];
-    __shared__ double Bs[32][17];
+    __shared__ E As[32][17];
+    __shared__ E Bs[32][17];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int64_t a0 = (int64_t)blockIdx.x * 16, b0 = (int64_t)blockIdx.y * 16;
@@ -295,24 +332,30 @@ __global__ void __launch_bounds__(256) gemm_tile16_kernel(int64_t m, int64_t n, 
         ob[q] = b0 + rb[q] < n ? v2row(B, b0 + rb[q]) : -1;
     }
     double acc0 = 0.0, acc1 = 0.0;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
     for (int64_t k0 = kb; k0 < ke; k0 += 32) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int64_t k1 = k0 + ka[q], k2 = k0 + kb2[q];
-            As[ka[q]][ra[q]] = (oa[q] >= 0 && k1 < ke) ? v2get(A, oa[q] + v2col(A, k1)) : 0.0;
-            Bs[kb2[q]][rb[q]] = (ob[q] >= 0 && k2 < ke) ? v2get(B, ob[q] + v2col(B, k2)) : 0.0;
+            As[ka[q]][ra[q]] = (E)((oa[q] >= 0 && k1 < ke) ? v2get(A, oa[q] + v2col(A, k1)) : 0.0);
+            Bs[kb2[q]][rb[q]] = (E)((ob[q] >= 0 && k2 < ke) ? v2get(B, ob[q] + v2col(B, k2)) : 0.0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 32; kk += 2) {
-            acc0 = fma(As[kk][tx], Bs[kk][ty], acc0);
-            acc1 = fma(As[kk + 1][tx], Bs[kk + 1][ty], acc1);
+            if (DFACC) {
+                dot2_step(h0, l0, (float)As[kk][tx], (float)Bs[kk][ty]);
+                dot2_step(h1, l1, (float)As[kk + 1][tx], (float)Bs[kk + 1][ty]);
+            } else {
+                acc0 = fma((double)As[kk][tx], (double)Bs[kk][ty], acc0);
+                acc1 = fma((double)As[kk + 1][tx], (double)Bs[kk + 1][ty], acc1);
+            }
         }
         __syncthreads();
     }
     const int64_t a = a0 + tx, b = b0 + ty;
     if (a >= m || b >= n) return;
-    const double sum = acc0 + acc1;
+    const double sum = DFACC ? ((double)h0 + (double)l0) + ((double)h1 + (double)l1) : acc0 + acc1;
     if (P) {
         P[(int64_t)blockIdx.z * m * n + a + m * b] = sum;
     } else {
@@ -337,7 +380,8 @@ __global__ void __launch_bounds__(256) gemm_small_kernel(int64_t m, int64_t n, i
     const int tid = threadIdx.x, o = tid % (T * T), g = tid / (T * T);
     const int tx = o % T, ty = o / T;
     const int64_t a0 = (int64_t)blockIdx.x * T, b0 = (int64_t)blockIdx.y * T;
-    const bool akf = (A.T1 == INT64_MAX && A.st1 == 1), bkf = (B.T1 == INT64_MAX && B.st1 == 1);
+    const bool akf = A.st1 == 1 && (A.T1 == INT64_MAX || A.T1 % 32 == 0);
+    const bool bkf = B.st1 == 1 && (B.T1 == INT64_MAX || B.T1 % 32 == 0);
     double acc = 0.0;
     for (int64_t k0 = 0; k0 < K; k0 += 32) {
         for (int e = tid; e < 64 * T; e += 256) {
@@ -371,9 +415,11 @@ __global__ void __launch_bounds__(256) gemm_small_kernel(int64_t m, int64_t n, i
 }
 
 void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const View2& B, double alpha, double beta,
-                 double* C, int64_t ldc, const int* skip) {
+                 double* C, int64_t ldc, const int* skip, bool df_ok) {
+    // double-float accumulation only where the caller allows it and both operands are FP32
+    const bool df = df_ok && A.dt == TK_F32 && B.dt == TK_F32;
     // short K and few 16 x 16 tiles: smaller tiles with K split inside the CTA
-    if (K < 128 && ((m + 15) / 16) * ((n + 15) / 16) < 152) {
+    if (!df && K < 128 && ((m + 15) / 16) * ((n + 15) / 16) < 152) {
         if (!c.exec || m == 0 || n == 0) return;
         const bool t8 = ((m + 7) / 8) * ((n + 7) / 8) >= 152;
         const int T = t8 ? 8 : 4;
@@ -403,9 +449,13 @@ void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const 
     if (!c.exec || m == 0 || n == 0) return;
     dim3 grid((unsigned)((m + 15) / 16), (unsigned)((n + 15) / 16), (unsigned)nsplit);
     {
-        ProfScope ps(c, "gemm_f64", 8.0 * (double)(m * ((n + 15) / 16) + n * ((m + 15) / 16)) * K + 8.0 * m * n * nsplit,
+        ProfScope ps(c, df ? "gemm_df" : "gemm_f64",
+                     8.0 * (double)(m * ((n + 15) / 16) + n * ((m + 15) / 16)) * K + 8.0 * m * n * nsplit,
                      2.0 * m * n * K);
-        gemm_tile16_kernel<<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, skip);
+        if (df)
+            gemm_tile16_kernel<true><<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, skip);
+        else
+            gemm_tile16_kernel<false><<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, skip);
         c.counted();
         c.check_launch();
     }
@@ -836,17 +886,6 @@ void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int
 
 constexpr int JM_MAX_THREADS = 1024;
 constexpr int JM_BPT = 2;  // blocks per update thread: h (h + 1) / 2 <= 2 * 992 for h <= 56
-
-// (hi, lo) += (bh, bl) for normalised double-float pairs.
-__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
-    const float s = __fadd_rn(hi, bh);
-    const float v = __fadd_rn(s, -hi);
-    const float e0 = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -v)), __fadd_rn(bh, -v));  // hi + bh = s + e0 exactly
-    const float e = __fadd_rn(e0, __fadd_rn(lo, bl));
-    const float h2 = __fadd_rn(s, e);
-    lo = __fadd_rn(e, -__fadd_rn(h2, -s));
-    hi = h2;
-}
 
 // The slot an entry at slot x moves to after a step (h = kp / 2 pairs).
 __device__ __forceinline__ int jm_pi(int x, int h) {
