@@ -150,7 +150,9 @@ static Tens ttm_to(Ctx& c, const Tens& T, int j, const Mat& M, bool mtrans, tk_d
     o.dt = acc;
     o.scale = 1.f;
     o.p = dst ? dst : c.alloc_bytes(dtype_size(acc) * o.numel());
-    if (c.use_tc && ttm_tc_eligible(T, j, m, acc))
+    if (c.use_tc && ttm_narrow_eligible(T, j, m, acc) && reinterpret_cast<uintptr_t>(o.p) % 16 == 0)
+        launch_ttm_narrow(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
+    else if (c.use_tc && ttm_tc_eligible(T, j, m, acc))
         launch_ttm_tc(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
     else if (c.use_tc && ttm_bf16_eligible(T, j, m, acc))
         launch_ttm_bf16(c, T, j, M, mtrans, m, static_cast<float*>(o.p));

@@ -1,0 +1,278 @@
+// Narrow TTMs that stream FP32 data: out = X x_j M^T with at most 8 output
+// columns (the widths of the Kronecker sketch factors).  At that width each
+// element needs 8 fused multiply-adds, well inside the FP32 pipe at HBM rate,
+// so the data is streamed by TMA into a ring of shared-memory stages (as the
+// tensor-core kernels do; the registers of a plain SIMT kernel cannot keep
+// enough bytes in flight) and consumed by FP32 FMA warps, with M held in
+// shared memory for the whole pass.  FP32 accumulation, as in the tensor-core
+// path, whose tf32 instruction count at this width would bound the pass.
+//
+// Work item: one tile of 128 rows (the same tiling and TMA boxes as the
+// tensor-core kernels).  Warp 0 issues the TMA loads; warps 1..4 consume, in
+// two groups of 2 that take alternate chunks (so two chunks are in work at
+// once): thread (q, kh) of a group sums K-columns [16 kh, 16 kh + 16) of its
+// chunks for the four rows q, q + 32, q + 64, q + 96, so that each row of M
+// read from shared memory (a broadcast, four wavefronts per 16-byte load)
+// serves four rows of X: the shared-memory pipe, not the FMA pipe, is what a
+// narrow pass exhausts first.  The four partial sums of a row are added
+// through shared memory at the end of the item.  Every wait is bounded (the
+// abort protocol of the tensor-core kernels); on a timeout the consumers keep
+// their control flow (so that the named barriers still match) and skip the
+// arithmetic.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "tk_internal.cuh"
+#include "tk_tc_common.cuh"
+
+namespace tk {
+namespace tc {
+
+constexpr int FS_COLS = 8;                       // output columns (zero-padded)
+constexpr int FS_GROUP = 2;                      // consumer warps per group (32 row quads x 2 K halves)
+constexpr int FS_CONS = 2 * FS_GROUP;            // consumer warps
+constexpr int FS_THREADS = 32 * (1 + FS_CONS);
+// X bytes in flight per SM are what bounds a streaming pass here (loaded HBM
+// latency is several microseconds), so the ring takes all the shared memory
+// that M and the partial sums leave: 12 stages of 16 KB.
+constexpr int FS_STAGES = 12;
+constexpr int FS_ROWS = 128;                     // tile rows
+constexpr int FS_CHUNK = 32;                     // K columns per stage
+constexpr int FS_XBYTES = FS_ROWS * FS_CHUNK * 4;
+constexpr int FS_MAX_NJ = 512;                   // M rows held in shared memory
+
+struct FsArgs {
+    int64_t L, nj, R, m;
+    int64_t ntiles, tiles_per_r, nk;
+    const float* M;
+    int64_t ldm;
+    int mtrans;
+    float* out;
+    unsigned* flags;
+};
+
+inline size_t fs_smem(int64_t nk) {
+    return 1024 + (size_t)FS_STAGES * FS_XBYTES + sizeof(float) * (size_t)nk * FS_CHUNK * FS_COLS +
+           sizeof(float) * 3 * FS_ROWS * FS_COLS + sizeof(uint64_t) * (2 * FS_STAGES + 1);
+}
+
+template <bool KMAJOR>
+__global__ void __launch_bounds__(FS_THREADS, 1)
+    ttm_fma_stream_kernel(const __grid_constant__ CUtensorMap tmX, FsArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int64_t nk = args.nk;
+    float* msm = reinterpret_cast<float*>(smem + FS_STAGES * FS_XBYTES);  // M(i, a), nk * 32 rows x 8
+    float* red = msm + nk * FS_CHUNK * FS_COLS;  // [3][row][col]: the partial sums other than (group 0, half 0)
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + 3 * FS_ROWS * FS_COLS);
+    uint64_t* xfree = full + FS_STAGES;
+    volatile int* abort = reinterpret_cast<volatile int*>(xfree + FS_STAGES);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int64_t e = tid; e < nk * FS_CHUNK * FS_COLS; e += blockDim.x) {
+        const int64_t i = e / FS_COLS, a = e % FS_COLS;
+        msm[e] = (i < args.nj && a < args.m) ? (args.mtrans ? args.M[a + args.ldm * i] : args.M[i + args.ldm * a])
+                                             : 0.f;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < FS_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&xfree[s], FS_GROUP);
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned* flags = args.flags;
+    const int64_t nitems = args.ntiles;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+                int64_t r0 = 0, l0 = 0, rr = 0;
+                if (KMAJOR) {
+                    r0 = t * FS_ROWS;
+                } else {
+                    rr = t / args.tiles_per_r;
+                    l0 = (t % args.tiles_per_r) * FS_ROWS;
+                }
+                for (int64_t kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = (int)(it % FS_STAGES);
+                    if (!mbar_wait(&xfree[s], (uint32_t)(((it / FS_STAGES) & 1) ^ 1), abort, flags)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* xs = smem + s * FS_XBYTES;
+                    mbar_expect_tx(&full[s], FS_XBYTES);
+                    if (KMAJOR)
+                        tma_load_2d(xs, &tmX, (int)(kc * FS_CHUNK), (int)r0, &full[s]);
+                    else
+                        tma_load_3d(xs, &tmX, (int)l0, (int)(kc * FS_CHUNK), (int)rr, &full[s]);
+                }
+            }
+            // drain: every issued load has landed before the CTA can exit
+            const int64_t n_out = it < FS_STAGES ? it : FS_STAGES;
+            for (int64_t q = it - n_out; q < it; ++q) {
+                const uint64_t t0 = gtimer();
+                while (!mbar_try_wait(&full[q % FS_STAGES], (uint32_t)((q / FS_STAGES) & 1)) &&
+                       gtimer() - t0 < kTimeoutNs) {
+                }
+            }
+        }
+        return;
+    }
+    // ------------------------------------------------ FMA consumers
+    const int ct = tid - 32, q = ct & 31, kh = (ct >> 5) & 1, grp = ct >> 6;
+    const float4* m4 = reinterpret_cast<const float4*>(msm);
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
+        float acc[4][FS_COLS];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int a = 0; a < FS_COLS; ++a) acc[u][a] = 0.f;
+        for (int64_t kc = 0; kc < nk; ++kc, ++it) {
+            if ((int)(it & 1) != grp) continue;
+            const int s = (int)(it % FS_STAGES);
+            const bool got = mbar_wait_warp(&full[s], (uint32_t)((it / FS_STAGES) & 1), abort, flags);
+            if (got) {
+                const uint8_t* xs = smem + s * FS_XBYTES;
+                const float4* mrow = m4 + (kc * FS_CHUNK + 16 * kh) * 2;
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {  // four K columns at a time
+                    float v[4][4];                 // [row u][k]
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rho = q + 32 * u;
+                        if (KMAJOR) {
+                            // row rho: 128 B, 16-byte chunk j stored at chunk j ^ (rho & 7)
+                            const int j = 4 * kh + k4;
+                            const float4 f =
+                                *reinterpret_cast<const float4*>(xs + rho * 128 + ((j ^ (rho & 7)) << 4));
+                            v[u][0] = f.x;
+                            v[u][1] = f.y;
+                            v[u][2] = f.z;
+                            v[u][3] = f.w;
+                        } else {
+                            // rows i of 128 floats (512 B): lanes read consecutive words
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                v[u][kk] = reinterpret_cast<const float*>(xs)[(16 * kh + 4 * k4 + kk) * FS_ROWS + rho];
+                        }
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const float4 ma = mrow[2 * (4 * k4 + kk)], mb = mrow[2 * (4 * k4 + kk) + 1];
+                        const float mv[FS_COLS] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+#pragma unroll
+                            for (int a = 0; a < FS_COLS; ++a) acc[u][a] = fmaf(v[u][kk], mv[a], acc[u][a]);
+                    }
+                }
+            }
+            __syncwarp();  // the warp's reads of the stage are done before lane 0 releases it
+            if (lane == 0) mbar_arrive(&xfree[s]);
+        }
+        // add the four partial sums, then store the rows
+        const int part = 2 * grp + kh;  // 0: (group 0, half 0) ... 3
+        if (part != 0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int a = 0; a < FS_COLS; ++a) red[((part - 1) * FS_ROWS + q + 32 * u) * FS_COLS + a] = acc[u][a];
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * FS_CONS) : "memory");
+        if (part == 0 && !*abort) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int rho = q + 32 * u;
+                int64_t base, stride;
+                bool valid;
+                if (KMAJOR) {
+                    const int64_t r = t * FS_ROWS + rho;
+                    valid = r < args.R;
+                    base = r * args.m;
+                    stride = 1;
+                } else {
+                    const int64_t rr = t / args.tiles_per_r;
+                    const int64_t l = (t % args.tiles_per_r) * FS_ROWS + rho;
+                    valid = l < args.L;
+                    base = l + args.L * args.m * rr;
+                    stride = args.L;
+                }
+                if (valid) {
+#pragma unroll
+                    for (int a = 0; a < FS_COLS; ++a)
+                        if (a < args.m)
+                            args.out[base + a * stride] = (acc[u][a] + red[rho * FS_COLS + a]) +
+                                                          (red[(FS_ROWS + rho) * FS_COLS + a] +
+                                                           red[(2 * FS_ROWS + rho) * FS_COLS + a]);
+                }
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * FS_CONS) : "memory");
+    }
+}
+
+}  // namespace tc
+
+bool ttm_narrow_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt) {
+    if (X.dt != TK_F32 || out_dt != TK_F32 || m < 1 || m > tc::FS_COLS) return false;
+    const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
+    if (nj < 1 || nj > tc::FS_MAX_NJ || L * nj * R < (1 << 22)) return false;  // small tensors: the general kernels
+    if (reinterpret_cast<uintptr_t>(X.p) % 16) return false;
+    // TMA: global strides are multiples of 16 bytes
+    return L == 1 ? nj % 4 == 0 : L % 4 == 0;
+}
+
+void launch_ttm_narrow(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out) {
+    if (!c.exec) return;
+    TK_REQUIRE(M.dt == TK_F32, TK_ERR_DTYPE, "narrow ttm: F32 matrix");
+    const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
+    const bool kmajor = (L == 1);
+    CUtensorMap tx;
+    if (kmajor) {
+        uint64_t dims[2] = {(uint64_t)nj, (uint64_t)R};
+        uint64_t str[1] = {(uint64_t)nj * 4};
+        uint32_t box[2] = {tc::FS_CHUNK, tc::FS_ROWS};
+        tc::encode(&tx, X.p, 2, dims, str, box);
+    } else {
+        uint64_t dims[3] = {(uint64_t)L, (uint64_t)nj, (uint64_t)R};
+        uint64_t str[2] = {(uint64_t)L * 4, (uint64_t)L * nj * 4};
+        uint32_t box[3] = {tc::FS_ROWS, tc::FS_CHUNK, 1};
+        tc::encode(&tx, X.p, 3, dims, str, box, false);
+    }
+    tc::FsArgs a;
+    a.L = L;
+    a.nj = nj;
+    a.R = R;
+    a.m = m;
+    a.nk = (nj + tc::FS_CHUNK - 1) / tc::FS_CHUNK;
+    a.tiles_per_r = kmajor ? 1 : (L + tc::FS_ROWS - 1) / tc::FS_ROWS;
+    a.ntiles = kmajor ? (R + tc::FS_ROWS - 1) / tc::FS_ROWS : R * a.tiles_per_r;
+    a.M = static_cast<const float*>(M.p);
+    a.ldm = M.ld;
+    a.mtrans = mtrans ? 1 : 0;
+    a.out = out;
+    a.flags = c.dflags;
+    const size_t smem = tc::fs_smem(a.nk);
+    const char* name = (const void*)X.p == c.xdata ? "xpass_narrow" : "ttm_narrow";
+    ProfScope ps(c, name, 4.0 * (double)L * nj * R + 4.0 * (double)L * m * R + 4.0 * nj * m, 2.0 * L * nj * R * m);
+    const int grid = (int)std::min<int64_t>(a.ntiles, tc::num_sms());
+    if (kmajor) {
+        TK_CUDA(cudaFuncSetAttribute(tc::ttm_fma_stream_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        tc::ttm_fma_stream_kernel<true><<<grid, tc::FS_THREADS, smem, c.stream>>>(tx, a);
+    } else {
+        TK_CUDA(cudaFuncSetAttribute(tc::ttm_fma_stream_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        tc::ttm_fma_stream_kernel<false><<<grid, tc::FS_THREADS, smem, c.stream>>>(tx, a);
+    }
+    c.counted();
+    c.check_launch();
+}
+
+}  // namespace tk

@@ -202,6 +202,10 @@ bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
 void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 // BF16 data: tcgen05 kind::f16 with A straight from shared memory and the
 // factor split into BF16 hi + lo (FP32 output).
+// Narrow TTMs (m <= 8 output columns) on large FP32 data: a TMA-fed FP32 FMA
+// streaming kernel (the tensor-core kernels' tiling; tk_fma_stream.cu).
+bool ttm_narrow_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
+void launch_ttm_narrow(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 bool ttm_bf16_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
 void launch_ttm_bf16(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 // Fused last step of a reconstruction: P = W x_j M^T is formed tile by tile and

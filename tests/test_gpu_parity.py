@@ -40,6 +40,22 @@ def test_sketch_parity(dev, dtype, dims, s):
         assert rel(to_np(Y[n]), ref) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("dims,s", [((192, 160, 200), (6, 7, 8)), ((190, 171, 160), (5, 8, 3)), ((256, 64, 300), (1, 8, 7))])
+def test_sketch_parity_streaming_fp32(dev, dims, s):
+    # FP32 tensors above 4M elements with sketch widths <= 8: the FP32 streaming kernels
+    # (strided contracted mode with L % 4 == 0, or contiguous); dims (190, ...) also take the
+    # tensor-core path where L % 4 != 0.  Each sampled entry against the FP64 oracle.
+    g = _rng(11)
+    X, xv, sc = make_X(g.standard_normal(dims), "f32", dev)
+    oms = synth.sketch_factors_reuse(dims, s, seed=12, dtype="f32")
+    Y = T.tucker_sketch(X, mats(oms, "f32", dev), scale=sc)
+    d = len(dims)
+    for n in range(d):
+        ref = O.multi_ttm(xv, [(j, oms[j].T) for j in range(d) if j != n])
+        assert tuple(Y[n].shape) == ref.shape
+        assert rel(to_np(Y[n]), ref) <= TOL["f32"]
+
+
 def test_sketch_matches_explicit_kronecker(dev):
     # Y_n(n) = X_(n) Omega_n with the Kronecker product formed explicitly (Section 4.2 identity).
     g = _rng(3)
