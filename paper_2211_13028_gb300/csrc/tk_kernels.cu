@@ -169,10 +169,60 @@ __global__ void __launch_bounds__(256) ttm_direct_kernel(const Tx* __restrict__ 
     out[o] = s;
 }
 
+// Few outputs per slab, long contraction (L m <= 256, e.g. the second product
+// of a sketch, 6 x 512 x 512 -> 6 x 7 x 512, or a core TTM along its first
+// mode): a CTA per r stages the slab X[:, :, r] in shared memory with
+// coalesced loads and splits each of the L m dot products over S threads,
+// summed in shared memory.  A thread per output would walk X with stride L
+// and leave most SMs idle.
+constexpr int SLAB_THREADS = 256;
+
+template <typename Tx, typename Ta>
+__global__ void __launch_bounds__(SLAB_THREADS) ttm_slab_kernel(const Tx* __restrict__ X, int64_t L, int64_t nj,
+                                                                int64_t R, const Ta* __restrict__ M, int64_t ldm,
+                                                                int mtrans, int64_t m, int S, Ta* __restrict__ out,
+                                                                Ta xinv) {
+    extern __shared__ __align__(16) unsigned char slab_raw[];
+    Ta* xs = reinterpret_cast<Ta*>(slab_raw);  // L x nj, X[l, i] at xs[l + L i]
+    Ta* part = xs + L * nj;                    // S x (L m) partial sums
+    const int64_t r = blockIdx.x;
+    const Tx* x = X + L * nj * r;
+    for (int64_t e = threadIdx.x; e < L * nj; e += blockDim.x) xs[e] = ldx(x, e, xinv);
+    __syncthreads();
+    const int64_t T = L * m;
+    const int64_t task = threadIdx.x % T, sp = threadIdx.x / T;
+    if (sp < S) {
+        const int64_t l = task % L, a = task / L;
+        const int64_t i0 = nj * sp / S, i1 = nj * (sp + 1) / S;
+        Ta acc = Ta(0);
+        for (int64_t i = i0; i < i1; ++i) acc += (mtrans ? M[a + ldm * i] : M[i + ldm * a]) * xs[l + L * i];
+        part[sp * T + task] = acc;
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < T; t += blockDim.x) {
+        Ta v = Ta(0);
+        for (int q = 0; q < S; ++q) v += part[q * T + t];
+        const int64_t l = t % L, a = t / L;
+        out[l + L * (a + m * r)] = v;
+    }
+}
+
 template <typename Tx, typename Ta>
 static void ttm_dispatch(const Ctx& c, const Tx* X, int64_t L, int64_t nj, int64_t R, const Ta* M, int64_t ldm,
                          bool mtrans, int64_t m, Ta* out, Ta xinv) {
     int64_t rows = L * R;
+    if (L * m <= SLAB_THREADS && nj >= 32 && (double)sizeof(Ta) * (L * nj + SLAB_THREADS) <= 40 * 1024 &&
+        R <= 0x7fffffff) {
+        const int S = (int)std::min<int64_t>(16, SLAB_THREADS / (L * m));
+        const size_t smem = sizeof(Ta) * (size_t)(L * nj + (int64_t)S * L * m);
+        const char* name = (const void*)X == c.xdata ? "xpass_simt" : "ttm_simt";
+        ProfScope ps(c, name, (double)rows * nj * sizeof(Tx) + (double)rows * m * sizeof(Ta), 2.0 * rows * nj * m);
+        ttm_slab_kernel<Tx, Ta><<<(unsigned)R, SLAB_THREADS, smem, c.stream>>>(X, L, nj, R, M, ldm, mtrans ? 1 : 0, m,
+                                                                               S, out, xinv);
+        c.counted();
+        c.check_launch();
+        return;
+    }
     if (rows * m <= (1 << 21) && nj <= 512) {
         const char* name = (const void*)X == c.xdata ? "xpass_simt" : "ttm_simt";
         ProfScope ps(c, name, (double)rows * nj * sizeof(Tx) + (double)rows * m * sizeof(Ta), 2.0 * rows * nj * m);
