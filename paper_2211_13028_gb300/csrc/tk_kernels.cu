@@ -956,9 +956,12 @@ __device__ __forceinline__ int jm_pi_inv(int y, int h) {
 __device__ __forceinline__ int jm_tri(int i, int j, int ld) { return i < j ? i * ld + j : j * ld + i; }
 
 // Rotation annihilating the (p, q) entry f against the diagonal (p: hp + lp,
-// q: hq + lq): the smaller root t = sgn(phi) psi / (|phi| + sqrt(phi^2 +
-// psi^2)) of t^2 + 2 t phi / psi - 1 = 0 (phi = a_qq - a_pp, psi = 2 a_pq),
-// c = 1 / sqrt(1 + t^2), s = t c; the diagonal moves by -+ t f.  Fast FP32
+// q: hq + lq), with phi = a_qq - a_pp, psi = 2 a_pq, rho = sqrt(phi^2 +
+// psi^2): the tangent is the smaller root t = sgn(phi) psi / (|phi| + rho) of
+// t^2 + 2 t phi / psi - 1 = 0 and the diagonal moves by -+ t f; (c, s) come
+// from the half angle, cos 2a = |phi| / rho, c = sqrt((1 + cos 2a) / 2),
+// s = sin 2a / (2 c) = sgn(phi) f / (rho c), so that t and (c, s) each sit two
+// special-function latencies after rho instead of c waiting on t.  Fast FP32
 // reciprocals and square roots suffice (the off-diagonal is zeroed explicitly
 // and convergence is measured).  Returns whether it rotates.
 template <bool DF>
@@ -970,9 +973,12 @@ __device__ __forceinline__ int jm_rotate(float f, float fthr, bool allow, float&
     if (DF) phi += lq - lp;
     const float psi = 2.f * f;
     const float r2 = fmaxf(fmaf(phi, phi, psi * psi), 1e-37f);
-    const float t = __fdividef(phi >= 0.f ? psi : -psi, fabsf(phi) + r2 * rsqrtf(r2));
-    const float c = rsqrtf(fmaf(t, t, 1.f));
-    cs = make_float2(c, t * c);
+    const float u = rsqrtf(r2);  // 1 / rho
+    const float aphi = fabsf(phi);
+    const float t = __fdividef(phi >= 0.f ? psi : -psi, aphi + r2 * u);
+    const float x = fmaf(0.5f * aphi, u, 0.5f);  // (1 + cos 2a) / 2, in [1/2, 1]
+    const float w = rsqrtf(x);
+    cs = make_float2(x * w, (phi >= 0.f ? f : -f) * u * w);
     if (DF) {
         const float ph = __fmul_rn(t, f);
         const float pl = fmaf(t, f, -ph);  // t f = ph + pl exactly
@@ -1039,8 +1045,7 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
     float* Hx = Hc + kp;
     float* Lc = Hx + kp;                          // diagonal (low part) per slot
     float* Lx = Lc + kp;
-    int* Ic = reinterpret_cast<int*>(Lx + kp);    // index label per slot
-    int* Ix = Ic + kp;
+    int* lab = reinterpret_cast<int*>(Lx + kp);   // final index label per slot (after the sweeps)
     __shared__ float2 meta[2][64];  // (c, s) per pair of the current / next step
     __shared__ double red[33];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
@@ -1060,7 +1065,6 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
             const float hv = (float)v;
             Hc[i] = hv;
             Lc[i] = DF ? (float)(v - (double)hv) : 0.f;
-            Ic[i] = i;
         }
     }
     const float fthr = (float)(tol * nrm * sc);
@@ -1096,7 +1100,7 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
     const bool has0 = rwarp && lane < h, has1 = rwarp && lane + 32 < h;
     JmPivot pv0 = jm_pivot_source(has0 ? lane : 0, h, ld), pv1 = jm_pivot_source(has1 ? lane + 32 : 0, h, ld);
     __syncthreads();
-    const int64_t total = (int64_t)max_sweeps * m;  // steps allowed
+    const int total = max_sweeps * m;  // steps allowed (the launcher bounds it)
     int any = 0;
     if (total > 0 && rwarp) {  // the first step's rotations, in place
 #pragma unroll
@@ -1118,7 +1122,8 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
     int active = __syncthreads_or(any);  // whether the current step rotates anything
     int cur = 0, steps = 0, s = 0, idle = 0;
     bool converged = false;
-    for (int64_t g = 0; g < total; ++g) {
+    float2* lg = rlog + h;  // the next step's log slot
+    for (int g = 0; g < total; ++g, lg += h) {
         if (s == 0) {
             int off = 0;
             for (int a = tid >> 5; a < kp; a += nt >> 5)
@@ -1138,7 +1143,6 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
         if (rwarp) {
             const bool want = g + 1 < total;
             float2* mn = meta[cur ^ 1];
-            float2* lg = rlog + (g + 1) * h;
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
                 if (!(o ? has1 : has0)) continue;
@@ -1149,7 +1153,6 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
                     lp = Lc[pv.sp];
                     lq = Lc[pv.sq];
                 }
-                const int ip = Ic[pv.sp], iq = Ic[pv.sq];
                 const float f = jm_pivot_value(pv, Fc, mc, ld);
                 float2 cs;
                 any |= jm_rotate<DF>(f, fthr, want, hp, lp, hq, lq, cs);
@@ -1159,8 +1162,6 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
                     Lx[2 * tp] = lp;
                     Lx[2 * tp + 1] = lq;
                 }
-                Ix[2 * tp] = ip;
-                Ix[2 * tp + 1] = iq;
                 mn[tp] = cs;
                 lg[tp] = cs;
             }
@@ -1190,7 +1191,6 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
         x = Fc; Fc = Fx; Fx = x;
         x = Hc; Hc = Hx; Hx = x;
         x = Lc; Lc = Lx; Lx = x;
-        int* y = Ic; Ic = Ix; Ix = y;
         cur ^= 1;
         ++steps;
         s = (s + 1 == m) ? 0 : s + 1;
@@ -1203,8 +1203,30 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
         converged = !__syncthreads_or(off);
     }
     if (!converged && tid == 0) atomicOr(flags, FLAG_NOT_CONVERGED);
+    // index labels: after `steps` moves slot x holds the index that started in
+    // slot pi^{-steps}(x); slots 1..kp-1 form one cycle of pi, walked once
+    if (tid == 0) {
+        lab[0] = 0;
+        if (m > 0) {
+            int* cyc = reinterpret_cast<int*>(Fx);  // the spare F buffer: cycle order, then positions
+            int* pos = cyc + kp;
+            int x = 1;
+            for (int j = 0; j < m; ++j) {
+                cyc[j] = x;
+                pos[x] = j;
+                x = jm_pi(x, h);
+            }
+            const int sh = steps % m;
+            for (int y = 1; y < kp; ++y) {
+                int j = pos[y] - sh;
+                if (j < 0) j += m;
+                lab[y] = cyc[j];
+            }
+        }
+    }
+    __syncthreads();
     for (int x = tid; x < kp; x += nt) {
-        const int i = Ic[x];
+        const int i = lab[x];
         if (i < k) Dout[i] = ((double)Hc[x] + (DF ? (double)Lc[x] : 0.0)) / sc;
         ginfo[1 + x] = i;
     }
@@ -1295,7 +1317,8 @@ __global__ void __launch_bounds__(JR_WARPS * 32) jacobi_replay_kernel(int k, con
 void launch_jacobi_mixed(Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
                          double tol, int max_sweeps, bool fp64_diag) {
     TK_REQUIRE(k >= 1 && k <= 112, TK_ERR_SHAPE, "jacobi_mixed: 1 <= k <= 112");
-    TK_REQUIRE(max_sweeps >= 0, TK_ERR_ARG, "jacobi_mixed: max_sweeps >= 0");
+    TK_REQUIRE(max_sweeps >= 0 && (int64_t)max_sweeps * (k + 1) < (1 << 30), TK_ERR_ARG,
+               "jacobi_mixed: 0 <= max_sweeps and max_sweeps * k below 2^30");
     const int64_t kp = k + (k & 1), h = kp / 2, nblk = h * (h + 1) / 2;
     float2* rlog = c.alloc<float2>(((int64_t)max_sweeps * (kp - 1) + 1) * h);
     int* ginfo = c.alloc<int>(1 + kp);
