@@ -8,13 +8,13 @@
 // path, whose tf32 instruction count at this width would bound the pass.
 //
 // Work item: one tile of 128 rows (the same tiling and TMA boxes as the
-// tensor-core kernels).  Warp 0 issues the TMA loads; warps 1..4 consume, in
-// two groups of 2 that take alternate chunks (so two chunks are in work at
+// tensor-core kernels).  Warp 0 issues the TMA loads; warps 1..8 consume, in
+// four groups of 2 that take every fourth chunk (so four chunks are in work at
 // once): thread (q, kh) of a group sums K-columns [16 kh, 16 kh + 16) of its
 // chunks for the four rows q, q + 32, q + 64, q + 96, so that each row of M
 // read from shared memory (a broadcast, four wavefronts per 16-byte load)
 // serves four rows of X: the shared-memory pipe, not the FMA pipe, is what a
-// narrow pass exhausts first.  The four partial sums of a row are added
+// narrow pass exhausts first.  The eight partial sums of a row are added
 // through shared memory at the end of the item.  Every wait is bounded (the
 // abort protocol of the tensor-core kernels); on a timeout the consumers keep
 // their control flow (so that the named barriers still match) and skip the
@@ -30,12 +30,14 @@ namespace tc {
 
 constexpr int FS_COLS = 8;                       // output columns (zero-padded)
 constexpr int FS_GROUP = 2;                      // consumer warps per group (32 row quads x 2 K halves)
-constexpr int FS_CONS = 2 * FS_GROUP;            // consumer warps
+constexpr int FS_NGRP = 4;                       // groups, taking chunks in turn
+constexpr int FS_PARTS = 2 * FS_NGRP;            // partial sums per row
+constexpr int FS_CONS = FS_NGRP * FS_GROUP;      // consumer warps
 constexpr int FS_THREADS = 32 * (1 + FS_CONS);
 // X bytes in flight per SM are what bounds a streaming pass here (loaded HBM
-// latency is several microseconds), so the ring takes all the shared memory
-// that M and the partial sums leave: 12 stages of 16 KB.
-constexpr int FS_STAGES = 12;
+// latency is several microseconds), so the ring takes the shared memory that
+// M and the partial sums leave: 11 stages of 16 KB.
+constexpr int FS_STAGES = 11;
 constexpr int FS_ROWS = 128;                     // tile rows
 constexpr int FS_CHUNK = 32;                     // K columns per stage
 constexpr int FS_XBYTES = FS_ROWS * FS_CHUNK * 4;
@@ -53,7 +55,7 @@ struct FsArgs {
 
 inline size_t fs_smem(int64_t nk) {
     return 1024 + (size_t)FS_STAGES * FS_XBYTES + sizeof(float) * (size_t)nk * FS_CHUNK * FS_COLS +
-           sizeof(float) * 3 * FS_ROWS * FS_COLS + sizeof(uint64_t) * (2 * FS_STAGES + 1);
+           sizeof(float) * (FS_PARTS - 1) * FS_ROWS * FS_COLS + sizeof(uint64_t) * (2 * FS_STAGES + 1);
 }
 
 template <bool KMAJOR>
@@ -63,8 +65,8 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int64_t nk = args.nk;
     float* msm = reinterpret_cast<float*>(smem + FS_STAGES * FS_XBYTES);  // M(i, a), nk * 32 rows x 8
-    float* red = msm + nk * FS_CHUNK * FS_COLS;  // [3][row][col]: the partial sums other than (group 0, half 0)
-    uint64_t* full = reinterpret_cast<uint64_t*>(red + 3 * FS_ROWS * FS_COLS);
+    float* red = msm + nk * FS_CHUNK * FS_COLS;  // [part - 1][row][col]: the partial sums but (group 0, half 0)
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + (FS_PARTS - 1) * FS_ROWS * FS_COLS);
     uint64_t* xfree = full + FS_STAGES;
     volatile int* abort = reinterpret_cast<volatile int*>(xfree + FS_STAGES);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
 #pragma unroll
             for (int a = 0; a < FS_COLS; ++a) acc[u][a] = 0.f;
         for (int64_t kc = 0; kc < nk; ++kc, ++it) {
-            if ((int)(it & 1) != grp) continue;
+            if ((int)(it % FS_NGRP) != grp) continue;
             const int s = (int)(it % FS_STAGES);
             const bool got = mbar_wait_warp(&full[s], (uint32_t)((it / FS_STAGES) & 1), abort, flags);
             if (got) {
@@ -176,8 +178,8 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
             __syncwarp();  // the warp's reads of the stage are done before lane 0 releases it
             if (lane == 0) mbar_arrive(&xfree[s]);
         }
-        // add the four partial sums, then store the rows
-        const int part = 2 * grp + kh;  // 0: (group 0, half 0) ... 3
+        // add the partial sums, then store the rows
+        const int part = 2 * grp + kh;  // 0: (group 0, half 0) ... FS_PARTS - 1
         if (part != 0) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -206,10 +208,12 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
                 if (valid) {
 #pragma unroll
                     for (int a = 0; a < FS_COLS; ++a)
-                        if (a < args.m)
-                            args.out[base + a * stride] = (acc[u][a] + red[rho * FS_COLS + a]) +
-                                                          (red[(FS_ROWS + rho) * FS_COLS + a] +
-                                                           red[(2 * FS_ROWS + rho) * FS_COLS + a]);
+                        if (a < args.m) {
+                            float v = acc[u][a];
+#pragma unroll
+                            for (int pp = 1; pp < FS_PARTS; ++pp) v += red[((pp - 1) * FS_ROWS + rho) * FS_COLS + a];
+                            args.out[base + a * stride] = v;
+                        }
                 }
             }
         }
