@@ -44,10 +44,11 @@ KERNEL_NAMES = {
     "ttm_tc": "ttm_tf32x3_kernel on intermediates",
 }
 # DRAM traffic / algorithmic bytes of one X-streaming launch, from an ncu capture of a 384^3 FP32
-# mode-3 sketch pass (231.4 MB moved for 230.0 MB of algorithmic bytes; summarised under
-# profiles/); traffic scales with the elements streamed.
-TRAFFIC_RATIO = {"xpass_tc": 231.4 / 230.0}
-TRAFFIC_NOTE = {"xpass_tc": "algorithmic bytes per launch x 1.006, the DRAM/algorithmic ratio of a 384^3 capture"}
+# core pass (243.0 MB moved for 251.5 MB of algorithmic bytes: part of the output stays in L2;
+# summarised under profiles/); traffic scales with the elements streamed.
+TRAFFIC_RATIO = {"xpass_tc": 243.0 / 251.5}
+TRAFFIC_NOTE = {"xpass_tc": "algorithmic bytes per launch x 0.966, the DRAM/algorithmic ratio of a 384^3 core-pass "
+                            "capture"}
 
 
 # ------------------------------------------------------------------ ranks (one process per GPU)
