@@ -262,6 +262,27 @@ TK_API tk_status tucker_rhkron_noreuse(tk_handle* h, const tk_tensor* X, const i
                                        const tk_matrix* Omega, const tk_opts* opts, tk_tensor* G, tk_matrix* U,
                                        double* rel_err);
 
+/* rHKron-re with the Kronecker-SRHT sketch of Section 5 (Eq. srht_kron):
+ * Y_n = X_(n) D_n (H_1 kron ... kron H_d without H_n), where Omega[j] = H_j is
+ * n_j x s_j (in the paper s_j sampled columns of the n_j x n_j Walsh-Hadamard
+ * matrix scaled by 1/sqrt(n_j); any matrix is accepted) and D_n is a
+ * Rademacher diagonal over the columns of the mode-n unfolding that is not a
+ * Kronecker product: entry c of D_n is tk_rademacher(seed, n, c) below.  The
+ * sketches share no products (each applies its own D_n to X), so X is
+ * streamed once per mode that needs a QR.  Other arguments and outputs as
+ * tucker_rhkron.  X: F64, F32, BF16 or FP8; the unfolding column count
+ * prod_{j!=n} n_j must be below 2^32.
+ *
+ * tk_rademacher(seed, n, c) = +1 or -1: with u = (uint32)seed +
+ * 0x9E3779B9 * (n + 1) (mod 2^32) and x = (uint32)c ^ u, take the MurmurHash3
+ * 32-bit finalizer h = fmix32(x) (x ^= x >> 16; x *= 0x85EBCA6B;
+ * x ^= x >> 13; x *= 0xC2B2AE35; x ^= x >> 16) and return -1 when the top bit
+ * of h is set.  c is the column index of X_(n) in column-major order (the
+ * other modes' indices, mode 1 fastest). */
+TK_API tk_status tucker_rhkron_srht(tk_handle* h, const tk_tensor* X, const int64_t* r, int p,
+                                    const tk_matrix* Omega, uint64_t seed, const tk_opts* opts, tk_tensor* G,
+                                    tk_matrix* U, double* rel_err);
+
 /* Algorithm rSTHKron: modes processed in opts->mode_order; for mode j the
  * sketch Y = Ghat x_{k!=j} Phi_{j,k}, its thin QR Q_j, and Ghat <- Ghat x_j Q_j^T;
  * then STHOSVD(Ghat, r) in the same order and U_j = Q_j V_j.

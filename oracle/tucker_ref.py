@@ -18,6 +18,9 @@ Pins (tests/test_oracle_*.py):
     (which fixes Q uniquely), classical Gram-Schmidt on tiny inputs.
   * sthosvd: closed-form error 0.4^r on the Section 7.1 tensor, the STHOSVD
     error identity (sum of discarded squared singular values).
+  * rademacher_signs / rhkron_srht: the Kronecker-SRHT sketch Y_(n) =
+    X_(n) D_n (kron H_j) checked against the explicitly formed matrix on tiny
+    inputs, balanced signs, exact recovery of exactly low-rank tensors.
   * rhkron / rsthkron / rhkron_noreuse: exact recovery of exactly low-rank
     tensors, the Section 5 invariants (core singular values bounded by those
     of X, the core error bound Eq. core_svals, Pythagoras for orthonormal
@@ -37,7 +40,7 @@ __all__ = [
     "unfold", "fold", "ttm", "ttm_loops", "multi_ttm", "kron_unfolded_multi_ttm", "kron_omega",
     "thin_qr", "leading_left_singular_vectors", "sthosvd", "canonical_signs",
     "subranks_reuse", "subranks_matrix", "balanced_factors",
-    "rhkron", "rsthkron", "rhkron_noreuse",
+    "rhkron", "rsthkron", "rhkron_noreuse", "rademacher_signs", "srht_sign_tensor", "rhkron_srht",
     "reconstruct", "rel_err", "loss", "loss_grads",
 ]
 
@@ -285,6 +288,67 @@ def rhkron(X: np.ndarray, r: Sequence[int], omegas: Sequence[np.ndarray], order:
     Q, Ys = [], []
     for n in range(d):
         Y = multi_ttm(X, [(j, omegas[j].T) for j in range(d) if j != n])
+        Ys.append(Y)
+        Q.append(thin_qr(unfold(Y, n)))
+    Ghat = multi_ttm(X, [(j, Q[j].T) for j in range(d)])
+    G, V, _ = sthosvd(Ghat, r, order)
+    U = [Q[j] @ V[j] for j in range(d)]
+    G, U = canonical_signs(G, U)
+    return dict(G=G, U=U, Q=Q, Y=Ys, Ghat=Ghat)
+
+
+# ---------------------------------------------------------------- Section 5, Eq. srht_kron
+
+def rademacher_signs(seed: int, n: int, c: np.ndarray) -> np.ndarray:
+    """Entries c of the Rademacher diagonal D_n of the Kronecker-SRHT sketch.
+
+    The paper draws D i.i.d. uniformly from {+1, -1} over the columns of the
+    unfolding, not as a Kronecker product; here the draw is the counter-based
+    generator the C header defines (tk_rademacher): u = seed + 0x9E3779B9 (n + 1)
+    mod 2^32, x = c XOR u, the MurmurHash3 32-bit finalizer of x, and -1 when
+    its top bit is set.
+    """
+    M32 = np.uint64(0xFFFFFFFF)
+    u = (np.uint64(seed) + np.uint64(0x9E3779B9) * np.uint64(n + 1)) & M32
+    x = (np.asarray(c, dtype=np.uint64) & M32) ^ u
+    x ^= x >> np.uint64(16)
+    x = (x * np.uint64(0x85EBCA6B)) & M32
+    x ^= x >> np.uint64(13)
+    x = (x * np.uint64(0xC2B2AE35)) & M32
+    x ^= x >> np.uint64(16)
+    return np.where((x >> np.uint64(31)) & np.uint64(1), -1.0, 1.0)
+
+
+def srht_sign_tensor(shape: Sequence[int], n: int, seed: int) -> np.ndarray:
+    """D_n laid out over X's index space: entry (i_1..i_d) is the sign of the
+    column of X_(n) that holds it (the other modes' indices, mode 1 fastest)."""
+    d = len(shape)
+    c = np.zeros(shape, dtype=np.int64)
+    stride = 1
+    for j in range(d):
+        if j == n:
+            continue
+        idx = np.arange(shape[j], dtype=np.int64).reshape([-1 if k == j else 1 for k in range(d)])
+        c = c + idx * stride
+        stride *= shape[j]
+    return rademacher_signs(seed, n, c)
+
+
+def rhkron_srht(X: np.ndarray, r: Sequence[int], H: Sequence[np.ndarray], seed: int,
+                order: Sequence[int] | None = None):
+    """rHKron-re with the Kronecker-SRHT sketch of Section 5.
+
+    H[j] is the n_j x s_j factor (sampled columns of the scaled Walsh-Hadamard
+    matrix); for each mode n, Y_(n) = X_(n) D_n (kron of the H_j, j != n), i.e.
+    Y_n = (D_n o X) x_{j != n} H_j^T, then the steps of rHKron-re: Q_n from the
+    thin QR, Ghat = X x_j Q_j^T, STHOSVD(Ghat, r), U_j = Q_j V_j.
+    """
+    d = X.ndim
+    order = list(range(d)) if order is None else list(order)
+    Q, Ys = [], []
+    for n in range(d):
+        Xs = X * srht_sign_tensor(X.shape, n, seed)
+        Y = multi_ttm(Xs, [(j, H[j].T) for j in range(d) if j != n])
         Ys.append(Y)
         Q.append(thin_qr(unfold(Y, n)))
     Ghat = multi_ttm(X, [(j, Q[j].T) for j in range(d)])

@@ -1046,6 +1046,87 @@ tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int 
     });
 }
 
+tk_status tucker_rhkron_srht(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
+                             uint64_t seed, const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err) {
+    double* errd = nullptr;
+    return run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X, "X", false);
+        c.xdata = Xt.p;
+        c.xnumel = Xt.numel();
+        const int d = Xt.d;
+        TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "rhkron_srht: d must be >= 2");
+        TK_REQUIRE(r && Omega, TK_ERR_ARG, "rhkron_srht: null r or Omega");
+        TK_REQUIRE(p >= 0, TK_ERR_ARG, "rhkron_srht: p must be >= 0");
+        Opts o = opts_in(opts, d);
+        set_opts(c, o);
+        tk_dtype acc = acc_of(Xt.dt);
+        Tens Gt;
+        std::vector<Mat> Um;
+        check_outputs(Xt, r, G, U, Gt, Um);
+        std::vector<Mat> Om(d);
+        std::vector<int64_t> s(d), k(d);
+        for (int j = 0; j < d; ++j) {
+            Mat om = mat_in(&Omega[j], "Omega");
+            TK_REQUIRE(om.rows == Xt.n[j] && om.cols >= 1, TK_ERR_SHAPE, "rhkron_srht: Omega_j must be n_j x s_j");
+            TK_REQUIRE(acc == TK_F64 ? om.dt == TK_F64 : om.dt != TK_F64, TK_ERR_DTYPE,
+                       "rhkron_srht: Omega must be F64 for F64 data, else F32/BF16");
+            s[j] = om.cols;
+            Om[j] = mat_to(c, om, acc);
+        }
+        std::vector<int> need;
+        for (int n = 0; n < d; ++n) {
+            double w = 1;
+            for (int j = 0; j < d; ++j)
+                if (j != n) w *= (double)s[j];
+            TK_REQUIRE(w >= (double)(r[n] + p), TK_ERR_SHAPE, "rhkron_srht: prod_{j!=n} s_j must be >= r_n + p");
+            TK_REQUIRE(Xt.numel() / std::max<int64_t>(1, Xt.n[n]) < ((int64_t)1 << 32), TK_ERR_SHAPE,
+                       "rhkron_srht: the mode-n unfolding needs fewer than 2^32 columns");
+            k[n] = (int64_t)std::min<double>((double)Xt.n[n], w);
+            TK_REQUIRE(r[n] >= 1 && r[n] <= k[n], TK_ERR_SHAPE, "rhkron_srht: need 1 <= r_n <= sketch width");
+            if (k[n] < Xt.n[n]) need.push_back(n);
+        }
+        // 1. Y_n = X_(n) D_n (kron_{j != n} H_j): D_n is applied to X as it is streamed by the first
+        // product (the narrow FP32 kernel), else to a sign-flipped copy of X
+        std::vector<Tens> Y(d);
+        void* flipped = nullptr;
+        for (int n : need) {
+            int j0 = -1;
+            double best = 1e300;
+            for (int j = 0; j < d; ++j) {
+                if (j == n) continue;
+                const double ratio = (double)s[j] / std::max<double>(1.0, (double)Xt.n[j]);
+                if (ratio < best - 1e-15 || (std::fabs(ratio - best) <= 1e-15 && j > j0)) {
+                    best = ratio;
+                    j0 = j;
+                }
+            }
+            Tens T1;
+            if (c.use_tc && ttm_narrow_eligible(Xt, j0, s[j0], acc)) {
+                T1 = Xt;
+                T1.n[j0] = s[j0];
+                T1.dt = acc;
+                T1.scale = 1.f;
+                T1.p = c.alloc_bytes(dtype_size(acc) * T1.numel());
+                const SignMap sm = sign_map(Xt, n, j0, seed);
+                launch_ttm_narrow(c, Xt, j0, Om[j0], false, s[j0], static_cast<float*>(T1.p), &sm);
+            } else {
+                if (!flipped) flipped = c.alloc_bytes(dtype_size(Xt.dt) * Xt.numel());
+                launch_sign_copy(c, Xt, n, seed, flipped);
+                Tens Xs = Xt;
+                Xs.p = flipped;
+                T1 = ttm_to(c, Xs, j0, Om[j0], false, acc);
+            }
+            std::vector<int> rest;
+            for (int j = 0; j < d; ++j)
+                if (j != n && j != j0) rest.push_back(j);
+            Y[n] = rest.empty() ? T1 : multi_ttm(c, T1, rest, Om.data(), false, acc);
+        }
+        if (rel_err) errd = c.alloc<double>(2);
+        rhkron_from_sketches(c, Xt, Y, k, r, o, Gt, Um, errd);
+        if (rel_err) read_err(h, c, errd, rel_err, false, o.async_outputs);
+    });
+}
+
 tk_status tucker_rhkron_noreuse(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
                                 const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err) {
     double* errd = nullptr;

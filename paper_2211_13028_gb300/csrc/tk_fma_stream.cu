@@ -51,6 +51,7 @@ struct FsArgs {
     int mtrans;
     float* out;
     unsigned* flags;
+    SignMap sm;  // SIGN instantiations: the Rademacher diagonal applied on load
 };
 
 inline size_t fs_smem(int64_t nk) {
@@ -58,7 +59,7 @@ inline size_t fs_smem(int64_t nk) {
            sizeof(float) * (FS_PARTS - 1) * FS_ROWS * FS_COLS + sizeof(uint64_t) * (2 * FS_STAGES + 1);
 }
 
-template <bool KMAJOR>
+template <bool KMAJOR, bool SIGN>
 __global__ void __launch_bounds__(FS_THREADS, 1)
     ttm_fma_stream_kernel(const __grid_constant__ CUtensorMap tmX, FsArgs args) {
     extern __shared__ uint8_t smem_raw[];
@@ -135,6 +136,17 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int a = 0; a < FS_COLS; ++a) acc[u][a] = 0.f;
+        uint32_t c0[4];  // SIGN: unfolding column of (row, i = 0) for this item's four rows
+        if (SIGN) {
+            const SignMap& sm = args.sm;
+            const int64_t rr = KMAJOR ? 0 : t / args.tiles_per_r;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t row = (KMAJOR ? t : t % args.tiles_per_r) * FS_ROWS + q + 32 * u;
+                c0[u] = (uint32_t)(sm.C1 * (row % sm.P1) + sm.P2 * (row / sm.P3) + sm.B1 * (rr % sm.Q1) +
+                                   sm.B2 * (rr / sm.Q2));
+            }
+        }
         for (int64_t kc = 0; kc < nk; ++kc, ++it) {
             if ((int)(it % FS_NGRP) != grp) continue;
             const int s = (int)(it % FS_STAGES);
@@ -162,6 +174,14 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk)
                                 v[u][kk] = reinterpret_cast<const float*>(xs)[(16 * kh + 4 * k4 + kk) * FS_ROWS + rho];
+                        }
+                        if (SIGN) {
+                            const uint32_t i0 = (uint32_t)(kc * FS_CHUNK + 16 * kh + 4 * k4);
+                            const uint32_t A = (uint32_t)args.sm.A;
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                v[u][kk] = __uint_as_float(__float_as_uint(v[u][kk]) ^
+                                                           tk_rad_bits(args.sm.key, c0[u] + A * (i0 + kk)));
                         }
                     }
 #pragma unroll
@@ -232,7 +252,8 @@ bool ttm_narrow_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt) {
     return L == 1 ? nj % 4 == 0 : L % 4 == 0;
 }
 
-void launch_ttm_narrow(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out) {
+void launch_ttm_narrow(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out,
+                       const SignMap* sm) {
     if (!c.exec) return;
     TK_REQUIRE(M.dt == TK_F32, TK_ERR_DTYPE, "narrow ttm: F32 matrix");
     const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
@@ -262,19 +283,19 @@ void launch_ttm_narrow(const Ctx& c, const Tens& X, int j, const Mat& M, bool mt
     a.mtrans = mtrans ? 1 : 0;
     a.out = out;
     a.flags = c.dflags;
+    if (sm) a.sm = *sm;
     const size_t smem = tc::fs_smem(a.nk);
     const char* name = (const void*)X.p == c.xdata ? "xpass_narrow" : "ttm_narrow";
     ProfScope ps(c, name, 4.0 * (double)L * nj * R + 4.0 * (double)L * m * R + 4.0 * nj * m, 2.0 * L * nj * R * m);
     const int grid = (int)std::min<int64_t>(a.ntiles, tc::num_sms());
-    if (kmajor) {
-        TK_CUDA(cudaFuncSetAttribute(tc::ttm_fma_stream_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-        tc::ttm_fma_stream_kernel<true><<<grid, tc::FS_THREADS, smem, c.stream>>>(tx, a);
-    } else {
-        TK_CUDA(cudaFuncSetAttribute(tc::ttm_fma_stream_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-        tc::ttm_fma_stream_kernel<false><<<grid, tc::FS_THREADS, smem, c.stream>>>(tx, a);
-    }
+    auto run = [&](auto kern) {
+        TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, tc::FS_THREADS, smem, c.stream>>>(tx, a);
+    };
+    if (kmajor)
+        sm ? run(tc::ttm_fma_stream_kernel<true, true>) : run(tc::ttm_fma_stream_kernel<true, false>);
+    else
+        sm ? run(tc::ttm_fma_stream_kernel<false, true>) : run(tc::ttm_fma_stream_kernel<false, false>);
     c.counted();
     c.check_launch();
 }

@@ -202,10 +202,41 @@ bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
 void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 // BF16 data: tcgen05 kind::f16 with A straight from shared memory and the
 // factor split into BF16 hi + lo (FP32 output).
+// Rademacher diagonal of the Kronecker-SRHT sketch (tk_rademacher in tucker.h):
+// the sign bit (0x80000000 for -1, 0 for +1) of entry c of D_n, with
+// u = (uint32)seed + 0x9E3779B9 (n + 1): the MurmurHash3 32-bit finalizer of
+// c ^ u, top bit.
+__host__ __device__ inline uint32_t tk_rad_key(uint64_t seed, int n) {
+    return (uint32_t)seed + 0x9E3779B9u * (uint32_t)(n + 1);
+}
+__host__ __device__ inline uint32_t tk_rad_bits(uint32_t u, uint32_t c) {
+    uint32_t x = c ^ u;
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x & 0x80000000u;
+}
+
+// Column index of the mode-n unfolding for the elements a streaming TTM along
+// mode j0 (X viewed as L x n_j0 x R) meets: c = C1 (row % P1) + P2 (row / P3)
+// + B1 (rr % Q1) + B2 (rr / Q2) + A i for row `row` of the tile layout (l, or
+// r when j0 is the leading mode), outer index rr and contracted index i.
+struct SignMap {
+    uint32_t key = 0;
+    int64_t C1 = 0, P1 = 1, P2 = 0, P3 = 1, B1 = 0, Q1 = 1, B2 = 0, Q2 = 1, A = 0;
+};
+SignMap sign_map(const Tens& X, int n, int j0, uint64_t seed);
+
 // Narrow TTMs (m <= 8 output columns) on large FP32 data: a TMA-fed FP32 FMA
 // streaming kernel (the tensor-core kernels' tiling; tk_fma_stream.cu).
 bool ttm_narrow_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
-void launch_ttm_narrow(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
+// With sm, X's elements are multiplied by the Rademacher signs of SignMap first.
+void launch_ttm_narrow(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out,
+                       const SignMap* sm = nullptr);
+// dst = D_n o X (X's dtype and layout): every element times its SRHT sign.
+void launch_sign_copy(const Ctx& c, const Tens& X, int n, uint64_t seed, void* dst);
 bool ttm_bf16_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
 void launch_ttm_bf16(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 // Fused last step of a reconstruction: P = W x_j M^T is formed tile by tile and

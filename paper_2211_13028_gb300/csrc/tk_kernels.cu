@@ -275,6 +275,77 @@ void launch_ttm(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, i
     }
 }
 
+// ------------------------------------------------------------------ Kronecker-SRHT signs
+
+SignMap sign_map(const Tens& X, int n, int j0, uint64_t seed) {
+    SignMap sm;
+    sm.key = tk_rad_key(seed, n);
+    const int64_t stride = X.left(n), nn = X.n[n], L = X.left(j0), nj0 = X.n[j0];
+    const int64_t big = INT64_MAX;
+    if (L == 1) {  // rows r of the unfolding along j0, i contiguous: lin = i + nj0 r
+        if (n > j0) {
+            const int64_t Sa = stride / nj0;
+            sm.C1 = nj0; sm.P1 = Sa; sm.P2 = stride; sm.P3 = Sa * nn; sm.A = 1;
+        } else {  // every mode before j0 has size 1: mode n is trivial
+            sm.C1 = nj0; sm.P1 = big; sm.P2 = 0; sm.P3 = 1; sm.A = 1;
+        }
+    } else if (n < j0) {  // lin = l + L i + L nj0 rr, mode n inside l
+        sm.C1 = 1; sm.P1 = stride; sm.P2 = stride; sm.P3 = stride * nn;
+        sm.A = L / nn; sm.B1 = (L / nn) * nj0; sm.Q1 = big; sm.B2 = 0; sm.Q2 = 1;
+    } else {  // mode n inside rr
+        const int64_t Sb = stride / (L * nj0);
+        sm.C1 = 1; sm.P1 = big; sm.P2 = 0; sm.P3 = 1;
+        sm.A = L; sm.B1 = L * nj0; sm.Q1 = Sb; sm.B2 = stride; sm.Q2 = Sb * nn;
+    }
+    return sm;
+}
+
+// dst[lin] = d_n(c) X[lin], c = lin mod stride_n + stride_n floor(lin / (stride_n n_n)):
+// the sign bit of the stored value is flipped, which is exact for every dtype.
+template <typename W>
+__global__ void sign_copy_kernel(const W* __restrict__ X, W* __restrict__ dst, int64_t numel, int64_t stride, int64_t nn,
+                                 uint32_t key, W top) {
+    for (int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; lin < numel;
+         lin += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = (uint32_t)(lin % stride + stride * (lin / (stride * nn)));
+        dst[lin] = tk_rad_bits(key, c) ? (W)(X[lin] ^ top) : X[lin];
+    }
+}
+
+void launch_sign_copy(const Ctx& c, const Tens& X, int n, uint64_t seed, void* dst) {
+    if (!c.exec) return;
+    const int64_t numel = X.numel();
+    if (numel == 0) return;
+    const int64_t stride = X.left(n), nn = X.n[n];
+    const uint32_t key = tk_rad_key(seed, n);
+    const unsigned grid = (unsigned)std::min<int64_t>((numel + 255) / 256, 152 * 32);
+    ProfScope ps(c, "elementwise", 2.0 * numel * dtype_size(X.dt), 0.0);
+    switch (dtype_size(X.dt)) {
+        case 8:
+            sign_copy_kernel<uint64_t><<<grid, 256, 0, c.stream>>>(static_cast<const uint64_t*>(X.p),
+                                                                   static_cast<uint64_t*>(dst), numel, stride, nn, key,
+                                                                   (uint64_t)1 << 63);
+            break;
+        case 4:
+            sign_copy_kernel<uint32_t><<<grid, 256, 0, c.stream>>>(static_cast<const uint32_t*>(X.p),
+                                                                   static_cast<uint32_t*>(dst), numel, stride, nn, key,
+                                                                   0x80000000u);
+            break;
+        case 2:
+            sign_copy_kernel<uint16_t><<<grid, 256, 0, c.stream>>>(static_cast<const uint16_t*>(X.p),
+                                                                   static_cast<uint16_t*>(dst), numel, stride, nn, key,
+                                                                   (uint16_t)0x8000);
+            break;
+        default:
+            sign_copy_kernel<uint8_t><<<grid, 256, 0, c.stream>>>(static_cast<const uint8_t*>(X.p),
+                                                                  static_cast<uint8_t*>(dst), numel, stride, nn, key,
+                                                                  (uint8_t)0x80);
+            break;
+    }
+    c.counted();
+    c.check_launch();
+}
+
 // ------------------------------------------------------------------ FP64 GEMM (NT) with split-K
 
 __global__ void gemm_reduce_kernel(int64_t m, int64_t n, int nsplit, const double* P, double alpha, double beta,

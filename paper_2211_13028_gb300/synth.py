@@ -102,6 +102,28 @@ def sketch_factors_reuse(dims: Sequence[int], s: Sequence[int], seed: int, dtype
     return out
 
 
+def hadamard_columns(n: int, s: int, seed: int, dtype: str = "f64") -> np.ndarray:
+    """H_j of the Kronecker-SRHT sketch: s distinct columns, drawn uniformly
+    without replacement, of the n x n Walsh-Hadamard matrix (Sylvester order,
+    entry (i, k) = (-1)^popcount(i & k)) scaled by 1/sqrt(n).  n must be a
+    power of two."""
+    if n < 1 or n & (n - 1):
+        raise ValueError("hadamard_columns: n must be a power of two")
+    cols = np.sort(_gen(seed).choice(n, size=int(s), replace=False))
+    i = np.arange(n, dtype=np.int64)[:, None]
+    bits = np.bitwise_and(i, cols[None, :].astype(np.int64))
+    par = np.zeros_like(bits)
+    while np.any(bits):
+        par ^= bits & 1
+        bits >>= 1
+    return round_to(np.where(par == 1, -1.0, 1.0) / np.sqrt(n), dtype)
+
+
+def sketch_factors_srht(dims: Sequence[int], s: Sequence[int], seed: int, dtype: str = "f64") -> List[np.ndarray]:
+    """One Walsh-Hadamard factor per mode, independent draws (Section 5)."""
+    return [hadamard_columns(int(n), int(sj), seed + 7919 * j, dtype) for j, (n, sj) in enumerate(zip(dims, s))]
+
+
 def sketch_factors_noreuse(dims: Sequence[int], S: np.ndarray, seed: int, dtype: str = "f64") -> Dict[Tuple[int, int], np.ndarray]:
     """Omega_{j,k} = Phi_{j,k}^T with Phi_{j,k} in R^{s_{j,k} x n_k} (appendix Algorithm rHKron)."""
     g = _gen(seed)

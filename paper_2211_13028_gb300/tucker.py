@@ -27,7 +27,8 @@ __all__ = [
     "tucker_sketch", "tucker_orth", "tucker_orth_noalloc", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
     "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
-    "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tk_graph_release", "TuckerGraph",
+    "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tucker_rhkron_srht", "tk_graph_release",
+    "TuckerGraph",
 ]
 
 TK_MAX_D = 8
@@ -117,6 +118,8 @@ def load():
                                  P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
             "tucker_rhkron_noreuse": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor),
                                  P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
+            "tucker_rhkron_srht": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), ctypes.c_uint64, P(TkOpts),
+                                    P(TkTensor), P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
             "tucker_reconstruct": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
             "tucker_loss": ([vp, P(TkTensor), P(TkTensor), P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
             "tucker_reconstruct_backward": ([vp, P(TkTensor), P(TkTensor), P(TkMatrix), ctypes.c_double, P(TkTensor),
@@ -438,6 +441,22 @@ def tucker_rsthkron(X: torch.Tensor, r: Sequence[int], p: int, Omega: Dict[Tuple
     lst = [Omega.get((j, k), dummy) if j != k else dummy for j in range(d) for k in range(d)]
     return _decomp(load().tucker_rsthkron, X, r, p, lst, order, qr_method, refine, max_jacobi_sweeps, rel_err,
                    out_dtype, scale, async_outputs)
+
+
+def tucker_rhkron_srht(X: torch.Tensor, r: Sequence[int], p: int, H: Sequence[torch.Tensor], seed: int, *,
+                       order=None, qr_method: int = 0, refine: int = 0, max_jacobi_sweeps: int = 0,
+                       rel_err: bool = True, out_dtype=None, scale: float = 1.0, async_outputs: bool = False):
+    """rHKron-re with the Kronecker-SRHT sketch (Section 5): H[j] = n_j x s_j sampled, scaled
+    Walsh-Hadamard columns; the Rademacher diagonals D_n come from the counter-based generator
+    tk_rademacher(seed, n, c) of the C header."""
+    lib = load()
+    sd = ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF)
+
+    def fn(h, x, rr, pp, om, o, g, u, e):
+        return lib.tucker_rhkron_srht(h, x, rr, pp, om, sd, o, g, u, e)
+
+    return _decomp(fn, X, r, p, list(H), order, qr_method, refine, max_jacobi_sweeps, rel_err, out_dtype, scale,
+                   async_outputs)
 
 
 def tucker_rhkron_noreuse(X: torch.Tensor, r: Sequence[int], p: int, Omega: Dict[Tuple[int, int], torch.Tensor], *,
