@@ -346,9 +346,10 @@ def run_bf16_workload(args):
                               "stored BF16 (rounded once) and FP32; rHKron-re r=(64,64,64), p=16, s=(9,9,9)"),
                     l2="X is 2 GiB (BF16) / 4 GiB (FP32), larger than L2: no flush"),
         forms=forms, speedup_bf16_over_f32=forms["f32"]["ms"] / forms["bf16"]["ms"],
-        oracle_check=dict(n=n_or, oracle_rel_err=err_or, gpu_rel_err=err_gpu_small,
-                          abs_diff=abs(err_or - err_gpu_small), oracle_seconds=t_or,
-                          note="FP64 oracle on the BF16-rounded %d^3 field of the same generator" % n_or),
+        cpu_baseline=dict(value=t_or * 1e3, unit="ms", cores=cpu_cores(), kind="oracle",
+                          sample="one FP64 oracle rHKron-re on the BF16-rounded %d^3 field of the same generator"
+                                 % n_or,
+                          oracle_rel_err=err_or, gpu_rel_err=err_gpu_small, abs_diff=abs(err_or - err_gpu_small)),
         device_status=st, clocks=clk)
     print(json.dumps(line), flush=True)
 
@@ -424,10 +425,88 @@ def run_tucker4_workload(args):
         xpass=dict(gbs=gbs, frac=gbs / hbm, launches_per_step=xp["launches"] / args.steps,
                    bytes_per_step=xp["bytes"] / args.steps),
         kernel_shares={kk: round(v["ms"] / tot, 4) for kk, v in sorted(prof_all.items(), key=lambda kv: -kv[1]["ms"])},
-        oracle_check=dict(n=n_or, oracle_rel_err=err_or, gpu_rel_err=err_gpu_small,
-                          abs_diff=abs(err_or - err_gpu_small), oracle_seconds=t_or,
-                          note="FP64 oracle on the %d^4 tensor of the same generator" % n_or),
+        cpu_baseline=dict(value=t_or * 1e3, unit="ms", cores=cpu_cores(), kind="oracle",
+                          sample="one FP64 oracle rSTHKron on the %d^4 tensor of the same generator" % n_or,
+                          oracle_rel_err=err_or, gpu_rel_err=err_gpu_small, abs_diff=abs(err_or - err_gpu_small)),
         device_status=T.tk_sync_status(dev)[0], clocks=clk)
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ Section 7.1 accuracy: SRHT vs Gaussian sketches
+
+def run_srht_workload(args):
+    """The accuracy experiment of Section 7.1 at 512^3 (a power of two, as the Walsh-Hadamard factors
+    need): X = sum_i 0.4^i q1_i o q2_i o q3_i (a superdiagonal core of 40 entries decaying by 0.4
+    times random orthonormal factors), rank (10,10,10), p = 5.  rHKron-re with Gaussian Kronecker
+    factors and with the Kronecker-SRHT sketch, fresh random factors per trial; the deterministic
+    (STHOSVD) error of this tensor is 0.4^10 in closed form.  Reports the relative errors over the
+    trials and the time of one decomposition of each kind."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_2211_13028_gb300 import synth
+    from paper_2211_13028_gb300 import tucker as T
+
+    n, rr, p, trials = 512, (10, 10, 10), 5, args.trials
+    so, _ = O.subranks_reuse(rr, p)
+    # oracle leg first, before any CUDA work in this process: a 64^3 tensor of the same construction,
+    # with the factors of the first GPU trial
+    no = 64
+    fo = [np.linalg.qr(np.random.Generator(np.random.PCG64(SEED + j)).standard_normal((no, 40)))[0] for j in range(3)]
+    xo = synth.round_to(np.einsum("i,ai,bi,ci->abc", 0.4 ** np.arange(40), *fo), "f32")
+    Ho = synth.sketch_factors_srht((no, no, no), so, SEED + 200, "f32")
+    t_or = time.perf_counter()
+    ref = O.rhkron_srht(xo, rr, Ho, SEED + 300)
+    t_or = time.perf_counter() - t_or
+    err_or = O.rel_err(xo, ref["G"], ref["U"])
+
+    dev = torch.device("cuda", 0)
+    T.load()
+    s, _ = T.tucker_subranks_reuse(rr, p)
+    gpu_o = T.tucker_rhkron_srht(synth.fortran(xo, "f32", dev), rr, p, [synth.fmat(h, "f32", dev) for h in Ho],
+                                 seed=SEED + 300)[2]
+    g = torch.Generator(device="cpu").manual_seed(SEED)
+    facs = [torch.linalg.qr(torch.randn(n, 40, generator=g, dtype=torch.float64))[0] for _ in range(3)]
+    lam = 0.4 ** torch.arange(40, dtype=torch.float64)
+    X = torch.einsum("i,ai,bi,ci->cba", lam.float().to(dev), *[f.float().to(dev) for f in facs]).permute(2, 1, 0)
+    # (a column-major view: the einsum writes index order (c, b, a) row-major)
+    det = 0.4 ** 10
+    errs = {"gaussian": [], "srht": []}
+    for t in range(trials):
+        om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse((n, n, n), s, SEED + 100 + t, "f32")]
+        H = [synth.fmat(h, "f32", dev) for h in synth.sketch_factors_srht((n, n, n), s, SEED + 200 + t, "f32")]
+        errs["gaussian"].append(T.tucker_rhkron(X, rr, p, om)[2])
+        errs["srht"].append(T.tucker_rhkron_srht(X, rr, p, H, seed=SEED + 300 + t)[2])
+    times = {}
+    for name in ("gaussian", "srht"):
+        fn = (lambda: T.tucker_rhkron(X, rr, p, om, async_outputs=True)) if name == "gaussian" else \
+             (lambda: T.tucker_rhkron_srht(X, rr, p, H, seed=SEED, async_outputs=True))
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / args.steps
+    summ = {k: dict(median=float(np.median(v)), min=float(np.min(v)), max=float(np.max(v)),
+                    median_over_deterministic=float(np.median(v) / det)) for k, v in errs.items()}
+    line = dict(
+        metric="rHKron-re, Section 7.1 tensor at 512^3, r=(10,10,10), p=5: Kronecker-SRHT vs Gaussian sketch",
+        value=times["srht"], unit="ms", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=times["srht"],
+        higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload=("srht512_f32: 512^3 FP32, superdiagonal core 0.4^i (40 entries) times random "
+                              "orthonormal factors; rHKron-re r=10, p=5, s=%s; %d trials per sketch" % (list(s), trials)),
+                    l2="X is 512 MiB, larger than L2: no flush"),
+        ms=times, rel_err=summ, deterministic_rel_err=det,
+        cpu_baseline=dict(value=t_or * 1e3, unit="ms", cores=cpu_cores(), kind="oracle",
+                          sample="one FP64 oracle rHKron-re with the Kronecker-SRHT sketch on the %d^3 tensor of "
+                                 "the same construction" % no,
+                          oracle_rel_err=err_or, gpu_rel_err=gpu_o, abs_diff=abs(err_or - gpu_o)),
+        device_status=T.tk_sync_status(dev)[0])
     print(json.dumps(line), flush=True)
 
 
@@ -516,10 +595,13 @@ def main():
                     help="run one building block on an n^3 FP32 field (for ncu captures) instead of the bench")
     ap.add_argument("--n", type=int, default=384, help="edge of the --profile-case tensor")
     ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32", help="storage of the --profile-case tensor")
-    ap.add_argument("--workload", choices=["bumps512_f32", "bumps1024_bf16", "tucker160x4_f32", "descent256_f32"],
+    ap.add_argument("--workload", choices=["bumps512_f32", "bumps1024_bf16", "tucker160x4_f32", "descent256_f32",
+                                           "srht512_f32"],
                     default="bumps512_f32",
                     help="bumps512_f32: the default step; bumps1024_bf16: the BF16 storage form vs FP32; "
-                         "tucker160x4_f32: 4-way rSTHKron; descent256_f32: rHKron-re init + 50 Adam steps")
+                         "tucker160x4_f32: 4-way rSTHKron; descent256_f32: rHKron-re init + 50 Adam steps; "
+                         "srht512_f32: the Section 7.1 accuracy experiment, Kronecker-SRHT vs Gaussian sketches")
+    ap.add_argument("--trials", type=int, default=20, help="random trials per sketch kind (srht512_f32)")
     ap.add_argument("--oracle-n", type=int, default=256, help="edge of the oracle check of --workload bumps1024_bf16")
     ap.add_argument("--oracle-n4", type=int, default=48, help="edge of the oracle check of --workload tucker160x4_f32")
     args = ap.parse_args()
@@ -535,6 +617,9 @@ def main():
         return
     if args.workload == "descent256_f32" and args.impl == "native":
         run_descent_workload(args)
+        return
+    if args.workload == "srht512_f32" and args.impl == "native":
+        run_srht_workload(args)
         return
 
     if args.impl == "reference":
