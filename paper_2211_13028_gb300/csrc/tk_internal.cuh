@@ -262,16 +262,23 @@ struct KDims {
     int k[TK_MAX_D];
 };
 
-// Batched Cholesky W = R^T R and R^{-1} (FP64, one CTA per matrix).  W: batch
-// matrices k_b x k_b (ld = kmax, stride kmax*kmax).  Rinv receives R^{-1}
-// (upper).  Matrix b is skipped when bad[b] != 0; a breakdown (pivot <= tol *
-// original diagonal) sets bad[b] = 1.
+// Batched Cholesky W = R^T R and R^{-1} (one CTA per matrix).  W: batch
+// matrices k_b x k_b (ld = kmax, stride kmax*kmax), FP64.  Rinv receives
+// R^{-1} (upper), FP64.  Matrix b is skipped when bad[b] != 0; a breakdown
+// (pivot <= tol * original diagonal) sets bad[b] = 1.  df: the factorisation
+// runs in double-float arithmetic (~48 bits) instead of FP64.
 void launch_chol_inv(const Ctx& c, int batch, const KDims& kd, int kmax, const double* W, double* Rinv, int* bad,
-                     double tol);
+                     double tol, bool df = false);
 
 // Q(i, c) = sum_{c' <= c} Y(i, c') Rinv(c', c), FP64 out (n x k, ld n).  Skipped when *skip != 0.
 void launch_apply_rinv(const Ctx& c, int64_t n, int64_t k, const View2& Y, const double* Rinv, int64_t ldr,
                        double* Q, const int* skip);
+
+// Q_b = Y_b R_b^{-1} for batch matrices in one launch, in double-float
+// arithmetic (Y_b FP32 or FP64, n_b x k_b; R_b = Rinv + b kmax^2, ld kmax;
+// Q_b FP64, ld n_b).  Matrix b is skipped when bad[b] != 0.
+void launch_apply_rinv_df(const Ctx& c, int batch, const View2* Y, const int64_t* n, const int64_t* k,
+                          const double* Rinv, int64_t kmax, double* const* Q, const int* bad);
 
 // Householder thin QR of Y (n x k, FP64 copy in A, ld n) producing Q with R_ii >= 0,
 // run only when *run != 0.  One CTA.  tau: k doubles scratch.

@@ -714,10 +714,235 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_inv_kernel(KDims kd, int km
     }
 }
 
+// ------------------------------------------------------------------ Cholesky + inverse, double-float
+
+// The same factorisation for Gram matrices of FP32-class data, carried out in
+// double-float arithmetic (value = hi + lo, two FP32 numbers, ~48 significant
+// bits) on the FP32 pipe, which is 64 times wider than the FP64 pipe here.
+// W is scaled by 4^-e (2^{2e} near its largest diagonal entry) so that every
+// entry is below ~4 in magnitude (|w_il| <= sqrt(w_ii w_ll)), far inside the
+// FP32 exponent range; R_W^{-1} = 2^-e R_A^{-1} undoes it exactly.
+//
+// The column loop is the LDL^T form: with p_j the j-th pivot and l_ij =
+// a_ji / p_j, step j updates the trailing upper triangle a_il -= l_ij a_jl
+// (j < i <= l) and the unit lower M = L^{-1} by M(i, 0..j) -= l_ij M(j, 0..j);
+// then R = D^{1/2} L^T and R^{-1} = M^T D^{-1/2}, i.e. R^{-1}(a, b) =
+// M(b, a) / sqrt(p_b).  Row j is never rescaled, so one barrier per column
+// suffices: warps own whole rows (row-major storage, lanes along the row), and
+// lane 0 of warp 0, which owns row j+1 alone and updates a_{j+1,j+1} first,
+// turns it into the next pivot's 1/p and 1/sqrt(p) while the others finish.
+
+__device__ __forceinline__ float2 df_norm(float s, float t) {  // fast two-sum, |s| >= |t|
+    const float h = __fadd_rn(s, t);
+    return make_float2(h, __fsub_rn(t, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ float2 df_mul2(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    return df_norm(p, e);
+}
+
+// a - f b
+__device__ __forceinline__ float2 df_fnms2(float2 a, float2 f, float2 b) {
+    const float p = __fmul_rn(f.x, b.x);
+    float e = fmaf(f.x, b.x, -p);
+    e = fmaf(f.x, b.y, e);
+    e = fmaf(f.y, b.x, e);
+    const float s = __fsub_rn(a.x, p);  // two-sum of a.x and -p
+    const float v = __fsub_rn(s, a.x);
+    const float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(-p, v));
+    return df_norm(s, __fadd_rn(t, __fsub_rn(a.y, e)));
+}
+
+// 1/p and 1/sqrt(p) of a positive double-float p: an FP32 seed and one
+// Newton step evaluated in double-float (error ~2^-46).
+__device__ __forceinline__ void df_rcp_rsqrt(float2 p, float2& inv, float2& ys) {
+    const float q0 = __frcp_rn(p.x);
+    float t = fmaf(-p.x, q0, 1.0f);
+    t = fmaf(-p.y, q0, t);
+    inv = df_norm(q0, __fmul_rn(q0, t));
+    const float y0 = __frsqrt_rn(p.x);
+    const float a = __fmul_rn(y0, y0);
+    const float2 y2 = make_float2(a, fmaf(y0, y0, -a));  // y0^2 exactly
+    const float2 py = df_mul2(p, y2);
+    const float d = __fsub_rn(__fsub_rn(1.0f, py.x), py.y);  // 1 - p y0^2 (~2^-22)
+    ys = df_norm(y0, __fmul_rn(__fmul_rn(0.5f, y0), d));
+}
+
+// w * 2^-sh as a double-float pair, by integer splitting of the FP64
+// significand (top 24 bits, then the next 29 rounded to FP32).  Magnitudes
+// below 2^-74 after scaling keep only the high part; below 2^-100 they are
+// flushed to zero (negligible next to the unit-scale diagonal).
+__device__ __forceinline__ float2 df_from_f64(double w, int sh) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(w);
+    const int ex = (int)((u >> 52) & 0x7FF);
+    const int E = ex - 1023 - sh;
+    if (ex == 0 || E < -100) return make_float2(0.f, 0.f);
+    const unsigned sg = (unsigned)(u >> 63) << 31;
+    const unsigned long long m = u & ((1ull << 52) - 1);
+    const float hi = __uint_as_float(sg | ((unsigned)(E + 127) << 23) | (unsigned)(m >> 29));
+    float lo = 0.f;
+    if (E >= -74) {
+        const float sc = __uint_as_float((unsigned)(E - 52 + 127) << 23);
+        lo = __fmul_rn(__uint2float_rn((unsigned)(m & ((1u << 29) - 1))), sc);
+        lo = __uint_as_float(__float_as_uint(lo) | sg);
+    }
+    return make_float2(hi, lo);
+}
+
+// One row of a column step: A(i, i..k-1) followed by M(i, 0..j), NQ 32-wide
+// slices (the last one partial), all loaded before any is updated.  Returns
+// the lane's first updated value (lane 0: A(i, i)).
+template <int NQ>
+__device__ __forceinline__ float2 chdf_row(float2* A, float2* M, const float2* Aj, const float2* Mj, int k, int i,
+                                           int j, float2 f, int lane) {
+    const int na = k - i, len = na + j + 1;
+    float2* dst[NQ];
+    float2 x[NQ], y[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int t = lane + 32 * q;
+        const bool inA = t < na;
+        dst[q] = inA ? A + (size_t)i * k + i + t : M + (size_t)i * k + (t - na);
+        const float2* src = inA ? Aj + i + t : Mj + (t - na);
+        if (t < len) {
+            x[q] = *dst[q];
+            y[q] = *src;
+        }
+    }
+    float2 v0 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        if (lane + 32 * q < len) {
+            const float2 v = df_fnms2(x[q], f, y[q]);
+            *dst[q] = v;
+            if (q == 0) v0 = v;
+        }
+    }
+    return v0;
+}
+
+constexpr int CHDF_THREADS = 768;
+
+__global__ void __launch_bounds__(CHDF_THREADS) chol_inv_df_kernel(KDims kd, int kmax, const double* W,
+                                                                   double* Rinv, int* bad, double tol) {
+    extern __shared__ float2 sf[];  // A: k x k row-major (upper part), M: k x k row-major (lower part)
+    __shared__ float2 s_ys[112];    // 1 / sqrt(p_j)
+    __shared__ float2 s_inv[2];     // 1 / p_j, double-buffered by column parity
+    __shared__ float s_dg[112];     // scaled original diagonal (breakdown test)
+    __shared__ int s_ok[113];       // s_ok[j]: pivot j accepted
+    __shared__ int s_e;
+    const int b = blockIdx.x;
+    if (bad[b]) return;
+    const int k = kd.k[b];
+    float2* A = sf;
+    float2* M = sf + (size_t)k * k;
+    const double* Wb = W + (int64_t)b * kmax * kmax;
+    double* Rb = Rinv + (int64_t)b * kmax * kmax;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    if (warp == 0) {
+        double m = 0.0;
+        for (int i = lane; i < k; i += 32) m = fmax(m, Wb[i + (int64_t)kmax * i]);
+        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            int e = 0;
+            if (m > 0.0 && m < 1e300) {
+                const int be = (int)((__double_as_longlong(m) >> 52) & 0x7FF) - 1023;  // floor(log2 m), m normal
+                e = (be >= 0 ? be : be - 1) / 2;
+            }
+            s_e = e;
+        }
+    }
+    __syncthreads();
+    const int e = s_e;
+    for (int idx = tid; idx < k * k; idx += nt) {
+        const int i = idx / k, l = idx - i * k;
+        A[idx] = l >= i ? df_from_f64(Wb[i + (int64_t)kmax * l], 2 * e) : make_float2(0.f, 0.f);
+        M[idx] = make_float2(i == l ? 1.f : 0.f, 0.f);
+    }
+    for (int i = tid; i < k; i += nt) {
+        s_dg[i] = df_from_f64(Wb[i + (int64_t)kmax * i], 2 * e).x;
+        s_ok[i] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const float2 p = A[0];
+        const bool ok = p.x > (float)tol * s_dg[0] && p.x > 0.f;
+        s_ok[0] = ok;
+        if (ok) {
+            float2 inv, ys;
+            df_rcp_rsqrt(p, inv, ys);
+            s_inv[0] = inv;
+            s_ys[0] = ys;
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j + 1 < k; ++j) {
+        if (!s_ok[j]) break;  // uniform: written before the last barrier
+        const float2 inv = s_inv[j & 1];
+        const float2* Aj = A + (size_t)j * k;
+        const float2* Mj = M + (size_t)j * k;
+        // warp 0 takes row j + 1 alone (its first element is the next pivot);
+        // warps 1 .. nw-1 share rows j + 2 .. k - 1, one pass per row
+        const int i0 = j + 1 + warp, di = warp == 0 ? k : nw - 1;
+        for (int i = i0; i < k; i += di) {
+            const float2 f = df_mul2(Aj[i], inv);  // l_ij
+            const int nq = (k - i + j + 1 + 31) >> 5;  // warp-uniform: 32-element slices of the row
+            float2 v;
+            if (nq == 1)
+                v = chdf_row<1>(A, M, Aj, Mj, k, i, j, f, lane);
+            else if (nq == 2)
+                v = chdf_row<2>(A, M, Aj, Mj, k, i, j, f, lane);
+            else if (nq == 3)
+                v = chdf_row<3>(A, M, Aj, Mj, k, i, j, f, lane);
+            else
+                v = chdf_row<4>(A, M, Aj, Mj, k, i, j, f, lane);
+            if (warp == 0 && lane == 0) {  // v = A(j+1, j+1): the next pivot
+                const bool ok = v.x > (float)tol * s_dg[j + 1] && v.x > 0.f;
+                s_ok[j + 1] = ok;
+                if (ok) {
+                    float2 ni, ys;
+                    df_rcp_rsqrt(v, ni, ys);
+                    s_inv[(j + 1) & 1] = ni;
+                    s_ys[j + 1] = ys;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!s_ok[k - 1]) {  // a rejected pivot ends the loop; the flags after it stay 0
+        if (tid == 0) bad[b] = 1;
+        return;
+    }
+    const double sc = __longlong_as_double((long long)(1023 - e) << 52);  // 2^-e
+    for (int idx = tid; idx < k * k; idx += nt) {
+        const int a = idx % k, c = idx / k;  // R^{-1}(a, c), column-major out
+        double v = 0.0;
+        if (a <= c) {
+            const float2 r = df_mul2(M[(size_t)c * k + a], s_ys[c]);
+            v = ((double)r.x + (double)r.y) * sc;
+        }
+        Rb[a + (int64_t)kmax * c] = v;
+    }
+}
+
 void launch_chol_inv(const Ctx& c, int batch, const KDims& kd, int kmax, const double* W, double* Rinv, int* bad,
-                     double tol) {
+                     double tol, bool df) {
     if (!c.exec) return;
     TK_REQUIRE(kmax <= 112, TK_ERR_SHAPE, "chol_inv: at most 112 columns");
+    if (df) {
+        const size_t smem = 2 * sizeof(float2) * kmax * kmax;
+        if (smem > 48 * 1024)
+            TK_CUDA(cudaFuncSetAttribute(chol_inv_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ProfScope ps(c, "chol_inv", 16.0 * batch * kmax * kmax, (2.0 / 3.0) * batch * kmax * kmax * kmax);
+        chol_inv_df_kernel<<<batch, CHDF_THREADS, smem, c.stream>>>(kd, kmax, W, Rinv, bad, tol);
+        c.counted();
+        c.check_launch();
+        return;
+    }
     size_t smem = 2 * sizeof(double) * kmax * kmax;
     if (smem > 48 * 1024)
         TK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -729,21 +954,21 @@ void launch_chol_inv(const Ctx& c, int batch, const KDims& kd, int kmax, const d
 
 // ------------------------------------------------------------------ Q = Y R^{-1}
 
-__global__ void __launch_bounds__(256) apply_rinv_kernel(int64_t n, int64_t k, View2 Y, const double* Rinv,
+__global__ void __launch_bounds__(256) apply_rinv_kernel(int64_t n, int64_t k, int rpc, View2 Y, const double* Rinv,
                                                          int64_t ldr, double* Q, const int* skip) {
-    extern __shared__ double ys[];  // 8 x k
+    extern __shared__ double ys[];  // rpc x k
     if (skip && *skip) return;
-    const int64_t i0 = (int64_t)blockIdx.x * 8;
-    for (int64_t e = threadIdx.x; e < 8 * k; e += blockDim.x) {
-        int64_t ii = e % 8, cc = e / 8;
+    const int64_t i0 = (int64_t)blockIdx.x * rpc;
+    for (int64_t e = threadIdx.x; e < rpc * k; e += blockDim.x) {
+        int64_t ii = e % rpc, cc = e / rpc;
         ys[e] = (i0 + ii < n) ? v2ld(Y, i0 + ii, cc) : 0.0;
     }
     __syncthreads();
-    for (int64_t e = threadIdx.x; e < 8 * k; e += blockDim.x) {
-        int64_t ii = e % 8, col = e / 8;
+    for (int64_t e = threadIdx.x; e < rpc * k; e += blockDim.x) {
+        int64_t ii = e % rpc, col = e / rpc;
         if (i0 + ii >= n) continue;
         double s = 0.0;
-        for (int64_t cp = 0; cp <= col; ++cp) s = fma(ys[ii + 8 * cp], Rinv[cp + ldr * col], s);
+        for (int64_t cp = 0; cp <= col; ++cp) s = fma(ys[ii + rpc * cp], __ldg(Rinv + cp + ldr * col), s);
         Q[(i0 + ii) + n * col] = s;
     }
 }
@@ -751,11 +976,117 @@ __global__ void __launch_bounds__(256) apply_rinv_kernel(int64_t n, int64_t k, V
 void launch_apply_rinv(const Ctx& c, int64_t n, int64_t k, const View2& Y, const double* Rinv, int64_t ldr, double* Q,
                        const int* skip) {
     if (!c.exec) return;
-    size_t smem = sizeof(double) * 8 * k;
+    // rows per CTA: enough CTAs to cover the SMs (the FP64 pipe of one SM is narrow), at most 8
+    const int rpc = (int)std::min<int64_t>(8, std::max<int64_t>(1, (n + 151) / 152));
+    size_t smem = sizeof(double) * rpc * k;
     if (smem > 48 * 1024)
         TK_CUDA(cudaFuncSetAttribute(apply_rinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(c, "apply_rinv", 16.0 * n * k + 8.0 * k * k, (double)n * k * k);
-    apply_rinv_kernel<<<(unsigned)((n + 7) / 8), 256, smem, c.stream>>>(n, k, Y, Rinv, ldr, Q, skip);
+    apply_rinv_kernel<<<(unsigned)((n + rpc - 1) / rpc), 256, smem, c.stream>>>(n, k, rpc, Y, Rinv, ldr, Q, skip);
+    c.counted();
+    c.check_launch();
+}
+
+// The same product for several matrices in one launch, in double-float
+// arithmetic on the FP32 pipe: Y (FP32 or FP64) and R^{-1} (FP64) are split
+// into hi + lo pairs and each output is a Dot2 sum (exact two-product of the
+// high parts, the cross terms and both rounding errors in the correction),
+// ~48 significant bits.  CTA (x, b): rows 32x .. 32x+31 of matrix b, a lane
+// per row; warps take the column pairs (c, k-1-c) in turn, so that every
+// warp sums about the same number of terms.
+struct ApplyBatch {
+    View2 Y[TK_MAX_D];
+    const double* R[TK_MAX_D];
+    double* Q[TK_MAX_D];
+    const int* skip[TK_MAX_D];
+    int64_t n[TK_MAX_D];
+    int k[TK_MAX_D];
+    int64_t ldr;
+};
+
+constexpr int APDF_THREADS = 256;
+
+__global__ void __launch_bounds__(APDF_THREADS) apply_rinv_df_kernel(ApplyBatch ab) {
+    extern __shared__ float2 sa[];  // R^{-1}: k x k column-major, then Y rows: k x 32 ([col][row])
+    const int b = blockIdx.y;
+    if (ab.skip[b] && *ab.skip[b]) return;
+    const int64_t n = ab.n[b];
+    const int k = ab.k[b];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    if (r0 >= n) return;
+    float2* rs = sa;
+    float2* ys = sa + (size_t)k * k;
+    const double* R = ab.R[b];
+    const View2 Y = ab.Y[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int e = tid; e < k * k; e += blockDim.x) {
+        const int a = e % k, c = e / k;
+        rs[e] = a <= c ? df_from_f64(R[a + ab.ldr * c], 0) : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < 32 * k; e += blockDim.x) {
+        const int rr = e & 31, c = e >> 5;
+        float2 v = make_float2(0.f, 0.f);
+        if (r0 + rr < n) {
+            if (Y.dt == TK_F64)
+                v = df_from_f64(static_cast<const double*>(Y.p)[v2off(Y, r0 + rr, c)], 0);
+            else
+                v = make_float2(static_cast<const float*>(Y.p)[v2off(Y, r0 + rr, c)], 0.f);
+        }
+        ys[e] = v;
+    }
+    __syncthreads();
+    const int64_t row = r0 + lane;
+    double* Q = ab.Q[b];
+    for (int pc = warp; pc < (k + 1) / 2; pc += nw) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int col = h ? k - 1 - pc : pc;
+            if (h && col == pc) break;
+            float sh = 0.f, sl = 0.f;
+            const float2* rc = rs + (size_t)k * col;
+            for (int cp = 0; cp <= col; ++cp) {
+                const float2 a = ys[cp * 32 + lane], r = rc[cp];
+                const float p = __fmul_rn(a.x, r.x);
+                float e = fmaf(a.x, r.x, -p);
+                e = fmaf(a.x, r.y, e);
+                e = fmaf(a.y, r.x, e);
+                const float t = __fadd_rn(sh, p);
+                const float z = __fsub_rn(t, sh);
+                const float q = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+                sh = t;
+                sl = __fadd_rn(sl, __fadd_rn(q, e));
+            }
+            if (row < n) Q[row + n * col] = (double)sh + (double)sl;
+        }
+    }
+}
+
+void launch_apply_rinv_df(const Ctx& c, int batch, const View2* Y, const int64_t* n, const int64_t* k,
+                          const double* Rinv, int64_t kmax, double* const* Q, const int* bad) {
+    if (!c.exec) return;
+    ApplyBatch ab;
+    int64_t nmax = 1;
+    for (int b = 0; b < batch; ++b) {
+        ab.Y[b] = Y[b];
+        ab.R[b] = Rinv + b * kmax * kmax;
+        ab.Q[b] = Q[b];
+        ab.skip[b] = bad + b;
+        ab.n[b] = n[b];
+        ab.k[b] = (int)k[b];
+        nmax = std::max(nmax, n[b]);
+    }
+    ab.ldr = kmax;
+    const size_t smem = sizeof(float2) * (kmax * kmax + 32 * kmax);
+    if (smem > 48 * 1024)
+        TK_CUDA(cudaFuncSetAttribute(apply_rinv_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    double bytes = 0.0, flops = 0.0;
+    for (int b = 0; b < batch; ++b) {
+        bytes += 16.0 * n[b] * k[b] + 8.0 * k[b] * k[b];
+        flops += (double)n[b] * k[b] * k[b];
+    }
+    ProfScope ps(c, "apply_rinv", bytes, flops);
+    dim3 grid((unsigned)((nmax + 31) / 32), (unsigned)batch);
+    apply_rinv_df_kernel<<<grid, APDF_THREADS, smem, c.stream>>>(ab);
     c.counted();
     c.check_launch();
 }
