@@ -26,7 +26,8 @@ RANKS = (32, 32, 32)
 P_OVER = 8
 SEED = 0
 WORKLOAD = ("bumps512_f32: 512^3 FP32 field, sum of 200 anisotropic Gaussian bumps + 1e-4 relative noise; "
-            "rHKron-re and rSTHKron at r=(32,32,32), p=8 (s=(6,7,7); S rows {5,8}); loss gradient at the rHKron-re result")
+            "rHKron-re and rSTHKron at r=(32,32,32), p=8 (s=(6,7,7); S rows {5,8}); loss gradient at the rHKron-re result; "
+            "Gaussian sketch factors drawn on the device (Philox4x32-10) inside every step")
 METRIC = "rHKron-re + rSTHKron (+ loss gradient) wall time per step, 512^3 FP32, r=32, p=8"
 
 
@@ -98,9 +99,17 @@ def oracle_step(n: int):
     s, _ = O.subranks_reuse(r, p)
     S, w = O.subranks_matrix(r, p)
     k = [min(n, ww) for ww in w]
-    om = synth.sketch_factors_reuse(x.shape, s, SEED + 1, "f32")
-    oms = synth.sketch_factors_matrix(x.shape, S, k, [0, 1, 2], SEED + 2, "f32")
     t0 = time.perf_counter()
+    # the Gaussian sketch factors from the oracle's statement of the device generator (Philox4x32-10,
+    # Box-Muller): rHKron-re's Phi_j from stream j, rSTHKron's Phi_{j,k} from stream 8 j + k
+    om = [synth.round_to(O.gaussian_factor(n, s[j], SEED + 1, j), "f32") for j in range(3)]
+    oms, done = {}, set()
+    for j in range(3):
+        for kk in range(3):
+            if kk != j:
+                cur = k[kk] if kk in done else n
+                oms[(j, kk)] = synth.round_to(O.gaussian_factor(cur, int(S[j][kk]), SEED + 2, 8 * j + kk), "f32")
+        done.add(j)
     a = O.rhkron(x, r, om)
     ea = O.rel_err(x, a["G"], a["U"])
     b = O.rsthkron(x, r, oms)
@@ -650,9 +659,6 @@ def main():
     s, _ = T.tucker_subranks_reuse(r, p)
     S, w = T.tucker_subranks_matrix(r, p)
     k = [min(n, ww) for n, ww in zip(dims, w)]
-    om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(dims, s, SEED + 1, "f32")]
-    oms = {key: synth.fmat(v, "f32", dev)
-           for key, v in synth.sketch_factors_matrix(dims, S, k, [0, 1, 2], SEED + 2, "f32").items()}
     torch.cuda.synchronize()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -671,6 +677,8 @@ def main():
         with torch.cuda.stream(sa):
             if marks:
                 marks[0].record(sa)
+            # fresh Gaussian sketch factors on the device (Philox4x32-10), as each decomposition draws them
+            om = T.gaussian_factors(dims, s, SEED + 1, torch.float32, dev)
             G1, U1, e1 = T.tucker_rhkron(Xin, r, p, om, async_outputs=True)
             done_rh = torch.cuda.Event()
             done_rh.record(sa)
@@ -682,6 +690,7 @@ def main():
         with torch.cuda.stream(sb):
             if marks:
                 marks[3].record(sb)
+            oms = T.gaussian_factors_matrix(dims, S, k, [0, 1, 2], SEED + 2, torch.float32, dev)
             G2, U2, e2 = T.tucker_rsthkron(Xin, r, p, oms, async_outputs=True)
             if marks:
                 marks[4].record(sb)

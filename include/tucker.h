@@ -192,6 +192,30 @@ TK_API tk_status tucker_subranks_matrix(int d, const int64_t* r, int p, const in
 
 /* ---- building blocks ---------------------------------------------------- */
 
+/* Gaussian sketch factors drawn on the device (the draw lines of Algorithms
+ * rHKron-re and rSTHKron: Phi_j with i.i.d. N(0, 1) entries) from the
+ * counter-based generator Philox4x32-10 (Salmon, Moraes, Dror and Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11), so that every draw
+ * is a pure function of (seed, stream, index) and reproducible anywhere.
+ *
+ * tk_philox4x32: blocks offset .. offset + nblocks - 1 of stream `stream`;
+ * block i is Philox4x32-10 of the counter (i mod 2^32, i div 2^32, stream, 0)
+ * under the key (seed mod 2^32, seed div 2^32).  out: 4 * nblocks uint32 on
+ * the device, 16-byte aligned, block-major.  Errors: TK_ERR_SHAPE for
+ * nblocks < 0, TK_ERR_ARG for a null out, TK_ERR_ALIGN.
+ *
+ * tucker_gaussian_factor: fills the device matrix M (F64, F32 or BF16;
+ * element e = i + rows * j of the column-major order) with N(0, 1) draws of
+ * stream `stream`: element e is output e mod 4 of block e div 4 (offset 0),
+ * where block (x0, x1, x2, x3) yields the Box-Muller pairs u = (x0 + 1) 2^-32,
+ * t = x1 2^-32, (r cos 2 pi t, r sin 2 pi t) with r = sqrt(-2 ln u), and the
+ * same from (x2, x3); evaluated in FP64 and rounded once to M's dtype.
+ * Asynchronous on the handle's stream.  Distinct streams give independent
+ * factors (the Python binding draws Phi_j of mode j from stream j). */
+TK_API tk_status tk_philox4x32(tk_handle* h, uint64_t seed, uint32_t stream, uint64_t offset, int64_t nblocks,
+                               uint32_t* out);
+TK_API tk_status tucker_gaussian_factor(tk_handle* h, uint64_t seed, uint32_t stream, tk_matrix* M);
+
 /* Kronecker-structured sketches of Algorithm rHKron-re (sketch line):
  * for every mode n, Y_n = X x_1 Phi_1 ... x_{n-1} Phi_{n-1} x_{n+1} Phi_{n+1} ... x_d Phi_d,
  * equivalently Y_n(n) = X_(n) (Phi_d kron ... kron Phi_1, skipping n)^T

@@ -28,6 +28,10 @@ Pins (tests/test_oracle_*.py):
   * subranks_reuse / subranks_matrix: the vectors and matrices printed for
     the Miranda and SP runs (Sections 7.5-7.6).
   * loss_grads: central finite differences in FP64.
+  * philox4x32_10 / gaussian_factor: the known-answer vectors published with
+    the Philox generator; uniformity and independence of the 32-bit words;
+    the Box-Muller draws against the normal distribution (moments and a
+    Kolmogorov-Smirnov test).
 """
 from __future__ import annotations
 
@@ -41,6 +45,7 @@ __all__ = [
     "thin_qr", "leading_left_singular_vectors", "sthosvd", "canonical_signs",
     "subranks_reuse", "subranks_matrix", "balanced_factors",
     "rhkron", "rsthkron", "rhkron_noreuse", "rademacher_signs", "srht_sign_tensor", "rhkron_srht",
+    "philox4x32_10", "philox_blocks", "gaussian_factor",
     "reconstruct", "rel_err", "loss", "loss_grads",
 ]
 
@@ -295,6 +300,67 @@ def rhkron(X: np.ndarray, r: Sequence[int], omegas: Sequence[np.ndarray], order:
     U = [Q[j] @ V[j] for j in range(d)]
     G, U = canonical_signs(G, U)
     return dict(G=G, U=U, Q=Q, Y=Ys, Ghat=Ghat)
+
+
+# ---------------------------------------------------------------- Gaussian sketch factors (Alg. rHKron-re draw lines)
+
+_M32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    """Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, "Parallel
+    random numbers: as easy as 1, 2, 3", SC'11), for arrays of counter blocks.
+
+    ctr: (N, 4) and key: (N, 2) arrays of 32-bit words.  A round multiplies
+    words 0 and 2 by 0xD2511F53 and 0xCD9E8D57 (64-bit products split into
+    high and low halves) and returns (hi_2 ^ c_1 ^ k_0, lo_2, hi_0 ^ c_3 ^ k_1,
+    lo_0); before every round but the first the key advances by the Weyl
+    increments (0x9E3779B9, 0xBB67AE85).  Returns (N, 4) uint64 words.
+    """
+    c = np.asarray(ctr, dtype=np.uint64) & _M32
+    k = np.asarray(key, dtype=np.uint64) & _M32
+    c0, c1, c2, c3 = (c[:, i].copy() for i in range(4))
+    k0, k1 = k[:, 0].copy(), k[:, 1].copy()
+    for rnd in range(10):
+        if rnd > 0:
+            k0 = (k0 + np.uint64(0x9E3779B9)) & _M32
+            k1 = (k1 + np.uint64(0xBB67AE85)) & _M32
+        p0 = np.uint64(0xD2511F53) * c0
+        p2 = np.uint64(0xCD9E8D57) * c2
+        c0, c1, c2, c3 = ((p2 >> np.uint64(32)) ^ c1 ^ k0, p2 & _M32,
+                          (p0 >> np.uint64(32)) ^ c3 ^ k1, p0 & _M32)
+    return np.stack([c0, c1, c2, c3], axis=1)
+
+
+def philox_blocks(seed: int, stream: int, offset: int, nblocks: int) -> np.ndarray:
+    """Blocks offset .. offset + nblocks - 1 of the sketch-factor stream: counter
+    (i mod 2^32, i div 2^32, stream, 0), key (seed mod 2^32, seed div 2^32).
+    Returns (nblocks, 4) uint64 words (each below 2^32)."""
+    i = np.arange(offset, offset + nblocks, dtype=np.uint64)
+    ctr = np.stack([i & _M32, i >> np.uint64(32), np.full_like(i, stream & 0xFFFFFFFF),
+                    np.zeros_like(i)], axis=1)
+    key = np.tile(np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint64), (nblocks, 1))
+    return philox4x32_10(ctr, key)
+
+
+def gaussian_factor(rows: int, cols: int, seed: int, stream: int) -> np.ndarray:
+    """A rows x cols matrix of N(0, 1) draws (the paper's Gaussian sketch
+    factors), FP64.  Element e = row + rows * col (column-major) is output
+    e mod 4 of block e div 4 of ``philox_blocks(seed, stream, 0, .)``; a block
+    (x0, x1, x2, x3) gives two Box-Muller pairs: with u = (x0 + 1) 2^-32 in
+    (0, 1] and t = x1 2^-32, r = sqrt(-2 ln u) and (r cos 2 pi t, r sin 2 pi t);
+    likewise from (x2, x3)."""
+    n = rows * cols
+    nb = (n + 3) // 4
+    x = philox_blocks(seed, stream, 0, nb).astype(np.float64)
+    out = np.empty((nb, 4))
+    for a in (0, 2):
+        u = (x[:, a] + 1.0) * 2.0 ** -32
+        t = x[:, a + 1] * 2.0 ** -32
+        r = np.sqrt(-2.0 * np.log(u))
+        out[:, a] = r * np.cos(2.0 * np.pi * t)
+        out[:, a + 1] = r * np.sin(2.0 * np.pi * t)
+    return out.reshape(-1)[:n].reshape((rows, cols), order="F")
 
 
 # ---------------------------------------------------------------- Section 5, Eq. srht_kron

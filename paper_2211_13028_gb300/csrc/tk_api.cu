@@ -918,6 +918,23 @@ tk_status tucker_orth(tk_handle* h, const tk_matrix* Y, tk_matrix* Q, int* info,
     return st;
 }
 
+tk_status tk_philox4x32(tk_handle* h, uint64_t seed, uint32_t stream, uint64_t offset, int64_t nblocks,
+                        uint32_t* out) {
+    return run_call(h, [&](Ctx& c) {
+        TK_REQUIRE(nblocks >= 0, TK_ERR_SHAPE, "philox: negative block count");
+        TK_REQUIRE(nblocks == 0 || out != nullptr, TK_ERR_ARG, "philox: null output");
+        TK_REQUIRE(((uintptr_t)out % 16) == 0, TK_ERR_ALIGN, "philox: output not 16-byte aligned");
+        launch_philox_blocks(c, seed, stream, offset, nblocks, out);
+    });
+}
+
+tk_status tucker_gaussian_factor(tk_handle* h, uint64_t seed, uint32_t stream, tk_matrix* M) {
+    return run_call(h, [&](Ctx& c) {
+        Mat m = mat_in(M, "M");
+        launch_gaussian_factor(c, seed, stream, m);
+    });
+}
+
 tk_status tucker_core(tk_handle* h, const tk_tensor* X, const tk_matrix* Q, tk_tensor* G) {
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X");

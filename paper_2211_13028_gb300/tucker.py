@@ -28,6 +28,7 @@ __all__ = [
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
     "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
     "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tucker_rhkron_srht", "tk_graph_release",
+    "tk_philox4x32", "tucker_gaussian_factor", "gaussian_factors", "gaussian_factors_matrix",
     "TuckerGraph",
 ]
 
@@ -106,6 +107,9 @@ def load():
             "tk_profile_only": ([vp, ctypes.c_char_p], ctypes.c_int),
             "tk_profile_read": ([vp, P(TkProfEntry), ctypes.c_int], ctypes.c_int),
             "tk_graph_release": ([vp], ctypes.c_int),
+            "tk_philox4x32": ([vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, vp],
+                              ctypes.c_int),
+            "tucker_gaussian_factor": ([vp, ctypes.c_uint64, ctypes.c_uint32, P(TkMatrix)], ctypes.c_int),
             "tucker_subranks_reuse": ([ctypes.c_int, i64p, ctypes.c_int, i64p, i64p], ctypes.c_int),
             "tucker_subranks_matrix": ([ctypes.c_int, i64p, ctypes.c_int, P(ctypes.c_int), i64p, i64p], ctypes.c_int),
             "tucker_sketch": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
@@ -457,6 +461,52 @@ def tucker_rhkron_srht(X: torch.Tensor, r: Sequence[int], p: int, H: Sequence[to
 
     return _decomp(fn, X, r, p, list(H), order, qr_method, refine, max_jacobi_sweeps, rel_err, out_dtype, scale,
                    async_outputs)
+
+
+def tk_philox4x32(seed: int, stream: int, offset: int, nblocks: int, device) -> torch.Tensor:
+    """Philox4x32-10 blocks offset .. offset + nblocks - 1 of ``stream`` (the C header's counter and key
+    layout) as an (nblocks, 4) int32 tensor holding the uint32 words' bits."""
+    out = torch.empty((int(nblocks), 4), dtype=torch.int32, device=device)
+    h = _handle(out.device)
+    _check(load().tk_philox4x32(h, ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), ctypes.c_uint32(int(stream)),
+                                ctypes.c_uint64(int(offset)), int(nblocks), out.data_ptr() if nblocks else None), h)
+    return out
+
+
+def tucker_gaussian_factor(rows: int, cols: int, seed: int, stream: int, dtype=torch.float32,
+                           device="cuda") -> torch.Tensor:
+    """A rows x cols column-major matrix of N(0, 1) draws from the device generator (Philox4x32-10 and
+    Box-Muller; the C header defines the element-to-draw map)."""
+    m = _colmajor_matrix(int(rows), int(cols), dtype, torch.device(device))
+    h = _handle(m.device)
+    _check(load().tucker_gaussian_factor(h, ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF),
+                                         ctypes.c_uint32(int(stream)), ctypes.byref(_matrix(m))), h)
+    return m
+
+
+def gaussian_factors(dims: Sequence[int], s: Sequence[int], seed: int, dtype=torch.float32, device="cuda"):
+    """The sketch factors Omega_j = Phi_j^T (n_j x s_j) of Algorithm rHKron-re, drawn on the device:
+    mode j from stream j."""
+    return [tucker_gaussian_factor(n, k, seed, j, dtype, device) for j, (n, k) in enumerate(zip(dims, s))]
+
+
+def gaussian_factors_matrix(dims: Sequence[int], S, kdims: Sequence[int], order: Sequence[int], seed: int,
+                            dtype=torch.float32, device="cuda") -> Dict[Tuple[int, int], torch.Tensor]:
+    """The sketch factors Omega_{j,k} = Phi_{j,k}^T of Algorithm rSTHKron, drawn on the device from stream
+    8 j + k: for the mode j processed at position t, Phi_{j,k} is s_{j,k} x (current size of mode k),
+    k_k for modes processed earlier and n_k otherwise.  S: d x d subranks (row j), as
+    tucker_subranks_matrix returns them."""
+    d = len(dims)
+    Sm = [[int(S[j][k]) for k in range(d)] for j in range(d)]
+    out, done = {}, set()
+    for j in order:
+        for k in range(d):
+            if k == j:
+                continue
+            cur = int(kdims[k]) if k in done else int(dims[k])
+            out[(j, k)] = tucker_gaussian_factor(cur, Sm[j][k], seed, 8 * j + k, dtype, device)
+        done.add(j)
+    return out
 
 
 def tucker_rhkron_noreuse(X: torch.Tensor, r: Sequence[int], p: int, Omega: Dict[Tuple[int, int], torch.Tensor], *,
