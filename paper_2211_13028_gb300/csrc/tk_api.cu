@@ -249,7 +249,7 @@ static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<in
     for (int b = 0; b < B; ++b) df = df && Y[b].dt == TK_F32;
     if (c.qr_method != 1) {
         // pass 1: W = Y^T Y, R1^{-1}, Q1 = Y R1^{-1}
-        for (int b = 0; b < B; ++b) {
+        c.fork(B, [&](int b) {
             const View2& A = Y[b];
             View2 At;  // (column, row) indexing of the same data
             At.p = A.p;
@@ -257,7 +257,7 @@ static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<in
             At.A1 = A.T1; At.sa1 = A.st1; At.sa2 = A.st2;
             At.T1 = A.A1; At.st1 = A.sa1; At.st2 = A.sa2;
             gemm_nt_f64(c, k[b], k[b], n[b], At, At, 1.0, 0.0, W + (int64_t)b * kmax * kmax, kmax, bad + b, df);
-        }
+        });
         launch_chol_inv(c, B, kd, kmax, W, Rinv, bad, 1e-12, df);
         if (df)
             launch_apply_rinv_df(c, B, Y.data(), n.data(), k.data(), Rinv, kmax, Q1.data(), bad);
@@ -265,10 +265,10 @@ static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<in
             for (int b = 0; b < B; ++b)
                 launch_apply_rinv(c, n[b], k[b], Y[b], Rinv + (int64_t)b * kmax * kmax, kmax, Q1[b], bad + b);
         // pass 2 on Q1
-        for (int b = 0; b < B; ++b) {
+        c.fork(B, [&](int b) {
             View2 Qt = view_cols(Q1[b], TK_F64, n[b]);
             gemm_nt_f64(c, k[b], k[b], n[b], Qt, Qt, 1.0, 0.0, W + (int64_t)b * kmax * kmax, kmax, bad + b);
-        }
+        });
         launch_chol_inv(c, B, kd, kmax, W, Rinv, bad, 1e-12, df);
         if (df) {
             std::vector<View2> Qr(B);
@@ -430,17 +430,16 @@ static void finish(Ctx& c, const Tens& X, const std::vector<double*>& Qd, const 
                    const std::vector<Mat>& Uout, double* err_dev) {
     const int d = X.d;
     std::vector<double*> U(d), sg(d);
-    for (int j = 0; j < d; ++j) {
+    c.fork(d, [&](int j) {
         U[j] = c.alloc<double>(X.n[j] * r[j]);
         sg[j] = c.alloc<double>(r[j]);
         gemm_nt_f64(c, X.n[j], r[j], kdim[j], view_rows(Qd[j], TK_F64, X.n[j]), view_cols(V[j], TK_F64, kdim[j]), 1.0,
                     0.0, U[j], X.n[j]);
         launch_sign_fix(c, U[j], X.n[j], r[j], sg[j]);
-    }
+        launch_convert(c, U[j], TK_F64, X.n[j], r[j], X.n[j], (void*)Uout[j].p, Uout[j].dt, Uout[j].ld, 1.f);
+    });
     launch_apply_signs(c, (double*)Gt.p, Gt, sg.data());
     launch_convert(c, Gt.p, TK_F64, Gt.numel(), 1, Gt.numel(), Gout.p, Gout.dt, Gt.numel(), 1.f);
-    for (int j = 0; j < d; ++j)
-        launch_convert(c, U[j], TK_F64, X.n[j], r[j], X.n[j], (void*)Uout[j].p, Uout[j].dt, Uout[j].ld, 1.f);
     if (!err_dev) return;
     // ||X - G x_j U_j|| from the returned G and U, in the accumulation dtype.
     tk_dtype acc = acc_of(X.dt);
@@ -510,6 +509,11 @@ static tk_status run_call(tk_handle* h, F&& body) {
         ex.launches = &h->launches;
         ex.prof = &h->prof;
         ex.use_tc = h->use_tc;
+        for (int i = 0; i < Ctx::kAux; ++i) {
+            ex.aux[i] = h->aux[i];
+            ex.ev_join[i] = h->ev_join[i];
+        }
+        ex.ev_fork = h->ev_fork;
         body(ex);
         return TK_OK;
     } catch (const Error& e) {
@@ -605,6 +609,15 @@ tk_status tk_create(tk_handle** h, void* stream) {
         delete x;
         return TK_ERR_CUDA;
     }
+    bool ok = cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < tk::Ctx::kAux && ok; ++i)
+        ok = cudaStreamCreateWithFlags(&x->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&x->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        tk_destroy(x);
+        return TK_ERR_CUDA;
+    }
     *h = x;
     return TK_OK;
 }
@@ -621,6 +634,14 @@ tk_status tk_destroy(tk_handle* h) {
         cudaEventDestroy(r.b);
     }
     for (auto e : h->prof.pool) cudaEventDestroy(e);
+    for (int i = 0; i < tk::Ctx::kAux; ++i) {
+        if (h->aux[i]) {
+            cudaStreamSynchronize(h->aux[i]);
+            cudaStreamDestroy(h->aux[i]);
+        }
+        if (h->ev_join[i]) cudaEventDestroy(h->ev_join[i]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     delete h;
     return TK_OK;
 }
@@ -1410,7 +1431,7 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
         Tens G64 = Gt.dt == TK_F64 ? Gt : tens_to(c, Gt, TK_F64);
         std::vector<double*> U64(d);
         std::vector<Mat> Cm(d);
-        for (int j = 0; j < d; ++j) {
+        c.fork(d, [&](int j) {
             const int64_t nj = n[j], rj = Gt.n[j];
             U64[j] = c.alloc<double>(nj * rj);
             launch_convert(c, Um[j].p, Um[j].dt, nj, rj, Um[j].ld, U64[j], TK_F64, nj, 1.f);
@@ -1421,10 +1442,19 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
             Cm[j].rows = rj;
             Cm[j].cols = rj;
             Cm[j].ld = rj;
-        }
+        });
         std::vector<Tens> Pm(d);  // P_n = G x_{j != n} C_j
         all_modes(c, G64, all, {}, Cm.data(), TK_F64, Pm, nullptr);
-        for (int j = 0; j < d && dU; ++j) {
+        // dU_n per mode and dG are independent: item j < d is dU_j, item d is dG
+        const int ndu = dU ? d : 0;
+        c.fork(ndu + (dG ? 1 : 0), [&](int j) {
+            if (j == ndu) {
+                // dG = -2s (X x_j U_j^T - G x_j C_j) = -2s (S_0 x_0 U_0^T - P_0 x_0 C_0)
+                Tens E = ttm_to(c, S[0], 0, Ua[0], false, acc);
+                Tens F = ttm_to(c, Pm[0], 0, Cm[0], false, TK_F64);
+                launch_axpby_residual(c, E, F.p, TK_F64, s2, dGt.p, dGt.dt);
+                return;
+            }
             const int64_t nj = n[j], rj = Gt.n[j];
             int64_t K = 1;
             for (int i = 0; i < d; ++i)
@@ -1438,13 +1468,7 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
             gemm_nt_f64(c, rj, rj, K, view_unfold_rows(Pm[j], j), view_unfold_rows(G64, j), 1.0, 0.0, B1, rj);
             gemm_nt_f64(c, nj, rj, rj, view_rows(U64[j], TK_F64, nj), view_cols(B1, TK_F64, rj), -s2, 1.0, A1, nj);
             launch_convert(c, A1, TK_F64, nj, rj, nj, (void*)dUm[j].p, dUm[j].dt, dUm[j].ld, 1.f);
-        }
-        // dG = -2s (X x_j U_j^T - G x_j C_j) = -2s (S_0 x_0 U_0^T - P_0 x_0 C_0)
-        if (dG) {
-            Tens E = ttm_to(c, S[0], 0, Ua[0], false, acc);
-            Tens F = ttm_to(c, Pm[0], 0, Cm[0], false, TK_F64);
-            launch_axpby_residual(c, E, F.p, TK_F64, s2, dGt.p, dGt.dt);
-        }
+        });
         if (dX) {
             Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
             double* nrm = c.alloc<double>(2);

@@ -165,6 +165,22 @@ struct Ctx {
     };
     std::vector<Split> splits;
     bool split_cache = false;
+    // Auxiliary streams of the handle for independent per-mode work (fork).
+    static constexpr int kAux = 3;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kAux] = {};
+
+    // Runs body(b) for b = 0 .. nb-1, item b on auxiliary stream b mod kAux,
+    // each forked from the call's stream by an event and joined back into it
+    // before fork returns, so the items overlap one another (latency-bound
+    // small kernels) while the call stays one stream-ordered unit (also when
+    // it is recorded into a CUDA graph: the fork and join become graph edges).
+    // Workspace allocations happen in item order in the planning pass and in
+    // the executing pass alike.  Without auxiliary streams, or in the planning
+    // pass, the items run in order on the call's stream.
+    template <typename F>
+    void fork(int nb, F&& body);
 
     template <typename T>
     T* alloc(int64_t count) {
@@ -179,6 +195,30 @@ struct Ctx {
     }
     void check_launch() const;
 };
+
+void ctx_fork_begin(Ctx& c, int used);
+void ctx_fork_end(Ctx& c, cudaStream_t main, int used);
+
+template <typename F>
+void Ctx::fork(int nb, F&& body) {
+    if (!exec || nb <= 1 || !aux[0]) {
+        for (int b = 0; b < nb; ++b) body(b);
+        return;
+    }
+    cudaStream_t main = stream;
+    const int used = nb < kAux ? nb : kAux;
+    ctx_fork_begin(*this, used);
+    try {
+        for (int b = 0; b < nb; ++b) {
+            stream = aux[b % kAux];
+            body(b);
+        }
+    } catch (...) {
+        ctx_fork_end(*this, main, used);
+        throw;
+    }
+    ctx_fork_end(*this, main, used);
+}
 
 // RAII event pair around one launch (no-op unless profiling is on).
 struct ProfScope {
@@ -363,4 +403,8 @@ struct tk_handle {
     // the workspace grows (freed by tk_graph_release or tk_destroy)
     bool ws_held = false;
     std::vector<char*> retired;
+    // auxiliary streams and fork / join events (Ctx::fork)
+    cudaStream_t aux[tk::Ctx::kAux] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[tk::Ctx::kAux] = {};
 };

@@ -16,6 +16,26 @@ void Ctx::check_launch() const {
     if (e != cudaSuccess) fail(TK_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
 }
 
+// Only the streams that receive work wait on the fork (a stream that joined a
+// graph recording must be joined back before the recording ends).
+void ctx_fork_begin(Ctx& c, int used) {
+    TK_CUDA(cudaEventRecord(c.ev_fork, c.stream));
+    for (int i = 0; i < used; ++i) TK_CUDA(cudaStreamWaitEvent(c.aux[i], c.ev_fork, 0));
+}
+
+// Joins the first `used` auxiliary streams back into `main` and makes it the
+// call's stream again (also on the error path, hence no throw before that).
+void ctx_fork_end(Ctx& c, cudaStream_t main, int used) {
+    c.stream = main;
+    cudaError_t first = cudaSuccess;
+    for (int i = 0; i < used; ++i) {
+        cudaError_t e = cudaEventRecord(c.ev_join[i], c.aux[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, c.ev_join[i], 0);
+        if (first == cudaSuccess) first = e;
+    }
+    if (first != cudaSuccess) fail(TK_ERR_CUDA, std::string("fork join: ") + cudaGetErrorString(first));
+}
+
 // ------------------------------------------------------------------ loads
 
 __device__ __forceinline__ float ldx(const float* p, int64_t i, float) { return p[i]; }
