@@ -281,13 +281,13 @@ static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<in
             }
         }
     }
-    for (int b = 0; b < B; ++b) {
+    c.fork(B, [&](int b) {
         if (c.qr_method != 2) {
             launch_copy_unfold_to_matrix(c, Y[b], n[b], k[b], Hsrc[b], bad + b);
             launch_householder(c, n[b], k[b], Hsrc[b], Q[b], Htau[b], bad + b);
         }
         if (slots[b] >= 0) launch_qr_info(c, c.dqr + slots[b], bad + b, c.qr_method == 2 ? 3 : 1);
-    }
+    });
 }
 
 static void orth_one(Ctx& c, const View2& Y, int64_t n, int64_t k, double* Q, int slot) {
@@ -514,6 +514,7 @@ static tk_status run_call(tk_handle* h, F&& body) {
             ex.ev_join[i] = h->ev_join[i];
         }
         ex.ev_fork = h->ev_fork;
+        ex.ctr = h->ctr;
         body(ex);
         return TK_OK;
     } catch (const Error& e) {
@@ -609,7 +610,9 @@ tk_status tk_create(tk_handle** h, void* stream) {
         delete x;
         return TK_ERR_CUDA;
     }
-    bool ok = cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    bool ok = cudaMalloc((void**)&x->ctr, sizeof(unsigned) * tk::Ctx::kCounters) == cudaSuccess &&
+              cudaMemset(x->ctr, 0, sizeof(unsigned) * tk::Ctx::kCounters) == cudaSuccess &&
+              cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; i < tk::Ctx::kAux && ok; ++i)
         ok = cudaStreamCreateWithFlags(&x->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&x->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
@@ -642,6 +645,7 @@ tk_status tk_destroy(tk_handle* h) {
         if (h->ev_join[i]) cudaEventDestroy(h->ev_join[i]);
     }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ctr) cudaFree(h->ctr);
     delete h;
     return TK_OK;
 }
@@ -1032,7 +1036,7 @@ static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, c
     // 3. core Ghat = X x_j Q_j^T (modes with Q = I are skipped)
     std::vector<Mat> Qa(d);
     std::vector<int> cm;
-    for (int j = 0; j < d; ++j) {
+    c.fork(d, [&](int j) {
         Mat qm;
         qm.p = Qd[j];
         qm.dt = TK_F64;
@@ -1040,8 +1044,9 @@ static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, c
         qm.cols = k[j];
         qm.ld = Xt.n[j];
         Qa[j] = acc == TK_F64 ? qm : mat_to(c, qm, acc);
+    });
+    for (int j = 0; j < d; ++j)
         if (k[j] < Xt.n[j]) cm.push_back(j);
-    }
     Tens Gh = cm.empty() ? Xt : multi_ttm(c, Xt, cm, Qa.data(), false, acc);
     Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
     // 4. STHOSVD of the core in FP64, U_j = Q_j V_j, gauge, casts, error

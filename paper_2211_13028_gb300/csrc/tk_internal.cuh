@@ -165,6 +165,19 @@ struct Ctx {
     };
     std::vector<Split> splits;
     bool split_cache = false;
+    // Zeroed arrival counters of the handle for split-K products whose last
+    // CTA per tile adds the partial tiles (each use leaves them at zero again);
+    // every product of a call takes its own slice, so forked products never
+    // share one.  nullptr: the separate reduction kernel is used.
+    static constexpr int kCounters = 16384;
+    unsigned* ctr = nullptr;
+    int ctr_used = 0;
+    unsigned* take_counters(int n) {
+        if (!ctr || ctr_used + n > kCounters) return nullptr;
+        unsigned* p = ctr + ctr_used;
+        ctr_used += n;
+        return p;
+    }
     // Auxiliary streams of the handle for independent per-mode work (fork).
     static constexpr int kAux = 3;
     cudaStream_t aux[kAux] = {};
@@ -403,6 +416,7 @@ struct tk_handle {
     // the workspace grows (freed by tk_graph_release or tk_destroy)
     bool ws_held = false;
     std::vector<char*> retired;
+    unsigned* ctr = nullptr;  // Ctx::kCounters zeroed split-K arrival counters
     // auxiliary streams and fork / join events (Ctx::fork)
     cudaStream_t aux[tk::Ctx::kAux] = {};
     cudaEvent_t ev_fork = nullptr;

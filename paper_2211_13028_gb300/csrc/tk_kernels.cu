@@ -452,7 +452,7 @@ __device__ __forceinline__ void dot2_step(float& s, float& c, float a, float b) 
 template <bool DFACC>
 __global__ void __launch_bounds__(256) gemm_tile16_kernel(int64_t m, int64_t n, int64_t K, int64_t kchunk, View2 A,
                                                           View2 B, double alpha, double beta, double* C, int64_t ldc,
-                                                          double* P, const int* skip) {
+                                                          double* P, unsigned* ctr, const int* skip) {
     using E = typename std::conditional<DFACC, float, double>::type;
     if (skip && *skip) return;
     __shared__ E As[32][17];
@@ -495,14 +495,34 @@ __global__ void __launch_bounds__(256) gemm_tile16_kernel(int64_t m, int64_t n, 
         __syncthreads();
     }
     const int64_t a = a0 + tx, b = b0 + ty;
-    if (a >= m || b >= n) return;
+    const bool in = a < m && b < n;
     const double sum = DFACC ? ((double)h0 + (double)l0) + ((double)h1 + (double)l1) : acc0 + acc1;
-    if (P) {
-        P[(int64_t)blockIdx.z * m * n + a + m * b] = sum;
-    } else {
-        double* dst = C + a + ldc * b;
-        *dst = beta == 0.0 ? alpha * sum : alpha * sum + beta * *dst;
+    if (!P) {
+        if (in) {
+            double* dst = C + a + ldc * b;
+            *dst = beta == 0.0 ? alpha * sum : alpha * sum + beta * *dst;
+        }
+        return;
     }
+    if (in) P[(int64_t)blockIdx.z * m * n + a + m * b] = sum;
+    if (!ctr) return;  // a separate reduction kernel adds the partial tiles
+    // the last CTA of this tile to arrive adds the partial tiles (and re-zeroes the counter)
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        unsigned* t = ctr + blockIdx.x + (int64_t)gridDim.x * blockIdx.y;
+        const unsigned prev = atomicAdd(t, 1u);
+        s_last = prev == gridDim.z - 1;
+        if (s_last) *t = 0u;
+    }
+    __syncthreads();
+    if (!s_last || !in) return;
+    __threadfence();
+    double tot = 0.0;
+    for (int z = 0; z < (int)gridDim.z; ++z) tot += __ldcg(P + (int64_t)z * m * n + a + m * b);
+    double* dst = C + a + ldc * b;
+    *dst = beta == 0.0 ? alpha * tot : alpha * tot + beta * *dst;
 }
 
 // Small FP64 products (FP64 runs at 2 FMA per clock per SM here, so a
@@ -588,19 +608,22 @@ void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const 
     nsplit = K > 0 ? (K + kchunk - 1) / kchunk : 1;
     double* P = nsplit > 1 ? c.alloc<double>(nsplit * m * n) : nullptr;
     if (!c.exec || m == 0 || n == 0) return;
+    unsigned* ctr = nsplit > 1 ? c.take_counters((int)tiles) : nullptr;
     dim3 grid((unsigned)((m + 15) / 16), (unsigned)((n + 15) / 16), (unsigned)nsplit);
     {
         ProfScope ps(c, df ? "gemm_df" : "gemm_f64",
                      8.0 * (double)(m * ((n + 15) / 16) + n * ((m + 15) / 16)) * K + 8.0 * m * n * nsplit,
                      2.0 * m * n * K);
         if (df)
-            gemm_tile16_kernel<true><<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, skip);
+            gemm_tile16_kernel<true>
+                <<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, ctr, skip);
         else
-            gemm_tile16_kernel<false><<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, skip);
+            gemm_tile16_kernel<false>
+                <<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, ctr, skip);
         c.counted();
         c.check_launch();
     }
-    if (nsplit > 1) {
+    if (nsplit > 1 && !ctr) {
         const int64_t tot = m * n;
         ProfScope ps(c, "gemm_f64", 8.0 * m * n * (nsplit + 1), (double)m * n * nsplit);
         gemm_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(m, n, (int)nsplit, P, alpha, beta, C,
