@@ -888,6 +888,7 @@ tk_status tucker_sketch(tk_handle* h, const tk_tensor* X, const tk_matrix* Omega
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X");
         c.xdata = Xt.p;
+        c.df64 = Xt.dt != TK_F64;
         c.xnumel = Xt.numel();
         const int d = Xt.d;
         TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "sketch: d must be >= 2");
@@ -964,6 +965,7 @@ tk_status tucker_core(tk_handle* h, const tk_tensor* X, const tk_matrix* Q, tk_t
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X");
         c.xdata = Xt.p;
+        c.df64 = Xt.dt != TK_F64;
         c.xnumel = Xt.numel();
         Tens Gt = tens_in(G, "G");
         const int d = Xt.d;
@@ -1063,6 +1065,7 @@ tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int 
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X", false);
         c.xdata = Xt.p;
+        c.df64 = Xt.dt != TK_F64;
         c.xnumel = Xt.numel();
         const int d = Xt.d;
         TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "rhkron: d must be >= 2");
@@ -1114,6 +1117,7 @@ tk_status tucker_rhkron_srht(tk_handle* h, const tk_tensor* X, const int64_t* r,
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X", false);
         c.xdata = Xt.p;
+        c.df64 = Xt.dt != TK_F64;
         c.xnumel = Xt.numel();
         const int d = Xt.d;
         TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "rhkron_srht: d must be >= 2");
@@ -1195,6 +1199,7 @@ tk_status tucker_rhkron_noreuse(tk_handle* h, const tk_tensor* X, const int64_t*
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X", false);
         c.xdata = Xt.p;
+        c.df64 = Xt.dt != TK_F64;
         c.xnumel = Xt.numel();
         const int d = Xt.d;
         TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "rhkron_noreuse: d must be >= 2");
@@ -1242,6 +1247,7 @@ tk_status tucker_rsthkron(tk_handle* h, const tk_tensor* X, const int64_t* r, in
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X", false);
         c.xdata = Xt.p;
+        c.df64 = Xt.dt != TK_F64;
         c.xnumel = Xt.numel();
         const int d = Xt.d;
         TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "rsthkron: d must be >= 2");
@@ -1359,6 +1365,7 @@ tk_status tucker_loss(tk_handle* h, const tk_tensor* X, const tk_tensor* G, cons
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X");
         c.xdata = Xt.p;
+        c.df64 = Xt.dt != TK_F64;
         c.xnumel = Xt.numel();
         Tens Gt = tens_in(G, "G");
         TK_REQUIRE(loss != nullptr, TK_ERR_ARG, "loss: null output");
@@ -1382,6 +1389,7 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X");
         c.xdata = Xt.p;
+        c.df64 = Xt.dt != TK_F64;
         c.xnumel = Xt.numel();
         Tens Gt = tens_in(G, "G");
         const int d = Xt.d;

@@ -154,6 +154,7 @@ struct Ctx {
     int64_t xnumel = 0;
     bool use_tc = true;            // tensor-core TTM where eligible
     bool capturing = false;        // the stream is recording a CUDA graph (launches are not run now)
+    bool df64 = false;             // FP32-class data: FP64 products may run in double-float arithmetic
     // Factor splits (TF32 hi / lo) made in this pass, reused while split_cache is
     // on: only inside a dimension tree, whose factors are not modified.
     struct Split {

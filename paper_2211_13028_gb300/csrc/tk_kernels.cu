@@ -227,10 +227,18 @@ __global__ void __launch_bounds__(SLAB_THREADS) ttm_slab_kernel(const Tx* __rest
     }
 }
 
+// FP64 TTM of FP32-class data in double-float arithmetic (defined with the
+// double-float helpers below); returns false where it does not apply.
+static bool ttm_direct_df(const Ctx& c, const double* X, int64_t L, int64_t nj, int64_t R, const double* M,
+                          int64_t ldm, bool mtrans, int64_t m, double* out);
+
 template <typename Tx, typename Ta>
 static void ttm_dispatch(const Ctx& c, const Tx* X, int64_t L, int64_t nj, int64_t R, const Ta* M, int64_t ldm,
                          bool mtrans, int64_t m, Ta* out, Ta xinv) {
     int64_t rows = L * R;
+    if constexpr (std::is_same<Tx, double>::value && std::is_same<Ta, double>::value) {
+        if (c.df64 && ttm_direct_df(c, X, L, nj, R, M, ldm, mtrans, m, out)) return;
+    }
     if (L * m <= SLAB_THREADS && nj >= 32 && (double)sizeof(Ta) * (L * nj + SLAB_THREADS) <= 40 * 1024 &&
         R <= 0x7fffffff) {
         const int S = (int)std::min<int64_t>(16, SLAB_THREADS / (L * m));
@@ -430,6 +438,29 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
     hi = h2;
 }
 
+// w * 2^-sh as a double-float pair, by integer splitting of the FP64
+// significand (top 24 bits, then the next 29 rounded to FP32), with no FP64
+// instruction.  Magnitudes below 2^-74 after scaling keep only the high part,
+// below 2^-126 (outside FP32's normal range) they become zero, and at or
+// above 2^128 the high part is an infinity.
+__device__ __forceinline__ float2 df_from_f64(double w, int sh) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(w);
+    const int ex = (int)((u >> 52) & 0x7FF);
+    const int E = ex - 1023 - sh;
+    if (ex == 0 || E < -126) return make_float2(0.f, 0.f);
+    const unsigned sg = (unsigned)(u >> 63) << 31;
+    if (E > 127) return make_float2(__uint_as_float(sg | 0x7F800000u), 0.f);
+    const unsigned long long m = u & ((1ull << 52) - 1);
+    const float hi = __uint_as_float(sg | ((unsigned)(E + 127) << 23) | (unsigned)(m >> 29));
+    float lo = 0.f;
+    if (E >= -74) {
+        const float sc = __uint_as_float((unsigned)(E - 52 + 127) << 23);
+        lo = __fmul_rn(__uint2float_rn((unsigned)(m & ((1u << 29) - 1))), sc);
+        lo = __uint_as_float(__float_as_uint(lo) | sg);
+    }
+    return make_float2(hi, lo);
+}
+
 // One step of the compensated dot product Dot2 (Ogita, Rump and Oishi,
 // "Accurate sum and dot product", 2005): the product is split exactly
 // (p + e, e = fma(a, b, -p)), p is added to the running sum s with Knuth's
@@ -446,14 +477,79 @@ __device__ __forceinline__ void dot2_step(float& s, float& c, float a, float b) 
     c = __fadd_rn(c, __fadd_rn(q, e));
 }
 
-// DFACC: both operands hold FP32 values (FP32 data), and the products are
+// One Dot2 step for double-float operands a = a.x + a.y, b = b.x + b.y: the
+// product of the high parts split exactly, the cross terms (their rounding is
+// ~2^-48 of the product) and both rounding errors into the correction c; the
+// low-low term (2^-48) is dropped.
+__device__ __forceinline__ void df_dot_step(float& s, float& c, float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
+// MODE 0: FP64 fma.  MODE 1: both operands hold FP32 values (FP32 data), and
+// the products are
 // accumulated on the FP32 pipe with Dot2 (as accurate as about 48 significant
 // bits, several times the FP64 rate here); otherwise FP64 fma.
-template <bool DFACC>
+// One thread per output of out[l + L (a + m r)] = sum_i M(i, a) X[l + L (i + nj r)],
+// FP64 operands split into double-float pairs (M staged split in shared
+// memory), Dot2 accumulation: the FP64 pipe here is 1/64 of the FP32 pipe.
+__global__ void __launch_bounds__(256) ttm_direct_df_kernel(const double* __restrict__ X, int64_t L, int64_t nj,
+                                                            int64_t R, const double* __restrict__ M, int64_t ldm,
+                                                            int mtrans, int64_t m, double* __restrict__ out) {
+    extern __shared__ float2 msp[];  // nj x m: msp[i + nj a] = split M(i, a)
+    for (int64_t e = threadIdx.x; e < nj * m; e += blockDim.x) {
+        const int64_t i = e % nj, a = e / nj;
+        msp[e] = df_from_f64(mtrans ? M[a + ldm * i] : M[i + ldm * a], 0);
+    }
+    __syncthreads();
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= L * m * R) return;
+    const int64_t l = o % L, rest = o / L;
+    const int64_t a = rest % m, r = rest / m;
+    const double* x = X + l + L * nj * r;
+    const float2* mc = msp + nj * a;
+    float sh = 0.f, sl = 0.f;
+    for (int64_t i = 0; i < nj; ++i) df_dot_step(sh, sl, df_from_f64(x[L * i], 0), mc[i]);
+    out[o] = (double)sh + (double)sl;
+}
+
+static bool ttm_direct_df(const Ctx& c, const double* X, int64_t L, int64_t nj, int64_t R, const double* M,
+                          int64_t ldm, bool mtrans, int64_t m, double* out) {
+    const int64_t rows = L * R;
+    const size_t smem = sizeof(float2) * (size_t)(nj * m);
+    if (rows * m > (1 << 22) || smem > 48 * 1024) return false;
+    ProfScope ps(c, "ttm_simt", 8.0 * rows * nj + 8.0 * rows * m, 2.0 * rows * nj * m);
+    ttm_direct_df_kernel<<<(unsigned)((rows * m + 255) / 256), 256, smem, c.stream>>>(X, L, nj, R, M, ldm,
+                                                                                     mtrans ? 1 : 0, m, out);
+    c.counted();
+    c.check_launch();
+    return true;
+}
+
+template <typename E>
+__device__ __forceinline__ E gemm_elem(double v) {
+    if constexpr (std::is_same<E, float2>::value)
+        return df_from_f64(v, 0);
+    else
+        return (E)v;
+}
+
+// MODE 2: the operands (FP64 or FP32) are split into double-float pairs on
+// load and the products accumulate with df_dot_step on the FP32 pipe (~47
+// significant bits; FP32's exponent range bounds the products).
+template <int MODE>
 __global__ void __launch_bounds__(256) gemm_tile16_kernel(int64_t m, int64_t n, int64_t K, int64_t kchunk, View2 A,
                                                           View2 B, double alpha, double beta, double* C, int64_t ldc,
                                                           double* P, unsigned* ctr, const int* skip) {
-    using E = typename std::conditional<DFACC, float, double>::type;
+    constexpr bool DFACC = MODE != 0;
+    using E = typename std::conditional<MODE == 0, double, typename std::conditional<MODE == 1, float, float2>::type>::type;
     if (skip && *skip) return;
     __shared__ E As[32][17];
     __shared__ E Bs[32][17];
@@ -478,18 +574,21 @@ __global__ void __launch_bounds__(256) gemm_tile16_kernel(int64_t m, int64_t n, 
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int64_t k1 = k0 + ka[q], k2 = k0 + kb2[q];
-            As[ka[q]][ra[q]] = (E)((oa[q] >= 0 && k1 < ke) ? v2get(A, oa[q] + v2col(A, k1)) : 0.0);
-            Bs[kb2[q]][rb[q]] = (E)((ob[q] >= 0 && k2 < ke) ? v2get(B, ob[q] + v2col(B, k2)) : 0.0);
+            As[ka[q]][ra[q]] = gemm_elem<E>((oa[q] >= 0 && k1 < ke) ? v2get(A, oa[q] + v2col(A, k1)) : 0.0);
+            Bs[kb2[q]][rb[q]] = gemm_elem<E>((ob[q] >= 0 && k2 < ke) ? v2get(B, ob[q] + v2col(B, k2)) : 0.0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 32; kk += 2) {
-            if (DFACC) {
-                dot2_step(h0, l0, (float)As[kk][tx], (float)Bs[kk][ty]);
-                dot2_step(h1, l1, (float)As[kk + 1][tx], (float)Bs[kk + 1][ty]);
+            if constexpr (MODE == 2) {
+                df_dot_step(h0, l0, As[kk][tx], Bs[kk][ty]);
+                df_dot_step(h1, l1, As[kk + 1][tx], Bs[kk + 1][ty]);
+            } else if constexpr (MODE == 1) {
+                dot2_step(h0, l0, As[kk][tx], Bs[kk][ty]);
+                dot2_step(h1, l1, As[kk + 1][tx], Bs[kk + 1][ty]);
             } else {
-                acc0 = fma((double)As[kk][tx], (double)Bs[kk][ty], acc0);
-                acc1 = fma((double)As[kk + 1][tx], (double)Bs[kk + 1][ty], acc1);
+                acc0 = fma(As[kk][tx], Bs[kk][ty], acc0);
+                acc1 = fma(As[kk + 1][tx], Bs[kk + 1][ty], acc1);
             }
         }
         __syncthreads();
@@ -577,10 +676,12 @@ __global__ void __launch_bounds__(256) gemm_small_kernel(int64_t m, int64_t n, i
 
 void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const View2& B, double alpha, double beta,
                  double* C, int64_t ldc, const int* skip, bool df_ok) {
-    // double-float accumulation only where the caller allows it and both operands are FP32
-    const bool df = df_ok && A.dt == TK_F32 && B.dt == TK_F32;
+    // Dot2 accumulation where the caller allows it and both operands are FP32; double-float
+    // operands throughout a call on FP32-class data (c.df64)
+    const int mode = (df_ok && A.dt == TK_F32 && B.dt == TK_F32) ? 1 : (c.df64 ? 2 : 0);
+    const bool df = mode != 0;
     // short K and few 16 x 16 tiles: smaller tiles with K split inside the CTA
-    if (!df && K < 128 && ((m + 15) / 16) * ((n + 15) / 16) < 152) {
+    if (mode != 1 && K < 128 && ((m + 15) / 16) * ((n + 15) / 16) < 152) {
         if (!c.exec || m == 0 || n == 0) return;
         const bool t8 = ((m + 7) / 8) * ((n + 7) / 8) >= 152;
         const int T = t8 ? 8 : 4;
@@ -614,11 +715,14 @@ void gemm_nt_f64(Ctx& c, int64_t m, int64_t n, int64_t K, const View2& A, const 
         ProfScope ps(c, df ? "gemm_df" : "gemm_f64",
                      8.0 * (double)(m * ((n + 15) / 16) + n * ((m + 15) / 16)) * K + 8.0 * m * n * nsplit,
                      2.0 * m * n * K);
-        if (df)
-            gemm_tile16_kernel<true>
+        if (mode == 1)
+            gemm_tile16_kernel<1>
+                <<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, ctr, skip);
+        else if (mode == 2)
+            gemm_tile16_kernel<2>
                 <<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, ctr, skip);
         else
-            gemm_tile16_kernel<false>
+            gemm_tile16_kernel<0>
                 <<<grid, 256, 0, c.stream>>>(m, n, K, kchunk, A, B, alpha, beta, C, ldc, P, ctr, skip);
         c.counted();
         c.check_launch();
@@ -813,27 +917,6 @@ __device__ __forceinline__ void df_rcp_rsqrt(float2 p, float2& inv, float2& ys) 
     const float2 py = df_mul2(p, y2);
     const float d = __fsub_rn(__fsub_rn(1.0f, py.x), py.y);  // 1 - p y0^2 (~2^-22)
     ys = df_norm(y0, __fmul_rn(__fmul_rn(0.5f, y0), d));
-}
-
-// w * 2^-sh as a double-float pair, by integer splitting of the FP64
-// significand (top 24 bits, then the next 29 rounded to FP32).  Magnitudes
-// below 2^-74 after scaling keep only the high part; below 2^-100 they are
-// flushed to zero (negligible next to the unit-scale diagonal).
-__device__ __forceinline__ float2 df_from_f64(double w, int sh) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(w);
-    const int ex = (int)((u >> 52) & 0x7FF);
-    const int E = ex - 1023 - sh;
-    if (ex == 0 || E < -100) return make_float2(0.f, 0.f);
-    const unsigned sg = (unsigned)(u >> 63) << 31;
-    const unsigned long long m = u & ((1ull << 52) - 1);
-    const float hi = __uint_as_float(sg | ((unsigned)(E + 127) << 23) | (unsigned)(m >> 29));
-    float lo = 0.f;
-    if (E >= -74) {
-        const float sc = __uint_as_float((unsigned)(E - 52 + 127) << 23);
-        lo = __fmul_rn(__uint2float_rn((unsigned)(m & ((1u << 29) - 1))), sc);
-        lo = __uint_as_float(__float_as_uint(lo) | sg);
-    }
-    return make_float2(hi, lo);
 }
 
 // One row of a column step: A(i, i..k-1) followed by M(i, 0..j), NQ 32-wide
