@@ -216,6 +216,12 @@ TK_API tk_status tk_philox4x32(tk_handle* h, uint64_t seed, uint32_t stream, uin
                                uint32_t* out);
 TK_API tk_status tucker_gaussian_factor(tk_handle* h, uint64_t seed, uint32_t stream, tk_matrix* M);
 
+/* count factors (0 <= count <= 64) in one launch: M[f] gets the draws of
+ * stream streams[f], exactly as tucker_gaussian_factor would write them.
+ * Errors: TK_ERR_ARG for a bad count or null arrays, then as above. */
+TK_API tk_status tucker_gaussian_factors(tk_handle* h, uint64_t seed, int count, const uint32_t* streams,
+                                         tk_matrix* M);
+
 /* Kronecker-structured sketches of Algorithm rHKron-re (sketch line):
  * for every mode n, Y_n = X x_1 Phi_1 ... x_{n-1} Phi_{n-1} x_{n+1} Phi_{n+1} ... x_d Phi_d,
  * equivalently Y_n(n) = X_(n) (Phi_d kron ... kron Phi_1, skipping n)^T

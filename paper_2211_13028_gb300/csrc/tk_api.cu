@@ -957,7 +957,22 @@ tk_status tk_philox4x32(tk_handle* h, uint64_t seed, uint32_t stream, uint64_t o
 tk_status tucker_gaussian_factor(tk_handle* h, uint64_t seed, uint32_t stream, tk_matrix* M) {
     return run_call(h, [&](Ctx& c) {
         Mat m = mat_in(M, "M");
-        launch_gaussian_factor(c, seed, stream, m);
+        unsigned s = stream;
+        launch_gaussian_factors(c, seed, 1, &s, &m);
+    });
+}
+
+tk_status tucker_gaussian_factors(tk_handle* h, uint64_t seed, int count, const uint32_t* streams, tk_matrix* M) {
+    return run_call(h, [&](Ctx& c) {
+        TK_REQUIRE(count >= 0 && count <= 64, TK_ERR_ARG, "gaussian factors: 0 <= count <= 64");
+        TK_REQUIRE(count == 0 || (streams && M), TK_ERR_ARG, "gaussian factors: null streams or M");
+        std::vector<Mat> m(count);
+        std::vector<unsigned> st(count);
+        for (int f = 0; f < count; ++f) {
+            m[f] = mat_in(&M[f], "M");
+            st[f] = streams[f];
+        }
+        launch_gaussian_factors(c, seed, count, st.data(), m.data());
     });
 }
 

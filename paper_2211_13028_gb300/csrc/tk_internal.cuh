@@ -296,7 +296,8 @@ void launch_sign_copy(const Ctx& c, const Tens& X, int n, uint64_t seed, void* d
 // (4 uint32 each, out 16-byte aligned); Gaussian factor draws into m.
 void launch_philox_blocks(const Ctx& c, unsigned long long seed, unsigned stream, unsigned long long offset,
                           int64_t nblocks, unsigned* out);
-void launch_gaussian_factor(const Ctx& c, unsigned long long seed, unsigned stream, const Mat& m);
+void launch_gaussian_factors(const Ctx& c, unsigned long long seed, int count, const unsigned* streams,
+                             const Mat* m);
 bool ttm_bf16_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
 void launch_ttm_bf16(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 // Fused last step of a reconstruction: P = W x_j M^T is formed tile by tile and

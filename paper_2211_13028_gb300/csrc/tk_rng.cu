@@ -19,6 +19,8 @@
 
 namespace tk {
 
+constexpr int GF_MAX = 64;  // factors per launch
+
 // One Philox4x32 round per iteration: words 0 and 2 multiplied by the round
 // constants, their high halves xored with the other words and the key; the
 // key advances by the Weyl increments before every round but the first.
@@ -56,9 +58,20 @@ __device__ __forceinline__ void gf_store(void* p, tk_dtype dt, int64_t o, double
         static_cast<__nv_bfloat16*>(p)[o] = __double2bfloat16(v);
 }
 
-// One thread per block of four outputs.
-__global__ void gaussian_factor_kernel(unsigned long long seed, unsigned stream, int64_t rows, int64_t cols,
-                                       int64_t ld, tk_dtype dt, void* out) {
+// One thread per block of four outputs; blockIdx.y selects the factor.
+struct GfBatch {
+    int64_t rows[GF_MAX], cols[GF_MAX], ld[GF_MAX];
+    void* out[GF_MAX];
+    unsigned stream[GF_MAX];
+    tk_dtype dt[GF_MAX];
+};
+
+__global__ void gaussian_factor_kernel(unsigned long long seed, GfBatch gb) {
+    const int f = blockIdx.y;
+    const int64_t rows = gb.rows[f], cols = gb.cols[f], ld = gb.ld[f];
+    const unsigned stream = gb.stream[f];
+    const tk_dtype dt = gb.dt[f];
+    void* out = gb.out[f];
     const int64_t n = rows * cols, nb = (n + 3) / 4;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
         const uint4 x = philox_block(seed, stream, (unsigned long long)b);
@@ -91,13 +104,27 @@ void launch_philox_blocks(const Ctx& c, unsigned long long seed, unsigned stream
     c.check_launch();
 }
 
-void launch_gaussian_factor(const Ctx& c, unsigned long long seed, unsigned stream, const Mat& m) {
-    if (!c.exec || m.rows * m.cols == 0) return;
-    const int64_t nb = (m.rows * m.cols + 3) / 4;
-    const unsigned grid = (unsigned)std::min<int64_t>((nb + 127) / 128, 152 * 8);
-    ProfScope ps(c, "rng", (double)dtype_size(m.dt) * m.rows * m.cols, 0.0);
-    gaussian_factor_kernel<<<grid, 128, 0, c.stream>>>(seed, stream, m.rows, m.cols, m.ld, m.dt,
-                                                        const_cast<void*>(m.p));
+void launch_gaussian_factors(const Ctx& c, unsigned long long seed, int count, const unsigned* streams,
+                             const Mat* m) {
+    if (!c.exec || count == 0) return;
+    TK_REQUIRE(count <= GF_MAX, TK_ERR_ARG, "gaussian factors: at most 64 per launch");
+    GfBatch gb;
+    int64_t nbmax = 0;
+    double bytes = 0.0;
+    for (int f = 0; f < count; ++f) {
+        gb.rows[f] = m[f].rows;
+        gb.cols[f] = m[f].cols;
+        gb.ld[f] = m[f].ld;
+        gb.out[f] = const_cast<void*>(m[f].p);
+        gb.stream[f] = streams[f];
+        gb.dt[f] = m[f].dt;
+        nbmax = std::max(nbmax, (m[f].rows * m[f].cols + 3) / 4);
+        bytes += (double)dtype_size(m[f].dt) * m[f].rows * m[f].cols;
+    }
+    if (nbmax == 0) return;
+    const unsigned gx = (unsigned)std::min<int64_t>((nbmax + 127) / 128, 152 * 8);
+    ProfScope ps(c, "rng", bytes, 0.0);
+    gaussian_factor_kernel<<<dim3(gx, (unsigned)count), 128, 0, c.stream>>>(seed, gb);
     c.counted();
     c.check_launch();
 }

@@ -28,7 +28,8 @@ __all__ = [
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
     "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
     "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tucker_rhkron_srht", "tk_graph_release",
-    "tk_philox4x32", "tucker_gaussian_factor", "gaussian_factors", "gaussian_factors_matrix",
+    "tk_philox4x32", "tucker_gaussian_factor", "tucker_gaussian_factors", "gaussian_factors",
+    "gaussian_factors_matrix",
     "TuckerGraph",
 ]
 
@@ -110,6 +111,8 @@ def load():
             "tk_philox4x32": ([vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, vp],
                               ctypes.c_int),
             "tucker_gaussian_factor": ([vp, ctypes.c_uint64, ctypes.c_uint32, P(TkMatrix)], ctypes.c_int),
+            "tucker_gaussian_factors": ([vp, ctypes.c_uint64, ctypes.c_int, P(ctypes.c_uint32), P(TkMatrix)],
+                                        ctypes.c_int),
             "tucker_subranks_reuse": ([ctypes.c_int, i64p, ctypes.c_int, i64p, i64p], ctypes.c_int),
             "tucker_subranks_matrix": ([ctypes.c_int, i64p, ctypes.c_int, P(ctypes.c_int), i64p, i64p], ctypes.c_int),
             "tucker_sketch": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
@@ -484,10 +487,32 @@ def tucker_gaussian_factor(rows: int, cols: int, seed: int, stream: int, dtype=t
     return m
 
 
+def _draw_factors(shapes, streams, seed: int, dtype, device) -> List[torch.Tensor]:
+    """One launch drawing a factor of each shape (rows, cols) from the given streams."""
+    dev = torch.device(device)
+    ms = [_colmajor_matrix(int(r), int(c), dtype, dev) for r, c in shapes]
+    if not ms:
+        return ms
+    st = (ctypes.c_uint32 * len(ms))(*[int(x) for x in streams])
+    h = _handle(ms[0].device)
+    _check(load().tucker_gaussian_factors(h, ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), len(ms), st,
+                                          _mats(ms)), h)
+    return ms
+
+
 def gaussian_factors(dims: Sequence[int], s: Sequence[int], seed: int, dtype=torch.float32, device="cuda"):
-    """The sketch factors Omega_j = Phi_j^T (n_j x s_j) of Algorithm rHKron-re, drawn on the device:
-    mode j from stream j."""
-    return [tucker_gaussian_factor(n, k, seed, j, dtype, device) for j, (n, k) in enumerate(zip(dims, s))]
+    """The sketch factors Omega_j = Phi_j^T (n_j x s_j) of Algorithm rHKron-re, drawn on the device in one
+    launch: mode j from stream j."""
+    return _draw_factors(list(zip(dims, s)), range(len(dims)), seed, dtype, device)
+
+
+def tucker_gaussian_factors(shapes: Sequence[Tuple[int, int]], seed: int, streams: Sequence[int],
+                            dtype=torch.float32, device="cuda") -> List[torch.Tensor]:
+    """Several column-major factors of N(0, 1) draws in one launch; factor f has shape shapes[f] and
+    the draws of stream streams[f] (the same values tucker_gaussian_factor gives)."""
+    if len(shapes) != len(streams):
+        raise TuckerError(1, "one stream per factor")
+    return _draw_factors(list(shapes), list(streams), seed, dtype, device)
 
 
 def gaussian_factors_matrix(dims: Sequence[int], S, kdims: Sequence[int], order: Sequence[int], seed: int,
@@ -498,15 +523,16 @@ def gaussian_factors_matrix(dims: Sequence[int], S, kdims: Sequence[int], order:
     tucker_subranks_matrix returns them."""
     d = len(dims)
     Sm = [[int(S[j][k]) for k in range(d)] for j in range(d)]
-    out, done = {}, set()
+    keys, shapes, done = [], [], set()
     for j in order:
         for k in range(d):
             if k == j:
                 continue
-            cur = int(kdims[k]) if k in done else int(dims[k])
-            out[(j, k)] = tucker_gaussian_factor(cur, Sm[j][k], seed, 8 * j + k, dtype, device)
+            keys.append((j, k))
+            shapes.append((int(kdims[k]) if k in done else int(dims[k]), Sm[j][k]))
         done.add(j)
-    return out
+    ms = _draw_factors(shapes, [8 * j + k for j, k in keys], seed, dtype, device)
+    return dict(zip(keys, ms))
 
 
 def tucker_rhkron_noreuse(X: torch.Tensor, r: Sequence[int], p: int, Omega: Dict[Tuple[int, int], torch.Tensor], *,

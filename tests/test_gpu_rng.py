@@ -76,3 +76,13 @@ def test_rhkron_with_device_factors(dev):
     g, u = align(to_np(G), [to_np(v) for v in U], ref["U"])
     assert rel(g, ref["G"]) <= tol
     assert rel(O.reconstruct(g, u), O.reconstruct(ref["G"], ref["U"])) <= tol
+
+
+def test_gaussian_factors_batched_equals_single(dev):
+    # one launch for several factors writes what one call per factor writes
+    shapes, streams = [(64, 5), (33, 7), (0, 3), (9, 1)], [0, 9, 2, 17]
+    many = T.tucker_gaussian_factors(shapes, 77, streams, torch.float64, dev)
+    for (r, c), s, m in zip(shapes, streams, many):
+        one = T.tucker_gaussian_factor(r, c, 77, s, torch.float64, dev)
+        assert torch.equal(m, one)
+        assert np.max(np.abs(to_np(m) - O.gaussian_factor(r, c, 77, s)), initial=0.0) <= 1e-13
