@@ -71,7 +71,7 @@ def test_sketch_matches_explicit_kronecker(dev):
 # ------------------------------------------------------------------ thin QR
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("n,k", [(512, 49), (97, 13), (300, 112)])
+@pytest.mark.parametrize("n,k", [(512, 49), (97, 13), (300, 112), (64, 1), (33, 2)])
 def test_orth_cholqr2_parity(dev, dtype, n, k):
     y = synth.round_to(_rng(5).standard_normal((n, k)), dtype)
     Q, info = T.tucker_orth(synth.fmat(y, dtype, dev), out_dtype=torch.float64)
@@ -94,6 +94,18 @@ def test_orth_rank_deficient_falls_back(dev):
     assert info == 1
     q = to_np(Q)
     assert np.max(np.abs(q.T @ q - np.eye(12))) <= 1e-13
+    assert np.linalg.norm(q @ (q.T @ y) - y) <= 1e-12 * np.linalg.norm(y)
+
+
+def test_orth_rank_deficient_f32_falls_back(dev):
+    # FP32 sketches take the double-float CholeskyQR2; a numerically rank-deficient one must
+    # still be caught by the pivot test and handed to Householder
+    g = _rng(17)
+    y = synth.round_to(g.standard_normal((300, 5)) @ g.standard_normal((5, 20)), "f32")
+    Q, info = T.tucker_orth(synth.fmat(y, "f32", dev), out_dtype=torch.float64)
+    assert info == 1
+    q = to_np(Q)
+    assert np.max(np.abs(q.T @ q - np.eye(20))) <= 1e-13
     assert np.linalg.norm(q @ (q.T @ y) - y) <= 1e-12 * np.linalg.norm(y)
 
 
