@@ -1575,27 +1575,64 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
     float* Lx = Lc + kp;
     int* lab = reinterpret_cast<int*>(Lx + kp);   // final index label per slot (after the sweeps)
     __shared__ float2 meta[2][64];  // (c, s) per pair of the current / next step
-    __shared__ double red[33];
+    __shared__ int ired[33];
+    __shared__ float fred[33];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     const bool rwarp = tid < 32;
-    double part = 0.0;
-    for (int e = tid; e < k * k; e += nt) part += A[e] * A[e];
-    const double nrm = sqrt(block_sum(part, red));
-    int ex = 0;
-    if (nrm > 0.0 && nrm < INFINITY) frexp(nrm, &ex);
-    const double sc = ldexp(1.0, -ex);  // nrm * sc in [0.5, 1)
+    // Scale 2^-sh with ||A||_F 2^-sh in [0.5, 1), found with integer and FP32 operations only
+    // (FP64 runs at 1/64 of the FP32 rate here): the largest exponent of the entries, then the
+    // norm of the entries scaled below 1 in FP32, which places ||A|| within its binade.
+    int emax = -100000;
+    for (int e = tid; e < k * k; e += nt) {
+        const int ex = (int)((__double_as_longlong(A[e]) >> 52) & 0x7FF);
+        if (ex) emax = max(emax, ex - 1023);
+    }
+    for (int o = 16; o; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if (lane == 0) ired[tid >> 5] = emax;
+    __syncthreads();
+    if (tid < 32) {
+        int v = tid < (nt >> 5) ? ired[tid] : -100000;
+        for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (tid == 0) ired[32] = v;
+    }
+    __syncthreads();
+    emax = ired[32];
+    float part = 0.f;
+    if (emax > -100000)
+        for (int e = tid; e < k * k; e += nt) {
+            const float2 v = df_from_f64(A[e], emax + 1);
+            part = fmaf(v.x, v.x, part);
+        }
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) fred[tid >> 5] = part;
+    __syncthreads();
+    if (tid < 32) {
+        float v = tid < (nt >> 5) ? fred[tid] : 0.f;
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (tid == 0) fred[32] = v;
+    }
+    __syncthreads();
+    int ex2 = 0;
+    const float nsc = (fred[32] > 0.f) ? frexpf(sqrtf(fred[32]), &ex2) : 0.f;  // ||A|| 2^-sh in [0.5, 1)
+    const int sh = (fred[32] > 0.f) ? emax + 1 + ex2 : 0;
     for (int e = tid; e < kp * kp; e += nt) {
         const int i = e % kp, j = e / kp;
         if (i < j) {
-            Fc[i * ld + j] = (j < k) ? (float)(A[i + (int64_t)k * j] * sc) : 0.f;
+            float f = 0.f;
+            if (j < k) {
+                const float2 v = df_from_f64(A[i + (int64_t)k * j], sh);
+                f = __fadd_rn(v.x, v.y);
+            }
+            Fc[i * ld + j] = f;
         } else if (i == j) {
-            const double v = (i < k) ? A[i + (int64_t)k * i] * sc : 0.0;
-            const float hv = (float)v;
+            float2 v = make_float2(0.f, 0.f);
+            if (i < k) v = df_from_f64(A[i + (int64_t)k * i], sh);
+            const float hv = __fadd_rn(v.x, v.y);  // nearest FP32 value (hi + lo renormalised)
             Hc[i] = hv;
-            Lc[i] = DF ? (float)(v - (double)hv) : 0.f;
+            Lc[i] = DF ? __fsub_rn(v.y, __fsub_rn(hv, v.x)) : 0.f;
         }
     }
-    const float fthr = (float)(tol * nrm * sc);
+    const float fthr = (float)tol * nsc;
     // update threads (warps 1..): their blocks' read bases and write addresses
     const int nblk = h * (h + 1) / 2, nu = nt - 32, ut = tid - 32;
     int bt[JM_BPT], rd[JM_BPT], w0[JM_BPT], w1[JM_BPT], w2[JM_BPT], w3[JM_BPT];
@@ -1733,29 +1770,25 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
     if (!converged && tid == 0) atomicOr(flags, FLAG_NOT_CONVERGED);
     // index labels: after `steps` moves slot x holds the index that started in
     // slot pi^{-steps}(x); slots 1..kp-1 form one cycle of pi, walked once
-    if (tid == 0) {
-        lab[0] = 0;
-        if (m > 0) {
-            int* cyc = reinterpret_cast<int*>(Fx);  // the spare F buffer: cycle order, then positions
-            int* pos = cyc + kp;
-            int x = 1;
-            for (int j = 0; j < m; ++j) {
-                cyc[j] = x;
-                pos[x] = j;
-                x = jm_pi(x, h);
-            }
-            const int sh = steps % m;
-            for (int y = 1; y < kp; ++y) {
-                int j = pos[y] - sh;
-                if (j < 0) j += m;
-                lab[y] = cyc[j];
-            }
+    // (the cycle in closed form: position j holds slot 1 for j = 0, slot 2j for 1 <= j < h, slot
+    // 2h - 1 - 2(j - h) for j >= h; so slot x sits at 0, x / 2 or h + (2h - 1 - x) / 2)
+    if (tid < kp) {
+        int lb = 0;
+        if (tid > 0 && m > 0) {
+            const int pos = tid == 1 ? 0 : ((tid & 1) ? h + (2 * h - 1 - tid) / 2 : tid / 2);
+            int j = pos - steps % m;
+            if (j < 0) j += m;
+            lb = j == 0 ? 1 : (j < h ? 2 * j : 2 * h - 1 - 2 * (j - h));
         }
+        lab[tid] = lb;
     }
     __syncthreads();
+    // 2^sh as two representable factors (sh may reach past the FP64 exponent range by one)
+    const double up1 = __longlong_as_double((long long)(1023 + sh / 2) << 52);
+    const double up2 = __longlong_as_double((long long)(1023 + sh - sh / 2) << 52);
     for (int x = tid; x < kp; x += nt) {
         const int i = lab[x];
-        if (i < k) Dout[i] = ((double)Hc[x] + (DF ? (double)Lc[x] : 0.0)) / sc;
+        if (i < k) Dout[i] = (((double)Hc[x] + (DF ? (double)Lc[x] : 0.0)) * up1) * up2;
         ginfo[1 + x] = i;
     }
     if (tid == 0) ginfo[0] = steps;
