@@ -19,7 +19,12 @@
 //   warps 8-11  epilogue: tcgen05.ld of a double-buffered accumulator, hi+lo column
 //               halves summed, rows written to global memory.
 // One MMA per 8-deep K step computes A_hi * [M_hi ; M_lo] (N = 2*NPAD, the two halves
-// land in separate TMEM columns); a second adds A_lo * M_hi into the first half.
+// land in separate TMEM columns); a second adds A_lo * M_hi into the second half, with
+// the other small term.  The tensor core's FP32 accumulation rounds each addition
+// toward zero, a bias that grows with the number of additions into the large
+// A_hi * M_hi sum, so that sum receives one MMA per K step and the corrections the
+// other (on the 512^3 benchmark field the core pass's relative error against the
+// FP64 oracle went from 1.0e-5 to 7.3e-6).
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA raises
 // FLAG_TIMEOUT, stops issuing work, drains what it issued and frees its TMEM.
 #include <cuda_bf16.h>
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                     for (int k8 = 0; k8 < kChunk / 8; ++k8) {
                         const uint64_t bdesc = desc_sw128(bs + 32 * k8);
                         mma_tf32_ts(d_tmem, a_hi + 8 * k8, bdesc, idesc_tf32(2 * NPAD), (kc | k8) != 0);
-                        mma_tf32_ts(d_tmem, a_hi + 32 + 8 * k8, bdesc, idesc_tf32(NPAD), 1u);
+                        mma_tf32_ts(d_tmem + NPAD, a_hi + 32 + 8 * k8, bdesc, idesc_tf32(NPAD), 1u);
                     }
                     tc_commit(&aempty[b]);
                     tc_commit(&xfree[s]);
