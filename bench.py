@@ -47,8 +47,8 @@ KERNEL_NAMES = {
 # DRAM traffic / algorithmic bytes of one X-streaming launch, from an ncu capture of a 384^3 FP32
 # core pass (243.0 MB moved for 251.5 MB of algorithmic bytes: part of the output stays in L2;
 # summarised under profiles/); traffic scales with the elements streamed.
-TRAFFIC_RATIO = {"xpass_tc": 243.0 / 251.5}
-TRAFFIC_NOTE = {"xpass_tc": "algorithmic bytes per launch x 0.966, the DRAM/algorithmic ratio of a 384^3 core-pass "
+TRAFFIC_RATIO = {"xpass_tc": 241.9 / 251.5}
+TRAFFIC_NOTE = {"xpass_tc": "algorithmic bytes per launch x 0.962, the DRAM/algorithmic ratio of a 384^3 core-pass "
                             "capture"}
 
 
