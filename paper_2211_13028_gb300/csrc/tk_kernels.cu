@@ -1131,6 +1131,7 @@ struct ApplyBatch {
 };
 
 constexpr int APDF_THREADS = 256;
+constexpr int APDF_U = 8;  // global loads in flight per thread while staging
 
 __global__ void __launch_bounds__(APDF_THREADS) apply_rinv_df_kernel(ApplyBatch ab) {
     extern __shared__ float2 sa[];  // R^{-1}: k x k column-major, then Y rows: k x 32 ([col][row])
@@ -1145,20 +1146,44 @@ __global__ void __launch_bounds__(APDF_THREADS) apply_rinv_df_kernel(ApplyBatch 
     const double* R = ab.R[b];
     const View2 Y = ab.Y[b];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int e = tid; e < k * k; e += blockDim.x) {
-        const int a = e % k, c = e / k;
-        rs[e] = a <= c ? df_from_f64(R[a + ab.ldr * c], 0) : make_float2(0.f, 0.f);
-    }
-    for (int e = tid; e < 32 * k; e += blockDim.x) {
-        const int rr = e & 31, c = e >> 5;
-        float2 v = make_float2(0.f, 0.f);
-        if (r0 + rr < n) {
-            if (Y.dt == TK_F64)
-                v = df_from_f64(static_cast<const double*>(Y.p)[v2off(Y, r0 + rr, c)], 0);
-            else
-                v = make_float2(static_cast<const float*>(Y.p)[v2off(Y, r0 + rr, c)], 0.f);
+    // staging: every thread issues its global loads in groups of APDF_U before using any of
+    // them (one round of L2 latency per group instead of one per element)
+    const int nt = blockDim.x;
+    for (int e0 = tid; e0 < k * k; e0 += APDF_U * nt) {
+        double v[APDF_U];
+#pragma unroll
+        for (int u = 0; u < APDF_U; ++u) {
+            const int e = e0 + u * nt, a = e % k, c = e / k;
+            v[u] = (e < k * k && a <= c) ? R[a + ab.ldr * c] : 0.0;
         }
-        ys[e] = v;
+#pragma unroll
+        for (int u = 0; u < APDF_U; ++u)
+            if (e0 + u * nt < k * k) rs[e0 + u * nt] = df_from_f64(v[u], 0);
+    }
+    if (Y.dt == TK_F64) {
+        for (int e0 = tid; e0 < 32 * k; e0 += APDF_U * nt) {
+            double v[APDF_U];
+#pragma unroll
+            for (int u = 0; u < APDF_U; ++u) {
+                const int e = e0 + u * nt, rr = e & 31, c = e >> 5;
+                v[u] = (e < 32 * k && r0 + rr < n) ? static_cast<const double*>(Y.p)[v2off(Y, r0 + rr, c)] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < APDF_U; ++u)
+                if (e0 + u * nt < 32 * k) ys[e0 + u * nt] = df_from_f64(v[u], 0);
+        }
+    } else {
+        for (int e0 = tid; e0 < 32 * k; e0 += APDF_U * nt) {
+            float v[APDF_U];
+#pragma unroll
+            for (int u = 0; u < APDF_U; ++u) {
+                const int e = e0 + u * nt, rr = e & 31, c = e >> 5;
+                v[u] = (e < 32 * k && r0 + rr < n) ? static_cast<const float*>(Y.p)[v2off(Y, r0 + rr, c)] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < APDF_U; ++u)
+                if (e0 + u * nt < 32 * k) ys[e0 + u * nt] = make_float2(v[u], 0.f);
+        }
     }
     __syncthreads();
     const int64_t row = r0 + lane;
