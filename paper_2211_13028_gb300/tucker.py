@@ -29,7 +29,7 @@ __all__ = [
     "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
     "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tucker_rhkron_srht", "tk_graph_release",
     "tk_philox4x32", "tucker_gaussian_factor", "tucker_gaussian_factors", "gaussian_factors",
-    "gaussian_factors_matrix",
+    "gaussian_factors_matrix", "rsthkron_factor_plan",
     "TuckerGraph",
 ]
 
@@ -515,23 +515,31 @@ def tucker_gaussian_factors(shapes: Sequence[Tuple[int, int]], seed: int, stream
     return _draw_factors(list(shapes), list(streams), seed, dtype, device)
 
 
+def rsthkron_factor_plan(dims: Sequence[int], S, kdims: Sequence[int], order: Sequence[int]):
+    """Host-side plan of Algorithm rSTHKron's factors: for the mode j processed at position t,
+    Omega_{j,k} is (current size of mode k) x s_{j,k} (k_k for modes processed earlier, n_k
+    otherwise), drawn from stream 8 j + k.  Returns (keys (j, k), shapes, streams) in draw order."""
+    d = len(dims)
+    keys, shapes, streams, done = [], [], [], set()
+    for j in order:
+        for k in range(d):
+            if k == j:
+                continue
+            keys.append((j, k))
+            shapes.append((int(kdims[k]) if k in done else int(dims[k]), int(S[j][k])))
+            streams.append(8 * j + k)
+        done.add(j)
+    return keys, shapes, streams
+
+
 def gaussian_factors_matrix(dims: Sequence[int], S, kdims: Sequence[int], order: Sequence[int], seed: int,
                             dtype=torch.float32, device="cuda") -> Dict[Tuple[int, int], torch.Tensor]:
     """The sketch factors Omega_{j,k} = Phi_{j,k}^T of Algorithm rSTHKron, drawn on the device from stream
     8 j + k: for the mode j processed at position t, Phi_{j,k} is s_{j,k} x (current size of mode k),
     k_k for modes processed earlier and n_k otherwise.  S: d x d subranks (row j), as
     tucker_subranks_matrix returns them."""
-    d = len(dims)
-    Sm = [[int(S[j][k]) for k in range(d)] for j in range(d)]
-    keys, shapes, done = [], [], set()
-    for j in order:
-        for k in range(d):
-            if k == j:
-                continue
-            keys.append((j, k))
-            shapes.append((int(kdims[k]) if k in done else int(dims[k]), Sm[j][k]))
-        done.add(j)
-    ms = _draw_factors(shapes, [8 * j + k for j, k in keys], seed, dtype, device)
+    keys, shapes, streams = rsthkron_factor_plan(dims, S, kdims, order)
+    ms = _draw_factors(shapes, streams, seed, dtype, device)
     return dict(zip(keys, ms))
 
 

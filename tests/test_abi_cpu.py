@@ -11,6 +11,7 @@ import pytest
 
 import oracle as O
 from paper_2211_13028_gb300 import build as B
+from paper_2211_13028_gb300 import synth
 from paper_2211_13028_gb300 import tucker as T
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -91,3 +92,20 @@ def test_binding_rejects_row_major_tensor():
     t = torch.zeros((3, 4, 5))
     assert not T.is_colmajor(t)
     assert T.is_colmajor(t.permute(2, 1, 0).contiguous().permute(2, 1, 0))
+
+
+def test_rsthkron_factor_plan_matches_host_draw_shapes(lib):
+    # the device-draw plan of rSTHKron's factors has the shapes of the host generator's factors
+    # (the oracle's inputs) and one distinct stream per factor
+    for r, p, order in [((32, 32, 32), 8, [0, 1, 2]), ((10, 20, 30, 40), 6, [3, 2, 1, 0])]:
+        d = len(r)
+        dims = tuple(64 + 16 * j for j in range(d))
+        S, w = T.tucker_subranks_matrix(r, p, order)
+        k = [min(n, ww) for n, ww in zip(dims, w)]
+        keys, shapes, streams = T.rsthkron_factor_plan(dims, S, k, order)
+        host = synth.sketch_factors_matrix(dims, np.array(S), k, order, seed=0, dtype="f32")
+        assert set(keys) == set(host.keys())
+        for key, shp in zip(keys, shapes):
+            assert shp == host[key].shape
+        assert len(set(streams)) == len(streams)
+        assert streams == [8 * j + kk for j, kk in keys]
