@@ -234,7 +234,10 @@ TK_API tk_status tucker_gaussian_factors(tk_handle* h, uint64_t seed, int count,
 TK_API tk_status tucker_sketch(tk_handle* h, const tk_tensor* X, const tk_matrix* Omega, tk_tensor* Y);
 
 /* Thin QR of a tall sketch, Y = Q R with R_ii > 0 (Algorithm RRF):
- * CholeskyQR2 with an FP64 Gram matrix and FP64 Cholesky; Householder QR in
+ * CholeskyQR2 with an FP64 Gram matrix and FP64 Cholesky for F64 Y; for F32 Y
+ * the first Gram accumulates with Dot2 (compensated FP32) and both Cholesky
+ * factorisations and products Y R^{-1} run in double-float arithmetic (about
+ * 48 significant bits, on the FP32 pipe); Householder QR in
  * FP64 when the Cholesky factorisation breaks down or a pivot falls below
  * 1e-12 of its column's squared norm; Q = I when Y has at least as many
  * columns as rows.  Y: rows x cols (F64 or F32).  Q: rows x min(rows, cols),
@@ -272,7 +275,9 @@ TK_API tk_status tucker_core(tk_handle* h, const tk_tensor* X, const tk_matrix* 
 /* Algorithm rHKron-re: sketches with the d reused factors Omega_j = Phi_j^T
  * (n_j x s_j), thin QR of each sketch unfolding into Q_n (n_n x k_n,
  * k_n = min(n_n, prod_{j!=n} s_j)), core Ghat = X x_j Q_j^T, STHOSVD of Ghat to
- * ranks r in FP64 (Gram matrix + Jacobi eigensolver per mode), U_j = Q_j V_j
+ * ranks r (Gram matrix + Jacobi eigensolver per mode: FP64 for F64 data; for
+ * the other dtypes double-float products and a two-stage mixed-precision
+ * Jacobi resolving the Gram to 1e-11 of its norm), U_j = Q_j V_j
  * (Section 4, holistic truncation).  Each column of U_j is signed so that its
  * largest-magnitude entry is positive; G's slices follow.
  * X: F64, F32, BF16 or FP8_E4M3.  r: d host ranks, 1 <= r_j <= k_j.
