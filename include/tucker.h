@@ -247,22 +247,27 @@ TK_API tk_status tucker_orth(tk_handle* h, const tk_matrix* Y, tk_matrix* Q, int
 
 /* Thin QR that allocates nothing (the paper has no counterpart; it is a
  * service for callers that cannot allocate device memory where they need the
- * factorisation: inside a CUDA-graph capture, under an allocator that owns all
- * device memory, or on a path that must not trigger an allocation's implicit
- * synchronisation).  Same result as tucker_orth with default options
- * (CholeskyQR2, Householder fallback, identity for cols >= rows), but it takes
- * no handle: work is queued on cuda_stream (void* cudaStream_t, NULL = legacy
- * default stream) and its scratch is a fixed 6 MiB device array inside the
- * library, present on every GPU that loads it until the process exits.
+ * factorisation: applications whose device memory belongs to a pool or arena
+ * (a framework's caching allocator holding the free memory, a deployment that
+ * forbids allocation after start-up), and latency-critical paths that must not
+ * risk the device-wide synchronisation cudaMalloc / cudaFree can cause).  Same
+ * result as tucker_orth with default options (CholeskyQR2, Householder
+ * fallback, identity for cols >= rows), but it takes no handle: work is queued
+ * on cuda_stream (void* cudaStream_t of the current device, NULL = legacy
+ * default stream) and its scratch is a fixed 8 MiB device array inside the
+ * library, present on every GPU that loads it until the process exits.  It
+ * calls no cudaMalloc, cudaFree or allocating library routine.
  * Limits: rows <= 4096 and min(rows, cols) <= 64, else TK_ERR_SHAPE.
- * The first call on a device looks up that array's device address, so make
- * it before any stream capture on that device.  Every call shares the array:
- * calls that overlap on the GPU (different streams, or several threads) race
- * and must be serialised by the caller.  Y: rows x cols, F64 or F32; Q: rows x
- * min(rows, cols), F64 or F32, both device pointers.  info (host, may be
- * NULL; non-NULL synchronises the stream): 0 CholeskyQR2, 1 Householder,
- * 2 identity.  Other errors: TK_ERR_ARG, TK_ERR_DTYPE, TK_ERR_ALIGN,
- * TK_ERR_CUDA. */
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current), so make the first call before any stream
+ * capture on that device.  Every call shares the array and finds the previous
+ * call's contents in it (each call sets what it reads first): calls that
+ * overlap on the GPU (different streams, or several threads) race and must be
+ * serialised by the caller.  Y: rows x cols, F64 or F32; Q: rows x
+ * min(rows, cols), F64 or F32, both device pointers on the current device.
+ * info (host, may be NULL; non-NULL synchronises the stream): 0 CholeskyQR2,
+ * 1 Householder, 2 identity.  Other errors: TK_ERR_ARG (also a stream of
+ * another device), TK_ERR_DTYPE, TK_ERR_ALIGN, TK_ERR_CUDA. */
 TK_API tk_status tucker_orth_noalloc(void* cuda_stream, const tk_matrix* Y, tk_matrix* Q, int* info);
 
 /* Core multi-TTM Ghat = X x_1 Q_1^T x_2 Q_2^T ... x_d Q_d^T (Algorithm

@@ -1,13 +1,14 @@
 // Thin QR entry point that allocates nothing.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// QR: code running inside a CUDA-graph capture (cudaMalloc is not a stream
-// operation and breaks the capture), applications whose memory is owned by a
-// pool or arena that forbids outside allocations, and latency-critical paths
-// that must not risk the device-wide synchronisation an allocation can cause.
-// tucker_orth_noalloc serves them: its scratch is a fixed file-scope device
-// array, so it needs no handle and no workspace, and it calls no cudaMalloc,
-// cudaFree or allocating library routine.
+// QR: applications whose device memory is owned by a pool or arena (a
+// framework's caching allocator that has reserved the free memory, an
+// embedded deployment that forbids allocation after start-up), and
+// latency-critical paths that must not risk the device-wide synchronisation
+// that cudaMalloc and cudaFree can cause.  tucker_orth_noalloc serves them:
+// its scratch is a fixed file-scope device array, so it needs no handle and
+// no workspace, and it calls no cudaMalloc, cudaFree or allocating library
+// routine.
 #include <mutex>
 
 #include "tk_internal.cuh"
@@ -18,9 +19,13 @@ namespace {
 // Largest sketch it accepts: rows <= kRowsMax, columns <= kColsMax.
 constexpr int64_t kRowsMax = 4096;
 constexpr int64_t kColsMax = 64;
-// CholeskyQR2 + Householder scratch for that size (three rows x cols FP64
-// matrices, two cols x cols FP64 matrices, flags), with room for alignment.
-constexpr size_t kScratchBytes = 6u << 20;
+// CholeskyQR2 + Householder scratch at that size, as the planning pass counts
+// it: three rows x cols FP64 matrices (Q, the first CholeskyQR factor, the
+// Householder copy: 6 MiB), the split-K partial tiles of the two Gram
+// products (19 slices of 64 x 64 FP64 each at 4096 rows: 1.2 MB), two
+// cols x cols FP64 matrices, the flag header and 256-byte alignment of every
+// block: 7.3 MB, rounded up to 8 MiB.
+constexpr size_t kScratchBytes = 8u << 20;
 
 // Shared by every call on a device and kept between calls.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -64,6 +69,11 @@ extern "C" tk_status tucker_orth_noalloc(void* cuda_stream, const tk_matrix* Y, 
         const int64_t k = std::min(y.rows, y.cols);
         if (q.rows != y.rows || q.cols != k) return TK_ERR_SHAPE;
         if (y.rows > kRowsMax || k > kColsMax) return TK_ERR_SHAPE;  // beyond the fixed scratch
+        // the scratch address and the launches belong to the current device: the stream must be one of its own
+        int cur = 0, sdev = 0;
+        TK_CUDA(cudaGetDevice(&cur));
+        TK_CUDA(cudaStreamGetDevice(static_cast<cudaStream_t>(cuda_stream), &sdev));
+        if (sdev != cur) return TK_ERR_ARG;
         char* base = nullptr;
         tk_status st = scratch_for_current_device(&base);
         if (st != TK_OK) return st;

@@ -374,16 +374,22 @@ def tucker_orth(Y: torch.Tensor, qr_method: int = 0, out_dtype=None) -> Tuple[to
     return Q, info.value
 
 
-def tucker_orth_noalloc(Y: torch.Tensor, out_dtype=None) -> Tuple[torch.Tensor, int]:
+def tucker_orth_noalloc(Y: torch.Tensor, out_dtype=None, Q: torch.Tensor | None = None) -> Tuple[torch.Tensor, int]:
     """Thin QR like tucker_orth, computed without any device allocation by the
-    library (fixed internal scratch; rows <= 4096, min(rows, cols) <= 64).
-    For callers that cannot allocate at the call site (graph capture, external
-    allocators).  Calls must not overlap on the GPU.  Returns (Q, info)."""
+    library (a fixed internal scratch array; rows <= 4096, min(rows, cols) <= 64).
+    For callers that cannot allocate device memory at the call site: memory
+    owned by a pool or arena, or paths that must not take the implicit
+    synchronisation of cudaMalloc / cudaFree.  Q (column-major, rows x
+    min(rows, cols)) may be passed in so that nothing is allocated here either.
+    Calls must not overlap on the GPU (they share the scratch).  Returns
+    (Q, info); info is read back, which synchronises the stream."""
     rows, cols = Y.shape
-    Q = _colmajor_matrix(rows, min(rows, cols), out_dtype or Y.dtype, Y.device)
+    if Q is None:
+        Q = _colmajor_matrix(rows, min(rows, cols), out_dtype or Y.dtype, Y.device)
     info = ctypes.c_int(-1)
-    st = load().tucker_orth_noalloc(ctypes.c_void_p(torch.cuda.current_stream(Y.device).cuda_stream),
-                                    ctypes.byref(_matrix(Y)), ctypes.byref(_matrix(Q)), ctypes.byref(info))
+    with torch.cuda.device(Y.device):
+        st = load().tucker_orth_noalloc(ctypes.c_void_p(torch.cuda.current_stream(Y.device).cuda_stream),
+                                        ctypes.byref(_matrix(Y)), ctypes.byref(_matrix(Q)), ctypes.byref(info))
     if st != 0:
         raise TuckerError(st, "tucker_orth_noalloc failed")
     return Q, info.value
