@@ -226,7 +226,7 @@ def profile_case(args):
     """Repetitions of one building block on an n^3 FP32 field of the bench generator:
     'sketch' (tucker_sketch, s = (6,7,7)), 'core' (tucker_core, k = (49,42,42)),
     'residual' (tucker_loss with r = 32: the fused tensor-core residual) or
-    'rhkron' (all of rHKron-re, r = 32, p = 8)."""
+    'rhkron' / 'rsthkron' (all of rHKron-re / rSTHKron, r = 32, p = 8), 'backward' (dG, dU)."""
     import torch
 
     from paper_2211_13028_gb300 import synth
@@ -255,6 +255,12 @@ def profile_case(args):
         s, _ = T.tucker_subranks_reuse(RANKS, P_OVER)
         om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(X.shape, s, SEED + 1, "f32")]
         fn = lambda: T.tucker_rhkron(X, RANKS, P_OVER, om)  # noqa: E731
+    elif args.profile_case == "rsthkron":
+        # the whole of rSTHKron at r = 32, p = 8 (S rows {5, 8}), factors drawn on the device
+        S, w = T.tucker_subranks_matrix(RANKS, P_OVER)
+        k = [min(n, ww) for ww in w]
+        oms = T.gaussian_factors_matrix(tuple(X.shape), S, k, [0, 1, 2], SEED + 2, torch.float32, dev)
+        fn = lambda: T.tucker_rsthkron(X, RANKS, P_OVER, oms)  # noqa: E731
     else:
         G = synth.fortran(g.standard_normal((32, 32, 32)), "f32", dev)
         U = [synth.fmat(__import__("numpy").linalg.qr(g.standard_normal((n, 32)))[0], "f32", dev) for _ in range(3)]
@@ -600,7 +606,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="time the step as eager launches only (default: the step is also recorded once into a "
                          "CUDA graph and the replays are the headline)")
-    ap.add_argument("--profile-case", choices=["sketch", "core", "residual", "rhkron", "backward"], default=None,
+    ap.add_argument("--profile-case", choices=["sketch", "core", "residual", "rhkron", "rsthkron", "backward"],
+                    default=None,
                     help="run one building block on an n^3 FP32 field (for ncu captures) instead of the bench")
     ap.add_argument("--n", type=int, default=384, help="edge of the --profile-case tensor")
     ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32", help="storage of the --profile-case tensor")
