@@ -42,6 +42,7 @@ def _peaks():
 
 KERNEL_NAMES = {
     "xpass_tc": "ttm_tf32x3_kernel (tcgen05 3xTF32 TTM streaming X: sketch/core passes and the fused residual)",
+    "xpass_narrow": "ttm_fma_stream_kernel (TMA-fed FP32 FMA TTM streaming X: the narrow sketch passes)",
     "ttm_tc": "ttm_tf32x3_kernel on intermediates",
 }
 # DRAM traffic / algorithmic bytes of one X-streaming launch, from an ncu capture of a 384^3 FP32
@@ -87,14 +88,19 @@ def max_over_ranks(x: float, dist) -> float:
 
 # ------------------------------------------------------------------ CPU oracle leg
 
-def oracle_step(n: int):
-    """One oracle step on an n^3 sample of the workload; returns (seconds, rel_errs)."""
+def oracle_step(n: int, x=None):
+    """One oracle step of the workload at edge n: rHKron-re and rSTHKron with their relative errors,
+    and the loss gradient at the rHKron-re result.  x: the field as a float64 host array (the GPU's
+    own X, copied back), else the same recipe generated on the host (its noise then comes from the
+    host generator, so it is not bit-identical to a field drawn on the device).  Returns
+    (seconds, (rel_err rHKron-re, rel_err rSTHKron)); the field is built outside the timed part."""
     import numpy as np
 
     import oracle as O
     from paper_2211_13028_gb300 import synth
 
-    x = synth.from_fortran(synth.gaussian_bumps(n, 3, 200, SEED, 1e-4, "cpu", "f32"))
+    if x is None:
+        x = synth.from_fortran(synth.gaussian_bumps(n, 3, 200, SEED, 1e-4, "cpu", "f32"))
     r, p = RANKS, P_OVER
     s, _ = O.subranks_reuse(r, p)
     S, w = O.subranks_matrix(r, p)
@@ -127,42 +133,74 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_baseline(n_sample: int, budget_s: float = 20.0):
-    times = []
-    t_start = time.perf_counter()
-    while True:
-        dt, errs = oracle_step(n_sample)
-        times.append(dt)
-        if time.perf_counter() - t_start > budget_s or len(times) >= 5:
-            break
-    times.sort()
-    med = times[len(times) // 2]
-    scale = (N_FULL / n_sample) ** 3
-    return dict(value=med * 1e3 * scale, unit="ms", cores=cpu_cores(), kind="oracle",
-                sample=(f"{n_sample}^3 sample of the same generator and ranks ({len(times)} runs, median "
-                        f"{med:.2f} s), scaled by the element ratio {scale:.0f} to the 512^3 workload; "
-                        f"oracle rel_err rHKron-re {errs[0]:.3e}, rSTHKron {errs[1]:.3e}"))
+_ONE_THREAD = {k: "1" for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+
+
+def oracle_one_thread(n: int, timeout_s: float = 240.0):
+    """The oracle step at edge n in a child process whose BLAS runs on one thread (the thread count of
+    a BLAS library is fixed when it loads).  Returns (seconds, rel_errs) or None."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print('ORACLE1', json.dumps(bench.oracle_step(%d)))" % (ROOT, n))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env={**os.environ, **_ONE_THREAD}, capture_output=True,
+                           text=True, timeout=timeout_s)
+        for ln in r.stdout.splitlines():
+            if ln.startswith("ORACLE1 "):
+                dt, errs = json.loads(ln[8:])
+                return float(dt), tuple(errs)
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(xh, gpu_errs, n_one_thread: int = 256):
+    """The FP64 oracle timed on the host cores: one full step of the workload at 512^3 on the GPU's own
+    field (all cores), and a one-thread run of the same recipe at n_one_thread^3."""
+    dt, errs = oracle_step(N_FULL, xh)
+    one = oracle_one_thread(n_one_thread)
+    out = dict(value=dt * 1e3, unit="ms", cores=cpu_cores(), kind="oracle",
+               sample=("one full step at 512^3 (rHKron-re + rSTHKron + loss gradient) on the GPU's own field, "
+                       "copied to the host; FP64 NumPy, BLAS on all %d cores" % cpu_cores()),
+               same_config=True,
+               oracle_rel_err=dict(rhkron=errs[0], rsthkron=errs[1]),
+               gpu_rel_err=dict(rhkron=gpu_errs[0], rsthkron=gpu_errs[1]),
+               abs_diff=dict(rhkron=abs(errs[0] - gpu_errs[0]), rsthkron=abs(errs[1] - gpu_errs[1])))
+    if one is not None:
+        out["one_thread"] = dict(ms=one[0] * 1e3, cores=1,
+                                 sample="%d^3 field of the same recipe (host-drawn noise), BLAS on 1 thread"
+                                        % n_one_thread,
+                                 rel_err=dict(rhkron=one[1][0], rsthkron=one[1][1]))
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores, each timed step one full
+    512^3 step of the workload (rHKron-re + rSTHKron + loss gradient).  The field is built once
+    before the timed steps; the untimed warm-up steps run the same code at 128^3."""
     rank = rank_env()[0]
     if rank != 0:  # the oracle runs once, on rank 0; the other ranks exit without work
         return
-    n_sample = args.sample
+    from paper_2211_13028_gb300 import synth
+
+    n = args.ref_n
     for _ in range(args.warmup):
-        oracle_step(n_sample)
+        oracle_step(min(n, 128))
+    xh = synth.from_fortran(synth.gaussian_bumps(n, 3, 200, SEED, 1e-4, "cpu", "f32"))
     times = []
     for _ in range(args.steps):
-        dt, errs = oracle_step(n_sample)
+        dt, errs = oracle_step(n, xh)
         times.append(dt)
-    scale = (N_FULL / n_sample) ** 3
-    ms = sum(times) / len(times) * 1e3 * scale
+    ms = sum(times) / len(times) * 1e3
     line = dict(metric=METRIC, value=ms, unit="ms", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD, sample=f"{n_sample}^3, time scaled by {scale:.0f}"),
+                config=dict(workload=WORKLOAD,
+                            sample=("every timed step is the full 512^3 workload" if n == N_FULL else
+                                    "every timed step is the workload's recipe at %d^3 (not the full size)" % n),
+                            field="the recipe with its noise drawn by the host generator"),
                 cpu_baseline=dict(value=ms, unit="ms", cores=cpu_cores(), kind="oracle",
-                                  sample=f"{n_sample}^3 sample per step, scaled by the element ratio {scale:.0f}"),
+                                  sample="%d^3 step (FP64 NumPy, BLAS on all cores); warm-up at %d^3"
+                                         % (n, min(n, 128))),
                 e2e=dict(value=ms, unit="ms", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
                 rel_err=dict(rhkron=errs[0], rsthkron=errs[1]))
     print(json.dumps(line), flush=True)
@@ -366,7 +404,7 @@ def run_bf16_workload(args):
                                  % n_or,
                           oracle_rel_err=err_or, gpu_rel_err=err_gpu_small, abs_diff=abs(err_or - err_gpu_small)),
         device_status=st, clocks=clk)
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------------ 4-way rSTHKron (160^4)
@@ -444,7 +482,7 @@ def run_tucker4_workload(args):
                           sample="one FP64 oracle rSTHKron on the %d^4 tensor of the same generator" % n_or,
                           oracle_rel_err=err_or, gpu_rel_err=err_gpu_small, abs_diff=abs(err_or - err_gpu_small)),
         device_status=T.tk_sync_status(dev)[0], clocks=clk)
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------------ Section 7.1 accuracy: SRHT vs Gaussian sketches
@@ -522,7 +560,7 @@ def run_srht_workload(args):
                                  "the same construction" % no,
                           oracle_rel_err=err_or, gpu_rel_err=gpu_o, abs_diff=abs(err_or - gpu_o)),
         device_status=T.tk_sync_status(dev)[0])
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------------ gradient descent on the loss (256^3)
@@ -589,7 +627,7 @@ def run_descent_workload(args):
                     l2="X is 64 MiB, inside L2 after the first pass of a step"),
         init_ms=init, adam_step_ms=(total - init) / nsteps, rel_err_init=err0, rel_err_final=final,
         device_status=T.tk_sync_status(dev)[0])
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------------ GPU leg
@@ -600,8 +638,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--sample", type=int, default=256, help="oracle sample edge (CPU legs)")
+    ap.add_argument("--sample", type=int, default=256, help="edge of the one-thread oracle sample")
+    ap.add_argument("--ref-n", type=int, default=N_FULL,
+                    help="edge of each timed step of the reference arm (default: the full 512^3 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the other configurations (BF16 1024^3 vs FP32, 4-way 160^4, 256^3 descent) that "
+                         "the default line carries under 'secondary'")
     ap.add_argument("--serial", action="store_true", help="run both algorithms on one stream")
     ap.add_argument("--no-graph", action="store_true",
                     help="time the step as eager launches only (default: the step is also recorded once into a "
@@ -625,17 +668,10 @@ def main():
     if args.profile_case:
         profile_case(args)
         return
-    if args.workload == "bumps1024_bf16" and args.impl == "native":
-        run_bf16_workload(args)
-        return
-    if args.workload == "tucker160x4_f32" and args.impl == "native":
-        run_tucker4_workload(args)
-        return
-    if args.workload == "descent256_f32" and args.impl == "native":
-        run_descent_workload(args)
-        return
-    if args.workload == "srht512_f32" and args.impl == "native":
-        run_srht_workload(args)
+    side = {"bumps1024_bf16": run_bf16_workload, "tucker160x4_f32": run_tucker4_workload,
+            "descent256_f32": run_descent_workload, "srht512_f32": run_srht_workload}
+    if args.workload in side and args.impl == "native":
+        print(json.dumps(side[args.workload](args)), flush=True)
         return
 
     if args.impl == "reference":
@@ -643,11 +679,6 @@ def main():
         return
 
     rank, world, local = rank_env()
-
-    # CPU baseline first (before any CUDA work in this process), rank 0 at N=1 only.
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.sample)
 
     import numpy as np
     import torch
@@ -823,21 +854,23 @@ def main():
     e2e_ms = e0.elapsed_time(e1) / args.steps
     e2e_ms = max_over_ranks(e2e_ms, dist)
 
-    # ---- roofline of the dominant kernel: the tcgen05 TTM kernel (its X-streaming launches timed live
-    # in the timed region; the kernel's share of the step from the extra all-class step)
+    # ---- roofline: the kernel classes' shares come from one extra all-class step; the roofline kernel is
+    # the HBM-streaming class (an X pass on the tensor cores or on the FP32 pipe) with the largest share,
+    # timed live in the timed region; the dominant class overall and the runner-up are reported beside it
     hbm, bf16, peak_src = _peaks()
     peak_note = "the kernel is timed inside the step, next to the other kernels"
-    name = "xpass_tc"
+    step_ms_total = sum(v["ms"] for v in prof_all.values())
+    ranked = sorted(prof_all.items(), key=lambda kv: -kv[1]["ms"])
+    shares = {kname: round(v["ms"] / step_ms_total, 4) for kname, v in ranked}
+    streaming = [kname for kname, _ in ranked if kname in ("xpass_tc", "xpass_narrow")]
+    name = streaming[0] if streaming else "xpass_tc"
     d = prof.get(name, dict(ms=0.0, launches=1, bytes=0.0, flops=0.0))
     per_launch_ms = d["ms"] / max(1, d["launches"])
     ach = (d["bytes"] / max(1, d["launches"])) / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
     ttm = [v for kname, v in prof_all.items() if kname.startswith(("ttm", "xpass"))]
     ttm_ms = sum(v["ms"] for v in ttm)
     ttm_tflops = (sum(v["flops"] for v in ttm) / (ttm_ms * 1e-3) / 1e12) if ttm_ms > 0 else 0.0
-    step_ms_total = sum(v["ms"] for v in prof_all.values())
-    shares = {kname: round(v["ms"] / step_ms_total, 4)
-              for kname, v in sorted(prof_all.items(), key=lambda kv: -kv[1]["ms"])}
-    tc_share = sum(v for kname, v in shares.items() if kname in ("xpass_tc", "ttm_tc"))
+    runner = ranked[1][0] if len(ranked) > 1 else None  # the class after the dominant one
 
     if rank != 0:
         return
@@ -862,19 +895,25 @@ def main():
         rel_err=dict(rhkron=errs[0], rsthkron=errs[1]),
         device_status=dev_status,
         multi_ttm=dict(tflops=ttm_tflops, ms_per_step=ttm_ms, frac_of_bf16_peak=ttm_tflops / bf16),
-        roofline=dict(bound="hbm" if name.startswith(("ttm", "xpass", "residual", "elementwise")) else "alu",
-                      kernel=KERNEL_NAMES.get(name, name), achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+        roofline=dict(bound="hbm",
+                      kernel=KERNEL_NAMES.get(name, name), kernel_class=name, achieved=ach, peak=hbm, unit="GB/s",
+                      frac=ach / hbm,
                       traffic=(TRAFFIC_RATIO[name] * d["bytes"] / max(1, d["launches"])
                                if name in TRAFFIC_RATIO else None),
                       traffic_note=TRAFFIC_NOTE.get(name),
                       peak_source=f"{peak_src} hbm_gbs (burst copy; {peak_note})",
                       bytes_per_launch=d["bytes"] / max(1, d["launches"]), ms_per_launch=per_launch_ms,
                       launches_per_step=d["launches"] / args.steps,
-                      kernel_share_of_step=tc_share,
-                      note=("tcgen05 TTM kernel: its X-streaming launches (10 per step) are timed live with "
-                            "CUDA events in the eager timed region (a recorded graph carries no per-launch "
-                            "events); kernel_share_of_step is the whole kernel's share "
-                            "(X passes and intermediates) of the summed kernel time of one extra profiled step")),
+                      kernel_share_of_step=shares.get(name, 0.0),
+                      dominant_class=dict(name=ranked[0][0], share=shares[ranked[0][0]]) if ranked else None,
+                      runner_up=(dict(name=runner, share=shares[runner],
+                                      bound=("hbm" if runner.startswith(("xpass", "ttm", "residual", "elementwise")) else
+                                             "latency (one-CTA small-matrix kernel or short FP64 product)"))
+                                 if runner else None),
+                      note=("the roofline kernel is the HBM-streaming class with the largest share of the summed "
+                            "kernel time (one extra all-class step); its %d launches per step are timed live with "
+                            "CUDA events in the eager timed region (a recorded graph carries no per-launch events)"
+                            % round(d["launches"] / args.steps))),
         kernel_shares=shares,
         kernel_shares_note="all kernel classes timed in one extra step after the timed region",
         kernel_ms_per_step=step_ms_total,
@@ -888,8 +927,30 @@ def main():
         host_queue_ms_per_step=host_ms,
         clocks=clk,
     )
-    if cpu is not None:
-        line["cpu_baseline"] = cpu
+    # ---- CPU baseline: the FP64 oracle on the GPU's own field at the full size (rank 0, N = 1)
+    if world == 1 and not args.no_cpu_baseline:
+        xh = synth.from_fortran(X)
+        line["cpu_baseline"] = cpu_baseline(xh, errs, args.sample)
+        del xh
+    # ---- the other configurations, each a bounded run, on the same GPU after the timed regions
+    if world == 1 and not args.no_secondary:
+        import types
+        del gE, X, Xd, Xh
+        torch.cuda.empty_cache()
+        sub = types.SimpleNamespace(steps=5, warmup=3, oracle_n=256, oracle_n4=48, trials=5)
+        sec = {}
+        for key, fn in (("bumps1024_bf16", run_bf16_workload), ("tucker160x4_f32", run_tucker4_workload),
+                        ("descent256_f32", run_descent_workload)):
+            t_s = time.perf_counter()
+            try:
+                sl = fn(sub)
+                sl.pop("clocks", None)
+                sl["driver_wall_s"] = time.perf_counter() - t_s
+                sec[key] = sl
+            except Exception as e:  # a failing side configuration must not hide the main line
+                sec[key] = dict(error=repr(e))
+            torch.cuda.empty_cache()
+        line["secondary"] = sec
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
