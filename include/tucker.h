@@ -142,6 +142,15 @@ TK_API const char* tk_last_error(const tk_handle* h);
  * NULL it receives, for the last QR of each mode (up to TK_MAX_D entries),
  * 0 = CholeskyQR2, 1 = Householder, 2 = identity (full-width sketch). */
 TK_API tk_status tk_sync_status(tk_handle* h, int* qr_info);
+/* Self-test of failure detection (the paper has no counterpart): one warp
+ * waits, through the same bounded mbarrier wait every tcgen05 / TMA kernel of
+ * the library uses, on an mbarrier that nothing ever arrives at.  The wait
+ * gives up after limit_ns (1e3 <= limit_ns <= 2e9, else TK_ERR_ARG; the
+ * kernels themselves use 2e9), records the timeout in the handle and returns,
+ * leaving the context usable: the next tk_sync_status reports
+ * TK_ERR_TIMEOUT (and clears it).  waited_ns (host, may be NULL; non-NULL
+ * synchronises): how long the wait lasted on the device clock. */
+TK_API tk_status tk_selftest_bounded_wait(tk_handle* h, int64_t limit_ns, int64_t* waited_ns);
 /* Bytes of device workspace the handle currently holds. */
 TK_API int64_t tk_workspace_bytes(const tk_handle* h);
 /* Number of kernel launches queued through this handle since creation. */
@@ -274,6 +283,55 @@ TK_API tk_status tucker_orth_noalloc(void* cuda_stream, const tk_matrix* Y, tk_m
  * rHKron-re, core line).  Q: d matrices n_j x k_j (F64 for F64 data, else F32).
  * G: tensor (k_1,...,k_d), F64 or F32. */
 TK_API tk_status tucker_core(tk_handle* h, const tk_tensor* X, const tk_matrix* Q, tk_tensor* G);
+
+/* ---- the sharded form: X split along its last mode into slabs ------------ */
+
+/* The data-parallel form of Algorithm rHKron-re (Section 6.3, parallel
+ * rHKron-re; Section 6.1, all-at-once multi-TTM): X is split along its last
+ * mode d into contiguous slabs (column-major storage makes each slab one
+ * contiguous block), one per rank, and every rank holds the full (small)
+ * factors.  Each slab call works on its slab only; the partial results are
+ * exchanged as stated (a SUM all-reduce or an all-gather over the ranks,
+ * outside the library), and the small steps in between run redundantly on
+ * every rank.  A slab is rows [offset, offset + X_slab.dims[d-1]) of the
+ * last mode, whose full length is n_last (0 <= offset, offset + rows <=
+ * n_last, else TK_ERR_SHAPE).
+ *
+ * tucker_sketch_slab: the Kronecker sketches of the slab, with Omega as in
+ * tucker_sketch (Omega[d-1] is the full n_last x s_d factor; its slab rows are
+ * used).  Y[n] for n < d-1 (dims as tucker_sketch's) receives the slab's
+ * partial sum of Y_n: SUM-reduce them over the slabs.  Y[d-1] (dims
+ * s_1..s_{d-1} x slab rows) receives the slab's rows of Y_d: gather them
+ * along the last mode.
+ *
+ * tucker_orth_sketches: thin QR Q_n of the mode-n unfolding of each of d
+ * sketch tensors Y[n] (k_n = min(n_n, prod_{j!=n} dims), Q = I when the sketch
+ * is at least as wide as the mode), as inside tucker_rhkron; Q[n]: n_n x k_n,
+ * F64 or F32.  The QR info goes to tk_sync_status.
+ *
+ * tucker_core_slab: the slab's partial core X_slab x_{j<d} Q_j^T x_d
+ * Q_d[slab rows]^T (Q[d-1] is the full n_last x k_d factor): SUM-reduce over
+ * the slabs to get Ghat.  G: (k_1..k_d), F64 or F32.
+ *
+ * tucker_sthosvd: steps 4-5 of Algorithm rHKron-re on a given core: STHOSVD
+ * of Ghat (k_1..k_d, F64: FP64 Jacobi; F32: the two-stage mixed eigensolver)
+ * to ranks r in opts->mode_order, U_j = Q_j V_j (Q[j]: n_j x k_j), each U_j
+ * column signed so that its largest-magnitude entry is positive, G's slices
+ * following.  G: (r_1..r_d), U: n_j x r_j, F64 or F32.
+ *
+ * tucker_loss_slab: norms2 (host, 2 doubles; synchronises) receives
+ * ||X_slab - G x_{j<d} U_j x_d U_d[slab rows]||^2 and ||X_slab||^2 (U[d-1] is
+ * the full n_last x r_d factor); SUM them over the slabs: the relative error
+ * is sqrt(sum first / sum second). */
+TK_API tk_status tucker_sketch_slab(tk_handle* h, const tk_tensor* X_slab, int64_t offset, int64_t n_last,
+                                    const tk_matrix* Omega, tk_tensor* Y);
+TK_API tk_status tucker_orth_sketches(tk_handle* h, int d, const tk_tensor* Y, tk_matrix* Q);
+TK_API tk_status tucker_core_slab(tk_handle* h, const tk_tensor* X_slab, int64_t offset, int64_t n_last,
+                                  const tk_matrix* Q, tk_tensor* G);
+TK_API tk_status tucker_sthosvd(tk_handle* h, const tk_tensor* Ghat, const tk_matrix* Q, const int64_t* r,
+                                const tk_opts* opts, tk_tensor* G, tk_matrix* U);
+TK_API tk_status tucker_loss_slab(tk_handle* h, const tk_tensor* X_slab, int64_t offset, int64_t n_last,
+                                  const tk_tensor* G, const tk_matrix* U, double* norms2);
 
 /* ---- the two algorithms -------------------------------------------------- */
 

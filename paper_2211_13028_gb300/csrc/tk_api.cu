@@ -755,6 +755,27 @@ tk_status tk_sync_status(tk_handle* h, int* qr_info) {
     return TK_OK;
 }
 
+tk_status tk_selftest_bounded_wait(tk_handle* h, int64_t limit_ns, int64_t* waited_ns) {
+    if (limit_ns < 1000 || limit_ns > 2000000000) {
+        if (h) h->last_error = "selftest: limit_ns must lie in [1e3, 2e9]";
+        return TK_ERR_ARG;
+    }
+    long long* dev = nullptr;
+    tk_status st = run_call(h, [&](Ctx& c) {
+        dev = c.alloc<long long>(1);
+        launch_wait_selftest(c, (uint64_t)limit_ns, dev);
+    });
+    if (st != TK_OK || !waited_ns) return st;
+    long long v = 0;
+    if (cudaMemcpyAsync(&v, dev, sizeof(v), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        h->last_error = "selftest: reading the waited time failed";
+        return TK_ERR_CUDA;
+    }
+    *waited_ns = v;
+    return TK_OK;
+}
+
 tk_status tk_profile(tk_handle* h, int enable) {
     if (!h) return TK_ERR_ARG;
     if (enable) {
@@ -941,37 +962,115 @@ tk_status tucker_subranks_matrix(int d, const int64_t* r, int p, const int* orde
 
 // ------------------------------------------------------------------ building blocks
 
+}  // extern "C"
+
+extern "C" {  // defined further down, inside the C-ABI block
+static void check_outputs(const Tens& X, const int64_t* r, const tk_tensor* G, const tk_matrix* U, Tens& Gt,
+                          std::vector<Mat>& Um);
+static void check_tucker(const Tens& Gt, const tk_matrix* U, std::vector<Mat>& Um, std::vector<int64_t>& n);
+}
+
+// Rows r0 .. r0 + nr - 1 of a column-major matrix (same ld).
+static Mat rows_of(const Mat& M, int64_t r0, int64_t nr) {
+    Mat v = M;
+    v.p = static_cast<const char*>(M.p) + (size_t)r0 * dtype_size(M.dt);
+    v.rows = nr;
+    return v;
+}
+
+// The last mode of X is the slab [off, off + X.n[d-1]) of a mode of length nd
+// (nd = X.n[d-1], off = 0 for a whole tensor); a factor of that mode with nd
+// rows is used through its slab rows.
+static Mat slab_factor(const Mat& M, const Tens& X, int j, int64_t off, int64_t nd, const char* what) {
+    const int d = X.d;
+    if (j != d - 1 || (off == 0 && nd == X.n[j])) {
+        TK_REQUIRE(M.rows == X.n[j], TK_ERR_SHAPE, std::string(what) + ": factor j must have n_j rows");
+        return M;
+    }
+    TK_REQUIRE(M.rows == nd, TK_ERR_SHAPE, std::string(what) + ": the last factor must have the full mode's rows");
+    return rows_of(M, off, X.n[j]);
+}
+
+static void check_slab(const Tens& X, int64_t off, int64_t nd, const char* what) {
+    TK_REQUIRE(X.d >= 2, TK_ERR_SHAPE, std::string(what) + ": d must be >= 2");
+    TK_REQUIRE(off >= 0 && nd >= 1 && X.n[X.d - 1] >= 1 && off + X.n[X.d - 1] <= nd, TK_ERR_SHAPE,
+               std::string(what) + ": the slab must lie inside the last mode (0 <= offset, offset + rows <= n_d)");
+}
+
+// Kronecker sketches of X (Section 4.2) whose last mode is the slab
+// [off, off + n) of a mode of length nd: Y[n] for n < d-1 are the slab's
+// partial sums of the full sketches (every slab adds to them), Y[d-1] holds
+// the slab's rows of the full Y_d.
+static void sketch_body(Ctx& c, const tk_tensor* X, int64_t off, int64_t nd, const tk_matrix* Omega, tk_tensor* Y,
+                        bool slab) {
+    Tens Xt = tens_in(X, "X");
+    c.xdata = Xt.p;
+    c.df64 = Xt.dt != TK_F64;
+    c.xnumel = Xt.numel();
+    const int d = Xt.d;
+    TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "sketch: d must be >= 2");
+    TK_REQUIRE(Omega && Y, TK_ERR_ARG, "sketch: null Omega or Y");
+    if (slab) check_slab(Xt, off, nd, "sketch_slab");
+    else nd = Xt.n[d - 1];
+    tk_dtype acc = acc_of(Xt.dt);
+    std::vector<Mat> Om(d);
+    std::vector<void*> dst(d);
+    for (int j = 0; j < d; ++j) {
+        Mat o = slab_factor(mat_in(&Omega[j], "Omega"), Xt, j, off, nd, "sketch");
+        TK_REQUIRE(acc == TK_F64 ? o.dt == TK_F64 : o.dt != TK_F64, TK_ERR_DTYPE,
+                   "sketch: Omega must be F64 for F64 data, else F32/BF16");
+        Om[j] = mat_to(c, o, acc);
+    }
+    for (int n = 0; n < d; ++n) {
+        Tens y = tens_in(&Y[n], "Y");
+        TK_REQUIRE(y.d == d && y.dt == acc, TK_ERR_DTYPE, "sketch: Y must have the data's d and F64/F32 dtype");
+        for (int j = 0; j < d; ++j)
+            TK_REQUIRE(y.n[j] == (j == n ? Xt.n[j] : Om[j].cols), TK_ERR_SHAPE, "sketch: Y[n] has wrong dims");
+        dst[n] = y.p;
+    }
+    std::vector<Tens> Ys(d);
+    std::vector<int> all(d);
+    std::iota(all.begin(), all.end(), 0);
+    all_modes(c, Xt, all, {}, Om.data(), acc, Ys, dst.data());
+}
+
+// Core multi-TTM of X whose last mode is the slab [off, off + n) of a mode of
+// length nd: the slab's partial sum X_slab x_{j<d} Q_j^T x_d Q_d[slab rows]^T.
+static void core_body(Ctx& c, const tk_tensor* X, int64_t off, int64_t nd, const tk_matrix* Q, tk_tensor* G,
+                      bool slab) {
+    Tens Xt = tens_in(X, "X");
+    c.xdata = Xt.p;
+    c.df64 = Xt.dt != TK_F64;
+    c.xnumel = Xt.numel();
+    Tens Gt = tens_in(G, "G");
+    const int d = Xt.d;
+    TK_REQUIRE(Q != nullptr, TK_ERR_ARG, "core: null Q");
+    if (slab) check_slab(Xt, off, nd, "core_slab");
+    else nd = Xt.n[d - 1];
+    tk_dtype acc = acc_of(Xt.dt);
+    TK_REQUIRE(Gt.d == d && (Gt.dt == TK_F64 || Gt.dt == TK_F32), TK_ERR_DTYPE, "core: G must be F64/F32, same d");
+    std::vector<Mat> Qm(d);
+    std::vector<int> modes(d);
+    for (int j = 0; j < d; ++j) {
+        Mat q = slab_factor(mat_in(&Q[j], "Q"), Xt, j, off, nd, "core");
+        TK_REQUIRE(q.cols == Gt.n[j], TK_ERR_SHAPE, "core: Q_j must be n_j x k_j");
+        Qm[j] = mat_to(c, q, acc);
+        modes[j] = j;
+    }
+    bool direct = Gt.dt == acc;
+    Tens out = multi_ttm(c, Xt, modes, Qm.data(), false, acc, direct ? Gt.p : nullptr);
+    if (!direct) launch_convert(c, out.p, acc, out.numel(), 1, out.numel(), Gt.p, Gt.dt, out.numel(), 1.f);
+}
+
+extern "C" {
+
 tk_status tucker_sketch(tk_handle* h, const tk_tensor* X, const tk_matrix* Omega, tk_tensor* Y) {
-    return run_call(h, [&](Ctx& c) {
-        Tens Xt = tens_in(X, "X");
-        c.xdata = Xt.p;
-        c.df64 = Xt.dt != TK_F64;
-        c.xnumel = Xt.numel();
-        const int d = Xt.d;
-        TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "sketch: d must be >= 2");
-        TK_REQUIRE(Omega && Y, TK_ERR_ARG, "sketch: null Omega or Y");
-        tk_dtype acc = acc_of(Xt.dt);
-        std::vector<Mat> Om(d);
-        std::vector<void*> dst(d);
-        for (int j = 0; j < d; ++j) {
-            Mat o = mat_in(&Omega[j], "Omega");
-            TK_REQUIRE(o.rows == Xt.n[j], TK_ERR_SHAPE, "sketch: Omega_j must have n_j rows");
-            TK_REQUIRE(acc == TK_F64 ? o.dt == TK_F64 : o.dt != TK_F64, TK_ERR_DTYPE,
-                       "sketch: Omega must be F64 for F64 data, else F32/BF16");
-            Om[j] = mat_to(c, o, acc);
-        }
-        for (int n = 0; n < d; ++n) {
-            Tens y = tens_in(&Y[n], "Y");
-            TK_REQUIRE(y.d == d && y.dt == acc, TK_ERR_DTYPE, "sketch: Y must have the data's d and F64/F32 dtype");
-            for (int j = 0; j < d; ++j)
-                TK_REQUIRE(y.n[j] == (j == n ? Xt.n[j] : Om[j].cols), TK_ERR_SHAPE, "sketch: Y[n] has wrong dims");
-            dst[n] = y.p;
-        }
-        std::vector<Tens> Ys(d);
-        std::vector<int> all(d);
-        std::iota(all.begin(), all.end(), 0);
-        all_modes(c, Xt, all, {}, Om.data(), acc, Ys, dst.data());
-    });
+    return run_call(h, [&](Ctx& c) { sketch_body(c, X, 0, 0, Omega, Y, false); });
+}
+
+tk_status tucker_sketch_slab(tk_handle* h, const tk_tensor* X_slab, int64_t offset, int64_t n_last,
+                             const tk_matrix* Omega, tk_tensor* Y) {
+    return run_call(h, [&](Ctx& c) { sketch_body(c, X_slab, offset, n_last, Omega, Y, true); });
 }
 
 tk_status tucker_orth(tk_handle* h, const tk_matrix* Y, tk_matrix* Q, int* info, const tk_opts* opts) {
@@ -1034,28 +1133,121 @@ tk_status tucker_gaussian_factors(tk_handle* h, uint64_t seed, int count, const 
 }
 
 tk_status tucker_core(tk_handle* h, const tk_tensor* X, const tk_matrix* Q, tk_tensor* G) {
+    return run_call(h, [&](Ctx& c) { core_body(c, X, 0, 0, Q, G, false); });
+}
+
+tk_status tucker_core_slab(tk_handle* h, const tk_tensor* X_slab, int64_t offset, int64_t n_last, const tk_matrix* Q,
+                           tk_tensor* G) {
+    return run_call(h, [&](Ctx& c) { core_body(c, X_slab, offset, n_last, Q, G, true); });
+}
+
+tk_status tucker_orth_sketches(tk_handle* h, int d, const tk_tensor* Y, tk_matrix* Q) {
     return run_call(h, [&](Ctx& c) {
-        Tens Xt = tens_in(X, "X");
+        TK_REQUIRE(d >= 1 && d <= TK_MAX_D, TK_ERR_ARG, "orth_sketches: 1 <= d <= TK_MAX_D");
+        TK_REQUIRE(Y && Q, TK_ERR_ARG, "orth_sketches: null Y or Q");
+        std::vector<Tens> Yt(d);
+        std::vector<Mat> Qm(d);
+        std::vector<double*> Qd(d);
+        std::vector<View2> Yv;
+        std::vector<int64_t> nb, kb;
+        std::vector<double*> qb;
+        std::vector<int> slots;
+        bool f32 = true;
+        for (int n = 0; n < d; ++n) {
+            Yt[n] = tens_in(&Y[n], "Y");
+            TK_REQUIRE(Yt[n].d == d, TK_ERR_SHAPE, "orth_sketches: every Y has order d");
+            TK_REQUIRE(Yt[n].dt == TK_F64 || Yt[n].dt == TK_F32, TK_ERR_DTYPE, "orth_sketches: Y must be F64/F32");
+            f32 = f32 && Yt[n].dt == TK_F32;
+        }
+        c.df64 = f32;
+        launch_fill_int(c, c.dqr, TK_MAX_D, 2);
+        for (int n = 0; n < d; ++n) {
+            const int64_t nn = Yt[n].n[n], cols = nn ? Yt[n].numel() / nn : 0, k = std::min(nn, cols);
+            TK_REQUIRE(nn >= 1 && cols >= 1, TK_ERR_SHAPE, "orth_sketches: empty sketch");
+            TK_REQUIRE(k <= 112, TK_ERR_SHAPE, "orth_sketches: sketch width above 112 is not supported");
+            Qm[n] = mat_in(&Q[n], "Q");
+            TK_REQUIRE(Qm[n].rows == nn && Qm[n].cols == k, TK_ERR_SHAPE, "orth_sketches: Q[n] must be n_n x k_n");
+            TK_REQUIRE(Qm[n].dt == TK_F64 || Qm[n].dt == TK_F32, TK_ERR_DTYPE, "orth_sketches: Q must be F64/F32");
+            Qd[n] = c.alloc<double>(nn * k);
+            if (k < nn) {
+                Yv.push_back(view_unfold_rows(Yt[n], n));
+                nb.push_back(nn);
+                kb.push_back(k);
+                qb.push_back(Qd[n]);
+                slots.push_back(n);
+            } else {
+                launch_fill_identity(c, Qd[n], nn);
+            }
+        }
+        orth_batch(c, Yv, nb, kb, qb, slots);
+        for (int n = 0; n < d; ++n)
+            launch_convert(c, Qd[n], TK_F64, Qm[n].rows, Qm[n].cols, Qm[n].rows, (void*)Qm[n].p, Qm[n].dt, Qm[n].ld,
+                           1.f);
+    });
+}
+
+tk_status tucker_sthosvd(tk_handle* h, const tk_tensor* Ghat, const tk_matrix* Q, const int64_t* r,
+                         const tk_opts* opts, tk_tensor* G, tk_matrix* U) {
+    return run_call(h, [&](Ctx& c) {
+        Tens Gh = tens_in(Ghat, "Ghat", false);
+        const int d = Gh.d;
+        TK_REQUIRE(Gh.dt == TK_F64 || Gh.dt == TK_F32, TK_ERR_DTYPE, "sthosvd: Ghat must be F64/F32");
+        TK_REQUIRE(Q && r && G && U, TK_ERR_ARG, "sthosvd: null argument");
+        Opts o = opts_in(opts, d);
+        set_opts(c, o);
+        c.df64 = Gh.dt != TK_F64;
+        Tens dims;  // the tensor's dims, from the factors' rows
+        dims.d = d;
+        std::vector<double*> Qd(d);
+        std::vector<int64_t> k(d);
+        for (int j = 0; j < d; ++j) {
+            Mat q = mat_in(&Q[j], "Q");
+            TK_REQUIRE(q.cols == Gh.n[j] && q.rows >= 1, TK_ERR_SHAPE, "sthosvd: Q_j must be n_j x k_j");
+            TK_REQUIRE(r[j] >= 1 && r[j] <= Gh.n[j], TK_ERR_SHAPE, "sthosvd: need 1 <= r_j <= k_j");
+            dims.n[j] = q.rows;
+            k[j] = q.cols;
+            Qd[j] = (double*)mat_to(c, q, TK_F64).p;
+        }
+        Tens Gt;
+        std::vector<Mat> Um;
+        check_outputs(dims, r, G, U, Gt, Um);
+        Tens G64 = Gh.dt == TK_F64 ? Gh : tens_to(c, Gh, TK_F64);
+        std::vector<double*> V;
+        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Gh.dt == TK_F64);
+        finish(c, dims, Qd, k, Gt64, V, r, Gt, Um, nullptr);
+    });
+}
+
+tk_status tucker_loss_slab(tk_handle* h, const tk_tensor* X_slab, int64_t offset, int64_t n_last, const tk_tensor* G,
+                           const tk_matrix* U, double* norms2) {
+    double* dev = nullptr;
+    tk_status st = run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X_slab, "X");
         c.xdata = Xt.p;
         c.df64 = Xt.dt != TK_F64;
         c.xnumel = Xt.numel();
+        check_slab(Xt, offset, n_last, "loss_slab");
         Tens Gt = tens_in(G, "G");
+        TK_REQUIRE(norms2 != nullptr, TK_ERR_ARG, "loss_slab: null output");
+        std::vector<Mat> Um;
+        std::vector<int64_t> n;
+        check_tucker(Gt, U, Um, n);
         const int d = Xt.d;
-        TK_REQUIRE(Q != nullptr, TK_ERR_ARG, "core: null Q");
+        TK_REQUIRE(Gt.d == d, TK_ERR_SHAPE, "loss_slab: X and G must have the same d");
         tk_dtype acc = acc_of(Xt.dt);
-        TK_REQUIRE(Gt.d == d && (Gt.dt == TK_F64 || Gt.dt == TK_F32), TK_ERR_DTYPE, "core: G must be F64/F32, same d");
-        std::vector<Mat> Qm(d);
-        std::vector<int> modes(d);
-        for (int j = 0; j < d; ++j) {
-            Mat q = mat_in(&Q[j], "Q");
-            TK_REQUIRE(q.rows == Xt.n[j] && q.cols == Gt.n[j], TK_ERR_SHAPE, "core: Q_j must be n_j x k_j");
-            Qm[j] = mat_to(c, q, acc);
-            modes[j] = j;
-        }
-        bool direct = Gt.dt == acc;
-        Tens out = multi_ttm(c, Xt, modes, Qm.data(), false, acc, direct ? Gt.p : nullptr);
-        if (!direct) launch_convert(c, out.p, acc, out.numel(), 1, out.numel(), Gt.p, Gt.dt, out.numel(), 1.f);
+        Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
+        std::vector<Mat> Ua(d);
+        for (int j = 0; j < d; ++j) Ua[j] = mat_to(c, slab_factor(Um[j], Xt, j, offset, n_last, "loss_slab"), acc);
+        dev = c.alloc<double>(2);
+        residual_pass(c, Xt, Ga, Ua, acc, dev, nullptr, TK_F32, 0.0);
     });
+    if (st != TK_OK) return st;
+    if (cudaMemcpyAsync(norms2, dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        h->last_error = "loss_slab: reading the norms failed";
+        return TK_ERR_CUDA;
+    }
+    return TK_OK;
 }
 
 // ------------------------------------------------------------------ algorithms

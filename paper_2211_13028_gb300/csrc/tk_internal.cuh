@@ -308,6 +308,10 @@ void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtr
                             tk_dtype xrdt, void* dx, float alpha, double* partials);
 int tc_num_ctas(const Tens& X, int j, int64_t m, bool residual);
 bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m);
+// One warp waits with the tcgen05 kernels' bounded wait on an mbarrier that
+// nothing arrives at (limit_ns), which raises FLAG_TIMEOUT; *waited (device)
+// receives how long it waited in ns (-1 had the wait completed).
+void launch_wait_selftest(const Ctx& c, uint64_t limit_ns, long long* waited);
 // out2 = {sum part[2i], sum part[2i+1]} over nb pairs
 void launch_sum_pairs(const Ctx& c, const double* part, int nb, double* out2);
 

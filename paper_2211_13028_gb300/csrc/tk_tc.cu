@@ -498,7 +498,31 @@ static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap
     kern<<<grid, Warps<EPI>::kThreads, Cf::kSmem, c.stream>>>(tx, th, tl, txr, a);
 }
 
+// Self-test of the bounded wait: one warp waits, through the same mbar_wait_warp
+// the tcgen05 kernels use, on an mbarrier that nothing ever arrives at, so the
+// wait must give up after limit_ns, raise FLAG_TIMEOUT and let the kernel
+// return.  waited[0] receives the nanoseconds the wait lasted.
+__global__ void __launch_bounds__(32) wait_selftest_kernel(uint64_t limit_ns, unsigned* flags, long long* waited) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort;
+    if (threadIdx.x == 0) {
+        abort = 0;
+        mbar_init(&bar, 1);
+    }
+    __syncthreads();
+    const uint64_t t0 = gtimer();
+    const bool ok = mbar_wait_warp(&bar, 0, &abort, flags, limit_ns);
+    if (threadIdx.x == 0) waited[0] = ok ? -1 : (long long)(gtimer() - t0);
+}
+
 }  // namespace tc
+
+void launch_wait_selftest(const Ctx& c, uint64_t limit_ns, long long* waited) {
+    if (!c.exec) return;
+    tc::wait_selftest_kernel<<<1, 32, 0, c.stream>>>(limit_ns, c.dflags, waited);
+    c.counted();
+    c.check_launch();
+}
 
 // Output columns: up to 96 (64 for the residual epilogue, whose X tiles share
 // shared memory with the pipeline) in one block padded to 16, else blocks of 64.

@@ -48,13 +48,14 @@ __device__ __forceinline__ uint64_t gtimer() {
 
 // Bounded wait: false when the CTA is aborting or the limit expired (which
 // also starts the abort and records FLAG_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, unsigned* flags) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, unsigned* flags,
+                                          uint64_t limit_ns = kTimeoutNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
-        if (gtimer() - t0 > kTimeoutNs) {
+        if (gtimer() - t0 > limit_ns) {
             *abort = 1;
             atomicOr(flags, FLAG_TIMEOUT);
             return false;
@@ -64,9 +65,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
 
 // Warp-wide bounded wait (every lane, warp-uniform result): lane 0 waits,
 // then each lane acquires the completed phase itself.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort, unsigned* flags) {
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort, unsigned* flags,
+                                               uint64_t limit_ns = kTimeoutNs) {
     int ok = 1;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort, flags) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort, flags, limit_ns) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (ok) {
         while (!mbar_try_wait(bar, parity)) {  // the phase has completed: returns at once

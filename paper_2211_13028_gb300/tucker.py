@@ -26,11 +26,12 @@ __all__ = [
     "tucker_subranks_reuse", "tucker_subranks_matrix",
     "tucker_sketch", "tucker_orth", "tucker_orth_noalloc", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
-    "tk_sync_status", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
+    "tk_sync_status", "tk_selftest_bounded_wait", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
     "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tucker_rhkron_srht", "tk_graph_release",
     "tk_philox4x32", "tucker_gaussian_factor", "tucker_gaussian_factors", "gaussian_factors",
     "gaussian_factors_matrix", "rsthkron_factor_plan",
-    "TuckerGraph",
+    "TuckerGraph", "tucker_sketch_slab", "tucker_orth_sketches", "tucker_core_slab", "tucker_sthosvd",
+    "tucker_loss_slab",
 ]
 
 TK_MAX_D = 8
@@ -102,6 +103,7 @@ def load():
             "tk_set_stream": ([vp, vp], ctypes.c_int),
             "tk_last_error": ([vp], ctypes.c_char_p),
             "tk_sync_status": ([vp, P(ctypes.c_int)], ctypes.c_int),
+            "tk_selftest_bounded_wait": ([vp, ctypes.c_int64, P(ctypes.c_int64)], ctypes.c_int),
             "tk_workspace_bytes": ([vp], ctypes.c_int64),
             "tk_launch_count": ([vp], ctypes.c_int64),
             "tk_profile": ([vp, ctypes.c_int], ctypes.c_int),
@@ -128,6 +130,15 @@ def load():
             "tucker_rhkron_srht": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), ctypes.c_uint64, P(TkOpts),
                                     P(TkTensor), P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
             "tucker_reconstruct": ([vp, P(TkTensor), P(TkMatrix), P(TkTensor)], ctypes.c_int),
+            "tucker_sketch_slab": ([vp, P(TkTensor), ctypes.c_int64, ctypes.c_int64, P(TkMatrix), P(TkTensor)],
+                                   ctypes.c_int),
+            "tucker_orth_sketches": ([vp, ctypes.c_int, P(TkTensor), P(TkMatrix)], ctypes.c_int),
+            "tucker_core_slab": ([vp, P(TkTensor), ctypes.c_int64, ctypes.c_int64, P(TkMatrix), P(TkTensor)],
+                                 ctypes.c_int),
+            "tucker_sthosvd": ([vp, P(TkTensor), P(TkMatrix), i64p, P(TkOpts), P(TkTensor), P(TkMatrix)],
+                               ctypes.c_int),
+            "tucker_loss_slab": ([vp, P(TkTensor), ctypes.c_int64, ctypes.c_int64, P(TkTensor), P(TkMatrix),
+                                  P(ctypes.c_double)], ctypes.c_int),
             "tucker_loss": ([vp, P(TkTensor), P(TkTensor), P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
             "tucker_reconstruct_backward": ([vp, P(TkTensor), P(TkTensor), P(TkMatrix), ctypes.c_double, P(TkTensor),
                                              P(TkMatrix), P(TkTensor)], ctypes.c_int),
@@ -276,6 +287,20 @@ def tk_sync_status(device=None) -> Tuple[int, List[int]]:
     return st, list(info)
 
 
+def tk_selftest_bounded_wait(limit_ns: int, device=None) -> int:
+    """Run the library's bounded-wait self-test on the handle of ``device``'s current stream: a warp
+    waits, with the tcgen05 kernels' bounded wait, on an mbarrier nothing arrives at, and gives up
+    after ``limit_ns``.  Returns the nanoseconds the wait lasted; the timeout is then reported by
+    the next tk_sync_status (TK_ERR_TIMEOUT)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    h = _handle(dev)
+    out = ctypes.c_int64(0)
+    st = load().tk_selftest_bounded_wait(h, int(limit_ns), ctypes.byref(out))
+    if st != 0:
+        raise TuckerError(st, load().tk_last_error(h).decode())
+    return int(out.value)
+
+
 def tk_launch_count(device=None) -> int:
     """Kernel launches queued through every handle of the device."""
     return int(sum(load().tk_launch_count(h) for h in _device_handles(device)))
@@ -359,6 +384,73 @@ def tucker_sketch(X: torch.Tensor, Omega: Sequence[torch.Tensor], scale: float =
     h = _handle(X.device)
     _check(load().tucker_sketch(h, ctypes.byref(_tensor(X, scale)), _mats(Omega), ys), h)
     return Y
+
+
+def tucker_sketch_slab(X_slab: torch.Tensor, offset: int, n_last: int, Omega: Sequence[torch.Tensor],
+                       scale: float = 1.0) -> List[torch.Tensor]:
+    """Sketches of a slab of X along its last mode (rows offset .. offset + X_slab.shape[-1] - 1 of a mode of
+    length n_last; Omega[-1] is the full n_last x s_d factor).  Y[n], n < d-1: the slab's partial sums of
+    Y_n (SUM them over the slabs); Y[d-1]: the slab's rows of Y_d (gather them along the last mode)."""
+    d = X_slab.dim()
+    s = [int(o.shape[1]) for o in Omega]
+    acc = _acc_dtype(X_slab)
+    Y = [empty_f([X_slab.shape[j] if j == n else s[j] for j in range(d)], acc, X_slab.device) for n in range(d)]
+    ys = (TkTensor * d)(*[_tensor(y) for y in Y])
+    h = _handle(X_slab.device)
+    _check(load().tucker_sketch_slab(h, ctypes.byref(_tensor(X_slab, scale)), int(offset), int(n_last),
+                                     _mats(Omega), ys), h)
+    return Y
+
+
+def tucker_orth_sketches(Y: Sequence[torch.Tensor], out_dtype=torch.float64) -> List[torch.Tensor]:
+    """Thin QR factor Q_n (n_n x k_n) of the mode-n unfolding of each sketch tensor Y[n] (Q = I when the sketch
+    is at least as wide as the mode), as inside tucker_rhkron."""
+    d = len(Y)
+    Q = []
+    for n, y in enumerate(Y):
+        nn = int(y.shape[n])
+        cols = y.numel() // max(1, nn)
+        Q.append(_colmajor_matrix(nn, min(nn, cols), out_dtype, y.device))
+    ys = (TkTensor * d)(*[_tensor(y) for y in Y])
+    h = _handle(Y[0].device)
+    _check(load().tucker_orth_sketches(h, d, ys, _mats(Q)), h)
+    return Q
+
+
+def tucker_core_slab(X_slab: torch.Tensor, offset: int, n_last: int, Q: Sequence[torch.Tensor], out_dtype=None,
+                     scale: float = 1.0) -> torch.Tensor:
+    """The slab's partial core X_slab x_{j<d} Q_j^T x_d Q_d[slab rows]^T (Q[-1] is the full n_last x k_d
+    factor); SUM it over the slabs."""
+    G = empty_f([int(q.shape[1]) for q in Q], out_dtype or _acc_dtype(X_slab), X_slab.device)
+    h = _handle(X_slab.device)
+    _check(load().tucker_core_slab(h, ctypes.byref(_tensor(X_slab, scale)), int(offset), int(n_last), _mats(Q),
+                                   ctypes.byref(_tensor(G))), h)
+    return G
+
+
+def tucker_sthosvd(Ghat: torch.Tensor, Q: Sequence[torch.Tensor], r: Sequence[int], order=None, out_dtype=None):
+    """STHOSVD of a given core to ranks r and U_j = Q_j V_j (steps 4-5 of Algorithm rHKron-re): (G, [U_j])."""
+    d = Ghat.dim()
+    dt = out_dtype or Ghat.dtype
+    G = empty_f(list(r), dt, Ghat.device)
+    U = [_colmajor_matrix(int(Q[j].shape[0]), int(r[j]), dt, Ghat.device) for j in range(d)]
+    rr = (ctypes.c_int64 * d)(*[int(x) for x in r])
+    o, keep = _opts(order)
+    h = _handle(Ghat.device)
+    _check(load().tucker_sthosvd(h, ctypes.byref(_tensor(Ghat)), _mats(Q), rr, ctypes.byref(o),
+                                 ctypes.byref(_tensor(G)), _mats(U)), h)
+    return G, U
+
+
+def tucker_loss_slab(X_slab: torch.Tensor, offset: int, n_last: int, G: torch.Tensor, U: Sequence[torch.Tensor],
+                     scale: float = 1.0) -> Tuple[float, float]:
+    """(||X_slab - G x_{j<d} U_j x_d U_d[slab rows]||^2, ||X_slab||^2) (U[-1] is the full n_last x r_d factor);
+    SUM both over the slabs."""
+    out = (ctypes.c_double * 2)()
+    h = _handle(X_slab.device)
+    _check(load().tucker_loss_slab(h, ctypes.byref(_tensor(X_slab, scale)), int(offset), int(n_last),
+                                   ctypes.byref(_tensor(G)), _mats(U), out), h)
+    return float(out[0]), float(out[1])
 
 
 def tucker_orth(Y: torch.Tensor, qr_method: int = 0, out_dtype=None) -> Tuple[torch.Tensor, int]:

@@ -1,12 +1,13 @@
-"""The exchange a sharded rHKron-re would need, checked on the FP64 oracle (CPU).
+"""The exchange of the sharded rHKron-re (CPU).
 
 With X split into slabs along its last mode d (rank q holds X[..., rows_q]), every quantity of
 rHKron-re that contracts mode d is a sum of per-slab partials, and the sketch of mode d itself is
-a row-wise concatenation (the one-exchange-per-phase design for several GPUs): Y_n for n != d is
-the sum over slabs of X_q x_{j!=n} Phi_j with Phi_d restricted to the slab's rows, Y_d stacks the
-slabs' Y_d rows, and Ghat is the sum of X_q x_{j<d} Q_j^T x_d Q_d[rows_q]^T.  The library runs on
-one GPU per box (replicas only), so this pins the exchange on the host: as identities, and as a
-SUM all-reduce across two gloo ranks.
+a row-wise concatenation (one exchange per phase): Y_n for n != d is the sum over slabs of
+X_q x_{j!=n} Phi_j with Phi_d restricted to the slab's rows, Y_d stacks the slabs' Y_d rows, and
+Ghat is the sum of X_q x_{j<d} Q_j^T x_d Q_d[rows_q]^T.  The first two tests pin these identities
+on the FP64 oracle alone; the gloo test runs the library's exchange helpers (sharded.allreduce_sum
+and sharded.gather_last_mode, the ones sharded.rhkron_sharded uses) across two ranks on the
+oracle's slab partials.  tests/test_gpu_sharded.py feeds the library's own slab calls into them.
 """
 import os
 import socket
@@ -18,7 +19,7 @@ import torch.multiprocessing as mp
 import oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-DIMS, S = (9, 8, 12), (3, 2, 4)
+DIMS, S = (9, 8, 13), (3, 2, 4)  # 13 rows: two ranks get uneven slabs (7 and 6)
 
 
 def _problem(seed=5):
@@ -42,7 +43,7 @@ def test_slab_sketches_sum_and_stack_to_the_full_sketch():
     x, oms = _problem()
     d = x.ndim
     full = [O.multi_ttm(x, [(j, oms[j].T) for j in range(d) if j != n]) for n in range(d)]
-    slabs = [np.arange(0, 5), np.arange(5, 9), np.arange(9, 12)]  # uneven slabs
+    slabs = [np.arange(0, 5), np.arange(5, 9), np.arange(9, 13)]  # uneven slabs
     parts = [_slab_partials(x, oms, rows) for rows in slabs]
     for n in range(d - 1):
         assert np.max(np.abs(sum(p[0][n] for p in parts) - full[n])) <= 1e-12 * np.max(np.abs(full[n]))
@@ -54,7 +55,7 @@ def test_slab_cores_sum_to_the_full_core():
     d = x.ndim
     qs = [O.thin_qr(O.unfold(O.multi_ttm(x, [(j, oms[j].T) for j in range(d) if j != n]), n)) for n in range(d)]
     full = O.multi_ttm(x, [(j, qs[j].T) for j in range(d)])
-    slabs = [np.arange(0, 7), np.arange(7, 12)]
+    slabs = [np.arange(0, 7), np.arange(7, 13)]
     parts = [O.multi_ttm(x[..., rows], [(j, qs[j].T) for j in range(d - 1)] + [(d - 1, qs[d - 1][rows, :].T)])
              for rows in slabs]
     assert np.max(np.abs(sum(parts) - full)) <= 1e-12 * np.max(np.abs(full))
@@ -66,31 +67,44 @@ def _free_port():
         return s.getsockname()[1]
 
 
+def _fortran(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a.transpose())).permute(*reversed(range(a.ndim)))
+
+
 def _rank_main(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     sys.path.insert(0, ROOT)
-    import torch
     import torch.distributed as dist
 
     import oracle as Ox
+    from paper_2211_13028_gb300 import sharded
 
     dist.init_process_group("gloo", rank=rank, world_size=world)
     x, oms = _problem(11)
-    rows = np.array_split(np.arange(DIMS[-1]), world)[rank]
+    off, nrows = sharded.slab_bounds(DIMS[-1], world, rank)
+    rows = np.arange(off, off + nrows)
     part, yd = _slab_partials(x, oms, rows)
-    reduced = []
-    for y in part:  # the all-reduce of the sketches of the modes other than d
-        t = torch.from_numpy(np.ascontiguousarray(y))
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        reduced.append(t.numpy())
-    gathered = [None] * world  # the all-gather of the mode-d sketch rows
-    dist.all_gather_object(gathered, yd)
+    reduced = [sharded.allreduce_sum(_fortran(y)).permute(*reversed(range(x.ndim))).numpy().transpose()
+               for y in part]  # the all-reduce of the sketches of the modes other than d
+    full_d = sharded.gather_last_mode(_fortran(yd), off, DIMS[-1])  # the gather of the mode-d rows
     dist.destroy_process_group()
     d = x.ndim
     full = [Ox.multi_ttm(x, [(j, oms[j].T) for j in range(d) if j != n]) for n in range(d)]
     err = max(float(np.max(np.abs(reduced[n] - full[n]))) for n in range(d - 1))
-    stacked = np.concatenate(gathered, axis=d - 1)
+    stacked = full_d.permute(*reversed(range(d))).numpy().transpose()
     q.put((rank, err, bool(np.array_equal(stacked, full[d - 1]))))
+
+
+def test_slab_bounds_cover_the_mode():
+    sys.path.insert(0, ROOT)
+    from paper_2211_13028_gb300 import sharded
+
+    for n, parts in ((12, 2), (13, 3), (512, 8), (5, 5), (7, 1)):
+        spans = [sharded.slab_bounds(n, parts, i) for i in range(parts)]
+        assert spans[0][0] == 0 and sum(r for _, r in spans) == n
+        assert all(a + r == b for (a, r), (b, _) in zip(spans, spans[1:]))
+        assert max(r for _, r in spans) - min(r for _, r in spans) <= 1
 
 
 def test_two_gloo_ranks_exchange_the_slab_sketches():
