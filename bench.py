@@ -273,15 +273,19 @@ def profile_case(args):
     dev = torch.device("cuda", 0)
     n = args.n
     X = synth.gaussian_bumps(n, 3, 200, SEED, 1e-4, dev, "f32")
+    xs = 1.0
     if args.dtype == "bf16":
         X = X.to(torch.bfloat16)
+    elif args.dtype == "fp8":  # per-tensor scale, q = e4m3(x * scale)
+        xs = 448.0 / float(X.abs().max())
+        X = (X * xs).to(torch.float8_e4m3fn)
     g = __import__("numpy").random.Generator(__import__("numpy").random.PCG64(SEED))
     if args.profile_case == "sketch":
         om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(X.shape, (6, 7, 7), SEED + 1, "f32")]
-        fn = lambda: T.tucker_sketch(X, om)  # noqa: E731
+        fn = lambda: T.tucker_sketch(X, om, scale=xs)  # noqa: E731
     elif args.profile_case == "core":
         qs = [synth.fmat(__import__("numpy").linalg.qr(g.standard_normal((n, k)))[0], "f32", dev) for k in (49, 42, 42)]
-        fn = lambda: T.tucker_core(X, qs)  # noqa: E731
+        fn = lambda: T.tucker_core(X, qs, scale=xs)  # noqa: E731
     elif args.profile_case == "backward":
         # dG and dU at an rHKron-re result (r = 32, p = 8)
         s, _ = T.tucker_subranks_reuse(RANKS, P_OVER)
@@ -292,7 +296,7 @@ def profile_case(args):
         # the whole of rHKron-re at r = 32, p = 8: the core sizes (49,42,42) do not depend on n
         s, _ = T.tucker_subranks_reuse(RANKS, P_OVER)
         om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(X.shape, s, SEED + 1, "f32")]
-        fn = lambda: T.tucker_rhkron(X, RANKS, P_OVER, om)  # noqa: E731
+        fn = lambda: T.tucker_rhkron(X, RANKS, P_OVER, om, scale=xs)  # noqa: E731
     elif args.profile_case == "rsthkron":
         # the whole of rSTHKron at r = 32, p = 8 (S rows {5, 8}), factors drawn on the device
         S, w = T.tucker_subranks_matrix(RANKS, P_OVER)
@@ -358,6 +362,9 @@ def run_bf16_workload(args):
     X32 = synth.gaussian_bumps(n, 3, 200, SEED, 1e-4, dev, "f32")
     X16 = X32.to(torch.bfloat16)
     assert T.is_colmajor(X16)
+    sc8 = 448.0 / float(X32.abs().max())  # FP8 storage: per-tensor scale, q = e4m3(x * scale)
+    X8 = (X32 * sc8).to(torch.float8_e4m3fn)
+    assert T.is_colmajor(X8)
     om = [synth.fmat(o, "f32", dev) for o in synth.sketch_factors_reuse(tuple(X32.shape), s, SEED + 1, "bf16")]
     nrm32 = float(torch.linalg.vector_norm(X32.double()))
     hbm = _peaks()[0]
@@ -365,40 +372,48 @@ def run_bf16_workload(args):
     clocks.start()
     time.sleep(0.3)
     forms = {}
-    for name, X in (("bf16", X16), ("f32", X32)):
+    for name, X, xs in (("bf16", X16, 1.0), ("f32", X32, 1.0), ("fp8", X8, sc8)):
         for _ in range(args.warmup):
-            out = T.tucker_rhkron(X, r, p, om)
+            out = T.tucker_rhkron(X, r, p, om, scale=xs)
         torch.cuda.synchronize()
-        T.tk_profile(True, dev, only="xpass")  # live timing of the X-streaming kernel only
+        T.tk_profile(True, dev, only="xpass")  # live timing of the X-streaming kernels only
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps):
-            out = T.tucker_rhkron(X, r, p, om, async_outputs=True)
+            out = T.tucker_rhkron(X, r, p, om, async_outputs=True, scale=xs)
         e1.record()
         torch.cuda.synchronize()
         prof = T.tk_profile_read(dev)
         T.tk_profile(False, dev)
         G, U, err = out
         loss32 = T.tucker_loss(X32, G, U)
-        xp = prof.get("xpass_tc", dict(ms=0.0, launches=1, bytes=0.0))
-        gbs = (xp["bytes"] / max(1, xp["launches"])) / (xp["ms"] / max(1, xp["launches"]) * 1e-3) / 1e9 \
-            if xp["ms"] > 0 else 0.0
+        passes = {}
+        for cls in ("xpass_tc", "xpass_simt", "xpass_narrow"):
+            xp = prof.get(cls)
+            if not xp or xp["ms"] <= 0:
+                continue
+            gbs = (xp["bytes"] / xp["launches"]) / (xp["ms"] / xp["launches"] * 1e-3) / 1e9
+            passes[cls] = dict(gbs=gbs, frac=gbs / hbm, launches_per_step=xp["launches"] / args.steps,
+                               us_per_launch=1e3 * xp["ms"] / xp["launches"],
+                               bytes_per_launch=xp["bytes"] / xp["launches"])
+        tc = passes.get("xpass_tc", dict(gbs=0.0, frac=0.0, launches_per_step=0, bytes_per_launch=0.0))
         forms[name] = dict(ms=e0.elapsed_time(e1) / args.steps, rel_err_vs_own_data=err.value,
                            rel_err_vs_f32_field=float(np.sqrt(max(loss32, 0.0))) / nrm32,
-                           xpass_gbs=gbs, xpass_frac=gbs / hbm,
-                           xpass_launches=xp["launches"] // args.steps,
-                           xpass_bytes_per_step=xp["bytes"] / args.steps)
+                           xpass_gbs=tc["gbs"], xpass_frac=tc["frac"], xpass_launches=tc["launches_per_step"],
+                           x_passes=passes)
     clk = clocks.stop()
     st, _ = T.tk_sync_status(dev)
     line = dict(
-        metric="rHKron-re wall time, 1024^3 field, r=64, p=16: BF16 storage (Q hi+lo refinement) vs FP32",
+        metric="rHKron-re wall time, 1024^3 field, r=64, p=16: BF16 storage (Q hi+lo refinement) vs FP32 (and FP8)",
         value=forms["bf16"]["ms"], unit="ms", n_gpus=1, steps=args.steps, warmup=args.warmup,
         ms_per_step=forms["bf16"]["ms"], higher_is_better=False, scaling="weak", vs_baseline=None,
         dtype="bf16", data="synthetic",
         config=dict(workload=("bumps1024_bf16: 1024^3 Gaussian-bump field (the 512^3 generator at n=1024), "
-                              "stored BF16 (rounded once) and FP32; rHKron-re r=(64,64,64), p=16, s=(9,9,9)"),
-                    l2="X is 2 GiB (BF16) / 4 GiB (FP32), larger than L2: no flush"),
+                              "stored BF16 (rounded once), FP32, and FP8 E4M3 (per-tensor scale 448/amax); "
+                              "rHKron-re r=(64,64,64), p=16, s=(9,9,9)"),
+                    l2="X is 2 GiB (BF16) / 4 GiB (FP32) / 1 GiB (FP8), larger than L2: no flush"),
         forms=forms, speedup_bf16_over_f32=forms["f32"]["ms"] / forms["bf16"]["ms"],
+        speedup_fp8_over_f32=forms["f32"]["ms"] / forms["fp8"]["ms"],
         cpu_baseline=dict(value=t_or * 1e3, unit="ms", cores=cpu_cores(), kind="oracle",
                           sample="one FP64 oracle rHKron-re on the BF16-rounded %d^3 field of the same generator"
                                  % n_or,
@@ -704,7 +719,7 @@ def main():
                     default=None,
                     help="run one building block on an n^3 FP32 field (for ncu captures) instead of the bench")
     ap.add_argument("--n", type=int, default=384, help="edge of the --profile-case tensor")
-    ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32", help="storage of the --profile-case tensor")
+    ap.add_argument("--dtype", choices=["f32", "bf16", "fp8"], default="f32", help="storage of the --profile-case tensor")
     ap.add_argument("--workload", choices=["bumps512_f32", "bumps1024_bf16", "tucker160x4_f32", "descent256_f32",
                                            "srht512_f32"],
                     default="bumps512_f32",

@@ -156,6 +156,8 @@ static Tens ttm_to(Ctx& c, const Tens& T, int j, const Mat& M, bool mtrans, tk_d
         launch_ttm_tc(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
     else if (c.use_tc && ttm_bf16_eligible(T, j, m, acc))
         launch_ttm_bf16(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
+    else if (c.use_tc && ttm_fp8_eligible(T, j, m, acc) && reinterpret_cast<uintptr_t>(o.p) % 16 == 0)
+        launch_ttm_fp8(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
     else
         launch_ttm(c, T, j, M, mtrans, m, o.p, acc);
     return o;
@@ -178,6 +180,10 @@ static Tens multi_ttm(Ctx& c, const Tens& T, std::vector<int> modes, const Mat* 
                 best = t;
             }
         }
+        // FP8 data streams through the tensor cores only along its contiguous mode: take that one first
+        // (the later products then read the much smaller FP32 intermediate)
+        for (size_t t = 0; t < modes.size() && c.use_tc && cur.dt == TK_FP8_E4M3; ++t)
+            if (modes[t] == 0 && ttm_fp8_eligible(cur, 0, mtrans ? M[0].rows : M[0].cols, acc)) best = t;
         int i = modes[best];
         modes.erase(modes.begin() + best);
         cur = ttm_to(c, cur, i, M[i], mtrans, acc, modes.empty() ? dst : nullptr);
@@ -465,13 +471,17 @@ static void residual_pass(Ctx& c, const Tens& X, const Tens& G, const std::vecto
         W = ttm_to(c, W, i, U[i], true, acc);
     }
     const int64_t m = U[f].rows;
-    // BF16 data: the epilogue reads the BF16 X tile (and writes a BF16 dX) itself
-    const bool fused = c.use_tc && (X.dt == TK_F32 || (X.dt == TK_BF16 && X.left(f) % 8 == 0)) &&
+    // BF16 data: the epilogue reads the BF16 X tile (and writes a BF16 dX) itself; FP8 data: the E4M3 X
+    // tile, scaled back by 1 / scale (norms only, no dX)
+    const bool fused = c.use_tc &&
+                       (X.dt == TK_F32 || (X.dt == TK_BF16 && X.left(f) % 8 == 0) ||
+                        (X.dt == TK_FP8_E4M3 && X.left(f) % 16 == 0 && !dx)) &&
                        acc == TK_F32 && (!dx || dxdt == X.dt) && ttm_tc_residual_eligible(W, f, m);
     if (fused) {
         const int nb = tc_num_ctas(W, f, m, true);
         double* part = c.alloc<double>(2 * nb);
-        launch_ttm_tc_residual(c, W, f, U[f], true, m, X.p, X.dt, dx, (float)alpha, part);
+        launch_ttm_tc_residual(c, W, f, U[f], true, m, X.p, X.dt, dx, (float)alpha, part,
+                               X.dt == TK_FP8_E4M3 ? 1.f / X.scale : 1.f);
         launch_sum_pairs(c, part, nb, err2);
         return;
     }

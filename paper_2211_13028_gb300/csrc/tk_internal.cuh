@@ -298,14 +298,20 @@ void launch_philox_blocks(const Ctx& c, unsigned long long seed, unsigned stream
                           int64_t nblocks, unsigned* out);
 void launch_gaussian_factors(const Ctx& c, unsigned long long seed, int count, const unsigned* streams,
                              const Mat* m);
+// FP8 (E4M3) data, contraction over the contiguous mode only (L == 1: X is a
+// K-major operand): tcgen05 kind::f8f6f4 with X straight from shared memory and
+// the factor split into four power-of-two-scaled E4M3 pieces (FP32 output).
+bool ttm_fp8_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
+void launch_ttm_fp8(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 bool ttm_bf16_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
 void launch_ttm_bf16(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 // Fused last step of a reconstruction: P = W x_j M^T is formed tile by tile and
 // compared with xref (P's dims, F32): per-CTA partial sums of (xref - P)^2 and
 // xref^2 go to partials[2 * cta]; with dx != NULL also dx = alpha * (xref - P).
 // P itself is never stored.  tc_num_ctas gives the number of partial pairs.
+// xref (F32, BF16, or FP8 for the norms only) is read as stored value * xr_scale.
 void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const void* xref,
-                            tk_dtype xrdt, void* dx, float alpha, double* partials);
+                            tk_dtype xrdt, void* dx, float alpha, double* partials, float xr_scale = 1.f);
 int tc_num_ctas(const Tens& X, int j, int64_t m, bool residual);
 bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m);
 // One warp waits with the tcgen05 kernels' bounded wait on an mbarrier that

@@ -28,6 +28,7 @@
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA raises
 // FLAG_TIMEOUT, stops issuing work, drains what it issued and frees its TMEM.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "tk_tc_common.cuh"
 
@@ -102,6 +103,7 @@ struct TcArgs {
     void* out;                              // EPI 0: product (FP32); EPI 2: alpha * (xref - product) (XR)
     const void* xref;                       // EPI 1, 2: tensor compared with the product (same layout, XR)
     float alpha;
+    float xr_scale;                         // EPI 1, 2: xref element = stored value * xr_scale (FP8: 1 / scale)
     double* partials;                       // EPI 1, 2: per CTA {sum (xref - product)^2, sum xref^2}
     unsigned* flags;
 };
@@ -128,6 +130,7 @@ struct Cfg {
 
 __device__ __forceinline__ float xr_to_f32(float v) { return v; }
 __device__ __forceinline__ float xr_to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float xr_to_f32(__nv_fp8_e4m3 v) { return static_cast<float>(v); }
 __device__ __forceinline__ void xr_store(float* p, float v) { *p = v; }
 __device__ __forceinline__ void xr_store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
@@ -413,11 +416,12 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             if (c0 + i < ncol) {
-                                const float xv = xr_to_f32(xt[(c0 + i) * kRows + rho]);
+                                const float xv = xr_to_f32(xt[(c0 + i) * kRows + rho]) * args.xr_scale;
                                 const float dv = xv - (h[i] + g[i]);
                                 fr = fmaf(dv, dv, fr);
                                 fx = fmaf(xv, xv, fx);
-                                if (EPI == 2) xr_store(static_cast<XR*>(args.out) + base + (c0 + i) * stride, args.alpha * dv);
+                                if constexpr (EPI == 2)
+                                    xr_store(static_cast<XR*>(args.out) + base + (c0 + i) * stride, args.alpha * dv);
                             }
                         }
                         sr += (double)fr;
@@ -549,7 +553,8 @@ bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt) {
 // xref (same dims as the product): partial norms per CTA into partials, and
 // for epi 2 out = alpha * (xref - product).
 static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, void* out, int epi,
-                       const void* xref, tk_dtype xrdt, float alpha, double* partials, const char* prof_name) {
+                       const void* xref, tk_dtype xrdt, float alpha, double* partials, const char* prof_name,
+                       float xr_scale = 1.f) {
     const int64_t L = X.left(j), nj = X.n[j], R = X.right(j);
     int64_t npad, nblk;
     tc_blocks(m, npad, nblk, epi != 0);
@@ -605,15 +610,18 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
     }
     CUtensorMap txr = tx;  // unused when epi == 0
     const bool xr_bf16 = epi != 0 && xrdt == TK_BF16;
+    const bool xr_fp8 = epi != 0 && xrdt == TK_FP8_E4M3;
     if (epi != 0) {
         TK_REQUIRE(!kmajor, TK_ERR_SHAPE, "ttm_tc: the fused residual needs a non-leading mode");
-        TK_REQUIRE(xrdt == TK_F32 || xrdt == TK_BF16, TK_ERR_DTYPE, "ttm_tc: residual reference must be F32/BF16");
-        const uint64_t es = xr_bf16 ? 2 : 4;
+        TK_REQUIRE(xrdt == TK_F32 || xrdt == TK_BF16 || (xrdt == TK_FP8_E4M3 && epi == 1), TK_ERR_DTYPE,
+                   "ttm_tc: residual reference must be F32/BF16 (FP8: norms only)");
+        const uint64_t es = xr_fp8 ? 1 : (xr_bf16 ? 2 : 4);
         uint64_t dims[3] = {(uint64_t)L, (uint64_t)m, (uint64_t)R};
         uint64_t str[2] = {(uint64_t)L * es, (uint64_t)L * m * es};
         uint32_t box[3] = {tc::kRows, (uint32_t)npad, 1};
         tc::encode(&txr, xref, 3, dims, str, box, false,
-                   xr_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+                   xr_fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                          : (xr_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32));
     }
     tc::TcArgs a;
     a.L = L;
@@ -627,9 +635,10 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
     a.out = out;
     a.xref = xref;
     a.alpha = alpha;
+    a.xr_scale = xr_scale;
     a.partials = partials;
     a.flags = c.dflags;
-    const double xres = xr_bf16 ? 2.0 : 4.0;
+    const double xres = xr_fp8 ? 1.0 : (xr_bf16 ? 2.0 : 4.0);
     double bytes = 4.0 * (double)L * R * nj + 8.0 * nj * m;
     if (epi == 0) bytes += 4.0 * (double)L * R * m;
     if (epi >= 1) bytes += xres * (double)L * R * m;
@@ -640,6 +649,8 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
         if (epi == 0) {                                                                            \
             if (kmajor) tc::launch_kernel<NP, true, 0>(c, tx, th, tl, txr, a);                          \
             else tc::launch_kernel<NP, false, 0>(c, tx, th, tl, txr, a);                                \
+        } else if (xr_fp8) {                                                                       \
+            tc::launch_kernel<NP, false, 1, __nv_fp8_e4m3>(c, tx, th, tl, txr, a);                      \
         } else if (xr_bf16) {                                                                      \
             if (epi == 1) tc::launch_kernel<NP, false, 1, __nv_bfloat16>(c, tx, th, tl, txr, a);         \
             else tc::launch_kernel<NP, false, 2, __nv_bfloat16>(c, tx, th, tl, txr, a);                  \
@@ -687,8 +698,8 @@ bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m) {
 }
 
 void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const void* xref,
-                            tk_dtype xrdt, void* dx, float alpha, double* partials) {
-    ttm_tc_run(c, W, j, M, mtrans, m, dx, dx ? 2 : 1, xref, xrdt, alpha, partials, "xpass_tc");
+                            tk_dtype xrdt, void* dx, float alpha, double* partials, float xr_scale) {
+    ttm_tc_run(c, W, j, M, mtrans, m, dx, dx ? 2 : 1, xref, xrdt, alpha, partials, "xpass_tc", xr_scale);
 }
 
 }  // namespace tk
