@@ -363,7 +363,9 @@ void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int
 // symmetric k x k FP64 matrix A (ld k): eigenvalue estimates in D (unsorted),
 // accumulated rotations in J (FP32, k x k, ld k; may be NULL) and, when
 // non-NULL, as FP64 copies in J64a and J64b.  Converged when every
-// off-diagonal |a_pq| <= tol * ||A||_F; otherwise FLAG_NOT_CONVERGED is raised.
+// off-diagonal |a_pq| <= tol * ||A||_F (fp64_diag: the resolving stage) or
+// |a_pq| <= max(tol sqrt(|a_pp a_qq|), 1e-13 ||A||_F) (otherwise: the seeding
+// stage); otherwise FLAG_NOT_CONVERGED is raised.
 void launch_jacobi_mixed(Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
                          double tol, int max_sweeps, bool fp64_diag);
 // Vr (k x r, ld k) = the columns of V (k x k) for the r largest entries of D, in descending order.

@@ -1485,7 +1485,9 @@ void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int
 // is scaled by a power of two to about unit Frobenius norm on entry (exact),
 // which keeps its FP32 entries and the rotation arithmetic clear of overflow
 // and underflow.  Converged: a sweep boundary at which no off-diagonal entry
-// exceeds the threshold, or kp - 1 consecutive steps without a rotation.
+// exceeds the threshold (absolute for the resolving stage, relative to the
+// pair's diagonal entries for the seeding stage), or kp - 1 consecutive steps
+// without a rotation.
 
 constexpr int JM_MAX_THREADS = 1024;
 constexpr int JM_BPT = 2;  // blocks per update thread: h (h + 1) / 2 <= 2 * 992 for h <= 56
@@ -1517,11 +1519,19 @@ __device__ __forceinline__ int jm_tri(int i, int j, int ld) { return i < j ? i *
 // special-function latencies after rho instead of c waiting on t.  Fast FP32
 // reciprocals and square roots suffice (the off-diagonal is zeroed explicitly
 // and convergence is measured).  Returns whether it rotates.
+// Whether the off-diagonal entry f of the pair with diagonal entries hp, hq
+// still needs a rotation: f^2 > max(trel2 |hp hq|, fthr2), a relative test
+// (trel2 = tol^2) with an absolute floor (fthr2); trel2 = 0 gives the plain
+// absolute test |f| > fthr.
+__device__ __forceinline__ bool jm_big(float f, float hp, float hq, float trel2, float fthr2) {
+    return f * f > fmaxf(trel2 * fabsf(hp * hq), fthr2);
+}
+
 template <bool DF>
-__device__ __forceinline__ int jm_rotate(float f, float fthr, bool allow, float& hp, float& lp, float& hq, float& lq,
-                                         float2& cs) {
+__device__ __forceinline__ int jm_rotate(float f, float trel2, float fthr2, bool allow, float& hp, float& lp,
+                                         float& hq, float& lq, float2& cs) {
     cs = make_float2(1.f, 0.f);
-    if (!(allow && fabsf(f) > fthr)) return 0;
+    if (!(allow && jm_big(f, hp, hq, trel2, fthr2))) return 0;
     float phi = hq - hp;
     if (DF) phi += lq - lp;
     const float psi = 2.f * f;
@@ -1657,7 +1667,16 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
             Lc[i] = DF ? __fsub_rn(v.y, __fsub_rn(hv, v.x)) : 0.f;
         }
     }
-    const float fthr = (float)tol * nsc;
+    // DF (the resolving stage): absolute threshold tol ||A||.  Otherwise (the
+    // seeding stage) relative: |a_pq| <= tol sqrt(|a_pp a_qq|), with a floor of
+    // 1e-13 ||A|| below which FP32 entries carry no information (an exactly
+    // rank-deficient tail would otherwise keep rotating on rounding noise).
+    // Resolving each pair against its own diagonal entries leaves the
+    // small-eigenvalue tail coupled only at ~1e-7 of its own scale, so the
+    // resolving stage then needs one or two sweeps instead of four to six.
+    const float trel2 = DF ? 0.f : (float)(tol * tol);
+    const float fthr = (DF ? (float)tol : 1e-13f) * nsc;
+    const float fthr2 = fthr * fthr;
     // update threads (warps 1..): their blocks' read bases and write addresses
     const int nblk = h * (h + 1) / 2, nu = nt - 32, ut = tid - 32;
     int bt[JM_BPT], rd[JM_BPT], w0[JM_BPT], w1[JM_BPT], w2[JM_BPT], w3[JM_BPT];
@@ -1700,7 +1719,7 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
             const int p = 2 * tp, q = p + 1;
             float hp = Hc[p], lp = Lc[p], hq = Hc[q], lq = Lc[q];
             float2 cs;
-            any |= jm_rotate<DF>(Fc[p * ld + q], fthr, true, hp, lp, hq, lq, cs);
+            any |= jm_rotate<DF>(Fc[p * ld + q], trel2, fthr2, true, hp, lp, hq, lq, cs);
             Hc[p] = hp;
             Lc[p] = lp;
             Hc[q] = hq;
@@ -1717,7 +1736,7 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
         if (s == 0) {
             int off = 0;
             for (int a = tid >> 5; a < kp; a += nt >> 5)
-                for (int b = a + 1 + lane; b < kp; b += 32) off |= fabsf(Fc[a * ld + b]) > fthr;
+                for (int b = a + 1 + lane; b < kp; b += 32) off |= jm_big(Fc[a * ld + b], Hc[a], Hc[b], trel2, fthr2);
             if (!__syncthreads_or(off)) {
                 converged = true;
                 break;
@@ -1745,7 +1764,7 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
                 }
                 const float f = jm_pivot_value(pv, Fc, mc, ld);
                 float2 cs;
-                any |= jm_rotate<DF>(f, fthr, want, hp, lp, hq, lq, cs);
+                any |= jm_rotate<DF>(f, trel2, fthr2, want, hp, lp, hq, lq, cs);
                 Hx[2 * tp] = hp;
                 Hx[2 * tp + 1] = hq;
                 if (DF) {
@@ -1789,7 +1808,7 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
     if (!converged) {  // the allowed sweeps ran out: measure once more
         int off = 0;
         for (int a = tid >> 5; a < kp; a += nt >> 5)
-            for (int b = a + 1 + lane; b < kp; b += 32) off |= fabsf(Fc[a * ld + b]) > fthr;
+            for (int b = a + 1 + lane; b < kp; b += 32) off |= jm_big(Fc[a * ld + b], Hc[a], Hc[b], trel2, fthr2);
         converged = !__syncthreads_or(off);
     }
     if (!converged && tid == 0) atomicOr(flags, FLAG_NOT_CONVERGED);
