@@ -346,7 +346,13 @@ TK_API tk_status tucker_loss_slab(tk_handle* h, const tk_tensor* X_slab, int64_t
  * X: F64, F32, BF16 or FP8_E4M3.  r: d host ranks, 1 <= r_j <= k_j.
  * p: oversampling, only checked against the Omega widths (prod_{j!=n} s_j >= r_n + p).
  * G: (r_1..r_d) F64 or F32.  U: d matrices n_j x r_j, F64 or F32.
- * rel_err (host, may be NULL): ||X - G x_j U_j|| / ||X||, which synchronises. */
+ * rel_err (host, may be NULL): ||X - G x_j U_j|| / ||X||, which synchronises.
+ * Sizes: every sketch width k_n (and so every core mode) must be <= 256, else
+ * TK_ERR_SHAPE.  Widths up to 112 take the fast one-CTA kernels above; widths
+ * 113-256 fall back to the FP64 Householder QR and the FP64 Jacobi eigensolver
+ * in global memory (correct, but one CTA does O(k^3) FP64 work per mode, i.e.
+ * milliseconds at k ~ 150).  The same limits hold for the other
+ * decompositions, tucker_orth, tucker_orth_sketches and tucker_sthosvd. */
 TK_API tk_status tucker_rhkron(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
                         const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err);
 

@@ -240,7 +240,10 @@ static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<in
         kmax = std::max<int>(kmax, (int)k[b]);
         kd.k[b] = (int)k[b];
     }
-    TK_REQUIRE(kmax <= 112, TK_ERR_SHAPE, "orth: sketch width above 112 is not supported");
+    TK_REQUIRE(kmax <= 256, TK_ERR_SHAPE, "orth: sketch width above 256 is not supported");
+    // Beyond 112 columns the one-CTA CholeskyQR2 kernels do not fit: Householder QR (FP64) for the batch.
+    const bool wide = kmax > 112;
+    const bool house_only = wide || c.qr_method == 1;
     int* bad = c.alloc<int>(2 * B);  // [0, B): any breakdown, [B, 2B): pass-2 breakdown
     double* W = c.alloc<double>((int64_t)B * kmax * kmax);
     double* Rinv = c.alloc<double>((int64_t)B * kmax * kmax);
@@ -250,10 +253,10 @@ static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<in
         Hsrc[b] = c.alloc<double>(n[b] * k[b]);
         Htau[b] = c.alloc<double>(k[b]);
     }
-    launch_fill_int(c, bad, 2 * B, c.qr_method == 1 ? 1 : 0);
+    launch_fill_int(c, bad, 2 * B, house_only ? 1 : 0);
     bool df = true;
     for (int b = 0; b < B; ++b) df = df && Y[b].dt == TK_F32;
-    if (c.qr_method != 1) {
+    if (!house_only) {
         // pass 1: W = Y^T Y, R1^{-1}, Q1 = Y R1^{-1}
         c.fork(B, [&](int b) {
             const View2& A = Y[b];
@@ -288,11 +291,11 @@ static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<in
         }
     }
     c.fork(B, [&](int b) {
-        if (c.qr_method != 2) {
+        if (c.qr_method != 2 || wide) {
             launch_copy_unfold_to_matrix(c, Y[b], n[b], k[b], Hsrc[b], bad + b);
             launch_householder(c, n[b], k[b], Hsrc[b], Q[b], Htau[b], bad + b);
         }
-        if (slots[b] >= 0) launch_qr_info(c, c.dqr + slots[b], bad + b, c.qr_method == 2 ? 3 : 1);
+        if (slots[b] >= 0) launch_qr_info(c, c.dqr + slots[b], bad + b, (c.qr_method == 2 && !wide) ? 3 : 1);
     });
 }
 
@@ -315,7 +318,8 @@ void orth_matrix(Ctx& c, const Mat& y, const Mat& q) {
 
 // Leading r eigenvectors of the symmetric k x k FP64 matrix A, as the columns
 // of Vr (k x r, ld k), in descending eigenvalue order.
-//  * FP64 data: cyclic Jacobi entirely in FP64.
+//  * FP64 data, and any k above 112 (beyond the shared-memory kernels): cyclic
+//    Jacobi entirely in FP64.
 //  * otherwise: a two-stage scheme built for a chip whose FP64 rate is a small
 //    fraction of its FP32 rate.  Stage 1, mixed Jacobi on A (FP32 accuracy),
 //    gives V0; one FP64 Newton-Schulz step V0 <- V0 (3I - V0^T V0) / 2 makes it
@@ -372,7 +376,8 @@ static void eig_resolve(Ctx& c, int64_t k, const double* A, const double* V1, in
 
 // Leading r eigenvectors of the symmetric k x k FP64 matrix A, as the columns
 // of Vr (k x r, ld k), in descending eigenvalue order.
-//  * FP64 data: cyclic Jacobi entirely in FP64.
+//  * FP64 data, and any k above 112 (beyond the shared-memory kernels): cyclic
+//    Jacobi entirely in FP64.
 //  * otherwise: a two-stage scheme built for a chip whose FP64 rate is a small
 //    fraction of its FP32 rate (eig_seed, then eig_resolve).  (A is the Gram
 //    of a core computed from FP32-class data, whose entries carry relative
@@ -384,8 +389,9 @@ static void eig_top(Ctx& c, int64_t k, const double* A, int64_t r, double* Vr, b
         double* Ac = c.alloc<double>(k * k);
         double* w = c.alloc<double>(k);
         double* Vf = c.alloc<double>(k * k);
+        double* gV = k > 112 ? c.alloc<double>(k * k) : nullptr;  // beyond shared memory: the global-memory variant
         launch_convert(c, A, TK_F64, k * k, 1, k * k, Ac, TK_F64, k * k, 1.f);
-        launch_jacobi(c, k, Ac, w, Vf, c.max_sweeps);
+        launch_jacobi(c, k, Ac, w, Vf, c.max_sweeps, gV);
         launch_convert(c, Vf, TK_F64, k, r, k, Vr, TK_F64, k, 1.f);
         return;
     }
@@ -407,11 +413,12 @@ static Tens sthosvd_core(Ctx& c, const Tens& G0, const int64_t* r, const std::ve
     const int d = G0.d;
     V.assign(d, nullptr);
     for (int j = 0; j < d; ++j)
-        TK_REQUIRE(G0.n[j] <= 112, TK_ERR_SHAPE, "sthosvd: core mode above 112 is not supported");
+        TK_REQUIRE(G0.n[j] <= 256, TK_ERR_SHAPE, "sthosvd: core mode above 256 is not supported");
     std::vector<double*> C0(d, nullptr), V1(d, nullptr);
     if (!fp64_path) {
         c.fork(d, [&](int j) {
             const int64_t kj = G0.n[j];
+            if (kj > 112) return;  // solved in FP64 below
             const int64_t K = kj ? G0.numel() / kj : 0;
             C0[j] = c.alloc<double>(kj * kj);
             const View2 A = view_unfold_rows(G0, j);
@@ -423,7 +430,7 @@ static Tens sthosvd_core(Ctx& c, const Tens& G0, const int64_t* r, const std::ve
         int64_t kj = G.n[j];
         int64_t K = kj ? G.numel() / kj : 0;
         double* Vj = c.alloc<double>(kj * r[j]);
-        if (fp64_path) {
+        if (fp64_path || kj > 112) {
             double* C = c.alloc<double>(kj * kj);
             View2 A = view_unfold_rows(G, j);
             gemm_nt_f64(c, kj, kj, K, A, A, 1.0, 0.0, C, kj);
@@ -1178,7 +1185,7 @@ tk_status tucker_orth_sketches(tk_handle* h, int d, const tk_tensor* Y, tk_matri
         for (int n = 0; n < d; ++n) {
             const int64_t nn = Yt[n].n[n], cols = nn ? Yt[n].numel() / nn : 0, k = std::min(nn, cols);
             TK_REQUIRE(nn >= 1 && cols >= 1, TK_ERR_SHAPE, "orth_sketches: empty sketch");
-            TK_REQUIRE(k <= 112, TK_ERR_SHAPE, "orth_sketches: sketch width above 112 is not supported");
+            TK_REQUIRE(k <= 256, TK_ERR_SHAPE, "orth_sketches: sketch width above 256 is not supported");
             Qm[n] = mat_in(&Q[n], "Q");
             TK_REQUIRE(Qm[n].rows == nn && Qm[n].cols == k, TK_ERR_SHAPE, "orth_sketches: Q[n] must be n_n x k_n");
             TK_REQUIRE(Qm[n].dt == TK_F64 || Qm[n].dt == TK_F32, TK_ERR_DTYPE, "orth_sketches: Q must be F64/F32");

@@ -356,8 +356,10 @@ void launch_apply_rinv_df(const Ctx& c, int batch, const View2* Y, const int64_t
 void launch_householder(const Ctx& c, int64_t n, int64_t k, double* A, double* Q, double* tau, const int* run);
 
 // Jacobi eigensolver (one CTA per matrix): A (k x k FP64 symmetric, destroyed),
-// eigenvalues descending in w, eigenvectors as columns of V (ld k).
-void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int max_sweeps);
+// eigenvalues descending in w, eigenvectors as columns of V (ld k).  k <= 112
+// works in shared memory; 112 < k <= 256 in global memory, with gV (k x k
+// doubles of scratch) required.
+void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int max_sweeps, double* gV = nullptr);
 
 // Mixed-precision Jacobi (FP64 diagonal, FP32 off-diagonal and rotations) on the
 // symmetric k x k FP64 matrix A (ld k): eigenvalue estimates in D (unsorted),

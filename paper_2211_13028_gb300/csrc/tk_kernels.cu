@@ -1439,16 +1439,17 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int k, double* Ag, double* 
     }
 }
 
-void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int max_sweeps) {
+void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int max_sweeps, double* gV) {
     if (!c.exec) return;
     TK_REQUIRE(k <= 256, TK_ERR_SHAPE, "jacobi: at most 256 rows");
     int use_smem = k <= 112;
     size_t smem = use_smem ? 2 * sizeof(double) * k * k : 0;
-    TK_REQUIRE(use_smem, TK_ERR_SHAPE, "jacobi: core mode above 112 needs the global-memory variant");
+    TK_REQUIRE(use_smem || gV, TK_ERR_SHAPE, "jacobi: above 112 rows the global-memory variant needs k x k scratch");
     if (smem > 48 * 1024)
         TK_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(c, "jacobi", 24.0 * k * k, 9.0 * k * k * k * 8);
-    jacobi_kernel<<<1, 256, smem, c.stream>>>((int)k, A, w, V, max_sweeps, use_smem, nullptr, c.dflags);
+    jacobi_kernel<<<1, 256, smem, c.stream>>>((int)k, A, w, V, max_sweeps, use_smem, use_smem ? nullptr : gV,
+                                              c.dflags);
     c.counted();
     c.check_launch();
 }

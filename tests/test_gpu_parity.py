@@ -416,3 +416,19 @@ def test_empty_dimension_is_rejected_before_launch(dev):
     with pytest.raises(T.TuckerError):
         T.tucker_rhkron(x, (1, 1, 1), 1, oms)
     assert T.tk_launch_count(dev) == l0
+
+
+# ------------------------------------------------------------------ sketch widths above the one-CTA kernels
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rhkron_sketch_widths_above_112(dev, dtype):
+    # widths 156, 143 and 132: the Householder QR and the FP64 Jacobi in global memory take over
+    dims, r, p = (200, 180, 170), (10, 9, 8), 5
+    x = synth.tucker_tensor(dims, (12, 12, 12), seed=41, noise_rel=1e-3)
+    X, xv, sc = make_X(x, dtype, dev)
+    oms = synth.sketch_factors_reuse(dims, (11, 12, 13), seed=42, dtype="f64" if dtype == "f64" else "f32")
+    G, U, err = T.tucker_rhkron(X, r, p, mats(oms, "f64" if dtype == "f64" else "f32", dev), scale=sc)
+    st, info = T.tk_sync_status(dev)
+    assert st == 0 and info[:3] == [1, 1, 1]  # Householder QR for the wide sketches
+    ref = O.rhkron(xv, r, oms)
+    _check_decomp(G, U, err, ref, xv, TOL[dtype])
