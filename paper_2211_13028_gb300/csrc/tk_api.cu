@@ -118,8 +118,10 @@ static Opts opts_in(const tk_opts* o, int d) {
 
 // ------------------------------------------------------------------ small helpers
 
-// Copy of a matrix into the accumulation dtype, contiguous (ld = rows).
+// The matrix in the accumulation dtype, contiguous (ld = rows): the matrix
+// itself when it already is, else a converted copy (the factors are read only).
 static Mat mat_to(Ctx& c, const Mat& M, tk_dtype dt) {
+    if (M.dt == dt && (M.ld == M.rows || M.cols <= 1)) return M;  // already what the consumers read
     Mat o;
     o.dt = dt;
     o.rows = M.rows;
@@ -291,11 +293,11 @@ static void orth_batch(Ctx& c, const std::vector<View2>& Y, const std::vector<in
         }
     }
     c.fork(B, [&](int b) {
-        if (c.qr_method != 2 || wide) {
-            launch_copy_unfold_to_matrix(c, Y[b], n[b], k[b], Hsrc[b], bad + b);
-            launch_householder(c, n[b], k[b], Hsrc[b], Q[b], Htau[b], bad + b);
-        }
-        if (slots[b] >= 0) launch_qr_info(c, c.dqr + slots[b], bad + b, (c.qr_method == 2 && !wide) ? 3 : 1);
+        int* slot = slots[b] >= 0 ? c.dqr + slots[b] : nullptr;
+        if (c.qr_method != 2 || wide)  // the fallback copies Y itself and records the method taken
+            launch_householder(c, n[b], k[b], Y[b], Hsrc[b], Q[b], Htau[b], bad + b, slot, 1);
+        else if (slot)
+            launch_qr_info(c, slot, bad + b, 3);
     });
 }
 
@@ -1576,7 +1578,9 @@ tk_status tucker_rsthkron(tk_handle* h, const tk_tensor* X, const int64_t* r, in
                 qm.rows = Xt.n[j];
                 qm.cols = k[j];
                 qm.ld = Xt.n[j];
-                Mat qa = acc == TK_F64 ? qm : mat_to(c, qm, acc);
+                // the tensor-core TTM splits an FP64 factor into TF32 parts itself: no FP32 copy needed
+                const bool tc64 = c.use_tc && !ttm_narrow_eligible(Gh, j, k[j], acc) && ttm_tc_eligible(Gh, j, k[j], acc);
+                Mat qa = (acc == TK_F64 || tc64) ? qm : mat_to(c, qm, acc);
                 Gh = ttm_to(c, Gh, j, qa, false, acc);
             } else {
                 launch_fill_identity(c, Qd[j], Xt.n[j]);

@@ -351,9 +351,12 @@ void launch_apply_rinv(const Ctx& c, int64_t n, int64_t k, const View2& Y, const
 void launch_apply_rinv_df(const Ctx& c, int batch, const View2* Y, const int64_t* n, const int64_t* k,
                           const double* Rinv, int64_t kmax, double* const* Q, const int* bad);
 
-// Householder thin QR of Y (n x k, FP64 copy in A, ld n) producing Q with R_ii >= 0,
-// run only when *run != 0.  One CTA.  tau: k doubles scratch.
-void launch_householder(const Ctx& c, int64_t n, int64_t k, double* A, double* Q, double* tau, const int* run);
+// Householder thin QR of Y (View2, n x k; copied to FP64 scratch A, ld n) producing Q with
+// R_ii >= 0, run only when *run != 0 (run may be NULL = always).  One CTA.  tau: k doubles
+// scratch.  When slot is given, *slot = slot_value if the QR runs, else 0 (the QR method a
+// matrix of a batch took).
+void launch_householder(const Ctx& c, int64_t n, int64_t k, const View2& Y, double* A, double* Q, double* tau,
+                        const int* run, int* slot = nullptr, int slot_value = 1);
 
 // Jacobi eigensolver (one CTA per matrix): A (k x k FP64 symmetric, destroyed),
 // eigenvalues descending in w, eigenvectors as columns of V (ld k).  k <= 112

@@ -1244,12 +1244,16 @@ void launch_apply_rinv_df(const Ctx& c, int batch, const View2* Y, const int64_t
 
 // ------------------------------------------------------------------ Householder QR (fallback)
 
-__global__ void __launch_bounds__(256) householder_kernel(int64_t n, int64_t k, double* A, double* Q, double* tau,
-                                                          const int* run) {
+__global__ void __launch_bounds__(256) householder_kernel(int64_t n, int64_t k, View2 Y, double* A, double* Q,
+                                                          double* tau, const int* run, int* slot, int slot_value) {
     __shared__ double red[33];
     __shared__ double v0s[256];
-    if (run && !*run) return;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const bool go = !run || *run;
+    if (slot && tid == 0) *slot = go ? slot_value : 0;  // the QR method this matrix took
+    if (!go) return;
+    for (int64_t idx = tid; idx < n * k; idx += nt) A[idx] = v2ld(Y, idx % n, idx / n);  // FP64 copy of Y
+    __syncthreads();
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     for (int64_t j = 0; j < k; ++j) {
         double* aj = A + n * j;
@@ -1316,11 +1320,12 @@ __global__ void __launch_bounds__(256) householder_kernel(int64_t n, int64_t k, 
     }
 }
 
-void launch_householder(const Ctx& c, int64_t n, int64_t k, double* A, double* Q, double* tau, const int* run) {
+void launch_householder(const Ctx& c, int64_t n, int64_t k, const View2& Y, double* A, double* Q, double* tau,
+                        const int* run, int* slot, int slot_value) {
     if (!c.exec) return;
     TK_REQUIRE(k <= 256, TK_ERR_SHAPE, "householder: at most 256 columns");
     ProfScope ps(c, "householder", 16.0 * n * k, 8.0 * n * k * k);
-    householder_kernel<<<1, 256, 0, c.stream>>>(n, k, A, Q, tau, run);
+    householder_kernel<<<1, 256, 0, c.stream>>>(n, k, Y, A, Q, tau, run, slot, slot_value);
     c.counted();
     c.check_launch();
 }
