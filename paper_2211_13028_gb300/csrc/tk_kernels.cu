@@ -1332,6 +1332,21 @@ void launch_householder(const Ctx& c, int64_t n, int64_t k, const View2& Y, doub
 
 // ------------------------------------------------------------------ Jacobi eigensolver
 
+// 1 / sqrt(a) and 1 / a for a positive double inside FP32's range: an FP32
+// seed (~2^-22) and two Newton steps in FP64 (quadratic: ~2^-88, i.e. FP64
+// rounding), FMAs only.
+__device__ __forceinline__ double jac_rsqrt(double a) {
+    double y = (double)rsqrtf((float)a);
+    const double h = 0.5 * a;
+    y = y * fma(-h * y, y, 1.5);
+    return y * fma(-h * y, y, 1.5);
+}
+__device__ __forceinline__ double jac_rcp(double a) {
+    double y = (double)__frcp_rn((float)a);
+    y = fma(y, fma(-a, y, 1.0), y);
+    return fma(y, fma(-a, y, 1.0), y);
+}
+
 __global__ void __launch_bounds__(256) jacobi_kernel(int k, double* Ag, double* w, double* Vout, int max_sweeps,
                                                      int use_smem, double* gV, unsigned* flags) {
     extern __shared__ double sm[];
@@ -1350,7 +1365,15 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int k, double* Ag, double* 
     __shared__ double red[33];
     double part = 0.0;
     for (int e = tid; e < k * k; e += nt) part += A[e] * A[e];
-    const double athr = 4.0 * eps * sqrt(block_sum(part, red));  // absolute off-diagonal threshold
+    const double fro = sqrt(block_sum(part, red));
+    // scale by a power of two to ||A||_F in [0.5, 1) (exact), so that the rotation's reciprocal and
+    // reciprocal square roots can start from FP32 seeds (the eigenvalues are scaled back at the end)
+    int ex = 0;
+    if (fro > 0.0 && fro < 1e300) frexp(fro, &ex);
+    const double dsc = ldexp(1.0, -ex), usc = ldexp(1.0, ex);
+    for (int e = tid; e < k * k; e += nt) A[e] *= dsc;
+    __syncthreads();
+    const double athr = 4.0 * eps * fro * dsc;  // absolute off-diagonal threshold
     bool converged = (k <= 1);
     for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
         int off = 0;
@@ -1380,9 +1403,16 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int k, double* Ag, double* 
                 if (q < k) {
                     double app = A[p + k * p], aqq = A[q + k * q], apq = A[p + k * q];
                     if (fabs(apq) > athr) {
-                        double tau = (aqq - app) / (2.0 * apq);
-                        double t1 = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
-                        c = 1.0 / hypot(1.0, t1);
+                        // t = sgn(phi) psi / (|phi| + rho), phi = a_qq - a_pp, psi = 2 a_pq,
+                        // rho = sqrt(phi^2 + psi^2): the smaller root of t^2 + 2 t phi / psi - 1 = 0;
+                        // c = 1 / sqrt(1 + t^2), s = t c.  Reciprocal and reciprocal square roots from
+                        // FP32 seeds and FP64 Newton steps (FMAs only; entries are O(1) after scaling
+                        // and rotated pairs have psi > 4 eps ||A||, so the seeds stay in FP32 range).
+                        const double phi = aqq - app, psi = 2.0 * apq;
+                        const double r2 = fma(phi, phi, psi * psi);
+                        const double u = jac_rsqrt(r2);                  // 1 / rho
+                        const double t1 = (phi >= 0.0 ? psi : -psi) * jac_rcp(fabs(phi) + r2 * u);
+                        c = jac_rsqrt(fma(t1, t1, 1.0));
                         s = t1 * c;
                     }
                 } else {
@@ -1439,7 +1469,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int k, double* Ag, double* 
             double wj = A[j2 + k * j2];
             rank += (wj > wi) || (wj == wi && j2 < i);
         }
-        w[rank] = wi;
+        w[rank] = wi * usc;
         for (int row = 0; row < k; ++row) Vout[row + k * rank] = V[row + k * i];
     }
 }
