@@ -415,10 +415,17 @@ TK_API tk_status tucker_loss(tk_handle* h, const tk_tensor* X, const tk_tensor* 
  * The products R x_{j!=n} U_j^T for all n reuse the sketch dimension tree.
  * dG: like G; dU: d matrices like U; dX: like X.  Each output may be NULL
  * (not computed; dU is all d matrices or NULL), so the dX pass and the dG / dU
- * part can be queued separately, e.g. on two streams.  At least one output
- * must be given (TK_ERR_ARG otherwise). */
+ * part can be queued separately, e.g. on two streams.
+ * norms2: DEVICE pointer to 2 doubles (8-byte aligned), or NULL: receives
+ * ||R||^2 and ||X||^2, summed in FP64 from the same residual tiles that dX is
+ * formed from (one pass over X serves both), written in stream order with no
+ * synchronisation; sqrt(norms2[0] / norms2[1]) is the relative error of
+ * (G, U), the value tucker_rhkron returns for its own outputs.  With norms2
+ * and no dX the residual pass runs for the norms alone.
+ * At least one output must be given (TK_ERR_ARG otherwise). */
 TK_API tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk_tensor* G, const tk_matrix* U,
-                                      double grad_scale, tk_tensor* dG, tk_matrix* dU, tk_tensor* dX);
+                                      double grad_scale, tk_tensor* dG, tk_matrix* dU, tk_tensor* dX,
+                                      double* norms2);
 
 #ifdef __cplusplus
 }

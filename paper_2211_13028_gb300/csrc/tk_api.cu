@@ -1674,7 +1674,8 @@ tk_status tucker_loss(tk_handle* h, const tk_tensor* X, const tk_tensor* G, cons
 }
 
 tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk_tensor* G, const tk_matrix* U,
-                                      double grad_scale, tk_tensor* dG, tk_matrix* dU, tk_tensor* dX) {
+                                      double grad_scale, tk_tensor* dG, tk_matrix* dU, tk_tensor* dX,
+                                      double* norms2) {
     return run_call(h, [&](Ctx& c) {
         Tens Xt = tens_in(X, "X");
         c.xdata = Xt.p;
@@ -1687,7 +1688,8 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
         check_tucker(Gt, U, Um, n);
         TK_REQUIRE(Xt.d == Gt.d && d >= 2, TK_ERR_SHAPE, "backward: X and G must have the same d >= 2");
         for (int j = 0; j < d; ++j) TK_REQUIRE(Xt.n[j] == n[j], TK_ERR_SHAPE, "backward: X dims != U rows");
-        TK_REQUIRE(dG || dU || dX, TK_ERR_ARG, "backward: no output requested");
+        TK_REQUIRE(dG || dU || dX || norms2, TK_ERR_ARG, "backward: no output requested");
+        TK_REQUIRE(((uintptr_t)norms2 & 7) == 0, TK_ERR_ARG, "backward: norms2 must be 8-byte aligned");
         Tens dGt;
         if (dG) {
             dGt = tens_in(dG, "dG");
@@ -1720,10 +1722,14 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
         const double s2 = -2.0 * grad_scale;
         std::vector<Mat> Ua(d);
         for (int j = 0; j < d; ++j) Ua[j] = Um[j].dt == acc ? Um[j] : mat_to(c, Um[j], acc);
-        if (!dG && !dU) {  // dX only: one fused residual pass
+        // dX and the norms come from one fused residual pass
+        auto residual = [&]() {
             Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
-            double* nrm = c.alloc<double>(2);
-            residual_pass(c, Xt, Ga, Ua, acc, nrm, dXt.p, dXt.dt, 2.0 * grad_scale);
+            double* nrm = norms2 ? norms2 : c.alloc<double>(2);
+            residual_pass(c, Xt, Ga, Ua, acc, nrm, dX ? dXt.p : nullptr, dX ? dXt.dt : TK_F32, 2.0 * grad_scale);
+        };
+        if (!dG && !dU) {
+            residual();
             return;
         }
         std::vector<Tens> S(d);
@@ -1771,11 +1777,7 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
             gemm_nt_f64(c, nj, rj, rj, view_rows(U64[j], TK_F64, nj), view_cols(B1, TK_F64, rj), -s2, 1.0, A1, nj);
             launch_convert(c, A1, TK_F64, nj, rj, nj, (void*)dUm[j].p, dUm[j].dt, dUm[j].ld, 1.f);
         });
-        if (dX) {
-            Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
-            double* nrm = c.alloc<double>(2);
-            residual_pass(c, Xt, Ga, Ua, acc, nrm, dXt.p, dXt.dt, 2.0 * grad_scale);
-        }
+        if (dX || norms2) residual();
     });
 }
 

@@ -141,7 +141,7 @@ def load():
                                   P(ctypes.c_double)], ctypes.c_int),
             "tucker_loss": ([vp, P(TkTensor), P(TkTensor), P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
             "tucker_reconstruct_backward": ([vp, P(TkTensor), P(TkTensor), P(TkMatrix), ctypes.c_double, P(TkTensor),
-                                             P(TkMatrix), P(TkTensor)], ctypes.c_int),
+                                             P(TkMatrix), P(TkTensor), vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -670,16 +670,23 @@ def tucker_loss(X: torch.Tensor, G: torch.Tensor, U: Sequence[torch.Tensor], sca
 
 
 def tucker_reconstruct_backward(X: torch.Tensor, G: torch.Tensor, U: Sequence[torch.Tensor], grad_scale: float = 1.0,
-                                need_dX: bool = True, scale: float = 1.0, need_dG: bool = True, need_dU: bool = True):
-    """Gradients of grad_scale * ||X - G x_j U_j||^2: returns (dG, [dU_j], dX), each None when not requested."""
+                                need_dX: bool = True, scale: float = 1.0, need_dG: bool = True, need_dU: bool = True,
+                                norms2: Optional[torch.Tensor] = None):
+    """Gradients of grad_scale * ||X - G x_j U_j||^2: returns (dG, [dU_j], dX), each None when not requested.
+    ``norms2``: an optional float64 device tensor of 2 elements that receives ||X - G x_j U_j||^2 and ||X||^2
+    from the residual pass (stream-ordered, no synchronisation)."""
     dG = empty_f(list(G.shape), G.dtype, G.device) if need_dG else None
     dU = [_colmajor_matrix(int(u.shape[0]), int(u.shape[1]), u.dtype, u.device) for u in U] if need_dU else None
     dX = empty_f(list(X.shape), X.dtype, X.device) if need_dX else None
+    if norms2 is not None and (norms2.dtype != torch.float64 or norms2.numel() < 2 or not norms2.is_contiguous()
+                               or norms2.device != X.device):
+        raise TuckerError(1, "norms2 must be a contiguous float64 tensor of 2 elements on X's device")
     h = _handle(X.device)
     _check(load().tucker_reconstruct_backward(h, ctypes.byref(_tensor(X, scale)), ctypes.byref(_tensor(G)), _mats(U),
                                               float(grad_scale), ctypes.byref(_tensor(dG)) if need_dG else None,
                                               _mats(dU) if need_dU else None,
-                                              ctypes.byref(_tensor(dX)) if need_dX else None), h)
+                                              ctypes.byref(_tensor(dX)) if need_dX else None,
+                                              norms2.data_ptr() if norms2 is not None else None), h)
     return dG, dU, dX
 
 

@@ -13,7 +13,7 @@ import torch
 import oracle as O
 from paper_2211_13028_gb300 import synth
 from paper_2211_13028_gb300 import tucker as T
-from tests.gpu_helpers import make_X, mats, require_gpu
+from tests.gpu_helpers import make_X, mats, require_gpu, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -90,3 +90,41 @@ def test_backward_outputs_can_be_requested_separately(dev):
     assert all(torch.equal(a, b) for a, b in zip(dU, dU2))
     with pytest.raises(T.TuckerError):
         T.tucker_reconstruct_backward(Xd, Gd, Ud, 0.5, need_dX=False, need_dG=False, need_dU=False)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_backward_norms_give_the_decompositions_relative_error(dev, dtype):
+    # the residual pass that forms dX also returns ||X - Xhat||^2 and ||X||^2: with the G, U that rHKron-re
+    # returns, their ratio is the relative error the decomposition reports for itself (same residual pass),
+    # and the oracle's for the same G, U
+    dims, r, p = (96, 80, 72), (12, 10, 9), 5
+    core = synth.decaying_core((20, 20, 20), 0.7, seed=43)
+    x = synth.tucker_tensor(dims, (20, 20, 20), seed=44, noise_rel=1e-3, core=core)
+    X, xv, _ = make_X(x, dtype, dev)
+    s = O.subranks_reuse(r, p)[0]
+    om = mats(synth.sketch_factors_reuse(dims, s, seed=45, dtype=dtype), dtype, dev)
+    G, U, err = T.tucker_rhkron(X, r, p, om)
+    G2, U2, none = T.tucker_rhkron(X, r, p, om, rel_err=False)
+    assert none is None and torch.equal(G, G2) and all(torch.equal(a, b) for a, b in zip(U, U2))
+    ref = O.rel_err(xv, to_np(G), [to_np(u) for u in U])
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    outs = {}
+    for need_dx, need_dgu in ((True, False), (False, False), (True, True), (False, True)):
+        n2 = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
+        dG, dU, dX = T.tucker_reconstruct_backward(X, G, U, 0.5, need_dX=need_dx, need_dG=need_dgu,
+                                                   need_dU=need_dgu, norms2=n2)
+        a, b = n2.cpu().tolist()
+        # FP32 data: the fused pass sums short runs of squares in FP32 before adding them in FP64
+        assert abs(b - np.sum(xv ** 2)) <= tol * np.sum(xv ** 2)
+        e = np.sqrt(a / b)
+        assert abs(e - ref) <= tol * max(ref, 1.0), (need_dx, need_dgu, e, ref)
+        outs[(need_dx, need_dgu)] = e
+        if need_dx:
+            r_ref = O.reconstruct(to_np(G), [to_np(u) for u in U]) - xv
+            assert np.max(np.abs(to_np(dX) + r_ref)) <= tol * np.max(np.abs(xv)) * 10
+    # one residual pass whichever other outputs are requested (the sums' order may differ between the
+    # fused kernel's norm-only and dX-writing forms)
+    vals = list(outs.values()) + [err]
+    assert max(vals) - min(vals) <= 1e-12 * max(vals)
+    with pytest.raises(T.TuckerError):  # wrong dtype
+        T.tucker_reconstruct_backward(X, G, U, 0.5, norms2=torch.zeros(2, dtype=torch.float32, device=dev))
