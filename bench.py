@@ -11,7 +11,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -75,14 +74,6 @@ def init_ranks(world: int):
 def barrier(dist) -> None:
     if dist is not None:
         dist.barrier()
-
-
-def _rel_err(v) -> float:
-    """A relative error held as a pending host scalar (.value) or as the device norms (||R||^2, ||X||^2)."""
-    if hasattr(v, "value"):
-        return float(v.value)
-    n = v.detach().cpu().tolist()
-    return math.sqrt(n[0] / n[1]) if n[1] > 0 else 0.0
 
 
 def max_over_ranks(x: float, dist) -> float:
@@ -795,32 +786,18 @@ def main():
                 marks[0].record(sa)
             # fresh Gaussian sketch factors on the device (Philox4x32-10), as each decomposition draws them
             om = T.gaussian_factors(dims, s, SEED + 1, torch.float32, dev)
-            # rHKron-re's relative error comes from the residual pass that forms dX below (the same
-            # ||X - G x_j U_j|| / ||X|| of the returned G, U): X is streamed once for both
-            G1, U1, _ = T.tucker_rhkron(Xin, r, p, om, rel_err=False)
-            e1 = torch.empty(2, dtype=torch.float64, device=dev)
-            done_rh = torch.cuda.Event()
-            done_rh.record(sa)
+            # rHKron-re and the loss gradient (dG, dU, dX) at its result in one call: the gradient's
+            # products come from the core's chain of TTMs and the relative error from the dX pass
+            G1, U1, e1, dG, dU, dX = T.tucker_rhkron_grad(Xin, r, p, om, 1.0, async_outputs=True)
             if marks:
                 marks[1].record(sa)
-            dG, dU, _ = T.tucker_reconstruct_backward(Xin, G1, U1, 1.0, need_dX=False)
-            if marks:
-                marks[2].record(sa)
         with torch.cuda.stream(sb):
             if marks:
-                marks[3].record(sb)
+                marks[2].record(sb)
             oms = T.gaussian_factors_matrix(dims, S, k, [0, 1, 2], SEED + 2, torch.float32, dev)
             G2, U2, e2 = T.tucker_rsthkron(Xin, r, p, oms, async_outputs=True)
             if marks:
-                marks[4].record(sb)
-            # the dX part of the gradient (one fused residual pass) only needs rHKron-re's result
-            sb.wait_event(done_rh)
-            for t in [G1, *U1]:
-                t.record_stream(sb)
-            e1.record_stream(sb)
-            _, _, dX = T.tucker_reconstruct_backward(Xin, G1, U1, 1.0, need_dG=False, need_dU=False, norms2=e1)
-            if marks:
-                marks[5].record(sb)
+                marks[3].record(sb)
         if sa is not main_s:
             main_s.wait_stream(sa)
             main_s.wait_stream(sb)
@@ -829,12 +806,12 @@ def main():
     for _ in range(args.warmup):
         out = step(X)
     torch.cuda.synchronize()
-    errs = (_rel_err(out[2]), out[5].value)
+    errs = (out[2].value, out[5].value)
     dev_status, qr_info = T.tk_sync_status(dev)  # 0: every Jacobi solve converged
 
 
     # ---- device-timed region (inputs resident in HBM; X = 512 MiB > L2)
-    marks = [[ev() for _ in range(6)] for _ in range(args.steps)]
+    marks = [[ev() for _ in range(4)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -880,12 +857,12 @@ def main():
         g1.record()
         torch.cuda.synchronize()
         graph_ms = g0.elapsed_time(g1) / args.steps
-        graph_errs = (_rel_err(gX.outputs[2]), gX.outputs[5].value)
+        graph_errs = (gX.outputs[2].value, gX.outputs[5].value)
         del gX
     barrier(dist)
     clk = clocks.stop()
     ph = [sum(marks[i][a].elapsed_time(marks[i][b]) for i in range(args.steps)) / args.steps
-          for a, b in ((0, 1), (3, 4), (1, 2), (4, 5))]
+          for a, b in ((0, 1), (2, 3))]
     ms = max_over_ranks(ms, dist)
     if graph_ms is not None:
         graph_ms = max_over_ranks(graph_ms, dist)
@@ -927,13 +904,12 @@ def main():
         else:
             out = step(Xd[b].permute(2, 1, 0))
         consumed[b].record(main_s)
-        host = [t.detach().to("cpu", non_blocking=True)
-                for t in [out[0], *out[1], out[3], *out[4], out[6], *out[7], out[2]]]
-        hosts.append((host, out[5]))
-        res_bytes = sum(t.numel() * t.element_size() for t in host) + 8  # dX stays on the device
+        host = [t.detach().to("cpu", non_blocking=True) for t in [out[0], *out[1], out[3], *out[4], out[6], *out[7]]]
+        hosts.append((host, out[2], out[5]))
+        res_bytes = sum(t.numel() * t.element_size() for t in host) + 16  # dX stays on the device
     e1.record()
     torch.cuda.synchronize()
-    assert all(np.isfinite(_rel_err(h[0][-1])) and np.isfinite(h[1].value) for h in hosts)
+    assert all(np.isfinite(h[1].value) and np.isfinite(h[2].value) for h in hosts)
     e2e_ms = e0.elapsed_time(e1) / args.steps
     e2e_ms = max_over_ranks(e2e_ms, dist)
 
@@ -965,17 +941,20 @@ def main():
         config=dict(workload=WORKLOAD, l2="X is 512 MiB, larger than the 129 MB L2: no flush between steps",
                     parallelism=("replicas" if world > 1 else "single GPU"),
                     streams=("one stream" if args.serial else
-                             "rHKron-re + (dG, dU) on one stream, rSTHKron + dX on a second, concurrently"),
-                    residual=("rHKron-re's relative error comes from the norms of the residual pass that forms dX "
-                              "(same G, U, same formula); rSTHKron computes its own"),
+                             "rHKron-re + its loss gradient (dG, dU, dX) on one stream, rSTHKron on a second, "
+                             "concurrently"),
+                    gradient=("rHKron-re and the gradient at its result in one call (tucker_rhkron_grad): the "
+                              "gradient's products R x_{j!=n} U_j^T come from the core's chain of TTMs (one X "
+                              "pass instead of two), and rHKron-re's relative error from the norms of the pass "
+                              "that forms dX; rSTHKron computes its own"),
                     launch=("the step recorded once into a CUDA graph (both streams), replayed every step"
                             if graph_ms is not None else "eager launches")),
         eager_ms_per_step=ms,
         graph_ms_per_step=graph_ms,
         graph_rel_err=(dict(rhkron=graph_errs[0], rsthkron=graph_errs[1]) if graph_errs else None),
-        phases_ms=dict(rhkron=ph[0], rsthkron=ph[1], backward_dG_dU=ph[2], backward_dX=ph[3],
+        phases_ms=dict(rhkron_and_gradient=ph[0], rsthkron=ph[1],
                        note=("sequential" if args.serial else
-                             "stream 1: rHKron-re then dG, dU; stream 2: rSTHKron then dX (after rHKron-re); "
+                             "stream 1: rHKron-re with the loss gradient (one call); stream 2: rSTHKron; "
                              "from the eager timed steps")),
         rel_err=dict(rhkron=errs[0], rsthkron=errs[1]),
         device_status=dev_status,

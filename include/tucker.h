@@ -427,6 +427,23 @@ TK_API tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, c
                                       double grad_scale, tk_tensor* dG, tk_matrix* dU, tk_tensor* dX,
                                       double* norms2);
 
+/* Algorithm rHKron-re followed by the gradient of grad_scale * ||X - G x_j U_j||^2
+ * at its result, in one call that shares the passes over X (no counterpart in
+ * the paper, which has no loss gradient; the same values as tucker_rhkron
+ * followed by tucker_reconstruct_backward).  The core
+ * Ghat = X x_{m_1} Q_{m_1}^T x_{m_2} Q_{m_2}^T .. is formed one mode at a time;
+ * with U_j = Q_j V_j, each product R x_{j!=n} U_j^T of the gradient is read
+ * from the last product of that chain in which mode n is still whole (so only
+ * the mode applied first streams X again), and the relative error comes from
+ * the norms of the pass that forms dX.  Arguments as tucker_rhkron and
+ * tucker_reconstruct_backward; G and U receive the decomposition, rel_err
+ * (host, may be NULL) its relative error, dG, dU, dX (each may be NULL) the
+ * gradient at (G, U) as given to the caller. */
+TK_API tk_status tucker_rhkron_grad(tk_handle* h, const tk_tensor* X, const int64_t* r, int p,
+                                    const tk_matrix* Omega, const tk_opts* opts, tk_tensor* G, tk_matrix* U,
+                                    double* rel_err, double grad_scale, tk_tensor* dG, tk_matrix* dU,
+                                    tk_tensor* dX);
+
 #ifdef __cplusplus
 }
 #endif

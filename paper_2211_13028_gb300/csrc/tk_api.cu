@@ -168,7 +168,7 @@ static Tens ttm_to(Ctx& c, const Tens& T, int j, const Mat& M, bool mtrans, tk_d
 // Apply M_i to every mode in `modes`, cheapest-shrinking mode first (smallest
 // output), the last product written to dst when given.
 static Tens multi_ttm(Ctx& c, const Tens& T, std::vector<int> modes, const Mat* M, bool mtrans, tk_dtype acc,
-                      void* dst = nullptr) {
+                      void* dst = nullptr, std::vector<std::pair<int, Tens>>* trace = nullptr) {
     Tens cur = T;
     while (!modes.empty()) {
         size_t best = 0;
@@ -189,6 +189,7 @@ static Tens multi_ttm(Ctx& c, const Tens& T, std::vector<int> modes, const Mat* 
         int i = modes[best];
         modes.erase(modes.begin() + best);
         cur = ttm_to(c, cur, i, M[i], mtrans, acc, modes.empty() ? dst : nullptr);
+        if (trace) trace->push_back({i, cur});  // the mode just applied and the product so far
     }
     return cur;
 }
@@ -507,7 +508,7 @@ static void residual_pass(Ctx& c, const Tens& X, const Tens& G, const std::vecto
 // into the caller's G and U, optional relative error.
 static void finish(Ctx& c, const Tens& X, const std::vector<double*>& Qd, const std::vector<int64_t>& kdim,
                    Tens Gt, const std::vector<double*>& V, const int64_t* r, const Tens& Gout,
-                   const std::vector<Mat>& Uout, double* err_dev) {
+                   const std::vector<Mat>& Uout, double* err_dev, std::vector<double*>* signs = nullptr) {
     const int d = X.d;
     std::vector<double*> U(d), sg(d);
     c.fork(d, [&](int j) {
@@ -520,6 +521,7 @@ static void finish(Ctx& c, const Tens& X, const std::vector<double*>& Qd, const 
     });
     launch_apply_signs(c, (double*)Gt.p, Gt, sg.data());
     launch_convert(c, Gt.p, TK_F64, Gt.numel(), 1, Gt.numel(), Gout.p, Gout.dt, Gt.numel(), 1.f);
+    if (signs) *signs = sg;
     if (!err_dev) return;
     // ||X - G x_j U_j|| from the returned G and U, in the accumulation dtype.
     tk_dtype acc = acc_of(X.dt);
@@ -1296,9 +1298,17 @@ static void check_outputs(const Tens& X, const int64_t* r, const tk_tensor* G, c
 // only in its sketches): thin QR of each sketch unfolding (Q = I where the
 // sketch is at least as wide as the mode), the core Ghat = X x_j Q_j^T, the FP64
 // STHOSVD of the core, U_j = Q_j V_j, and the relative error into errd.
+// What the gradient of the loss at the result can reuse: the core's chain of
+// products (chain[t] = X x_{modes[0..t]} Q^T, in the order applied), the
+// factors V_j (k_j x r_j, FP64, ld k_j) and the column signs of U_j.
+struct CoreTrace {
+    std::vector<std::pair<int, Tens>> chain;
+    std::vector<double*> V, sg;
+};
+
 static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, const std::vector<int64_t>& k,
                                  const int64_t* r, const Opts& o, const Tens& Gt, const std::vector<Mat>& Um,
-                                 double* errd) {
+                                 double* errd, CoreTrace* tr = nullptr) {
     const int d = Xt.d;
     const tk_dtype acc = acc_of(Xt.dt);
     // 2. thin QR of each sketch unfolding
@@ -1336,12 +1346,13 @@ static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, c
     });
     for (int j = 0; j < d; ++j)
         if (k[j] < Xt.n[j]) cm.push_back(j);
-    Tens Gh = cm.empty() ? Xt : multi_ttm(c, Xt, cm, Qa.data(), false, acc);
+    Tens Gh = cm.empty() ? Xt : multi_ttm(c, Xt, cm, Qa.data(), false, acc, nullptr, tr ? &tr->chain : nullptr);
     Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
     // 4. STHOSVD of the core in FP64, U_j = Q_j V_j, gauge, casts, error
     std::vector<double*> V;
     Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
-    finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, errd);
+    finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, errd, tr ? &tr->sg : nullptr);
+    if (tr) tr->V = V;
 }
 
 extern "C" {
@@ -1673,6 +1684,100 @@ tk_status tucker_loss(tk_handle* h, const tk_tensor* X, const tk_tensor* G, cons
     });
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------ gradient of the loss
+// The gradient outputs, checked against X (dims n) and G.
+struct GradOut {
+    Tens dG, dX;
+    std::vector<Mat> dU;
+};
+
+static GradOut grad_outputs_in(const Tens& Xt, const Tens& Gt, const std::vector<int64_t>& n, tk_tensor* dG,
+                               tk_matrix* dU, tk_tensor* dX) {
+    const int d = Xt.d;
+    GradOut g;
+    if (dG) {
+        g.dG = tens_in(dG, "dG");
+        TK_REQUIRE(g.dG.d == d && (g.dG.dt == TK_F64 || g.dG.dt == TK_F32), TK_ERR_DTYPE,
+                   "backward: dG must be F64/F32");
+        for (int j = 0; j < d; ++j) TK_REQUIRE(g.dG.n[j] == Gt.n[j], TK_ERR_SHAPE, "backward: dG dims != G dims");
+    }
+    g.dU.resize(d);
+    if (dU) {
+        for (int j = 0; j < d; ++j) {
+            g.dU[j] = mat_in(&dU[j], "dU");
+            TK_REQUIRE(g.dU[j].rows == n[j] && g.dU[j].cols == Gt.n[j], TK_ERR_SHAPE,
+                       "backward: dU_j must be n_j x r_j");
+            TK_REQUIRE(g.dU[j].dt == TK_F64 || g.dU[j].dt == TK_F32, TK_ERR_DTYPE, "backward: dU must be F64/F32");
+        }
+    }
+    if (dX) {
+        g.dX = tens_in(dX, "dX");
+        TK_REQUIRE(g.dX.d == d && g.dX.dt == Xt.dt, TK_ERR_DTYPE, "backward: dX must have X's dims and dtype");
+        for (int j = 0; j < d; ++j) TK_REQUIRE(g.dX.n[j] == Xt.n[j], TK_ERR_SHAPE, "backward: dX dims != X dims");
+    }
+    return g;
+}
+
+// dG and dU from S_n = X x_{j!=n} U_j^T (n = 0..d-1).  With R = X - G x_j U_j
+// and C_j = U_j^T U_j:
+//   R x_{j!=n} U_j^T = S_n - G x_n U_n x_{j!=n} C_j,
+// so every product with the residual comes from the S_n plus small core-sized
+// corrections in FP64.  Gt / Um: G and U as given (F64/F32); Ua: U in the
+// accumulation dtype.
+static void grad_from_sketches(Ctx& c, const Tens& Gt, const std::vector<Mat>& Um, const std::vector<Mat>& Ua,
+                               const std::vector<int64_t>& n, std::vector<Tens>& S, tk_dtype acc, double grad_scale,
+                               bool want_dG, bool want_dU, GradOut& g) {
+    const int d = Gt.d;
+    const double s2 = -2.0 * grad_scale;
+    std::vector<int> all(d);
+    std::iota(all.begin(), all.end(), 0);
+    Tens G64 = Gt.dt == TK_F64 ? Gt : tens_to(c, Gt, TK_F64);
+    std::vector<double*> U64(d);
+    std::vector<Mat> Cm(d);
+    c.fork(d, [&](int j) {
+        const int64_t nj = n[j], rj = Gt.n[j];
+        U64[j] = c.alloc<double>(nj * rj);
+        launch_convert(c, Um[j].p, Um[j].dt, nj, rj, Um[j].ld, U64[j], TK_F64, nj, 1.f);
+        double* Cj = c.alloc<double>(rj * rj);
+        gemm_nt_f64(c, rj, rj, nj, view_cols(U64[j], TK_F64, nj), view_cols(U64[j], TK_F64, nj), 1.0, 0.0, Cj, rj);
+        Cm[j].p = Cj;
+        Cm[j].dt = TK_F64;
+        Cm[j].rows = rj;
+        Cm[j].cols = rj;
+        Cm[j].ld = rj;
+    });
+    std::vector<Tens> Pm(d);  // P_n = G x_{j != n} C_j
+    all_modes(c, G64, all, {}, Cm.data(), TK_F64, Pm, nullptr);
+    // dU_n per mode and dG are independent: item j < d is dU_j, item d is dG
+    const int ndu = want_dU ? d : 0;
+    c.fork(ndu + (want_dG ? 1 : 0), [&](int j) {
+        if (j == ndu) {
+            // dG = -2s (X x_j U_j^T - G x_j C_j) = -2s (S_0 x_0 U_0^T - P_0 x_0 C_0)
+            Tens E = ttm_to(c, S[0], 0, Ua[0], false, acc);
+            Tens F = ttm_to(c, Pm[0], 0, Cm[0], false, TK_F64);
+            launch_axpby_residual(c, E, F.p, TK_F64, s2, g.dG.p, g.dG.dt);
+            return;
+        }
+        const int64_t nj = n[j], rj = Gt.n[j];
+        int64_t K = 1;
+        for (int i = 0; i < d; ++i)
+            if (i != j) K *= Gt.n[i];
+        double* A1 = c.alloc<double>(nj * rj);
+        double* B1 = c.alloc<double>(rj * rj);
+        // S_n carries the FP32 rounding of the sketch pass, far above double-float accumulation error,
+        // so for FP32 data this product (the largest of the gradient) runs on the FP32 pipe
+        gemm_nt_f64(c, nj, rj, K, view_unfold_rows(S[j], j), view_unfold_rows(Gt.dt == TK_F32 ? Gt : G64, j), s2,
+                    0.0, A1, nj, nullptr, true);
+        gemm_nt_f64(c, rj, rj, K, view_unfold_rows(Pm[j], j), view_unfold_rows(G64, j), 1.0, 0.0, B1, rj);
+        gemm_nt_f64(c, nj, rj, rj, view_rows(U64[j], TK_F64, nj), view_cols(B1, TK_F64, rj), -s2, 1.0, A1, nj);
+        launch_convert(c, A1, TK_F64, nj, rj, nj, (void*)g.dU[j].p, g.dU[j].dt, g.dU[j].ld, 1.f);
+    });
+}
+
+extern "C" {
+
 tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk_tensor* G, const tk_matrix* U,
                                       double grad_scale, tk_tensor* dG, tk_matrix* dU, tk_tensor* dX,
                                       double* norms2) {
@@ -1690,94 +1795,137 @@ tk_status tucker_reconstruct_backward(tk_handle* h, const tk_tensor* X, const tk
         for (int j = 0; j < d; ++j) TK_REQUIRE(Xt.n[j] == n[j], TK_ERR_SHAPE, "backward: X dims != U rows");
         TK_REQUIRE(dG || dU || dX || norms2, TK_ERR_ARG, "backward: no output requested");
         TK_REQUIRE(((uintptr_t)norms2 & 7) == 0, TK_ERR_ARG, "backward: norms2 must be 8-byte aligned");
-        Tens dGt;
-        if (dG) {
-            dGt = tens_in(dG, "dG");
-            TK_REQUIRE(dGt.d == d && (dGt.dt == TK_F64 || dGt.dt == TK_F32), TK_ERR_DTYPE,
-                       "backward: dG must be F64/F32");
-            for (int j = 0; j < d; ++j) TK_REQUIRE(dGt.n[j] == Gt.n[j], TK_ERR_SHAPE, "backward: dG dims != G dims");
-        }
-        std::vector<Mat> dUm(d);
-        if (dU) {
-            for (int j = 0; j < d; ++j) {
-                dUm[j] = mat_in(&dU[j], "dU");
-                TK_REQUIRE(dUm[j].rows == n[j] && dUm[j].cols == Gt.n[j], TK_ERR_SHAPE,
-                           "backward: dU_j must be n_j x r_j");
-                TK_REQUIRE(dUm[j].dt == TK_F64 || dUm[j].dt == TK_F32, TK_ERR_DTYPE, "backward: dU must be F64/F32");
-            }
-        }
-        Tens dXt;
-        if (dX) {
-            dXt = tens_in(dX, "dX");
-            TK_REQUIRE(dXt.d == d && dXt.dt == Xt.dt, TK_ERR_DTYPE, "backward: dX must have X's dims and dtype");
-            for (int j = 0; j < d; ++j) TK_REQUIRE(dXt.n[j] == Xt.n[j], TK_ERR_SHAPE, "backward: dX dims != X dims");
-        }
-        // With R = X - G x_j U_j and C_j = U_j^T U_j:
-        //   R x_{j!=n} U_j^T = S_n - G x_n U_n x_{j!=n} C_j,   S_n = X x_{j!=n} U_j^T,
-        // so every product with the residual comes from sketches of X (the
-        // dimension tree, recomputed, never stored across calls) plus small
-        // core-sized corrections in FP64; the residual itself is only formed,
-        // tile by tile, when dX is requested.
+        GradOut g = grad_outputs_in(Xt, Gt, n, dG, dU, dX);
         tk_dtype acc = acc_of(Xt.dt);
-        const double s2 = -2.0 * grad_scale;
         std::vector<Mat> Ua(d);
         for (int j = 0; j < d; ++j) Ua[j] = Um[j].dt == acc ? Um[j] : mat_to(c, Um[j], acc);
-        // dX and the norms come from one fused residual pass
-        auto residual = [&]() {
+        if (dG || dU) {
+            // the S_n by the dimension tree (recomputed, never stored across calls)
+            std::vector<Tens> S(d);
+            std::vector<int> all(d);
+            std::iota(all.begin(), all.end(), 0);
+            all_modes(c, Xt, all, {}, Ua.data(), acc, S, nullptr);
+            grad_from_sketches(c, Gt, Um, Ua, n, S, acc, grad_scale, dG != nullptr, dU != nullptr, g);
+        }
+        if (dX || norms2) {
+            // dX and the norms from one fused residual pass (the residual is only formed, tile by tile,
+            // for them)
             Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
             double* nrm = norms2 ? norms2 : c.alloc<double>(2);
-            residual_pass(c, Xt, Ga, Ua, acc, nrm, dX ? dXt.p : nullptr, dX ? dXt.dt : TK_F32, 2.0 * grad_scale);
-        };
-        if (!dG && !dU) {
-            residual();
-            return;
+            residual_pass(c, Xt, Ga, Ua, acc, nrm, dX ? g.dX.p : nullptr, dX ? g.dX.dt : TK_F32, 2.0 * grad_scale);
         }
-        std::vector<Tens> S(d);
-        std::vector<int> all(d);
-        std::iota(all.begin(), all.end(), 0);
-        all_modes(c, Xt, all, {}, Ua.data(), acc, S, nullptr);
-        Tens G64 = Gt.dt == TK_F64 ? Gt : tens_to(c, Gt, TK_F64);
-        std::vector<double*> U64(d);
-        std::vector<Mat> Cm(d);
-        c.fork(d, [&](int j) {
-            const int64_t nj = n[j], rj = Gt.n[j];
-            U64[j] = c.alloc<double>(nj * rj);
-            launch_convert(c, Um[j].p, Um[j].dt, nj, rj, Um[j].ld, U64[j], TK_F64, nj, 1.f);
-            double* Cj = c.alloc<double>(rj * rj);
-            gemm_nt_f64(c, rj, rj, nj, view_cols(U64[j], TK_F64, nj), view_cols(U64[j], TK_F64, nj), 1.0, 0.0, Cj, rj);
-            Cm[j].p = Cj;
-            Cm[j].dt = TK_F64;
-            Cm[j].rows = rj;
-            Cm[j].cols = rj;
-            Cm[j].ld = rj;
-        });
-        std::vector<Tens> Pm(d);  // P_n = G x_{j != n} C_j
-        all_modes(c, G64, all, {}, Cm.data(), TK_F64, Pm, nullptr);
-        // dU_n per mode and dG are independent: item j < d is dU_j, item d is dG
-        const int ndu = dU ? d : 0;
-        c.fork(ndu + (dG ? 1 : 0), [&](int j) {
-            if (j == ndu) {
-                // dG = -2s (X x_j U_j^T - G x_j C_j) = -2s (S_0 x_0 U_0^T - P_0 x_0 C_0)
-                Tens E = ttm_to(c, S[0], 0, Ua[0], false, acc);
-                Tens F = ttm_to(c, Pm[0], 0, Cm[0], false, TK_F64);
-                launch_axpby_residual(c, E, F.p, TK_F64, s2, dGt.p, dGt.dt);
-                return;
+    });
+}
+
+tk_status tucker_rhkron_grad(tk_handle* h, const tk_tensor* X, const int64_t* r, int p, const tk_matrix* Omega,
+                             const tk_opts* opts, tk_tensor* G, tk_matrix* U, double* rel_err, double grad_scale,
+                             tk_tensor* dG, tk_matrix* dU, tk_tensor* dX) {
+    double* errd = nullptr;
+    return run_call(h, [&](Ctx& c) {
+        Tens Xt = tens_in(X, "X", false);
+        c.xdata = Xt.p;
+        c.df64 = Xt.dt != TK_F64;
+        c.xnumel = Xt.numel();
+        const int d = Xt.d;
+        TK_REQUIRE(d >= 2, TK_ERR_SHAPE, "rhkron_grad: d must be >= 2");
+        TK_REQUIRE(r && Omega, TK_ERR_ARG, "rhkron_grad: null r or Omega");
+        TK_REQUIRE(p >= 0, TK_ERR_ARG, "rhkron_grad: p must be >= 0");
+        Opts o = opts_in(opts, d);
+        set_opts(c, o);
+        tk_dtype acc = acc_of(Xt.dt);
+        Tens Gt;
+        std::vector<Mat> Um;
+        check_outputs(Xt, r, G, U, Gt, Um);
+        std::vector<int64_t> n(Xt.n, Xt.n + d);
+        GradOut g = grad_outputs_in(Xt, Gt, n, dG, dU, dX);
+        std::vector<Mat> Om(d);
+        std::vector<int64_t> s(d), k(d);
+        for (int j = 0; j < d; ++j) {
+            Mat om = mat_in(&Omega[j], "Omega");
+            TK_REQUIRE(om.rows == Xt.n[j] && om.cols >= 1, TK_ERR_SHAPE, "rhkron_grad: Omega_j must be n_j x s_j");
+            TK_REQUIRE(acc == TK_F64 ? om.dt == TK_F64 : om.dt != TK_F64, TK_ERR_DTYPE,
+                       "rhkron_grad: Omega must be F64 for F64 data, else F32/BF16");
+            s[j] = om.cols;
+            Om[j] = mat_to(c, om, acc);
+        }
+        std::vector<int> need;
+        for (int m = 0; m < d; ++m) {
+            double w = 1;
+            for (int j = 0; j < d; ++j)
+                if (j != m) w *= (double)s[j];
+            TK_REQUIRE(w >= (double)(r[m] + p), TK_ERR_SHAPE, "rhkron_grad: prod_{j!=n} s_j must be >= r_n + p");
+            k[m] = (int64_t)std::min<double>((double)Xt.n[m], w);
+            TK_REQUIRE(r[m] >= 1 && r[m] <= k[m], TK_ERR_SHAPE, "rhkron_grad: need 1 <= r_n <= sketch width");
+            if (k[m] < Xt.n[m]) need.push_back(m);
+        }
+        // 1-4. rHKron-re (sketches, QR, core, STHOSVD), keeping the core's chain of products
+        std::vector<Tens> Y(d);
+        if (!need.empty()) {
+            std::vector<int> rest;
+            for (int j = 0; j < d; ++j)
+                if (std::find(need.begin(), need.end(), j) == need.end()) rest.push_back(j);
+            all_modes(c, Xt, need, rest, Om.data(), acc, Y, nullptr);
+        }
+        CoreTrace tr;
+        rhkron_from_sketches(c, Xt, Y, k, r, o, Gt, Um, nullptr, &tr);
+        // 5. the gradient at the result (G, U).  U_j = Q_j V_j' (V_j' = V_j with U_j's column signs), so
+        // for the core's chain C_t = X x_{m_1..m_t} Q^T (m_1, m_2, .. the modes in the order applied)
+        //   S_n = X x_{j!=n} U_j^T = C_t x_{j in m_1..m_t} V_j'^T x_{other j != n} U_j^T,
+        // C_t the last product in which mode n is still whole.  Only S_{m_1} reads X itself; the other
+        // S_n read the much smaller products.  The residual pass (dX, and the norms of the relative
+        // error) runs beside it on the side stream.
+        std::vector<Mat> Ua(d);
+        for (int j = 0; j < d; ++j) Ua[j] = Um[j].dt == acc ? Um[j] : mat_to(c, Um[j], acc);
+        Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
+        const bool want_res = dX || rel_err;
+        if (want_res) errd = c.alloc<double>(2);
+        std::vector<Mat> Va(d);
+        if (dG || dU) {
+            for (int j = 0; j < d; ++j) {
+                double* sgn[2] = {nullptr, tr.sg[j]};
+                Tens sh;
+                sh.d = 2;
+                sh.n[0] = k[j];
+                sh.n[1] = r[j];
+                launch_apply_signs(c, tr.V[j], sh, sgn);
+                Mat v;
+                v.p = tr.V[j];
+                v.dt = TK_F64;
+                v.rows = k[j];
+                v.cols = r[j];
+                v.ld = k[j];
+                Va[j] = acc == TK_F64 ? v : mat_to(c, v, acc);
             }
-            const int64_t nj = n[j], rj = Gt.n[j];
-            int64_t K = 1;
-            for (int i = 0; i < d; ++i)
-                if (i != j) K *= Gt.n[i];
-            double* A1 = c.alloc<double>(nj * rj);
-            double* B1 = c.alloc<double>(rj * rj);
-            // S_n carries the FP32 rounding of the sketch pass, far above double-float accumulation error,
-            // so for FP32 data this product (the largest of the gradient) runs on the FP32 pipe
-            gemm_nt_f64(c, nj, rj, K, view_unfold_rows(S[j], j), view_unfold_rows(Gt.dt == TK_F32 ? Gt : G64, j), s2,
-                        0.0, A1, nj, nullptr, true);
-            gemm_nt_f64(c, rj, rj, K, view_unfold_rows(Pm[j], j), view_unfold_rows(G64, j), 1.0, 0.0, B1, rj);
-            gemm_nt_f64(c, nj, rj, rj, view_rows(U64[j], TK_F64, nj), view_cols(B1, TK_F64, rj), -s2, 1.0, A1, nj);
-            launch_convert(c, A1, TK_F64, nj, rj, nj, (void*)dUm[j].p, dUm[j].dt, dUm[j].ld, 1.f);
-        });
-        if (dX || norms2) residual();
+        }
+        c.side(
+            [&]() {
+                if (!dG && !dU) return;
+                std::vector<Tens> S(d);
+                c.fork(d, [&](int m) {
+                    Tens C = Xt;
+                    std::vector<char> applied(d, 0);
+                    for (const auto& st : tr.chain) {
+                        if (st.first == m) break;
+                        C = st.second;
+                        applied[st.first] = 1;
+                    }
+                    std::vector<Mat> M(d);
+                    std::vector<int> modes;
+                    for (int j = 0; j < d; ++j) {
+                        if (j == m) continue;
+                        M[j] = applied[j] ? Va[j] : Ua[j];
+                        modes.push_back(j);
+                    }
+                    S[m] = multi_ttm(c, C, modes, M.data(), false, acc);
+                });
+                grad_from_sketches(c, Gt, Um, Ua, n, S, acc, grad_scale, dG != nullptr, dU != nullptr, g);
+            },
+            [&]() {
+                if (want_res)
+                    residual_pass(c, Xt, Ga, Ua, acc, errd, dX ? g.dX.p : nullptr, dX ? g.dX.dt : TK_F32,
+                                  2.0 * grad_scale);
+            });
+        if (rel_err) read_err(h, c, errd, rel_err, false, o.async_outputs);
     });
 }
 

@@ -179,8 +179,11 @@ struct Ctx {
         ctr_used += n;
         return p;
     }
-    // Auxiliary streams of the handle for independent per-mode work (fork).
-    static constexpr int kAux = 3;
+    // Auxiliary streams of the handle: the first kFork for independent
+    // per-mode work (fork), the last for a long branch that runs beside the
+    // rest of the call (side).
+    static constexpr int kFork = 3;
+    static constexpr int kAux = kFork + 1;
     cudaStream_t aux[kAux] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kAux] = {};
@@ -195,6 +198,14 @@ struct Ctx {
     // pass, the items run in order on the call's stream.
     template <typename F>
     void fork(int nb, F&& body);
+
+    // Runs side_body on the side stream (forked from the call's stream) and
+    // then main_body on the call's stream, joining the side stream back
+    // before returning: the two overlap, and forks inside main_body never
+    // queue behind side_body.  side_body must not fork.  Without auxiliary
+    // streams, or in the planning pass, both run in order on the call's stream.
+    template <typename M, typename S>
+    void side(M&& main_body, S&& side_body);
 
     template <typename T>
     T* alloc(int64_t count) {
@@ -220,11 +231,11 @@ void Ctx::fork(int nb, F&& body) {
         return;
     }
     cudaStream_t main = stream;
-    const int used = nb < kAux ? nb : kAux;
+    const int used = nb < kFork ? nb : kFork;
     ctx_fork_begin(*this, used);
     try {
         for (int b = 0; b < nb; ++b) {
-            stream = aux[b % kAux];
+            stream = aux[b % kFork];
             body(b);
         }
     } catch (...) {
@@ -232,6 +243,29 @@ void Ctx::fork(int nb, F&& body) {
         throw;
     }
     ctx_fork_end(*this, main, used);
+}
+
+void ctx_side_begin(Ctx& c);
+void ctx_side_end(Ctx& c, cudaStream_t main);
+
+template <typename M, typename S>
+void Ctx::side(M&& main_body, S&& side_body) {
+    if (!exec || !aux[kFork]) {
+        side_body();
+        main_body();
+        return;
+    }
+    cudaStream_t main = stream;
+    ctx_side_begin(*this);  // the side stream waits for the call's stream; the call's stream becomes it
+    try {
+        side_body();
+        stream = main;
+        main_body();
+    } catch (...) {
+        ctx_side_end(*this, main);
+        throw;
+    }
+    ctx_side_end(*this, main);
 }
 
 // RAII event pair around one launch (no-op unless profiling is on).

@@ -36,6 +36,21 @@ void ctx_fork_end(Ctx& c, cudaStream_t main, int used) {
     if (first != cudaSuccess) fail(TK_ERR_CUDA, std::string("fork join: ") + cudaGetErrorString(first));
 }
 
+// The side stream (the last auxiliary stream) waits for the call's stream and
+// becomes the call's stream; ctx_side_end joins it back into `main`.
+void ctx_side_begin(Ctx& c) {
+    TK_CUDA(cudaEventRecord(c.ev_fork, c.stream));
+    TK_CUDA(cudaStreamWaitEvent(c.aux[Ctx::kFork], c.ev_fork, 0));
+    c.stream = c.aux[Ctx::kFork];
+}
+
+void ctx_side_end(Ctx& c, cudaStream_t main) {
+    c.stream = main;
+    cudaError_t e = cudaEventRecord(c.ev_join[Ctx::kFork], c.aux[Ctx::kFork]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(main, c.ev_join[Ctx::kFork], 0);
+    if (e != cudaSuccess) fail(TK_ERR_CUDA, std::string("side join: ") + cudaGetErrorString(e));
+}
+
 // ------------------------------------------------------------------ loads
 
 __device__ __forceinline__ float ldx(const float* p, int64_t i, float) { return p[i]; }
@@ -2147,7 +2162,7 @@ __global__ void apply_signs_kernel(double* G, int64_t tot, SignPtrs sp) {
     for (int j = 0; j < sp.d; ++j) {
         int64_t ij = rem % sp.n[j];
         rem /= sp.n[j];
-        f *= sp.s[j][ij];
+        if (sp.s[j]) f *= sp.s[j][ij];  // no sign array: the mode keeps its signs
     }
     G[idx] *= f;
 }

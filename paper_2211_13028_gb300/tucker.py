@@ -25,7 +25,7 @@ __all__ = [
     "TuckerError", "load", "empty_f", "is_colmajor",
     "tucker_subranks_reuse", "tucker_subranks_matrix",
     "tucker_sketch", "tucker_orth", "tucker_orth_noalloc", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
-    "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward",
+    "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward", "tucker_rhkron_grad",
     "tk_sync_status", "tk_selftest_bounded_wait", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
     "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tucker_rhkron_srht", "tk_graph_release",
     "tk_philox4x32", "tucker_gaussian_factor", "tucker_gaussian_factors", "gaussian_factors",
@@ -123,6 +123,9 @@ def load():
             "tucker_orth_noalloc": ([vp, P(TkMatrix), P(TkMatrix), P(ctypes.c_int)], ctypes.c_int),
             "tucker_rhkron": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor), P(TkMatrix),
                                P(ctypes.c_double)], ctypes.c_int),
+            "tucker_rhkron_grad": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor),
+                                    P(TkMatrix), P(ctypes.c_double), ctypes.c_double, P(TkTensor), P(TkMatrix),
+                                    P(TkTensor)], ctypes.c_int),
             "tucker_rsthkron": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor),
                                  P(TkMatrix), P(ctypes.c_double)], ctypes.c_int),
             "tucker_rhkron_noreuse": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor),
@@ -535,6 +538,40 @@ def tucker_rhkron(X: torch.Tensor, r: Sequence[int], p: int, Omega: Sequence[tor
     with async_outputs the relative error is a PendingScalar and the call does not synchronise."""
     return _decomp(load().tucker_rhkron, X, r, p, list(Omega), order, qr_method, refine, max_jacobi_sweeps, rel_err,
                    out_dtype, scale, async_outputs)
+
+
+def tucker_rhkron_grad(X: torch.Tensor, r: Sequence[int], p: int, Omega: Sequence[torch.Tensor],
+                       grad_scale: float = 1.0, *, need_dG: bool = True, need_dU: bool = True, need_dX: bool = True,
+                       order=None, qr_method: int = 0, refine: int = 0, max_jacobi_sweeps: int = 0,
+                       rel_err: bool = True, out_dtype=None, scale: float = 1.0, async_outputs: bool = False):
+    """Algorithm rHKron-re and the gradient of grad_scale * ||X - G x_j U_j||^2 at its result in one call
+    (the passes over X shared).  Returns (G, [U_j], rel_err or None, dG, [dU_j], dX), gradients None when
+    not requested; rel_err as tucker_rhkron."""
+    d = X.dim()
+    dt = out_dtype or _acc_dtype(X)
+    G = empty_f(list(r), dt, X.device)
+    U = [_colmajor_matrix(int(X.shape[j]), int(r[j]), dt, X.device) for j in range(d)]
+    dG = empty_f(list(r), dt, X.device) if need_dG else None
+    dU = [_colmajor_matrix(int(X.shape[j]), int(r[j]), dt, X.device) for j in range(d)] if need_dU else None
+    dX = empty_f(list(X.shape), X.dtype, X.device) if need_dX else None
+    rr = (ctypes.c_int64 * d)(*[int(x) for x in r])
+    o, keep = _opts(order, qr_method, refine, max_jacobi_sweeps, async_outputs)
+    pend = PendingScalar()
+    h = _handle(X.device)
+    st = load().tucker_rhkron_grad(h, ctypes.byref(_tensor(X, scale)), rr, int(p), _mats(list(Omega)),
+                                   ctypes.byref(o), ctypes.byref(_tensor(G)), _mats(U),
+                                   ctypes.byref(pend._c) if rel_err else None, float(grad_scale),
+                                   ctypes.byref(_tensor(dG)) if need_dG else None, _mats(dU) if need_dU else None,
+                                   ctypes.byref(_tensor(dX)) if need_dX else None)
+    _check(st, h)
+    if not rel_err:
+        err = None
+    elif async_outputs:
+        _pending.setdefault(h.value, collections.deque(maxlen=64)).append(pend)
+        err = pend
+    else:
+        err = pend.value
+    return G, U, err, dG, dU, dX
 
 
 def tucker_rsthkron(X: torch.Tensor, r: Sequence[int], p: int, Omega: Dict[Tuple[int, int], torch.Tensor], *,
