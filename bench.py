@@ -710,6 +710,8 @@ def main():
                     help="skip the other configurations (BF16 1024^3 vs FP32, 4-way 160^4, 256^3 descent) that "
                          "the default line carries under 'secondary'")
     ap.add_argument("--serial", action="store_true", help="run both algorithms on one stream")
+    ap.add_argument("--priority", choices=["none", "rhkron", "rsthkron"], default="none",
+                    help="which algorithm's stream gets the higher CUDA stream priority")
     ap.add_argument("--sharded", action="store_true",
                     help="one rHKron-re decomposition of the 512^3 field split along mode 3, one slab per rank")
     ap.add_argument("--no-graph", action="store_true",
@@ -772,8 +774,9 @@ def main():
     # The two algorithms are independent: rHKron-re and its gradient run on one stream, rSTHKron on a
     # second, so the latency-bound small kernels of one overlap the other (--serial: one stream).
     main_s = torch.cuda.current_stream(dev)
-    sa = torch.cuda.Stream(dev) if not args.serial else main_s
-    sb = torch.cuda.Stream(dev) if not args.serial else main_s
+    pa, pb = {"none": (0, 0), "rhkron": (-1, 0), "rsthkron": (0, -1)}[args.priority]
+    sa = torch.cuda.Stream(dev, priority=pa) if not args.serial else main_s
+    sb = torch.cuda.Stream(dev, priority=pb) if not args.serial else main_s
     use_graph = not args.no_graph and not args.serial
 
     def step(Xin, marks=None):

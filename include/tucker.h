@@ -126,7 +126,10 @@ typedef struct tk_handle tk_handle;
 TK_API tk_status tk_graph_release(tk_handle* h);
 
 /* Create a handle bound to a CUDA stream (cudaStream_t passed as void*, NULL =
- * legacy default stream) on the current device.  *h receives the handle. */
+ * legacy default stream) on the current device.  *h receives the handle.
+ * The handle's auxiliary streams (independent per-mode work is forked onto
+ * them and joined back within each call) are created with the priority of
+ * that stream, so a stream's priority ranks all of a call's work. */
 TK_API tk_status tk_create(tk_handle** h, void* cuda_stream);
 /* Destroy a handle and free its workspace (synchronises its stream). */
 TK_API tk_status tk_destroy(tk_handle* h);

@@ -695,8 +695,15 @@ tk_status tk_create(tk_handle** h, void* stream) {
     bool ok = cudaMalloc((void**)&x->ctr, sizeof(unsigned) * tk::Ctx::kCounters) == cudaSuccess &&
               cudaMemset(x->ctr, 0, sizeof(unsigned) * tk::Ctx::kCounters) == cudaSuccess &&
               cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    // the auxiliary streams take the priority of the handle's stream, so that a caller can rank the
+    // whole of a call (its forked work included) against work on other streams
+    int prio = 0;
+    if (cudaStreamGetPriority(x->stream, &prio) != cudaSuccess) {
+        cudaGetLastError();
+        prio = 0;
+    }
     for (int i = 0; i < tk::Ctx::kAux && ok; ++i)
-        ok = cudaStreamCreateWithFlags(&x->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+        ok = cudaStreamCreateWithPriority(&x->aux[i], cudaStreamNonBlocking, prio) == cudaSuccess &&
              cudaEventCreateWithFlags(&x->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
