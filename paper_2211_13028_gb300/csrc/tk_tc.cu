@@ -128,6 +128,16 @@ struct Cfg {
     static_assert(kStages >= 2, "SMEM budget");
 };
 
+// (hi, lo) += b with Knuth's two-sum on the high part; the low part collects
+// the rounding errors (a double-float running sum of FP32 terms).
+__device__ __forceinline__ void ef_add(float& hi, float& lo, float b) {
+    const float s = __fadd_rn(hi, b);
+    const float v = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(b, v));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
 __device__ __forceinline__ float xr_to_f32(float v) { return v; }
 __device__ __forceinline__ float xr_to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float xr_to_f32(__nv_fp8_e4m3 v) { return static_cast<float>(v); }
@@ -368,7 +378,9 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
         const int cg = (warp - W::kFirstEpi) >> 2;
         const int rho = 32 * q + lane;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        double sr = 0.0, sx = 0.0;
+        // running sums as double-float pairs (hi + lo, Knuth two-sum): FP32 instructions only, the FP64
+        // pipe (1/64 of FP32 here) stays out of the per-item work
+        float srh = 0.f, srl = 0.f, sxh = 0.f, sxl = 0.f;
         int64_t acc = 0;
         for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x, ++acc) {
             const int64_t t = w / args.nblk, nb = w % args.nblk;
@@ -424,8 +436,8 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                                     xr_store(static_cast<XR*>(args.out) + base + (c0 + i) * stride, args.alpha * dv);
                             }
                         }
-                        sr += (double)fr;
-                        sx += (double)fx;
+                        ef_add(srh, srl, fr);
+                        ef_add(sxh, sxl, fx);
                     }
                 }
             }
@@ -439,6 +451,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
         if (EPI != 0) {
             // reduce over the epilogue threads: warp shuffles, then named barrier 1, then one
             // thread sums the warps in a fixed order
+            double sr = (double)srh + (double)srl, sx = (double)sxh + (double)sxl;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
