@@ -337,20 +337,27 @@ void orth_matrix(Ctx& c, const Mat& y, const Mat& q) {
 //    where 1e-14 takes 17.)
 // Stage 1 of the FP32-class eigensolver: FP32 Jacobi on A until every
 // |a_pq| <= 1e-6 sqrt(|a_pp a_qq|) (relative to the pair's own diagonal
-// entries), then one FP64 Newton-Schulz step; V1 (k x k, ld k) is orthonormal
-// to FP64 rounding and diagonalises A, small eigenvalues included, to ~1e-7
-// of each entry's own scale (on the benchmark's cores: the eigenvectors to a
-// singular-value-weighted 1e-6 already, and stage 2 then needs one or two
-// sweeps; an absolute 1e-6 ||A|| stop leaves the small-eigenvalue tail
-// unresolved and stage 2 with four to six).
-static double* eig_seed(Ctx& c, int64_t k, const double* A) {
+// entries), then FP64 Newton-Schulz steps V <- V (3I - V^T V) / 2, each of
+// which squares the distance from orthonormality (the FP32 rotations leave
+// J about 1e-6 off, one step ~1e-12, two FP64 rounding); V1 (k x k, ld k)
+// diagonalises A, small eigenvalues included, to ~1e-7 of each entry's own
+// scale (on the benchmark's cores: the eigenvectors to a singular-value-
+// weighted 1e-6 already, and stage 2 then needs one or two sweeps; an
+// absolute 1e-6 ||A|| stop leaves the small-eigenvalue tail unresolved and
+// stage 2 with four to six).  One step serves FP32-class data (stage 2 makes
+// the final factor orthonormal itself); FP64 data, whose stage 2 works in the
+// V1 basis, takes two.
+static double* eig_seed(Ctx& c, int64_t k, const double* A, int ns_steps = 1) {
     double* D = c.alloc<double>(k);
     double* V0 = c.alloc<double>(k * k);
     double* V1 = c.alloc<double>(k * k);
     double* W = c.alloc<double>(k * k);
     launch_jacobi_mixed(c, k, A, D, nullptr, V0, V1, 1e-6, c.max_sweeps, false);  // V0 = V1 = J in FP64
-    gemm_nt_f64(c, k, k, k, view_cols(V0, TK_F64, k), view_cols(V0, TK_F64, k), 1.0, 0.0, W, k);
-    gemm_nt_f64(c, k, k, k, view_rows(V0, TK_F64, k), view_cols(W, TK_F64, k), -0.5, 1.5, V1, k);
+    for (int step = 0; step < ns_steps; ++step) {
+        if (step > 0) launch_convert(c, V1, TK_F64, k * k, 1, k * k, V0, TK_F64, k * k, 1.f);  // V0 = V1
+        gemm_nt_f64(c, k, k, k, view_cols(V0, TK_F64, k), view_cols(V0, TK_F64, k), 1.0, 0.0, W, k);
+        gemm_nt_f64(c, k, k, k, view_rows(V0, TK_F64, k), view_cols(W, TK_F64, k), -0.5, 1.5, V1, k);
+    }
     return V1;
 }
 
@@ -388,14 +395,30 @@ static void eig_resolve(Ctx& c, int64_t k, const double* A, const double* V1, in
 //    error of the leading eigenvectors is ~2e-8 at a 1e-11 stage-2 threshold,
 //    ~3e-9 at 1e-14 and ~3e-7 at 1e-10.)
 static void eig_top(Ctx& c, int64_t k, const double* A, int64_t r, double* Vr, bool fp64_path) {
-    if (fp64_path) {
+    if (fp64_path && k > 112) {  // beyond the shared-memory kernels: FP64 Jacobi in global memory
         double* Ac = c.alloc<double>(k * k);
         double* w = c.alloc<double>(k);
         double* Vf = c.alloc<double>(k * k);
-        double* gV = k > 112 ? c.alloc<double>(k * k) : nullptr;  // beyond shared memory: the global-memory variant
+        double* gV = c.alloc<double>(k * k);
         launch_convert(c, A, TK_F64, k * k, 1, k * k, Ac, TK_F64, k * k, 1.f);
         launch_jacobi(c, k, Ac, w, Vf, c.max_sweeps, gV);
         launch_convert(c, Vf, TK_F64, k, r, k, Vr, TK_F64, k, 1.f);
+        return;
+    }
+    if (fp64_path) {
+        // FP64 data: the FP32 seeding stage, then FP64 Jacobi on B = V1^T A V1, which is diagonal up to
+        // ~1e-7 of each entry's scale, so its quadratic convergence takes two or three sweeps instead
+        // of the ten or so from A itself; V = V1 Vb keeps FP64 accuracy (V1 is orthonormal to FP64
+        // rounding after two Newton-Schulz steps)
+        const double* V1 = eig_seed(c, k, A, 2);
+        double* Pm = c.alloc<double>(k * k);
+        double* B = c.alloc<double>(k * k);
+        double* w = c.alloc<double>(k);
+        double* Vb = c.alloc<double>(k * k);
+        gemm_nt_f64(c, k, k, k, view_rows(A, TK_F64, k), view_cols(V1, TK_F64, k), 1.0, 0.0, Pm, k);
+        gemm_nt_f64(c, k, k, k, view_cols(V1, TK_F64, k), view_cols(Pm, TK_F64, k), 1.0, 0.0, B, k);
+        launch_jacobi(c, k, B, w, Vb, c.max_sweeps);  // eigenpairs sorted by descending eigenvalue
+        gemm_nt_f64(c, k, r, k, view_rows(V1, TK_F64, k), view_cols(Vb, TK_F64, k), 1.0, 0.0, Vr, k);
         return;
     }
     eig_resolve(c, k, A, eig_seed(c, k, A), r, Vr);
