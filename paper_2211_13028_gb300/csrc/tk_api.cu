@@ -321,8 +321,9 @@ void orth_matrix(Ctx& c, const Mat& y, const Mat& q) {
 
 // Leading r eigenvectors of the symmetric k x k FP64 matrix A, as the columns
 // of Vr (k x r, ld k), in descending eigenvalue order.
-//  * FP64 data, and any k above 112 (beyond the shared-memory kernels): cyclic
-//    Jacobi entirely in FP64.
+//  * any k above 112 (beyond the shared-memory kernels): cyclic Jacobi
+//    entirely in FP64.
+//  * FP64 data: stage 1 below, then FP64 Jacobi on V1^T A V1 (eig_top).
 //  * otherwise: a two-stage scheme built for a chip whose FP64 rate is a small
 //    fraction of its FP32 rate.  Stage 1, mixed Jacobi on A (FP32 accuracy),
 //    gives V0; one FP64 Newton-Schulz step V0 <- V0 (3I - V0^T V0) / 2 makes it
@@ -386,8 +387,10 @@ static void eig_resolve(Ctx& c, int64_t k, const double* A, const double* V1, in
 
 // Leading r eigenvectors of the symmetric k x k FP64 matrix A, as the columns
 // of Vr (k x r, ld k), in descending eigenvalue order.
-//  * FP64 data, and any k above 112 (beyond the shared-memory kernels): cyclic
-//    Jacobi entirely in FP64.
+//  * any k above 112 (beyond the shared-memory kernels): cyclic Jacobi
+//    entirely in FP64.
+//  * FP64 data: the FP32 seeding stage (eig_seed with two Newton-Schulz
+//    steps), then FP64 Jacobi on V1^T A V1.
 //  * otherwise: a two-stage scheme built for a chip whose FP64 rate is a small
 //    fraction of its FP32 rate (eig_seed, then eig_resolve).  (A is the Gram
 //    of a core computed from FP32-class data, whose entries carry relative
