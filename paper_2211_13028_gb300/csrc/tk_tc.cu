@@ -30,6 +30,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <type_traits>
+
 #include "tk_tc_common.cuh"
 
 namespace tk {
@@ -425,16 +427,23 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                             if (c0 + i < ncol) static_cast<float*>(args.out)[base + (c0 + i) * stride] = h[i] + g[i];
                     } else {
                         float fr = 0.f, fx = 0.f;
+                        const XR* xcol = xt + c0 * kRows + rho;
+                        XR* op = EPI == 2 ? static_cast<XR*>(args.out) + base + c0 * stride : nullptr;
+                        auto one = [&](int i) {
+                            float xv = xr_to_f32(xcol[i * kRows]);
+                            if constexpr (std::is_same<XR, __nv_fp8_e4m3>::value) xv *= args.xr_scale;  // 1 / scale
+                            const float dv = xv - (h[i] + g[i]);
+                            fr = fmaf(dv, dv, fr);
+                            fx = fmaf(xv, xv, fx);
+                            if constexpr (EPI == 2) xr_store(op + i * stride, args.alpha * dv);
+                        };
+                        if (c0 + 16 <= ncol) {  // a full slice: no per-column test
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            if (c0 + i < ncol) {
-                                const float xv = xr_to_f32(xt[(c0 + i) * kRows + rho]) * args.xr_scale;
-                                const float dv = xv - (h[i] + g[i]);
-                                fr = fmaf(dv, dv, fr);
-                                fx = fmaf(xv, xv, fx);
-                                if constexpr (EPI == 2)
-                                    xr_store(static_cast<XR*>(args.out) + base + (c0 + i) * stride, args.alpha * dv);
-                            }
+                            for (int i = 0; i < 16; ++i) one(i);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                if (c0 + i < ncol) one(i);
                         }
                         ef_add(srh, srl, fr);
                         ef_add(sxh, sxl, fx);
