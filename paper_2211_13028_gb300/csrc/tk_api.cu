@@ -370,17 +370,15 @@ static double* eig_seed(Ctx& c, int64_t k, const double* A, int ns_steps = 1) {
 // absolute threshold either way).
 static void eig_resolve(Ctx& c, int64_t k, const double* A, const double* V1, int64_t r, double* Vr) {
     double* D = c.alloc<double>(k);
-    float* J = c.alloc<float>(k * k);
     double* Pm = c.alloc<double>(k * k);
     double* B = c.alloc<double>(k * k);
-    double* V = c.alloc<double>(k * k);
     double* Vt = c.alloc<double>(k * r);
     double* Wr = c.alloc<double>(r * r);
     gemm_nt_f64(c, k, k, k, view_rows(A, TK_F64, k), view_cols(V1, TK_F64, k), 1.0, 0.0, Pm, k);
     gemm_nt_f64(c, k, k, k, view_cols(V1, TK_F64, k), view_cols(Pm, TK_F64, k), 1.0, 0.0, B, k);
-    launch_jacobi_mixed(c, k, B, D, J, nullptr, nullptr, 1e-11, c.max_sweeps, true);
-    gemm_nt_f64(c, k, k, k, view_rows(V1, TK_F64, k), view_cols(J, TK_F32, k), 1.0, 0.0, V, k);
-    launch_select_top(c, k, r, D, V, Vt, Vr);  // Vr starts as a copy of Vt for the Newton-Schulz step
+    // the rotations replayed on the rows of V1 give V = V1 J, whose top-r columns go to Vt and to Vr
+    // (Vr starts as a copy of Vt for the Newton-Schulz step)
+    launch_jacobi_mixed(c, k, B, D, nullptr, nullptr, nullptr, 1e-11, c.max_sweeps, true, V1, r, Vt, Vr);
     gemm_nt_f64(c, r, r, k, view_cols(Vt, TK_F64, k), view_cols(Vt, TK_F64, k), 1.0, 0.0, Wr, r);
     gemm_nt_f64(c, k, r, r, view_rows(Vt, TK_F64, k), view_cols(Wr, TK_F64, r), -0.5, 1.5, Vr, k);
 }
@@ -1914,7 +1912,7 @@ tk_status tucker_rhkron_grad(tk_handle* h, const tk_tensor* X, const int64_t* r,
         if (want_res) errd = c.alloc<double>(2);
         std::vector<Mat> Va(d);
         if (dG || dU) {
-            for (int j = 0; j < d; ++j) {
+            c.fork(d, [&](int j) {
                 double* sgn[2] = {nullptr, tr.sg[j]};
                 Tens sh;
                 sh.d = 2;
@@ -1928,7 +1926,7 @@ tk_status tucker_rhkron_grad(tk_handle* h, const tk_tensor* X, const int64_t* r,
                 v.cols = r[j];
                 v.ld = k[j];
                 Va[j] = acc == TK_F64 ? v : mat_to(c, v, acc);
-            }
+            });
         }
         c.side(
             [&]() {

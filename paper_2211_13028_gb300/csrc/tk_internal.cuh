@@ -406,7 +406,11 @@ void launch_jacobi(const Ctx& c, int64_t k, double* A, double* w, double* V, int
 // |a_pq| <= max(tol sqrt(|a_pp a_qq|), 1e-13 ||A||_F) (otherwise: the seeding
 // stage); otherwise FLAG_NOT_CONVERGED is raised.
 void launch_jacobi_mixed(Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
-                         double tol, int max_sweeps, bool fp64_diag);
+                         double tol, int max_sweeps, bool fp64_diag, const double* V1 = nullptr, int64_t r = 0,
+                         double* Vt = nullptr, double* Vr = nullptr);
+// (With V1: the rotations are replayed on the rows of V1, giving V = V1 J
+// without forming J, and the columns of V of the r largest eigenvalue
+// estimates, in descending order, go to Vt and Vr (k x r, ld k).)
 // Vr (k x r, ld k) = the columns of V (k x k) for the r largest entries of D, in descending order.
 void launch_select_top(const Ctx& c, int64_t k, int64_t r, const double* D, const double* V, double* Vr,
                        double* Vr2 = nullptr);

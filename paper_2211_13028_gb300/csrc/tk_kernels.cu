@@ -1897,9 +1897,23 @@ __global__ void __launch_bounds__(JM_MAX_THREADS) jacobi_sweep_kernel(int k, con
 constexpr int JR_WARPS = 4;
 constexpr int JR_STAGE = 8;  // log entries a thread carries while staging
 
+// Order key of a double (an int64 that compares as the value does; -0.0 as +0.0).
+__device__ __forceinline__ long long jr_key(double d) {
+    if (d == 0.0) return 0;
+    const long long u = __double_as_longlong(d);
+    return u >= 0 ? u : (u ^ 0x7FFFFFFFFFFFFFFFll);
+}
+
+// With V1 (k x k, FP64, ld k) the rows replayed are those of V1 instead of the
+// identity, i.e. the kernel forms V = V1 J without J, and writes the columns
+// of V of the r largest D (ties: lower index first) into Vt and Vr (k x r,
+// ld k), ordered by rank.
 __global__ void __launch_bounds__(JR_WARPS * 32) jacobi_replay_kernel(int k, const float2* __restrict__ rlog,
                                                                       const int* __restrict__ ginfo, float* Jout,
-                                                                      double* J64a, double* J64b) {
+                                                                      double* J64a, double* J64b,
+                                                                      const double* __restrict__ V1,
+                                                                      const double* __restrict__ D, int r,
+                                                                      double* Vt, double* Vr) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int kp = k + (k & 1), h = kp / 2;
     const int nt = JR_WARPS * 32, cr = JR_STAGE * nt / h;  // steps per chunk
@@ -1907,9 +1921,16 @@ __global__ void __launch_bounds__(JR_WARPS * 32) jacobi_replay_kernel(int k, con
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float* ra = reinterpret_cast<float*>(stage + (size_t)cr * h) + (size_t)warp * 2 * kp;  // this warp's row
     float* rb = ra + kp;
+    long long* keys = reinterpret_cast<long long*>(ra - (size_t)warp * 2 * kp + (size_t)JR_WARPS * 2 * kp);
     const int i = blockIdx.x * JR_WARPS + warp;
     const int steps = ginfo[0];
-    for (int x = lane; x < kp; x += 32) ra[x] = (x == i) ? 1.f : 0.f;
+    if (V1) {
+        for (int x = lane; x < kp; x += 32) ra[x] = (i < k && x < k) ? (float)V1[i + (int64_t)k * x] : 0.f;
+        for (int x = tid; x < k; x += nt) keys[x] = jr_key(D[x]);
+    } else {
+        for (int x = lane; x < kp; x += 32) ra[x] = (x == i) ? 1.f : 0.f;
+    }
+    __syncthreads();  // the keys are read by every warp at the end (also when no step was taken)
     const int t0 = lane, t1 = lane + 32;
     const int d00 = jm_pi(2 * t0, h), d01 = jm_pi(2 * t0 + 1, h);
     const int d10 = jm_pi(2 * t1, h), d11 = jm_pi(2 * t1 + 1, h);
@@ -1964,6 +1985,19 @@ __global__ void __launch_bounds__(JR_WARPS * 32) jacobi_replay_kernel(int k, con
         const int j = ginfo[1 + x];
         if (j >= k) continue;
         const float v = ra[x];
+        if (V1) {
+            const long long kj = keys[j];
+            int rank = 0;
+            for (int l = 0; l < k; ++l) {
+                const long long kl = keys[l];
+                rank += (kl > kj) || (kl == kj && l < j);
+            }
+            if (rank < r) {
+                Vt[i + (int64_t)k * rank] = (double)v;
+                Vr[i + (int64_t)k * rank] = (double)v;
+            }
+            continue;
+        }
         if (Jout) Jout[i + (int64_t)k * j] = v;
         if (J64a) J64a[i + (int64_t)k * j] = (double)v;
         if (J64b) J64b[i + (int64_t)k * j] = (double)v;
@@ -1971,7 +2005,8 @@ __global__ void __launch_bounds__(JR_WARPS * 32) jacobi_replay_kernel(int k, con
 }
 
 void launch_jacobi_mixed(Ctx& c, int64_t k, const double* A, double* D, float* J, double* J64a, double* J64b,
-                         double tol, int max_sweeps, bool fp64_diag) {
+                         double tol, int max_sweeps, bool fp64_diag, const double* V1, int64_t r, double* Vt,
+                         double* Vr) {
     TK_REQUIRE(k >= 1 && k <= 112, TK_ERR_SHAPE, "jacobi_mixed: 1 <= k <= 112");
     TK_REQUIRE(max_sweeps >= 0 && (int64_t)max_sweeps * (k + 1) < (1 << 30), TK_ERR_ARG,
                "jacobi_mixed: 0 <= max_sweeps and max_sweeps * k below 2^30");
@@ -2001,12 +2036,13 @@ void launch_jacobi_mixed(Ctx& c, int64_t k, const double* A, double* D, float* J
         c.counted();
         c.check_launch();
     }
-    if (!J && !J64a && !J64b) return;
+    if (!J && !J64a && !J64b && !V1) return;
+    TK_REQUIRE(!V1 || (Vt && Vr && r >= 1 && r <= k), TK_ERR_ARG, "jacobi_mixed: V1 needs Vt, Vr and 1 <= r <= k");
     const int cr = JR_STAGE * JR_WARPS * 32 / (int)h;
-    const size_t rsmem = sizeof(float2) * cr * h + sizeof(float) * JR_WARPS * 2 * kp;
+    const size_t rsmem = sizeof(float2) * cr * h + sizeof(float) * JR_WARPS * 2 * kp + sizeof(long long) * kp;
     ProfScope ps(c, "jacobi", 8.0 * h * (max_sweeps * (kp - 1) + 1) + 8.0 * k * k, 6.0 * k * k * k * max_sweeps);
     jacobi_replay_kernel<<<(unsigned)((k + JR_WARPS - 1) / JR_WARPS), JR_WARPS * 32, rsmem, c.stream>>>(
-        (int)k, rlog, ginfo, J, J64a, J64b);
+        (int)k, rlog, ginfo, J, J64a, J64b, V1, D, (int)r, Vt, Vr);
     c.counted();
     c.check_launch();
 }
