@@ -152,16 +152,24 @@ static Tens ttm_to(Ctx& c, const Tens& T, int j, const Mat& M, bool mtrans, tk_d
     o.dt = acc;
     o.scale = 1.f;
     o.p = dst ? dst : c.alloc_bytes(dtype_size(acc) * o.numel());
-    if (c.use_tc && ttm_narrow_eligible(T, j, m, acc) && reinterpret_cast<uintptr_t>(o.p) % 16 == 0)
-        launch_ttm_narrow(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
-    else if (c.use_tc && ttm_tc_eligible(T, j, m, acc))
-        launch_ttm_tc(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
-    else if (c.use_tc && ttm_bf16_eligible(T, j, m, acc))
-        launch_ttm_bf16(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
-    else if (c.use_tc && ttm_fp8_eligible(T, j, m, acc) && reinterpret_cast<uintptr_t>(o.p) % 16 == 0)
-        launch_ttm_fp8(c, T, j, M, mtrans, m, static_cast<float*>(o.p));
+    const bool aligned = reinterpret_cast<uintptr_t>(o.p) % 16 == 0;
+    const bool narrow = c.use_tc && ttm_narrow_eligible(T, j, m, acc) && aligned;
+    const bool tc = !narrow && c.use_tc && ttm_tc_eligible(T, j, m, acc);
+    const bool bf = !narrow && !tc && c.use_tc && ttm_bf16_eligible(T, j, m, acc);
+    const bool f8 = !narrow && !tc && !bf && c.use_tc && ttm_fp8_eligible(T, j, m, acc) && aligned;
+    // the tensor-core kernels split an FP64 factor themselves; the narrow and SIMT kernels of FP32-class
+    // data read FP32 factors
+    const Mat Mu = (M.dt == TK_F64 && acc != TK_F64 && !(tc || bf || f8)) ? mat_to(c, M, acc) : M;
+    if (narrow)
+        launch_ttm_narrow(c, T, j, Mu, mtrans, m, static_cast<float*>(o.p));
+    else if (tc)
+        launch_ttm_tc(c, T, j, Mu, mtrans, m, static_cast<float*>(o.p));
+    else if (bf)
+        launch_ttm_bf16(c, T, j, Mu, mtrans, m, static_cast<float*>(o.p));
+    else if (f8)
+        launch_ttm_fp8(c, T, j, Mu, mtrans, m, static_cast<float*>(o.p));
     else
-        launch_ttm(c, T, j, M, mtrans, m, o.p, acc);
+        launch_ttm(c, T, j, Mu, mtrans, m, o.p, acc);
     return o;
 }
 
@@ -1366,15 +1374,13 @@ static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, c
     // 3. core Ghat = X x_j Q_j^T (modes with Q = I are skipped)
     std::vector<Mat> Qa(d);
     std::vector<int> cm;
-    c.fork(d, [&](int j) {
-        Mat qm;
-        qm.p = Qd[j];
-        qm.dt = TK_F64;
-        qm.rows = Xt.n[j];
-        qm.cols = k[j];
-        qm.ld = Xt.n[j];
-        Qa[j] = acc == TK_F64 ? qm : mat_to(c, qm, acc);
-    });
+    for (int j = 0; j < d; ++j) {  // FP64: the TTMs take the factor in the form they read (ttm_to)
+        Qa[j].p = Qd[j];
+        Qa[j].dt = TK_F64;
+        Qa[j].rows = Xt.n[j];
+        Qa[j].cols = k[j];
+        Qa[j].ld = Xt.n[j];
+    }
     for (int j = 0; j < d; ++j)
         if (k[j] < Xt.n[j]) cm.push_back(j);
     Tens Gh = cm.empty() ? Xt : multi_ttm(c, Xt, cm, Qa.data(), false, acc, nullptr, tr ? &tr->chain : nullptr);
@@ -1919,13 +1925,11 @@ tk_status tucker_rhkron_grad(tk_handle* h, const tk_tensor* X, const int64_t* r,
                 sh.n[0] = k[j];
                 sh.n[1] = r[j];
                 launch_apply_signs(c, tr.V[j], sh, sgn);
-                Mat v;
-                v.p = tr.V[j];
-                v.dt = TK_F64;
-                v.rows = k[j];
-                v.cols = r[j];
-                v.ld = k[j];
-                Va[j] = acc == TK_F64 ? v : mat_to(c, v, acc);
+                Va[j].p = tr.V[j];  // FP64: the TTMs take the factor in the form they read (ttm_to)
+                Va[j].dt = TK_F64;
+                Va[j].rows = k[j];
+                Va[j].cols = r[j];
+                Va[j].ld = k[j];
             });
         }
         c.side(
