@@ -173,10 +173,19 @@ static Tens ttm_to(Ctx& c, const Tens& T, int j, const Mat& M, bool mtrans, tk_d
     return o;
 }
 
-// Apply M_i to every mode in `modes`, cheapest-shrinking mode first (smallest
-// output), the last product written to dst when given.
-static Tens multi_ttm(Ctx& c, const Tens& T, std::vector<int> modes, const Mat* M, bool mtrans, tk_dtype acc,
-                      void* dst = nullptr, std::vector<std::pair<int, Tens>>* trace = nullptr) {
+// Whether ttm_to takes a tensor-core kernel that splits the factor (tf32x3)
+// for this product (a workspace output, 16-byte aligned).
+static bool ttm_uses_tc(const Ctx& c, const Tens& T, int j, int64_t m, tk_dtype acc) {
+    return c.use_tc && !ttm_narrow_eligible(T, j, m, acc) && ttm_tc_eligible(T, j, m, acc);
+}
+
+// The order multi_ttm applies the factors in: cheapest-shrinking mode first
+// (smallest output; ties: the higher mode); FP8 data streams through the
+// tensor cores only along its contiguous mode, so that one goes first (the
+// later products then read the much smaller FP32 intermediate).
+static std::vector<int> mtt_order(const Ctx& c, const Tens& T, std::vector<int> modes, const Mat* M, bool mtrans,
+                                  tk_dtype acc) {
+    std::vector<int> order;
     Tens cur = T;
     while (!modes.empty()) {
         size_t best = 0;
@@ -190,13 +199,46 @@ static Tens multi_ttm(Ctx& c, const Tens& T, std::vector<int> modes, const Mat* 
                 best = t;
             }
         }
-        // FP8 data streams through the tensor cores only along its contiguous mode: take that one first
-        // (the later products then read the much smaller FP32 intermediate)
         for (size_t t = 0; t < modes.size() && c.use_tc && cur.dt == TK_FP8_E4M3; ++t)
             if (modes[t] == 0 && ttm_fp8_eligible(cur, 0, mtrans ? M[0].rows : M[0].cols, acc)) best = t;
-        int i = modes[best];
+        const int i = modes[best];
         modes.erase(modes.begin() + best);
-        cur = ttm_to(c, cur, i, M[i], mtrans, acc, modes.empty() ? dst : nullptr);
+        order.push_back(i);
+        cur.n[i] = mtrans ? M[i].rows : M[i].cols;
+        cur.dt = acc;
+    }
+    return order;
+}
+
+// Apply M_i to every mode in `modes` in mtt_order, the last product written to
+// dst when given; trace (optional) receives (mode, product so far) per step.
+// The factors of the tensor-core steps are split in one launch beforehand.
+static Tens multi_ttm(Ctx& c, const Tens& T, std::vector<int> modes, const Mat* M, bool mtrans, tk_dtype acc,
+                      void* dst = nullptr, std::vector<std::pair<int, Tens>>* trace = nullptr) {
+    const std::vector<int> order = mtt_order(c, T, modes, M, mtrans, acc);
+    struct CacheOn {
+        Ctx& c;
+        bool was;
+        CacheOn(Ctx& cc, bool on) : c(cc), was(cc.split_cache) { c.split_cache = was || on; }
+        ~CacheOn() { c.split_cache = was; }
+    };
+    std::vector<TcSplitReq> reqs;
+    if (c.use_tc && acc == TK_F32 && order.size() >= 2) {
+        Tens sh = T;
+        for (int i : order) {
+            const int64_t m = mtrans ? M[i].rows : M[i].cols;
+            if (ttm_uses_tc(c, sh, i, m, acc)) reqs.push_back({M[i], mtrans, sh.n[i], m, false});
+            sh.n[i] = m;
+            sh.dt = acc;
+            sh.p = reinterpret_cast<void*>(uintptr_t(256));  // a workspace block: 256-byte aligned
+        }
+        if (reqs.size() >= 2) tc_presplit(c, reqs);
+    }
+    CacheOn cache_on(c, reqs.size() >= 2);
+    Tens cur = T;
+    for (size_t s = 0; s < order.size(); ++s) {
+        const int i = order[s];
+        cur = ttm_to(c, cur, i, M[i], mtrans, acc, s + 1 == order.size() ? dst : nullptr);
         if (trace) trace->push_back({i, cur});  // the mode just applied and the product so far
     }
     return cur;
@@ -500,10 +542,9 @@ static void residual_pass(Ctx& c, const Tens& X, const Tens& G, const std::vecto
                           double* err2, void* dx, tk_dtype dxdt, double alpha) {
     const int d = X.d;
     int f = d - 1;
-    std::vector<int> todo;
+    std::vector<int> todo, order;
     for (int j = 0; j < d; ++j)
         if (j != f) todo.push_back(j);
-    Tens W = G;
     while (!todo.empty()) {
         size_t best = 0;
         double bestr = 1e300;
@@ -512,17 +553,43 @@ static void residual_pass(Ctx& c, const Tens& X, const Tens& G, const std::vecto
             double ratio = (double)U[i].rows / std::max<double>(1.0, (double)U[i].cols);
             if (ratio < bestr) { bestr = ratio; best = t; }
         }
-        int i = todo[best];
+        order.push_back(todo[best]);
         todo.erase(todo.begin() + best);
-        W = ttm_to(c, W, i, U[i], true, acc);
     }
     const int64_t m = U[f].rows;
     // BF16 data: the epilogue reads the BF16 X tile (and writes a BF16 dX) itself; FP8 data: the E4M3 X
     // tile, scaled back by 1 / scale (norms only, no dX)
+    Tens Ws = G;  // the shape the last product starts from
+    for (int i : order) {
+        Ws.n[i] = U[i].rows;
+        Ws.dt = acc;
+        Ws.p = reinterpret_cast<void*>(uintptr_t(256));  // a workspace block: 256-byte aligned
+    }
     const bool fused = c.use_tc &&
                        (X.dt == TK_F32 || (X.dt == TK_BF16 && X.left(f) % 8 == 0) ||
                         (X.dt == TK_FP8_E4M3 && X.left(f) % 16 == 0 && !dx)) &&
-                       acc == TK_F32 && (!dx || dxdt == X.dt) && ttm_tc_residual_eligible(W, f, m);
+                       acc == TK_F32 && (!dx || dxdt == X.dt) && ttm_tc_residual_eligible(Ws, f, m);
+    // the factors of the tensor-core products split in one launch
+    std::vector<TcSplitReq> reqs;
+    if (c.use_tc && acc == TK_F32) {
+        Tens sh = G;
+        for (int i : order) {
+            if (ttm_uses_tc(c, sh, i, U[i].rows, acc)) reqs.push_back({U[i], true, sh.n[i], U[i].rows, false});
+            sh.n[i] = U[i].rows;
+            sh.dt = acc;
+            sh.p = reinterpret_cast<void*>(uintptr_t(256));
+        }
+        if (fused) reqs.push_back({U[f], true, Ws.n[f], m, true});
+        if (reqs.size() >= 2) tc_presplit(c, reqs);
+    }
+    struct CacheOn {
+        Ctx& c;
+        bool was;
+        CacheOn(Ctx& cc, bool on) : c(cc), was(cc.split_cache) { c.split_cache = was || on; }
+        ~CacheOn() { c.split_cache = was; }
+    } cache_on(c, reqs.size() >= 2);
+    Tens W = G;
+    for (int i : order) W = ttm_to(c, W, i, U[i], true, acc);
     if (fused) {
         const int nb = tc_num_ctas(W, f, m, true);
         double* part = c.alloc<double>(2 * nb);
@@ -548,11 +615,9 @@ static void finish(Ctx& c, const Tens& X, const std::vector<double*>& Qd, const 
         sg[j] = c.alloc<double>(r[j]);
         gemm_nt_f64(c, X.n[j], r[j], kdim[j], view_rows(Qd[j], TK_F64, X.n[j]), view_cols(V[j], TK_F64, kdim[j]), 1.0,
                     0.0, U[j], X.n[j]);
-        launch_sign_fix(c, U[j], X.n[j], r[j], sg[j]);
-        launch_convert(c, U[j], TK_F64, X.n[j], r[j], X.n[j], (void*)Uout[j].p, Uout[j].dt, Uout[j].ld, 1.f);
+        launch_sign_fix(c, U[j], X.n[j], r[j], sg[j], (void*)Uout[j].p, Uout[j].dt, Uout[j].ld);
     });
-    launch_apply_signs(c, (double*)Gt.p, Gt, sg.data());
-    launch_convert(c, Gt.p, TK_F64, Gt.numel(), 1, Gt.numel(), Gout.p, Gout.dt, Gt.numel(), 1.f);
+    launch_apply_signs(c, (double*)Gt.p, Gt, sg.data(), Gout.p, Gout.dt);
     if (signs) *signs = sg;
     if (!err_dev) return;
     // ||X - G x_j U_j|| from the returned G and U, in the accumulation dtype.

@@ -287,6 +287,17 @@ void launch_ttm(const Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, i
 // Tensor-core (tcgen05, 3xTF32) version of launch_ttm for FP32 data and output,
 // m <= 96; ttm_tc_eligible says whether a TTM qualifies (shape, dtype, alignment).
 bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt);
+// A factor a tensor-core TTM will split (the contracted mode's size nj, output
+// width m; residual: the fused-residual blocking).
+struct TcSplitReq {
+    Mat M;
+    bool mtrans;
+    int64_t nj, m;
+    bool residual;
+};
+// Makes the splits of several factors in one launch and enters them in the
+// call's split cache (which must be on while the TTMs run).
+void tc_presplit(Ctx& c, const std::vector<TcSplitReq>& reqs);
 void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out);
 // BF16 data: tcgen05 kind::f16 with A straight from shared memory and the
 // factor split into BF16 hi + lo (FP32 output).
@@ -433,8 +444,14 @@ void launch_fill_int(const Ctx& c, int* p, int count, int value);
 void launch_qr_info(const Ctx& c, int* slot, const int* bad, int bad_value);
 // Sign gauge: for each column of U (n x r, F64, ld n) make the largest-|.|
 // entry positive; sign[c] = +-1.
-void launch_sign_fix(const Ctx& c, double* U, int64_t n, int64_t r, double* sign);
-void launch_apply_signs(const Ctx& c, double* G, const Tens& shape, double* const* signs_dev);
+// out (may be NULL): the signed U also stored there in odt (ld ldo).
+void launch_sign_fix(const Ctx& c, double* U, int64_t n, int64_t r, double* sign, void* out = nullptr,
+                     tk_dtype odt = TK_F64, int64_t ldo = 0);
+// G (a tensor of the given shape, FP64) times the product of the modes' signs
+// (a NULL sign array leaves its mode alone); out (may be NULL): also stored
+// there in odt, dense.
+void launch_apply_signs(const Ctx& c, double* G, const Tens& shape, double* const* signs_dev, void* out = nullptr,
+                        tk_dtype odt = TK_F64);
 // partial sums of (X - Y)^2 and X^2 over a tensor, reduced into out[0..1] (FP64).
 void launch_residual_norms(Ctx& c, const Tens& X, const void* Y, tk_dtype ydt, double* out2);
 // dst = alpha * (X - Y) elementwise (dst dtype = X dtype or F32/F64)

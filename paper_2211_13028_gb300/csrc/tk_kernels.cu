@@ -2145,7 +2145,8 @@ void launch_qr_info(const Ctx& c, int* slot, const int* bad, int bad_value) {
     c.check_launch();
 }
 
-__global__ void __launch_bounds__(256) sign_fix_kernel(double* U, int64_t n, double* sign) {
+__global__ void __launch_bounds__(256) sign_fix_kernel(double* U, int64_t n, double* sign, void* out, tk_dtype odt,
+                                                       int64_t ldo) {
     __shared__ double bv[256];
     __shared__ int64_t bi[256];
     const int64_t col = blockIdx.x;
@@ -2172,14 +2173,19 @@ __global__ void __launch_bounds__(256) sign_fix_kernel(double* U, int64_t n, dou
     }
     double sg = u[bi[0]] < 0.0 ? -1.0 : 1.0;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) u[i] *= sg;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = u[i] * sg;
+        u[i] = v;
+        if (out) st_any(out, odt, i + ldo * col, v);
+    }
     if (threadIdx.x == 0) sign[col] = sg;
 }
 
-void launch_sign_fix(const Ctx& c, double* U, int64_t n, int64_t r, double* sign) {
+void launch_sign_fix(const Ctx& c, double* U, int64_t n, int64_t r, double* sign, void* out, tk_dtype odt,
+                     int64_t ldo) {
     if (!c.exec || r == 0) return;
     ProfScope ps(c, "elementwise", 16.0 * n * r, 0.0);
-    sign_fix_kernel<<<(unsigned)r, 256, 0, c.stream>>>(U, n, sign);
+    sign_fix_kernel<<<(unsigned)r, 256, 0, c.stream>>>(U, n, sign, out, odt, ldo);
     c.counted();
     c.check_launch();
 }
@@ -2190,7 +2196,7 @@ struct SignPtrs {
     int d;
 };
 
-__global__ void apply_signs_kernel(double* G, int64_t tot, SignPtrs sp) {
+__global__ void apply_signs_kernel(double* G, int64_t tot, SignPtrs sp, void* out, tk_dtype odt) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= tot) return;
     int64_t rem = idx;
@@ -2200,10 +2206,12 @@ __global__ void apply_signs_kernel(double* G, int64_t tot, SignPtrs sp) {
         rem /= sp.n[j];
         if (sp.s[j]) f *= sp.s[j][ij];  // no sign array: the mode keeps its signs
     }
-    G[idx] *= f;
+    const double v = G[idx] * f;
+    G[idx] = v;
+    if (out) st_any(out, odt, idx, v);
 }
 
-void launch_apply_signs(const Ctx& c, double* G, const Tens& shape, double* const* signs) {
+void launch_apply_signs(const Ctx& c, double* G, const Tens& shape, double* const* signs, void* out, tk_dtype odt) {
     if (!c.exec) return;
     SignPtrs sp;
     sp.d = shape.d;
@@ -2214,7 +2222,7 @@ void launch_apply_signs(const Ctx& c, double* G, const Tens& shape, double* cons
     int64_t tot = shape.numel();
     if (tot == 0) return;
     ProfScope ps(c, "elementwise", 16.0 * tot, (double)tot * shape.d);
-    apply_signs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(G, tot, sp);
+    apply_signs_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(G, tot, sp, out, odt);
     c.counted();
     c.check_launch();
 }

@@ -510,6 +510,37 @@ __global__ void split_tf32_kernel(const void* M, tk_dtype dt, int64_t ldm, int m
     lo[idx] = l;
 }
 
+// Several factors split in one launch (blockIdx.y = factor): the same split
+// as split_tf32_kernel for each.
+struct SplitJob {
+    const void* M;
+    int dt, mtrans;
+    int64_t ldm, nj, m, rows_b, ldo;
+    float* hi;
+    float* lo;
+};
+constexpr int kMaxSplitJobs = 8;
+struct SplitBatch {
+    SplitJob job[kMaxSplitJobs];
+};
+
+__global__ void split_tf32_batch_kernel(SplitBatch sb) {
+    const SplitJob& jb = sb.job[blockIdx.y];
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < jb.ldo * jb.rows_b;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx % jb.ldo, a = idx / jb.ldo;
+        double v = 0.0;
+        if (i < jb.nj && a < jb.m) {
+            const int64_t o = jb.mtrans ? a + jb.ldm * i : i + jb.ldm * a;
+            v = jb.dt == TK_F64 ? static_cast<const double*>(jb.M)[o] : (double)static_cast<const float*>(jb.M)[o];
+        }
+        const float h = __uint_as_float(tf32_rna((float)v));
+        const float l = __uint_as_float(tf32_rna((float)(v - (double)h)));
+        jb.hi[idx] = h;
+        jb.lo[idx] = l;
+    }
+}
+
 template <int NPAD, bool KMAJOR, int EPI, typename XR = float>
 static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap& th, const CUtensorMap& tl,
                           const CUtensorMap& txr, const TcArgs& a) {
@@ -560,6 +591,36 @@ static void tc_blocks(int64_t m, int64_t& npad, int64_t& nblk, bool residual = f
         npad = 64;
         nblk = (m + 63) / 64;
     }
+}
+
+// The factor splits that tensor-core TTMs about to run will need, made in one
+// launch and entered in the call's split cache (c.split_cache must be on while
+// those TTMs run).  Factors already split are skipped.
+void tc_presplit(Ctx& c, const std::vector<TcSplitReq>& reqs) {
+    tc::SplitBatch sb;
+    int nj_ = 0;
+    int64_t most = 0;
+    for (const TcSplitReq& q : reqs) {
+        int64_t npad, nblk;
+        tc_blocks(q.m, npad, nblk, q.residual);
+        const int64_t ldo = (q.nj + 3) / 4 * 4, rows_b = npad * nblk;
+        bool have = false;
+        for (const Ctx::Split& e : c.splits)
+            have = have || (e.p == q.M.p && e.dt == (int)q.M.dt && e.ld == q.M.ld && e.mtrans == (q.mtrans ? 1 : 0) &&
+                            e.nj == q.nj && e.m == q.m && e.npad == npad && e.rows == rows_b);
+        if (have || nj_ == tc::kMaxSplitJobs) continue;
+        float* hi = c.alloc<float>(ldo * rows_b);
+        float* lo = c.alloc<float>(ldo * rows_b);
+        c.splits.push_back({q.M.p, q.M.ld, q.nj, q.m, npad, rows_b, (int)q.M.dt, q.mtrans ? 1 : 0, hi, lo});
+        sb.job[nj_++] = {q.M.p, (int)q.M.dt, q.mtrans ? 1 : 0, q.M.ld, q.nj, q.m, rows_b, ldo, hi, lo};
+        most = std::max(most, ldo * rows_b);
+    }
+    if (!c.exec || nj_ == 0) return;
+    ProfScope ps(c, "elementwise", 16.0 * most * nj_, 0.0);
+    tc::split_tf32_batch_kernel<<<dim3((unsigned)std::min<int64_t>((most + 255) / 256, 1024), (unsigned)nj_), 256, 0,
+                                  c.stream>>>(sb);
+    c.counted();
+    c.check_launch();
 }
 
 bool ttm_tc_eligible(const Tens& X, int j, int64_t m, tk_dtype out_dt) {
