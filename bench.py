@@ -712,6 +712,10 @@ def main():
     ap.add_argument("--serial", action="store_true", help="run both algorithms on one stream")
     ap.add_argument("--priority", choices=["none", "rhkron", "rsthkron"], default="none",
                     help="which algorithm's stream gets the higher CUDA stream priority")
+    ap.add_argument("--h2d-chunks", type=int, default=1,
+                    help="pieces (copy streams) of the end-to-end run's host-to-device copy of X")
+    ap.add_argument("--sm-reserve", type=int, default=16,
+                    help="SMs the streaming kernels of each stream leave to the other stream's kernels")
     ap.add_argument("--sharded", action="store_true",
                     help="one rHKron-re decomposition of the 512^3 field split along mode 3, one slab per rank")
     ap.add_argument("--no-graph", action="store_true",
@@ -778,6 +782,12 @@ def main():
     sa = torch.cuda.Stream(dev, priority=pa) if not args.serial else main_s
     sb = torch.cuda.Stream(dev, priority=pb) if not args.serial else main_s
     use_graph = not args.no_graph and not args.serial
+    # the two algorithms' streams run concurrently: each one's passes over X leave SMs to the other's
+    # chains of small kernels (one stream: every SM)
+    reserve = args.sm_reserve if sa is not sb else 0
+    for st in {sa, sb}:
+        with torch.cuda.stream(st):
+            T.tk_set_sm_reserve(reserve, dev)
 
     def step(Xin, marks=None):
         main_s = torch.cuda.current_stream(dev)  # the recording stream when the step is captured
@@ -875,9 +885,24 @@ def main():
     # step i's compute) and reads its results back (G, U, dG, dU and the two relative errors)
     Xh = X.detach().permute(2, 1, 0).contiguous().cpu().pin_memory()
     Xd = [torch.empty_like(X.permute(2, 1, 0).contiguous()) for _ in range(2)]
-    cs = torch.cuda.Stream(dev)
-    copied = [torch.cuda.Event() for _ in range(2)]
+    # the host-to-device copy of a step's X in args.h2d_chunks pieces, each on its own copy stream (one
+    # cudaMemcpyAsync per piece), so that several copy engines share it
+    nch = max(1, args.h2d_chunks)
+    css = [torch.cuda.Stream(dev) for _ in range(nch)]
+    hflat = Xh.view(-1)
+    bounds = [(hflat.numel() * q // nch, hflat.numel() * (q + 1) // nch) for q in range(nch)]
+    copied = [[torch.cuda.Event() for _ in range(nch)] for _ in range(2)]
     consumed = [torch.cuda.Event() for _ in range(2)]
+
+    def copy_in(b, after=None):
+        dflat = Xd[b].view(-1)
+        for q, cs in enumerate(css):
+            with torch.cuda.stream(cs):
+                if after is not None:
+                    cs.wait_event(after)
+                dflat[bounds[q][0]:bounds[q][1]].copy_(hflat[bounds[q][0]:bounds[q][1]], non_blocking=True)
+                copied[b][q].record(cs)
+
     res_bytes = 0
     for b in range(2):
         Xd[b].copy_(Xh)
@@ -887,20 +912,16 @@ def main():
     barrier(dist)
     torch.cuda.synchronize()
     e0.record()
-    cs.wait_stream(main_s)
-    with torch.cuda.stream(cs):
-        Xd[0].copy_(Xh, non_blocking=True)
-        copied[0].record(cs)
+    for cs in css:
+        cs.wait_stream(main_s)
+    copy_in(0)
     hosts = []
     for i in range(args.steps):
         b = i & 1
         if i + 1 < args.steps:
-            with torch.cuda.stream(cs):
-                if i >= 1:
-                    cs.wait_event(consumed[1 - b])  # step i-1 has finished with that buffer
-                Xd[1 - b].copy_(Xh, non_blocking=True)
-                copied[1 - b].record(cs)
-        main_s.wait_event(copied[b])
+            copy_in(1 - b, consumed[1 - b] if i >= 1 else None)  # after step i-1 has finished with that buffer
+        for q in range(nch):
+            main_s.wait_event(copied[b][q])
         if gE is not None:
             gE[b].replay()
             out = gE[b].outputs
@@ -945,7 +966,8 @@ def main():
                     parallelism=("replicas" if world > 1 else "single GPU"),
                     streams=("one stream" if args.serial else
                              "rHKron-re + its loss gradient (dG, dU, dX) on one stream, rSTHKron on a second, "
-                             "concurrently"),
+                             "concurrently; the streaming kernels of each leave %d SMs to the other's kernels "
+                             "(tk_set_sm_reserve)" % reserve),
                     gradient=("rHKron-re and the gradient at its result in one call (tucker_rhkron_grad): the "
                               "gradient's products R x_{j!=n} U_j^T come from the core's chain of TTMs (one X "
                               "pass instead of two), and rHKron-re's relative error from the norms of the pass "
@@ -986,7 +1008,8 @@ def main():
         kernel_ms_per_step=step_ms_total,
         e2e=dict(value=e2e_ms, unit="ms", h2d_bytes_per_step=Xh.numel() * Xh.element_size(),
                  d2h_bytes_per_step=res_bytes,
-                 note="X copied from pinned host memory every step on a copy stream into two device buffers "
+                 note=("X copied from pinned host memory every step (%d piece(s), one copy stream each) into two "
+                       "device buffers " % nch) +
                       "(step i+1's copy overlaps step i's compute); G, U, dG, dU and rel_err read back every step"
                       + ("; one recorded graph per input buffer, replayed" if gE is not None else "")),
         gpu_launches=launches,

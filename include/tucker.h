@@ -135,6 +135,13 @@ TK_API tk_status tk_create(tk_handle** h, void* cuda_stream);
 TK_API tk_status tk_destroy(tk_handle* h);
 /* Rebind the handle to another stream. */
 TK_API tk_status tk_set_stream(tk_handle* h, void* cuda_stream);
+/* The persistent streaming kernels of this handle's calls (the passes over X
+ * and the other tensor-core and narrow TTMs, one CTA per SM) leave `sms` SMs
+ * free, so that kernels queued on other streams (another decomposition's
+ * chains of small, latency-bound kernels) find SMs while a pass runs instead
+ * of waiting for its end.  0 (default): every SM.  TK_ERR_ARG unless
+ * 0 <= sms < the SM count.  Results do not depend on it. */
+TK_API tk_status tk_set_sm_reserve(tk_handle* h, int sms);
 /* Message of the last failing call on this handle ("" if none).  The string
  * is owned by the handle and valid until the next call. */
 TK_API const char* tk_last_error(const tk_handle* h);

@@ -8,6 +8,7 @@
 #include <numeric>
 
 #include "tk_internal.cuh"
+#include "tk_tc_common.cuh"
 
 namespace tk {
 
@@ -591,7 +592,7 @@ static void residual_pass(Ctx& c, const Tens& X, const Tens& G, const std::vecto
     Tens W = G;
     for (int i : order) W = ttm_to(c, W, i, U[i], true, acc);
     if (fused) {
-        const int nb = tc_num_ctas(W, f, m, true);
+        const int nb = tc_num_ctas(c, W, f, m, true);
         double* part = c.alloc<double>(2 * nb);
         launch_ttm_tc_residual(c, W, f, U[f], true, m, X.p, X.dt, dx, (float)alpha, part,
                                X.dt == TK_FP8_E4M3 ? 1.f / X.scale : 1.f);
@@ -653,6 +654,7 @@ static tk_status run_call(tk_handle* h, F&& body) {
         plan.stream = h->stream;
         plan.exec = false;
         plan.use_tc = h->use_tc;
+        plan.grid_sms = h->sm_reserve > 0 ? std::max(1, tc::num_sms() - h->sm_reserve) : 0;
         plan.capturing = capturing;
         body(plan);
         size_t need = plan.used + 512;
@@ -688,6 +690,7 @@ static tk_status run_call(tk_handle* h, F&& body) {
         ex.launches = &h->launches;
         ex.prof = &h->prof;
         ex.use_tc = h->use_tc;
+        ex.grid_sms = plan.grid_sms;
         for (int i = 0; i < Ctx::kAux; ++i) {
             ex.aux[i] = h->aux[i];
             ex.ev_join[i] = h->ev_join[i];
@@ -852,6 +855,16 @@ tk_status tk_graph_release(tk_handle* h) {
 tk_status tk_set_stream(tk_handle* h, void* stream) {
     if (!h) return TK_ERR_ARG;
     h->stream = (cudaStream_t)stream;
+    return TK_OK;
+}
+
+tk_status tk_set_sm_reserve(tk_handle* h, int sms) {
+    if (!h) return TK_ERR_ARG;
+    if (sms < 0 || sms >= tk::tc::num_sms()) {
+        h->last_error = "tk_set_sm_reserve: need 0 <= sms < the SM count";
+        return TK_ERR_ARG;
+    }
+    h->sm_reserve = sms;
     return TK_OK;
 }
 

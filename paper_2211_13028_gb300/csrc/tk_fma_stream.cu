@@ -287,7 +287,7 @@ void launch_ttm_narrow(const Ctx& c, const Tens& X, int j, const Mat& M, bool mt
     const size_t smem = tc::fs_smem(a.nk);
     const char* name = (const void*)X.p == c.xdata ? "xpass_narrow" : "ttm_narrow";
     ProfScope ps(c, name, 4.0 * (double)L * nj * R + 4.0 * (double)L * m * R + 4.0 * nj * m, 2.0 * L * nj * R * m);
-    const int grid = (int)std::min<int64_t>(a.ntiles, tc::num_sms());
+    const int grid = (int)std::min<int64_t>(a.ntiles, tc::grid_sms(c));
     auto run = [&](auto kern) {
         TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<grid, tc::FS_THREADS, smem, c.stream>>>(tx, a);

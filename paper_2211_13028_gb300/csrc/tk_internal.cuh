@@ -153,6 +153,7 @@ struct Ctx {
     const void* xdata = nullptr;   // the caller's data tensor (tags its full passes)
     int64_t xnumel = 0;
     bool use_tc = true;            // tensor-core TTM where eligible
+    int grid_sms = 0;              // CTAs of the persistent streaming kernels (0: every SM)
     bool capturing = false;        // the stream is recording a CUDA graph (launches are not run now)
     bool df64 = false;             // FP32-class data: FP64 products may run in double-float arithmetic
     // Factor splits (TF32 hi / lo) made in this pass, reused while split_cache is
@@ -357,7 +358,7 @@ void launch_ttm_bf16(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, in
 // xref (F32, BF16, or FP8 for the norms only) is read as stored value * xr_scale.
 void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const void* xref,
                             tk_dtype xrdt, void* dx, float alpha, double* partials, float xr_scale = 1.f);
-int tc_num_ctas(const Tens& X, int j, int64_t m, bool residual);
+int tc_num_ctas(const Ctx& c, const Tens& X, int j, int64_t m, bool residual);
 bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m);
 // One warp waits with the tcgen05 kernels' bounded wait on an mbarrier that
 // nothing arrives at (limit_ns), which raises FLAG_TIMEOUT; *waited (device)
@@ -474,6 +475,7 @@ struct tk_handle {
     int64_t launches = 0;
     tk::Profiler prof;
     bool use_tc = true;  // TUCKER_TTM=simt selects the SIMT TTM kernels instead
+    int sm_reserve = 0;  // SMs the persistent streaming kernels leave free (tk_set_sm_reserve)
     // pinned ring for host scalar outputs delivered by stream-ordered callbacks
     static constexpr int kHostSlots = 64;
     struct HostSlot {

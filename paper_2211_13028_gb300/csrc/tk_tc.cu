@@ -551,7 +551,7 @@ static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap
         TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::kSmem));
         attr_set = true;
     }
-    int grid = (int)std::min<int64_t>(a.ntiles * a.nblk, num_sms());
+    int grid = (int)std::min<int64_t>(a.ntiles * a.nblk, grid_sms(c));
     kern<<<grid, Warps<EPI>::kThreads, Cf::kSmem, c.stream>>>(tx, th, tl, txr, a);
 }
 
@@ -765,12 +765,12 @@ void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int6
     ttm_tc_run(c, X, j, M, mtrans, m, out, 0, nullptr, TK_F32, 0.f, nullptr, name);
 }
 
-int tc_num_ctas(const Tens& X, int j, int64_t m, bool residual) {
+int tc_num_ctas(const Ctx& c, const Tens& X, int j, int64_t m, bool residual) {
     int64_t npad, nblk;
     tc_blocks(m, npad, nblk, residual);
     const int64_t L = X.left(j), R = X.right(j);
     const int64_t tiles = (L == 1) ? (R + tc::kRows - 1) / tc::kRows : R * ((L + tc::kRows - 1) / tc::kRows);
-    return (int)std::min<int64_t>(tiles * nblk, tc::num_sms());
+    return (int)std::min<int64_t>(tiles * nblk, tc::grid_sms(c));
 }
 
 bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m) {

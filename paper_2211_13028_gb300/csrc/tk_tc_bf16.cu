@@ -304,7 +304,7 @@ static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap
         TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::kSmem));
         attr_set = true;
     }
-    const int grid = (int)std::min<int64_t>(a.ntiles * a.nblk, tc::num_sms());
+    const int grid = (int)std::min<int64_t>(a.ntiles * a.nblk, tc::grid_sms(c));
     kern<<<grid, kThreads, Cf::kSmem, c.stream>>>(tx, tb, a);
 }
 

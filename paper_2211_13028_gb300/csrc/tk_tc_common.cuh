@@ -164,5 +164,9 @@ inline int num_sms() {
     return n;
 }
 
+// CTAs of a persistent streaming kernel: one per SM, minus the SMs the call's
+// handle leaves to other streams (tk_set_sm_reserve).
+inline int grid_sms(const Ctx& c) { return c.grid_sms > 0 ? c.grid_sms : num_sms(); }
+
 }  // namespace tc
 }  // namespace tk

@@ -26,7 +26,7 @@ __all__ = [
     "tucker_subranks_reuse", "tucker_subranks_matrix",
     "tucker_sketch", "tucker_orth", "tucker_orth_noalloc", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward", "tucker_rhkron_grad",
-    "tk_sync_status", "tk_selftest_bounded_wait", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
+    "tk_sync_status", "tk_selftest_bounded_wait", "tk_set_sm_reserve", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
     "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tucker_rhkron_srht", "tk_graph_release",
     "tk_philox4x32", "tucker_gaussian_factor", "tucker_gaussian_factors", "gaussian_factors",
     "gaussian_factors_matrix", "rsthkron_factor_plan",
@@ -123,6 +123,7 @@ def load():
             "tucker_orth_noalloc": ([vp, P(TkMatrix), P(TkMatrix), P(ctypes.c_int)], ctypes.c_int),
             "tucker_rhkron": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor), P(TkMatrix),
                                P(ctypes.c_double)], ctypes.c_int),
+            "tk_set_sm_reserve": ([vp, ctypes.c_int], ctypes.c_int),
             "tucker_rhkron_grad": ([vp, P(TkTensor), i64p, ctypes.c_int, P(TkMatrix), P(TkOpts), P(TkTensor),
                                     P(TkMatrix), P(ctypes.c_double), ctypes.c_double, P(TkTensor), P(TkMatrix),
                                     P(TkTensor)], ctypes.c_int),
@@ -343,6 +344,14 @@ class TuckerGraph:
 
     def replay(self) -> None:
         self.graph.replay()
+
+
+def tk_set_sm_reserve(sms: int, device=None) -> None:
+    """The streaming kernels of calls queued on the current stream of ``device`` leave ``sms`` SMs free
+    for kernels of other streams (0: every SM); results do not depend on it."""
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    h = _handle(dev)
+    _check(load().tk_set_sm_reserve(h, int(sms)), h)
 
 
 def tk_profile(enable: bool, device=None, only: Optional[str] = None) -> None:

@@ -128,3 +128,28 @@ def test_backward_norms_give_the_decompositions_relative_error(dev, dtype):
     assert max(vals) - min(vals) <= 1e-12 * max(vals)
     with pytest.raises(T.TuckerError):  # wrong dtype
         T.tucker_reconstruct_backward(X, G, U, 0.5, norms2=torch.zeros(2, dtype=torch.float32, device=dev))
+
+
+def test_sm_reserve_leaves_results_unchanged(dev):
+    # the streaming kernels on fewer CTAs (SMs left to other streams): the same products element by
+    # element; only the order of the residual's per-CTA partial sums changes
+    dims, r, p = (128, 96, 160), (12, 10, 9), 5
+    core = synth.decaying_core((20, 20, 20), 0.7, seed=47)
+    x = synth.tucker_tensor(dims, (20, 20, 20), seed=48, noise_rel=1e-3, core=core)
+    X, xv, _ = make_X(x, "f32", dev)
+    s = O.subranks_reuse(r, p)[0]
+    om = mats(synth.sketch_factors_reuse(dims, s, seed=49, dtype="f32"), "f32", dev)
+    G0, U0, e0 = T.tucker_rhkron(X, r, p, om)
+    try:
+        for sms in (1, 24, 100):
+            T.tk_set_sm_reserve(sms, dev)
+            G1, U1, e1 = T.tucker_rhkron(X, r, p, om)
+            assert torch.equal(G0, G1) and all(torch.equal(a, b) for a, b in zip(U0, U1)), sms
+            assert abs(e1 - e0) <= 1e-12 * e0, sms
+        with pytest.raises(T.TuckerError):
+            T.tk_set_sm_reserve(-1, dev)
+        with pytest.raises(T.TuckerError):
+            T.tk_set_sm_reserve(100000, dev)
+    finally:
+        T.tk_set_sm_reserve(0, dev)
+    assert T.tk_sync_status(dev)[0] == 0
