@@ -188,6 +188,24 @@ typedef struct {
 TK_API tk_status tk_profile(tk_handle* h, int enable);
 TK_API tk_status tk_profile_only(tk_handle* h, const char* prefix);
 TK_API int tk_profile_read(tk_handle* h, tk_prof_entry* out, int max);
+/* The same records one by one, in the order they were queued: class name,
+ * launching stream (0: the handle's stream, 1..4: its auxiliary streams),
+ * start and end in microseconds after the latest tk_profile(., 1) on the
+ * device (any handle; the origin event is recorded on that handle's stream),
+ * algorithmic bytes and flops.  Synchronises the handle's streams, fills up
+ * to max entries, returns the number of records (-1 on error) and clears
+ * them, like tk_profile_read; with out == NULL it only returns the number of
+ * records and keeps them. */
+typedef struct {
+    char name[32];
+    int stream;
+    int reserved;
+    double start_us;
+    double end_us;
+    double bytes;
+    double flops;
+} tk_trace_entry;
+TK_API int tk_profile_trace(tk_handle* h, tk_trace_entry* out, int max);
 
 /* ---- host-side integer planning (no device work; h may be NULL) -------- */
 

@@ -5,6 +5,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <numeric>
 
 #include "tk_internal.cuh"
@@ -28,7 +30,7 @@ cudaEvent_t Profiler::get() {
 ProfScope::ProfScope(const Ctx& ctx, const char* name, double bytes, double flops) : c(ctx) {
     if (!c.exec || c.capturing || !c.prof || !c.prof->on) return;
     if (!c.prof->only.empty() && strncmp(name, c.prof->only.c_str(), c.prof->only.size()) != 0) return;
-    ProfRec r{name, c.prof->get(), c.prof->get(), bytes, flops};
+    ProfRec r{name, c.prof->get(), c.prof->get(), bytes, flops, c.stream};
     TK_CUDA(cudaEventRecord(r.a, c.stream));
     c.prof->recs.push_back(r);
     rec = &c.prof->recs.back();
@@ -918,6 +920,9 @@ tk_status tk_selftest_bounded_wait(tk_handle* h, int64_t limit_ns, int64_t* wait
     return TK_OK;
 }
 
+static std::mutex g_origin_mu;
+static std::map<int, cudaEvent_t> g_origin;  // per device: recorded by the latest tk_profile(h, 1)
+
 tk_status tk_profile(tk_handle* h, int enable) {
     if (!h) return TK_ERR_ARG;
     if (enable) {
@@ -939,6 +944,15 @@ tk_status tk_profile(tk_handle* h, int enable) {
         }
     }
     h->prof.on = enable != 0;
+    if (enable) {  // the time origin of tk_profile_trace, shared by the device's handles
+        std::lock_guard<std::mutex> lk(g_origin_mu);
+        cudaEvent_t& o = g_origin[h->device];
+        if (!o && cudaEventCreate(&o) != cudaSuccess) {
+            cudaGetLastError();
+            o = nullptr;
+        }
+        if (o) cudaEventRecord(o, h->stream);
+    }
     return TK_OK;
 }
 
@@ -975,6 +989,46 @@ int tk_profile_read(tk_handle* h, tk_prof_entry* out, int max) {
     int n = (int)std::min<size_t>(acc.size(), (size_t)std::max(0, max));
     for (int i = 0; i < n; ++i) out[i] = acc[i];
     return (int)acc.size();
+}
+
+int tk_profile_trace(tk_handle* h, tk_trace_entry* out, int max) {
+    if (!h) return -1;
+    if (!out) return (int)h->prof.recs.size();  // count only; the records stay
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return -1;
+    for (auto s : h->aux)
+        if (s && cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    cudaEvent_t o = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_origin_mu);
+        auto it = g_origin.find(h->device);
+        if (it != g_origin.end()) o = it->second;
+    }
+    int n = 0;
+    for (auto& r : h->prof.recs) {
+        if (n < max) {
+            tk_trace_entry e;
+            memset(&e, 0, sizeof(e));
+            strncpy(e.name, r.name, sizeof(e.name) - 1);
+            e.stream = -1;
+            if (r.st == h->stream) e.stream = 0;
+            for (int i = 0; i < tk::Ctx::kAux; ++i)
+                if (r.st == h->aux[i]) e.stream = 1 + i;
+            float a = 0.f, b = 0.f;
+            if (!o || cudaEventElapsedTime(&a, o, r.a) != cudaSuccess) a = 0.f;
+            if (!o || cudaEventElapsedTime(&b, o, r.b) != cudaSuccess) b = a;
+            cudaGetLastError();
+            e.start_us = 1e3 * (double)a;
+            e.end_us = 1e3 * (double)b;
+            e.bytes = r.bytes;
+            e.flops = r.flops;
+            out[n] = e;
+        }
+        ++n;
+        h->prof.pool.push_back(r.a);
+        h->prof.pool.push_back(r.b);
+    }
+    h->prof.recs.clear();
+    return n;
 }
 
 int64_t tk_workspace_bytes(const tk_handle* h) { return h ? (int64_t)h->ws_bytes : 0; }
@@ -1418,10 +1472,26 @@ static void check_outputs(const Tens& X, const int64_t* r, const tk_tensor* G, c
 // What the gradient of the loss at the result can reuse: the core's chain of
 // products (chain[t] = X x_{modes[0..t]} Q^T, in the order applied), the
 // factors V_j (k_j x r_j, FP64, ld k_j) and the column signs of U_j.
+// With want_T the call also forms T = X x_{j != m_1} Q_j^T (m_1: the chain's
+// first mode, the one product of the gradient the chain does not hold) on the
+// side stream while the core is truncated, on a fraction of the SMs; Tapplied
+// marks the modes T has applied.
 struct CoreTrace {
     std::vector<std::pair<int, Tens>> chain;
     std::vector<double*> V, sg;
+    bool want_T = false;
+    Tens T;
+    std::vector<char> Tapplied;
 };
+
+// SMs for a streaming pass that runs beside a latency-bound chain of small
+// kernels and has that chain's length to finish in: two thirds of the call's
+// (measured on the 512^3 benchmark step: a third starves the pass, all of them
+// starve the chain).
+static int background_grid(const Ctx& c) {
+    const int full = c.grid_sms > 0 ? c.grid_sms : tc::num_sms();
+    return std::max(8, 2 * full / 3);
+}
 
 static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, const std::vector<int64_t>& k,
                                  const int64_t* r, const Opts& o, const Tens& Gt, const std::vector<Mat>& Um,
@@ -1462,11 +1532,33 @@ static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, c
     for (int j = 0; j < d; ++j)
         if (k[j] < Xt.n[j]) cm.push_back(j);
     Tens Gh = cm.empty() ? Xt : multi_ttm(c, Xt, cm, Qa.data(), false, acc, nullptr, tr ? &tr->chain : nullptr);
-    Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
     // 4. STHOSVD of the core in FP64, U_j = Q_j V_j, gauge, casts, error
     std::vector<double*> V;
-    Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
-    finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, errd, tr ? &tr->sg : nullptr);
+    auto truncate = [&]() {
+        Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
+        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
+        finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, errd, tr ? &tr->sg : nullptr);
+    };
+    std::vector<int> tm;
+    if (tr && tr->want_T && !tr->chain.empty())
+        for (int j : cm)
+            if (j != tr->chain[0].first) tm.push_back(j);
+    if (tm.empty()) {
+        truncate();
+    } else {
+        c.side(truncate, [&]() {
+            // the side stream's pass leaves most SMs to the truncation's kernels; the splits it makes
+            // are its own (the main stream must not find them in the cache)
+            const int keep = c.grid_sms;
+            const size_t ns = c.splits.size();
+            c.grid_sms = background_grid(c);
+            tr->T = multi_ttm(c, Xt, tm, Qa.data(), false, acc);
+            c.grid_sms = keep;
+            c.splits.resize(ns);
+            tr->Tapplied.assign(d, 0);
+            for (int j : tm) tr->Tapplied[j] = 1;
+        });
+    }
     if (tr) tr->V = V;
 }
 
@@ -1982,13 +2074,15 @@ tk_status tucker_rhkron_grad(tk_handle* h, const tk_tensor* X, const int64_t* r,
             all_modes(c, Xt, need, rest, Om.data(), acc, Y, nullptr);
         }
         CoreTrace tr;
+        tr.want_T = dG || dU;
         rhkron_from_sketches(c, Xt, Y, k, r, o, Gt, Um, nullptr, &tr);
         // 5. the gradient at the result (G, U).  U_j = Q_j V_j' (V_j' = V_j with U_j's column signs), so
         // for the core's chain C_t = X x_{m_1..m_t} Q^T (m_1, m_2, .. the modes in the order applied)
         //   S_n = X x_{j!=n} U_j^T = C_t x_{j in m_1..m_t} V_j'^T x_{other j != n} U_j^T,
-        // C_t the last product in which mode n is still whole.  Only S_{m_1} reads X itself; the other
-        // S_n read the much smaller products.  The residual pass (dX, and the norms of the relative
-        // error) runs beside it on the side stream.
+        // C_t the last product in which mode n is still whole.  S_{m_1} = T x_{j != m_1} V_j'^T with
+        // T = X x_{j != m_1} Q_j^T, the one further pass over X, made beside the truncation (it needs
+        // only the Q_j); the other S_n read the much smaller products of the chain.  The residual pass
+        // (dX, and the norms of the relative error) runs beside them on the side stream.
         std::vector<Mat> Ua(d);
         for (int j = 0; j < d; ++j) Ua[j] = Um[j].dt == acc ? Um[j] : mat_to(c, Um[j], acc);
         Tens Ga = Gt.dt == acc ? Gt : tens_to(c, Gt, acc);
@@ -2017,10 +2111,15 @@ tk_status tucker_rhkron_grad(tk_handle* h, const tk_tensor* X, const int64_t* r,
                 c.fork(d, [&](int m) {
                     Tens C = Xt;
                     std::vector<char> applied(d, 0);
-                    for (const auto& st : tr.chain) {
-                        if (st.first == m) break;
-                        C = st.second;
-                        applied[st.first] = 1;
+                    if (tr.T.p && m == tr.chain[0].first) {  // formed beside the truncation
+                        C = tr.T;
+                        applied = tr.Tapplied;
+                    } else {
+                        for (const auto& st : tr.chain) {
+                            if (st.first == m) break;
+                            C = st.second;
+                            applied[st.first] = 1;
+                        }
                     }
                     std::vector<Mat> M(d);
                     std::vector<int> modes;
@@ -2034,9 +2133,13 @@ tk_status tucker_rhkron_grad(tk_handle* h, const tk_tensor* X, const int64_t* r,
                 grad_from_sketches(c, Gt, Um, Ua, n, S, acc, grad_scale, dG != nullptr, dU != nullptr, g);
             },
             [&]() {
-                if (want_res)
-                    residual_pass(c, Xt, Ga, Ua, acc, errd, dX ? g.dX.p : nullptr, dX ? g.dX.dt : TK_F32,
-                                  2.0 * grad_scale);
+                if (!want_res) return;
+                // the pass has the gradient's chain of small kernels to finish in: it leaves them SMs
+                const int keep = c.grid_sms;
+                if (dG || dU) c.grid_sms = background_grid(c);
+                residual_pass(c, Xt, Ga, Ua, acc, errd, dX ? g.dX.p : nullptr, dX ? g.dX.dt : TK_F32,
+                              2.0 * grad_scale);
+                c.grid_sms = keep;
             });
         if (rel_err) read_err(h, c, errd, rel_err, false, o.async_outputs);
     });

@@ -123,6 +123,7 @@ struct ProfRec {
     const char* name;
     cudaEvent_t a, b;
     double bytes, flops;
+    cudaStream_t st;  // the launching stream (the handle's or one of its auxiliary streams)
 };
 struct Profiler {
     bool on = false;

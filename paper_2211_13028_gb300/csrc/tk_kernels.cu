@@ -531,7 +531,15 @@ __global__ void __launch_bounds__(256) ttm_direct_df_kernel(const double* __rest
     const double* x = X + l + L * nj * r;
     const float2* mc = msp + nj * a;
     float sh = 0.f, sl = 0.f;
-    for (int64_t i = 0; i < nj; ++i) df_dot_step(sh, sl, df_from_f64(x[L * i], 0), mc[i]);
+    int64_t i = 0;
+    for (; i + 8 <= nj; i += 8) {  // the eight loads issued before the products that use them
+        double xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xv[u] = x[L * (i + u)];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) df_dot_step(sh, sl, df_from_f64(xv[u], 0), mc[i + u]);
+    }
+    for (; i < nj; ++i) df_dot_step(sh, sl, df_from_f64(x[L * i], 0), mc[i]);
     out[o] = (double)sh + (double)sl;
 }
 

@@ -26,7 +26,7 @@ __all__ = [
     "tucker_subranks_reuse", "tucker_subranks_matrix",
     "tucker_sketch", "tucker_orth", "tucker_orth_noalloc", "tucker_core", "tucker_rhkron", "tucker_rsthkron",
     "tucker_reconstruct", "tucker_loss", "tucker_reconstruct_backward", "tucker_rhkron_grad",
-    "tk_sync_status", "tk_selftest_bounded_wait", "tk_set_sm_reserve", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "TuckerLoss",
+    "tk_sync_status", "tk_selftest_bounded_wait", "tk_set_sm_reserve", "tk_launch_count", "tk_workspace_bytes", "tk_profile", "tk_profile_read", "tk_profile_trace", "TuckerLoss",
     "library_path", "PendingScalar", "tucker_rhkron_noreuse", "tucker_rhkron_srht", "tk_graph_release",
     "tk_philox4x32", "tucker_gaussian_factor", "tucker_gaussian_factors", "gaussian_factors",
     "gaussian_factors_matrix", "rsthkron_factor_plan",
@@ -62,6 +62,12 @@ class TkMatrix(ctypes.Structure):
 class TkProfEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+class TkTraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("stream", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("start_us", ctypes.c_double), ("end_us", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("flops", ctypes.c_double)]
 
 
 class TkOpts(ctypes.Structure):
@@ -109,6 +115,7 @@ def load():
             "tk_profile": ([vp, ctypes.c_int], ctypes.c_int),
             "tk_profile_only": ([vp, ctypes.c_char_p], ctypes.c_int),
             "tk_profile_read": ([vp, P(TkProfEntry), ctypes.c_int], ctypes.c_int),
+            "tk_profile_trace": ([vp, P(TkTraceEntry), ctypes.c_int], ctypes.c_int),
             "tk_graph_release": ([vp], ctypes.c_int),
             "tk_philox4x32": ([vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, vp],
                               ctypes.c_int),
@@ -378,6 +385,25 @@ def tk_profile_read(device=None) -> Dict[str, dict]:
             e["ms"] += buf[i].ms
             e["bytes"] += buf[i].bytes
             e["flops"] += buf[i].flops
+    return out
+
+
+def tk_profile_trace(device=None) -> List[dict]:
+    """Synchronise and return every launch recorded since tk_profile(True), one dict per launch
+    (handle, stream, cls, start_us, end_us, bytes, flops), times after the latest tk_profile(True)
+    on the device, sorted by start time."""
+    out: List[dict] = []
+    for hi, h in enumerate(_device_handles(device)):
+        n = load().tk_profile_trace(h, None, 0)
+        if n < 0:
+            raise TuckerError(6, "tk_profile_trace failed")
+        buf = (TkTraceEntry * max(n, 1))()
+        n = load().tk_profile_trace(h, buf, n)
+        if n < 0:
+            raise TuckerError(6, "tk_profile_trace failed")
+        out.extend(dict(handle=hi, stream=e.stream, cls=e.name.decode(), start_us=e.start_us, end_us=e.end_us,
+                        bytes=e.bytes, flops=e.flops) for e in buf[:n])
+    out.sort(key=lambda e: e["start_us"])
     return out
 
 

@@ -153,3 +153,35 @@ def test_sm_reserve_leaves_results_unchanged(dev):
     finally:
         T.tk_set_sm_reserve(0, dev)
     assert T.tk_sync_status(dev)[0] == 0
+
+
+def test_profile_trace_lists_every_recorded_launch(dev):
+    # the per-launch records of two concurrent calls: one per launch the class totals count, each with
+    # its stream, ordered intervals after the common origin
+    X, r, p, om, oms = _setup(dev)
+    sa, sb = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    for _ in range(2):  # the second round is recorded
+        torch.cuda.synchronize()
+        with torch.cuda.stream(sa):
+            T.tk_profile(True, dev)
+        with torch.cuda.stream(sb):
+            T.tk_profile(True, dev)
+        sa.wait_stream(torch.cuda.current_stream(dev))
+        sb.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(sa):
+            T.tucker_rhkron(X, r, p, om, async_outputs=True)
+        with torch.cuda.stream(sb):
+            T.tucker_rsthkron(X, r, p, oms, async_outputs=True)
+        torch.cuda.synchronize()
+    n = [T.load().tk_profile_trace(h, None, 0) for h in T._device_handles(dev)]  # counts, records kept
+    assert min(n) >= 0
+    tr = T.tk_profile_trace(dev)
+    assert len(tr) == sum(n) > 20
+    assert T.tk_profile_trace(dev) == []  # consumed
+    assert [e["start_us"] for e in tr] == sorted(e["start_us"] for e in tr)
+    assert all(0.0 <= e["start_us"] <= e["end_us"] for e in tr)
+    assert all(-1 <= e["stream"] <= 4 for e in tr) and any(e["stream"] > 0 for e in tr)  # forked chains
+    cls = {e["cls"] for e in tr}
+    assert "jacobi" in cls and any(c.startswith("xpass") for c in cls)
+    for h in T._device_handles(dev):
+        T.load().tk_profile(h, 0)
