@@ -1938,8 +1938,6 @@ static void grad_from_sketches(Ctx& c, const Tens& Gt, const std::vector<Mat>& U
                                bool want_dG, bool want_dU, GradOut& g) {
     const int d = Gt.d;
     const double s2 = -2.0 * grad_scale;
-    std::vector<int> all(d);
-    std::iota(all.begin(), all.end(), 0);
     Tens G64 = Gt.dt == TK_F64 ? Gt : tens_to(c, Gt, TK_F64);
     std::vector<double*> U64(d);
     std::vector<Mat> Cm(d);
@@ -1955,8 +1953,13 @@ static void grad_from_sketches(Ctx& c, const Tens& Gt, const std::vector<Mat>& U
         Cm[j].cols = rj;
         Cm[j].ld = rj;
     });
-    std::vector<Tens> Pm(d);  // P_n = G x_{j != n} C_j
-    all_modes(c, G64, all, {}, Cm.data(), TK_F64, Pm, nullptr);
+    std::vector<Tens> Pm(d);  // P_n = G x_{j != n} C_j: one short chain per mode, side by side
+    c.fork(d, [&](int n) {
+        std::vector<int> modes;
+        for (int j = 0; j < d; ++j)
+            if (j != n) modes.push_back(j);
+        Pm[n] = multi_ttm(c, G64, modes, Cm.data(), false, TK_F64);
+    });
     // dU_n per mode and dG are independent: item j < d is dU_j, item d is dG
     const int ndu = want_dU ? d : 0;
     c.fork(ndu + (want_dG ? 1 : 0), [&](int j) {

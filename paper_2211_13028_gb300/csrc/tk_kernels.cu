@@ -254,8 +254,9 @@ static void ttm_dispatch(const Ctx& c, const Tx* X, int64_t L, int64_t nj, int64
     if constexpr (std::is_same<Tx, double>::value && std::is_same<Ta, double>::value) {
         if (c.df64 && ttm_direct_df(c, X, L, nj, R, M, ldm, mtrans, m, out)) return;
     }
-    if (L * m <= SLAB_THREADS && nj >= 32 && (double)sizeof(Ta) * (L * nj + SLAB_THREADS) <= 40 * 1024 &&
-        R <= 0x7fffffff) {
+    // (a slab of fewer than 256 elements leaves each CTA too little work: one thread per output then)
+    if (L * m <= SLAB_THREADS && nj >= 32 && L * nj >= 256 &&
+        (double)sizeof(Ta) * (L * nj + SLAB_THREADS) <= 40 * 1024 && R <= 0x7fffffff) {
         const int S = (int)std::min<int64_t>(16, SLAB_THREADS / (L * m));
         const size_t smem = sizeof(Ta) * (size_t)(L * nj + (int64_t)S * L * m);
         const char* name = (const void*)X == c.xdata ? "xpass_simt" : "ttm_simt";
