@@ -898,10 +898,8 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_inv_kernel(KDims kd, int km
 // a_ji / p_j, step j updates the trailing upper triangle a_il -= l_ij a_jl
 // (j < i <= l) and the unit lower M = L^{-1} by M(i, 0..j) -= l_ij M(j, 0..j);
 // then R = D^{1/2} L^T and R^{-1} = M^T D^{-1/2}, i.e. R^{-1}(a, b) =
-// M(b, a) / sqrt(p_b).  Row j is never rescaled, so one barrier per column
-// suffices: warps own whole rows (row-major storage, lanes along the row), and
-// lane 0 of warp 0, which owns row j+1 alone and updates a_{j+1,j+1} first,
-// turns it into the next pivot's 1/p and 1/sqrt(p) while the others finish.
+// M(b, a) / sqrt(p_b).  Row j is never rescaled, so warps can own whole rows
+// (row-major storage, lanes along the row).
 
 __device__ __forceinline__ float2 df_norm(float s, float t) {  // fast two-sum, |s| >= |t|
     const float h = __fadd_rn(s, t);
@@ -928,14 +926,16 @@ __device__ __forceinline__ float2 df_fnms2(float2 a, float2 f, float2 b) {
     return df_norm(s, __fadd_rn(t, __fsub_rn(a.y, e)));
 }
 
-// 1/p and 1/sqrt(p) of a positive double-float p: an FP32 seed and one
-// Newton step evaluated in double-float (error ~2^-46).
+// 1/p and 1/sqrt(p) of a positive double-float p: an FP32 seed (the fast
+// approximate reciprocal and square root, a few ulp) and one Newton step
+// evaluated in double-float, which squares the seed's relative error
+// (~2^-44, then limited by the double-float format).
 __device__ __forceinline__ void df_rcp_rsqrt(float2 p, float2& inv, float2& ys) {
-    const float q0 = __frcp_rn(p.x);
+    const float q0 = __fdividef(1.0f, p.x);
     float t = fmaf(-p.x, q0, 1.0f);
     t = fmaf(-p.y, q0, t);
     inv = df_norm(q0, __fmul_rn(q0, t));
-    const float y0 = __frsqrt_rn(p.x);
+    const float y0 = rsqrtf(p.x);
     const float a = __fmul_rn(y0, y0);
     const float2 y2 = make_float2(a, fmaf(y0, y0, -a));  // y0^2 exactly
     const float2 py = df_mul2(p, y2);
@@ -943,47 +943,26 @@ __device__ __forceinline__ void df_rcp_rsqrt(float2 p, float2& inv, float2& ys) 
     ys = df_norm(y0, __fmul_rn(__fmul_rn(0.5f, y0), d));
 }
 
-// One row of a column step: A(i, i..k-1) followed by M(i, 0..j), NQ 32-wide
-// slices (the last one partial), all loaded before any is updated.  Returns
-// the lane's first updated value (lane 0: A(i, i)).
-template <int NQ>
-__device__ __forceinline__ float2 chdf_row(float2* A, float2* M, const float2* Aj, const float2* Mj, int k, int i,
-                                           int j, float2 f, int lane) {
-    const int na = k - i, len = na + j + 1;
-    float2* dst[NQ];
-    float2 x[NQ], y[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const int t = lane + 32 * q;
-        const bool inA = t < na;
-        dst[q] = inA ? A + (size_t)i * k + i + t : M + (size_t)i * k + (t - na);
-        const float2* src = inA ? Aj + i + t : Mj + (t - na);
-        if (t < len) {
-            x[q] = *dst[q];
-            y[q] = *src;
-        }
-    }
-    float2 v0 = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        if (lane + 32 * q < len) {
-            const float2 v = df_fnms2(x[q], f, y[q]);
-            *dst[q] = v;
-            if (q == 0) v0 = v;
-        }
-    }
-    return v0;
-}
-
 constexpr int CHDF_THREADS = 768;
+constexpr int CHDF_PANEL = 8;  // columns per panel (warps 0 .. CHDF_PANEL-1 own its rows)
 
+// Blocked over panels of CHDF_PANEL columns.  Within a panel, warp w owns row
+// j0 + w: at step j every warp whose row lies below j reads the pivot p_j
+// (final: row j was last updated at step j - 1), forms 1/p_j itself, its
+// multiplier l_ij and updates its row of A and of M; the panel's warps meet at
+// a named barrier per column.  The rows below the panel then take the panel's
+// updates in one pass, a_il -= sum_j l_ij a_jl and M(i, .) -= sum_j l_ij M(j, .),
+// in the same order of j as the column-by-column form, so every entry sees the
+// same operations on the same values (the result is that form's, bit for
+// bit) with two CTA barriers per panel instead of one per column.
 __global__ void __launch_bounds__(CHDF_THREADS) chol_inv_df_kernel(KDims kd, int kmax, const double* W,
                                                                    double* Rinv, int* bad, double tol) {
     extern __shared__ float2 sf[];  // A: k x k row-major (upper part), M: k x k row-major (lower part)
     __shared__ float2 s_ys[112];    // 1 / sqrt(p_j)
-    __shared__ float2 s_inv[2];     // 1 / p_j, double-buffered by column parity
+    __shared__ float2 s_inv[CHDF_PANEL];         // 1 / p_j of the panel's columns
+    __shared__ float2 s_l[CHDF_PANEL][112];      // l_ij of the panel's columns for the rows below the panel
     __shared__ float s_dg[112];     // scaled original diagonal (breakdown test)
-    __shared__ int s_ok[113];       // s_ok[j]: pivot j accepted
+    __shared__ int s_fail;
     __shared__ int s_e;
     const int b = blockIdx.x;
     if (bad[b]) return;
@@ -992,7 +971,7 @@ __global__ void __launch_bounds__(CHDF_THREADS) chol_inv_df_kernel(KDims kd, int
     float2* M = sf + (size_t)k * k;
     const double* Wb = W + (int64_t)b * kmax * kmax;
     double* Rb = Rinv + (int64_t)b * kmax * kmax;
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     if (warp == 0) {
         double m = 0.0;
         for (int i = lane; i < k; i += 32) m = fmax(m, Wb[i + (int64_t)kmax * i]);
@@ -1004,6 +983,7 @@ __global__ void __launch_bounds__(CHDF_THREADS) chol_inv_df_kernel(KDims kd, int
                 e = (be >= 0 ? be : be - 1) / 2;
             }
             s_e = e;
+            s_fail = 0;
         }
     }
     __syncthreads();
@@ -1013,57 +993,64 @@ __global__ void __launch_bounds__(CHDF_THREADS) chol_inv_df_kernel(KDims kd, int
         A[idx] = l >= i ? df_from_f64(Wb[i + (int64_t)kmax * l], 2 * e) : make_float2(0.f, 0.f);
         M[idx] = make_float2(i == l ? 1.f : 0.f, 0.f);
     }
-    for (int i = tid; i < k; i += nt) {
-        s_dg[i] = df_from_f64(Wb[i + (int64_t)kmax * i], 2 * e).x;
-        s_ok[i] = 0;
-    }
+    for (int i = tid; i < k; i += nt) s_dg[i] = df_from_f64(Wb[i + (int64_t)kmax * i], 2 * e).x;
     __syncthreads();
-    if (tid == 0) {
-        const float2 p = A[0];
-        const bool ok = p.x > (float)tol * s_dg[0] && p.x > 0.f;
-        s_ok[0] = ok;
-        if (ok) {
-            float2 inv, ys;
-            df_rcp_rsqrt(p, inv, ys);
-            s_inv[0] = inv;
-            s_ys[0] = ys;
-        }
-    }
-    __syncthreads();
-    for (int j = 0; j + 1 < k; ++j) {
-        if (!s_ok[j]) break;  // uniform: written before the last barrier
-        const float2 inv = s_inv[j & 1];
-        const float2* Aj = A + (size_t)j * k;
-        const float2* Mj = M + (size_t)j * k;
-        // warp 0 takes row j + 1 alone (its first element is the next pivot);
-        // warps 1 .. nw-1 share rows j + 2 .. k - 1, one pass per row
-        const int i0 = j + 1 + warp, di = warp == 0 ? k : nw - 1;
-        for (int i = i0; i < k; i += di) {
-            const float2 f = df_mul2(Aj[i], inv);  // l_ij
-            const int nq = (k - i + j + 1 + 31) >> 5;  // warp-uniform: 32-element slices of the row
-            float2 v;
-            if (nq == 1)
-                v = chdf_row<1>(A, M, Aj, Mj, k, i, j, f, lane);
-            else if (nq == 2)
-                v = chdf_row<2>(A, M, Aj, Mj, k, i, j, f, lane);
-            else if (nq == 3)
-                v = chdf_row<3>(A, M, Aj, Mj, k, i, j, f, lane);
-            else
-                v = chdf_row<4>(A, M, Aj, Mj, k, i, j, f, lane);
-            if (warp == 0 && lane == 0) {  // v = A(j+1, j+1): the next pivot
-                const bool ok = v.x > (float)tol * s_dg[j + 1] && v.x > 0.f;
-                s_ok[j + 1] = ok;
-                if (ok) {
-                    float2 ni, ys;
-                    df_rcp_rsqrt(v, ni, ys);
-                    s_inv[(j + 1) & 1] = ni;
-                    s_ys[j + 1] = ys;
+    for (int j0 = 0; j0 < k; j0 += CHDF_PANEL) {
+        const int jb = min(CHDF_PANEL, k - j0);
+        if (warp < CHDF_PANEL) {
+            const int i = j0 + warp;  // this warp's row (none when warp >= jb)
+            for (int jj = 0; jj < jb; ++jj) {
+                const int j = j0 + jj;
+                const float2 p = A[(size_t)j * k + j];
+                if (!(p.x > (float)tol * s_dg[j] && p.x > 0.f)) {  // the same test in every warp
+                    if (warp == 0 && lane == 0) s_fail = 1;
+                    break;
                 }
+                float2 inv, ys;
+                df_rcp_rsqrt(p, inv, ys);
+                if (warp == jj && lane == 0) {
+                    s_inv[jj] = inv;
+                    s_ys[j] = ys;
+                }
+                if (warp < jb && i > j) {
+                    const float2* Aj = A + (size_t)j * k;
+                    const float2* Mj = M + (size_t)j * k;
+                    const float2 f = df_mul2(Aj[i], inv);  // l_ij
+                    float2* Ai = A + (size_t)i * k;
+                    float2* Mi = M + (size_t)i * k;
+                    for (int l = i + lane; l < k; l += 32) Ai[l] = df_fnms2(Ai[l], f, Aj[l]);
+                    for (int cc = lane; cc <= j; cc += 32) Mi[cc] = df_fnms2(Mi[cc], f, Mj[cc]);
+                }
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * CHDF_PANEL) : "memory");
             }
         }
         __syncthreads();
+        if (s_fail) break;  // uniform: written before the barrier
+        const int t0 = j0 + jb, nr = k - t0;
+        if (nr <= 0) break;
+        // the panel's multipliers for the rows below it
+        for (int x = tid; x < jb * nr; x += nt) {
+            const int jj = x / nr, i = t0 + x % nr;
+            s_l[jj][i] = df_mul2(A[(size_t)(j0 + jj) * k + i], s_inv[jj]);
+        }
+        __syncthreads();
+        for (int x = tid; x < nr * nr; x += nt) {  // A(i, l), t0 <= i <= l < k
+            const int i = t0 + x / nr, l = t0 + x % nr;
+            if (l < i) continue;
+            float2 v = A[(size_t)i * k + l];
+            for (int jj = 0; jj < jb; ++jj) v = df_fnms2(v, s_l[jj][i], A[(size_t)(j0 + jj) * k + l]);
+            A[(size_t)i * k + l] = v;
+        }
+        for (int x = tid; x < nr * t0; x += nt) {  // M(i, c), t0 <= i < k, c < t0 (M(j, c) = 0 for c > j)
+            const int i = t0 + x / t0, c = x % t0;
+            float2 v = M[(size_t)i * k + c];
+            for (int jj = 0; jj < jb; ++jj)
+                if (c <= j0 + jj) v = df_fnms2(v, s_l[jj][i], M[(size_t)(j0 + jj) * k + c]);
+            M[(size_t)i * k + c] = v;
+        }
+        __syncthreads();
     }
-    if (!s_ok[k - 1]) {  // a rejected pivot ends the loop; the flags after it stay 0
+    if (s_fail) {  // a rejected pivot
         if (tid == 0) bad[b] = 1;
         return;
     }
