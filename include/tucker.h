@@ -175,9 +175,12 @@ TK_API int64_t tk_launch_count(const tk_handle* h);
  * of classes (or -1 on error) and clears the records.  Each recorded launch
  * costs two cudaEventRecord calls on the host, so tk_profile_only restricts
  * recording to the classes whose name starts with `prefix` (NULL or "" = all
- * classes; the filter persists until changed).  Class names: "xpass_tc",
- * "ttm_tc", "xpass_simt", "ttm_simt", "gemm_f64", "chol_inv", "apply_rinv",
- * "householder", "jacobi", "residual", "elementwise". */
+ * classes; the filter persists until changed).  Class names ("xpass_*": a
+ * pass over the whole data tensor): "xpass_tc", "xpass_tc_bg" (a tensor-core
+ * pass on part of the SMs, beside a chain of small kernels of the same call),
+ * "xpass_narrow", "xpass_simt", "ttm_tc", "ttm_narrow", "ttm_simt",
+ * "gemm_f64", "gemm_df", "chol_inv", "apply_rinv", "householder", "jacobi",
+ * "residual", "elementwise", "rng". */
 typedef struct {
     char name[32];
     int64_t launches;

@@ -1552,7 +1552,9 @@ static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, c
             const int keep = c.grid_sms;
             const size_t ns = c.splits.size();
             c.grid_sms = background_grid(c);
+            c.background = true;
             tr->T = multi_ttm(c, Xt, tm, Qa.data(), false, acc);
+            c.background = false;
             c.grid_sms = keep;
             c.splits.resize(ns);
             tr->Tapplied.assign(d, 0);
@@ -2139,9 +2141,13 @@ tk_status tucker_rhkron_grad(tk_handle* h, const tk_tensor* X, const int64_t* r,
                 if (!want_res) return;
                 // the pass has the gradient's chain of small kernels to finish in: it leaves them SMs
                 const int keep = c.grid_sms;
-                if (dG || dU) c.grid_sms = background_grid(c);
+                if (dG || dU) {
+                    c.grid_sms = background_grid(c);
+                    c.background = true;
+                }
                 residual_pass(c, Xt, Ga, Ua, acc, errd, dX ? g.dX.p : nullptr, dX ? g.dX.dt : TK_F32,
                               2.0 * grad_scale);
+                c.background = false;
                 c.grid_sms = keep;
             });
         if (rel_err) read_err(h, c, errd, rel_err, false, o.async_outputs);

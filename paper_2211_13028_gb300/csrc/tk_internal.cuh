@@ -155,6 +155,7 @@ struct Ctx {
     int64_t xnumel = 0;
     bool use_tc = true;            // tensor-core TTM where eligible
     int grid_sms = 0;              // CTAs of the persistent streaming kernels (0: every SM)
+    bool background = false;       // a streaming pass on part of the SMs beside a chain of small kernels
     bool capturing = false;        // the stream is recording a CUDA graph (launches are not run now)
     bool df64 = false;             // FP32-class data: FP64 products may run in double-float arithmetic
     // Factor splits (TF32 hi / lo) made in this pass, reused while split_cache is

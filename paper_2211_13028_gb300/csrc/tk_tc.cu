@@ -761,7 +761,8 @@ void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int6
     const int64_t L = X.left(j), R = X.right(j);
     // kernel classes: "xpass_tc" streams all of X (a pass over the input),
     // "ttm_tc" contracts an intermediate
-    const char* name = ((const void*)X.p == c.xdata || L * R * m == c.xnumel) ? "xpass_tc" : "ttm_tc";
+    const char* name = ((const void*)X.p == c.xdata || L * R * m == c.xnumel) ? (c.background ? "xpass_tc_bg" : "xpass_tc")
+                                                                              : "ttm_tc";
     ttm_tc_run(c, X, j, M, mtrans, m, out, 0, nullptr, TK_F32, 0.f, nullptr, name);
 }
 
@@ -782,7 +783,8 @@ bool ttm_tc_residual_eligible(const Tens& W, int j, int64_t m) {
 
 void launch_ttm_tc_residual(Ctx& c, const Tens& W, int j, const Mat& M, bool mtrans, int64_t m, const void* xref,
                             tk_dtype xrdt, void* dx, float alpha, double* partials, float xr_scale) {
-    ttm_tc_run(c, W, j, M, mtrans, m, dx, dx ? 2 : 1, xref, xrdt, alpha, partials, "xpass_tc", xr_scale);
+    ttm_tc_run(c, W, j, M, mtrans, m, dx, dx ? 2 : 1, xref, xrdt, alpha, partials,
+               c.background ? "xpass_tc_bg" : "xpass_tc", xr_scale);
 }
 
 }  // namespace tk
