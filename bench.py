@@ -872,6 +872,19 @@ def main():
         graph_ms = g0.elapsed_time(g1) / args.steps
         graph_errs = (gX.outputs[2].value, gX.outputs[5].value)
         del gX
+    # ---- the roofline kernel alone: the first (X-streaming) product of tucker_core on the same field with
+    # factors of the core's widths (49, 42, 42), nothing else on the GPU (5 repetitions, live event timing)
+    rng_q = np.random.Generator(np.random.PCG64(SEED + 5))
+    qs = [synth.fmat(np.linalg.qr(rng_q.standard_normal((N_FULL, kq)))[0], "f32", dev) for kq in (49, 42, 42)]
+    T.tucker_core(X, qs)
+    torch.cuda.synchronize()
+    T.tk_profile(True, dev, only="xpass")
+    for _ in range(5):
+        T.tucker_core(X, qs)
+    prof_alone = T.tk_profile_read(dev)
+    T.tk_profile(False, dev)
+    alone = prof_alone.get("xpass_tc")
+    del qs
     barrier(dist)
     clk = clocks.stop()
     ph = [sum(marks[i][a].elapsed_time(marks[i][b]) for i in range(args.steps)) / args.steps
@@ -956,6 +969,13 @@ def main():
     runner = ranked[1][0] if len(ranked) > 1 else None  # the class after the dominant one
     # the same tensor-core kernel launched on part of the SMs beside a chain of small kernels (the gradient's
     # product pass and its dX pass): slower per launch by design, reported beside the roofline kernel
+    isolated = None
+    if alone and alone["launches"] > 0 and alone["ms"] > 0:
+        a_gbs = (alone["bytes"] / alone["launches"]) / (alone["ms"] / alone["launches"] * 1e-3) / 1e9
+        isolated = dict(achieved=a_gbs, frac=a_gbs / hbm, ms_per_launch=alone["ms"] / alone["launches"],
+                        bytes_per_launch=alone["bytes"] / alone["launches"],
+                        note="the same kernel timed alone: the X pass of tucker_core on the 512^3 field (mode 3, "
+                             "42 output columns), 5 repetitions, nothing else running")
     bg = prof.get("xpass_tc_bg")
     background = None
     if bg and bg["launches"] > 0 and bg["ms"] > 0:
@@ -1014,7 +1034,7 @@ def main():
                             "kernel time (one extra all-class step); its %d launches per step are timed live with "
                             "CUDA events in the eager timed region (a recorded graph carries no per-launch events)"
                             % round(d["launches"] / args.steps)),
-                      background=background),
+                      background=background, isolated=isolated),
         kernel_shares=shares,
         kernel_shares_note="all kernel classes timed in one extra step after the timed region",
         kernel_ms_per_step=step_ms_total,
