@@ -102,6 +102,10 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
 struct TcArgs {
     int64_t L, nj, R, m;
     int64_t ntiles, tiles_per_r, nk, nblk;  // work item = (row tile, block of NPAD output columns)
+    // strided mode with L < 64 (EPI 0 only): a tile holds `pack` consecutive r of L rows each
+    // (pack L <= 128 rows) instead of one r, so that short rows fill the 128-row tile; 1 otherwise
+    int pack;
+    uint32_t xbytes;                        // TMA bytes of one X chunk (128 x 32 x 4, or L x 32 x pack x 4)
     void* out;                              // EPI 0: product (FP32); EPI 2: alpha * (xref - product) (XR)
     const void* xref;                       // EPI 1, 2: tensor compared with the product (same layout, XR)
     float alpha;
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                 if (KMAJOR) {
                     r0 = t * kRows;
                 } else {
-                    rr = t / args.tiles_per_r;
+                    rr = (t / args.tiles_per_r) * args.pack;
                     l0 = (t % args.tiles_per_r) * kRows;
                 }
                 if (EPI) {  // the X tile the epilogue compares this item's product with
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                     }
                     uint8_t* xs = smem + s * C::kStage;
                     uint8_t* bs = xs + kXBytes;
-                    mbar_expect_tx(&full[s], kXBytes + 2 * C::kBBytes);
+                    mbar_expect_tx(&full[s], args.xbytes + 2 * C::kBBytes);
                     if (KMAJOR) {
                         tma_load_2d(xs, &tmX, (int)(kc * kChunk), (int)r0, &full[s]);
                     } else {
@@ -318,6 +322,9 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
         const int q = warp & 3, hs = (cw >> 2) & 1, grp = cw >> 3;
         const int rho = 32 * q + lane;  // tile row == TMEM lane
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        const int Lp = (int)args.L;     // packed tiles only (L < 64)
+        const int xoff = args.pack > 1 ? (rho < Lp * args.pack ? (rho / Lp) * kChunk * Lp + rho % Lp : -1) : rho;
+        const int istride = args.pack > 1 ? Lp : kRows;
         int64_t it = 0, ab = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
@@ -346,11 +353,14 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                         v[4 * jj + 3] = f.w;
                     }
                 } else {
-                    // rows i of 128 floats (512 B, no swizzle): lanes read consecutive words
+                    // rows i of 128 floats (512 B, no swizzle): lanes read consecutive words.  Packed
+                    // tiles hold [p][i][l] (p < pack, rows of L floats): tile row rho = l + L p; the
+                    // rows past L pack are padding (zero)
+                    const float* xf = reinterpret_cast<const float*>(xs);
 #pragma unroll
                     for (int ii = 0; ii < 16; ++ii) {
                         const int i = 16 * hs + ii;
-                        v[ii] = *reinterpret_cast<const float*>(xs + i * 512 + rho * 4);
+                        v[ii] = xoff >= 0 ? xf[xoff + i * istride] : 0.f;
                     }
                 }
                 uint32_t hi[16], lo[16];
@@ -400,6 +410,13 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                 valid = r < args.R;
                 base = r * args.m;
                 stride = 1;
+            } else if (args.pack > 1) {  // packed tile: row rho = l + L p holds (l, r = pack t + p)
+                const int Lp = (int)args.L;
+                const int64_t rr = t * args.pack + rho / Lp;
+                const int64_t l = rho % Lp;
+                valid = rho < Lp * args.pack && rr < args.R;
+                base = l + args.L * args.m * rr;
+                stride = args.L;
             } else {
                 const int64_t rr = t / args.tiles_per_r;
                 const int64_t l = (t % args.tiles_per_r) * kRows + rho;
@@ -673,6 +690,8 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
     }
     CUtensorMap tx, th, tl;
     const bool kmajor = (L == 1);
+    // a strided mode with under 64 rows before it: several r per 128-row tile (plain product only)
+    const int pack = (!kmajor && epi == 0 && L < tc::kRows / 2) ? (int)(tc::kRows / L) : 1;
     if (kmajor) {
         uint64_t dims[2] = {(uint64_t)nj, (uint64_t)R};
         uint64_t str[1] = {(uint64_t)nj * 4};
@@ -682,6 +701,10 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
         uint64_t dims[3] = {(uint64_t)L, (uint64_t)nj, (uint64_t)R};
         uint64_t str[2] = {(uint64_t)L * 4, (uint64_t)L * nj * 4};
         uint32_t box[3] = {tc::kRows, tc::kChunk, 1};
+        if (pack > 1) {  // L rows of pack consecutive r per box (L x 4 bytes: a multiple of 16)
+            box[0] = (uint32_t)L;
+            box[2] = (uint32_t)pack;
+        }
         tc::encode(&tx, X.p, 3, dims, str, box, false);
     }
     {
@@ -715,6 +738,12 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
     a.nblk = nblk;
     a.tiles_per_r = kmajor ? 1 : (L + tc::kRows - 1) / tc::kRows;
     a.ntiles = kmajor ? (R + tc::kRows - 1) / tc::kRows : R * a.tiles_per_r;
+    a.pack = pack;
+    a.xbytes = (uint32_t)tc::kXBytes;
+    if (pack > 1) {
+        a.ntiles = (R + pack - 1) / pack;
+        a.xbytes = (uint32_t)(L * tc::kChunk * pack * 4);
+    }
     a.out = out;
     a.xref = xref;
     a.alpha = alpha;

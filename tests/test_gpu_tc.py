@@ -111,3 +111,20 @@ def test_tc_rel_err_fused_matches_oracle(dev):
     assert abs(err - O.rel_err(xv, ref["G"], ref["U"])) <= 1e-5
     # the error the GPU reports is the error of the factors it returned
     assert abs(err - O.rel_err(xv, to_np(G), [to_np(u) for u in U])) <= 1e-6
+
+
+@pytest.mark.parametrize("dims,k", [((40, 96, 77), (40, 20, 77)), ((32, 130, 65), (32, 48, 65)),
+                                    ((60, 64, 50), (60, 16, 50)), ((44, 512, 9), (44, 64, 9))])
+def test_tc_short_rows_packed_tiles(dev, dims, k):
+    # the first product contracts mode 2 with only L = dims[0] (32..60) rows before it: the tensor-core
+    # kernel packs floor(128 / L) consecutive slabs into each 128-row tile (the last one partial)
+    g = _rng(11)
+    X, xv, _ = make_X(g.standard_normal(dims), "f32", dev)
+    qs = [synth.round_to(O.thin_qr(g.standard_normal((n, kk))), "f32") for n, kk in zip(dims, k)]
+    T.tk_profile(True, dev)
+    G = T.tucker_core(X, mats(qs, "f32", dev))
+    prof = T.tk_profile_read(dev)
+    T.tk_profile(False, dev)
+    assert "xpass_tc" in prof  # X was streamed by the tensor-core kernel
+    ref = O.multi_ttm(xv, [(j, qs[j].T) for j in range(3)])
+    assert rel(to_np(G), ref) <= 1e-5
