@@ -106,6 +106,11 @@ struct TcArgs {
     // (pack L <= 128 rows) instead of one r, so that short rows fill the 128-row tile; 1 otherwise
     int pack;
     uint32_t xbytes;                        // TMA bytes of one X chunk (128 x 32 x 4, or L x 32 x pack x 4)
+    // EPI 0 with few row tiles: the K chunks of a tile are split over ksplit work items, each writing
+    // its partial product to part + s out_numel (summed in order by a second kernel); 1 otherwise
+    int ksplit;
+    float* part;
+    int64_t out_numel;
     void* out;                              // EPI 0: product (FP32); EPI 2: alpha * (xref - product) (XR)
     const void* xref;                       // EPI 1, 2: tensor compared with the product (same layout, XR)
     float alpha;
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
     const uint32_t tbase = *tmem_slot;
     unsigned* flags = args.flags;
     const int64_t nk = args.nk;
-    const int64_t nitems = args.ntiles * args.nblk;
+    const int64_t nitems = args.ntiles * args.nblk * args.ksplit;
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -221,7 +226,9 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
             int64_t it = 0, item = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x, ++item) {
-                const int64_t t = w / args.nblk, nb = w % args.nblk;
+                const int64_t w2 = w / args.ksplit, sk = w % args.ksplit;
+                const int64_t t = w2 / args.nblk, nb = w2 % args.nblk;
+                const int64_t kc0 = nk * sk / args.ksplit, kc1 = nk * (sk + 1) / args.ksplit;
                 int64_t r0 = 0, l0 = 0, rr = 0;
                 if (KMAJOR) {
                     r0 = t * kRows;
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                     tma_load_3d(reinterpret_cast<uint8_t*>(xr_buf) + xb * C::kXrBytes, &tmXr, (int)l0, (int)(nb * NPAD),
                                 (int)rr, &xrfull[xb]);
                 }
-                for (int64_t kc = 0; kc < nk; ++kc, ++it) {
+                for (int64_t kc = kc0; kc < kc1; ++kc, ++it) {
                     const int s = (int)(it % S);
                     const uint32_t ph = (uint32_t)((it / S) & 1);
                     if (!mbar_wait(&xfree[s], ph ^ 1, abort, flags)) {
@@ -285,7 +292,9 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tbase + C::kAcc0 + a * C::kAccCols;
-                for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
+                const int64_t sk = w % args.ksplit;
+                const int64_t kc0 = nk * sk / args.ksplit, kc1 = nk * (sk + 1) / args.ksplit;
+                for (int64_t kc = kc0; kc < kc1; ++kc, ++it, ++ab) {
                     const int s = (int)(it % S);
                     const int b = (int)(ab % NA);
                     if (!mbar_wait(&full[s], (uint32_t)((it / S) & 1), abort, flags) ||
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
 #pragma unroll
                     for (int k8 = 0; k8 < kChunk / 8; ++k8) {
                         const uint64_t bdesc = desc_sw128(bs + 32 * k8);
-                        mma_tf32_ts(d_tmem, a_hi + 8 * k8, bdesc, idesc_tf32(2 * NPAD), (kc | k8) != 0);
+                        mma_tf32_ts(d_tmem, a_hi + 8 * k8, bdesc, idesc_tf32(2 * NPAD), (kc != kc0 || k8 != 0) ? 1u : 0u);
                         mma_tf32_ts(d_tmem + NPAD, a_hi + 32 + 8 * k8, bdesc, idesc_tf32(NPAD), 1u);
                     }
                     tc_commit(&aempty[b]);
@@ -328,7 +337,9 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
         int64_t it = 0, ab = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
-            for (int64_t kc = 0; kc < nk; ++kc, ++it, ++ab) {
+            const int64_t sk = w % args.ksplit;
+            const int64_t kc0 = nk * sk / args.ksplit, kc1 = nk * (sk + 1) / args.ksplit;
+            for (int64_t kc = kc0; kc < kc1; ++kc, ++it, ++ab) {
                 if (W::kGroups == 2 && (it & 1) != grp) continue;
                 const int s = (int)(it % S);
                 const int b = (int)(ab % NA);
@@ -395,7 +406,9 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
         float srh = 0.f, srl = 0.f, sxh = 0.f, sxl = 0.f;
         int64_t acc = 0;
         for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x, ++acc) {
-            const int64_t t = w / args.nblk, nb = w % args.nblk;
+            const int64_t w2 = w / args.ksplit, sk = w % args.ksplit;
+            const int64_t t = w2 / args.nblk, nb = w2 % args.nblk;
+            float* const outp = args.ksplit > 1 ? args.part + sk * args.out_numel : static_cast<float*>(args.out);
             const int a = (int)(acc & 1);
             const int xb = (int)(acc % XB);
             bool got = mbar_wait(&accfull[a], (uint32_t)((acc >> 1) & 1), abort, flags);
@@ -441,7 +454,7 @@ __global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
                     if (EPI == 0) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (c0 + i < ncol) static_cast<float*>(args.out)[base + (c0 + i) * stride] = h[i] + g[i];
+                            if (c0 + i < ncol) outp[base + (c0 + i) * stride] = h[i] + g[i];
                     } else {
                         float fr = 0.f, fx = 0.f;
                         const XR* xcol = xt + c0 * kRows + rho;
@@ -558,6 +571,15 @@ __global__ void split_tf32_batch_kernel(SplitBatch sb) {
     }
 }
 
+// out = the sum of the ksplit partial products part[s n .. s n + n), in order of s.
+__global__ void splitk_sum_kernel(const float* __restrict__ part, int ksplit, int64_t n, float* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        float v = part[e];
+        for (int sk = 1; sk < ksplit; ++sk) v += part[(int64_t)sk * n + e];
+        out[e] = v;
+    }
+}
+
 template <int NPAD, bool KMAJOR, int EPI, typename XR = float>
 static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap& th, const CUtensorMap& tl,
                           const CUtensorMap& txr, const TcArgs& a) {
@@ -568,7 +590,7 @@ static void launch_kernel(const Ctx& c, const CUtensorMap& tx, const CUtensorMap
         TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::kSmem));
         attr_set = true;
     }
-    int grid = (int)std::min<int64_t>(a.ntiles * a.nblk, grid_sms(c));
+    int grid = (int)std::min<int64_t>(a.ntiles * a.nblk * a.ksplit, grid_sms(c));
     kern<<<grid, Warps<EPI>::kThreads, Cf::kSmem, c.stream>>>(tx, th, tl, txr, a);
 }
 
@@ -679,6 +701,23 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
         if (c.split_cache)
             c.splits.push_back({M.p, M.ld, nj, m, npad, rows_b, (int)M.dt, mtrans ? 1 : 0, hi, lo});
     }
+    // the work items: 128-row tiles (a strided mode with under 64 rows before it packs several slabs
+    // per tile) x blocks of NPAD output columns; a plain product with too few of them for half the
+    // SMs splits each tile's K chunks over several items (at least two chunks each), whose partial
+    // products are summed in order afterwards
+    const bool kmajor = (L == 1);
+    const int pack = (!kmajor && epi == 0 && L < tc::kRows / 2) ? (int)(tc::kRows / L) : 1;
+    const int64_t nk = (nj + tc::kChunk - 1) / tc::kChunk;
+    const int64_t tiles_per_r = kmajor ? 1 : (L + tc::kRows - 1) / tc::kRows;
+    const int64_t ntiles = kmajor ? (R + tc::kRows - 1) / tc::kRows
+                                  : (pack > 1 ? (R + pack - 1) / pack : R * tiles_per_r);
+    int ksplit = 1;
+    {
+        const int64_t items = ntiles * nblk, sms = tc::grid_sms(c);
+        if (epi == 0 && items * 2 <= sms && nk >= 4)
+            ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(nk / 2, sms / items));
+    }
+    float* part = ksplit > 1 ? c.alloc<float>(ksplit * L * m * R) : nullptr;
     if (!c.exec) return;
     if (!have) {
         int64_t tot = ldo * rows_b;
@@ -689,9 +728,6 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
         c.check_launch();
     }
     CUtensorMap tx, th, tl;
-    const bool kmajor = (L == 1);
-    // a strided mode with under 64 rows before it: several r per 128-row tile (plain product only)
-    const int pack = (!kmajor && epi == 0 && L < tc::kRows / 2) ? (int)(tc::kRows / L) : 1;
     if (kmajor) {
         uint64_t dims[2] = {(uint64_t)nj, (uint64_t)R};
         uint64_t str[1] = {(uint64_t)nj * 4};
@@ -734,16 +770,15 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
     a.nj = nj;
     a.R = R;
     a.m = m;
-    a.nk = (nj + tc::kChunk - 1) / tc::kChunk;
+    a.nk = nk;
     a.nblk = nblk;
-    a.tiles_per_r = kmajor ? 1 : (L + tc::kRows - 1) / tc::kRows;
-    a.ntiles = kmajor ? (R + tc::kRows - 1) / tc::kRows : R * a.tiles_per_r;
+    a.tiles_per_r = tiles_per_r;
+    a.ntiles = ntiles;
     a.pack = pack;
-    a.xbytes = (uint32_t)tc::kXBytes;
-    if (pack > 1) {
-        a.ntiles = (R + pack - 1) / pack;
-        a.xbytes = (uint32_t)(L * tc::kChunk * pack * 4);
-    }
+    a.xbytes = (uint32_t)(pack > 1 ? L * tc::kChunk * pack * 4 : tc::kXBytes);
+    a.ksplit = ksplit;
+    a.part = part;
+    a.out_numel = L * m * R;
     a.out = out;
     a.xref = xref;
     a.alpha = alpha;
@@ -784,6 +819,13 @@ static void ttm_tc_run(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, 
 #undef TK_TC_CASE
     c.counted();
     c.check_launch();
+    if (ksplit > 1) {
+        const int64_t n = L * m * R;
+        tc::splitk_sum_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c.stream>>>(
+            part, ksplit, n, static_cast<float*>(out));
+        c.counted();
+        c.check_launch();
+    }
 }
 
 void launch_ttm_tc(Ctx& c, const Tens& X, int j, const Mat& M, bool mtrans, int64_t m, float* out) {

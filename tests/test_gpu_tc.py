@@ -128,3 +128,22 @@ def test_tc_short_rows_packed_tiles(dev, dims, k):
     assert "xpass_tc" in prof  # X was streamed by the tensor-core kernel
     ref = O.multi_ttm(xv, [(j, qs[j].T) for j in range(3)])
     assert rel(to_np(G), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dims,k", [((500, 40, 40), (48, 40, 40)), ((40, 40, 500), (40, 40, 44)),
+                                    ((48, 44, 1000), (48, 44, 64))])
+def test_tc_few_tiles_split_k(dev, dims, k):
+    # the first product has a long contraction (500-1000) and only 13-17 row tiles: its K chunks are
+    # split over several CTAs and the partial products summed in order afterwards
+    g = _rng(12)
+    X, xv, _ = make_X(g.standard_normal(dims), "f32", dev)
+    qs = [synth.round_to(O.thin_qr(g.standard_normal((n, kk))), "f32") for n, kk in zip(dims, k)]
+    T.tk_profile(True, dev)
+    G = T.tucker_core(X, mats(qs, "f32", dev))
+    prof = T.tk_profile_read(dev)
+    T.tk_profile(False, dev)
+    assert "xpass_tc" in prof
+    ref = O.multi_ttm(xv, [(j, qs[j].T) for j in range(3)])
+    assert rel(to_np(G), ref) <= 1e-5
+    G2 = T.tucker_core(X, mats(qs, "f32", dev))
+    assert torch.equal(G, G2)  # the partial sums are added in a fixed order
