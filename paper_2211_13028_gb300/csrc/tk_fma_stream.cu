@@ -59,7 +59,8 @@ inline size_t fs_smem(int64_t nk) {
            sizeof(float) * (FS_PARTS - 1) * FS_ROWS * FS_COLS + sizeof(uint64_t) * (2 * FS_STAGES + 1);
 }
 
-template <bool KMAJOR, bool SIGN>
+// NC: the output columns computed (m <= NC <= FS_COLS; M is held zero-padded to FS_COLS columns).
+template <bool KMAJOR, bool SIGN, int NC>
 __global__ void __launch_bounds__(FS_THREADS, 1)
     ttm_fma_stream_kernel(const __grid_constant__ CUtensorMap tmX, FsArgs args) {
     extern __shared__ uint8_t smem_raw[];
@@ -131,11 +132,11 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
     const float4* m4 = reinterpret_cast<const float4*>(msm);
     int64_t it = 0;
     for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
-        float acc[4][FS_COLS];
+        float acc[4][NC];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int a = 0; a < FS_COLS; ++a) acc[u][a] = 0.f;
+            for (int a = 0; a < NC; ++a) acc[u][a] = 0.f;
         uint32_t c0[4];  // SIGN: unfolding column of (row, i = 0) for this item's four rows
         if (SIGN) {
             const SignMap& sm = args.sm;
@@ -186,12 +187,13 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
                     }
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        const float4 ma = mrow[2 * (4 * k4 + kk)], mb = mrow[2 * (4 * k4 + kk) + 1];
+                        const float4 ma = mrow[2 * (4 * k4 + kk)];
+                        const float4 mb = NC > 4 ? mrow[2 * (4 * k4 + kk) + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
                         const float mv[FS_COLS] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
 #pragma unroll
-                            for (int a = 0; a < FS_COLS; ++a) acc[u][a] = fmaf(v[u][kk], mv[a], acc[u][a]);
+                            for (int a = 0; a < NC; ++a) acc[u][a] = fmaf(v[u][kk], mv[a], acc[u][a]);
                     }
                 }
             }
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int a = 0; a < FS_COLS; ++a) red[((part - 1) * FS_ROWS + q + 32 * u) * FS_COLS + a] = acc[u][a];
+                for (int a = 0; a < NC; ++a) red[((part - 1) * FS_ROWS + q + 32 * u) * FS_COLS + a] = acc[u][a];
         }
         asm volatile("bar.sync 1, %0;" ::"n"(32 * FS_CONS) : "memory");
         if (part == 0 && !*abort) {
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(FS_THREADS, 1)
                 }
                 if (valid) {
 #pragma unroll
-                    for (int a = 0; a < FS_COLS; ++a)
+                    for (int a = 0; a < NC; ++a)
                         if (a < args.m) {
                             float v = acc[u][a];
 #pragma unroll
@@ -292,10 +294,21 @@ void launch_ttm_narrow(const Ctx& c, const Tens& X, int j, const Mat& M, bool mt
         TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<grid, tc::FS_THREADS, smem, c.stream>>>(tx, a);
     };
-    if (kmajor)
-        sm ? run(tc::ttm_fma_stream_kernel<true, true>) : run(tc::ttm_fma_stream_kernel<true, false>);
-    else
-        sm ? run(tc::ttm_fma_stream_kernel<false, true>) : run(tc::ttm_fma_stream_kernel<false, false>);
+    // the FMAs of the output columns the factor has (5..8; the Kronecker-SRHT path always takes 8)
+    const int nc = sm ? 8 : (int)std::max<int64_t>(5, m);
+    if (sm) {
+        kmajor ? run(tc::ttm_fma_stream_kernel<true, true, 8>) : run(tc::ttm_fma_stream_kernel<false, true, 8>);
+    } else if (kmajor) {
+        nc == 5 ? run(tc::ttm_fma_stream_kernel<true, false, 5>)
+                : nc == 6 ? run(tc::ttm_fma_stream_kernel<true, false, 6>)
+                          : nc == 7 ? run(tc::ttm_fma_stream_kernel<true, false, 7>)
+                                    : run(tc::ttm_fma_stream_kernel<true, false, 8>);
+    } else {
+        nc == 5 ? run(tc::ttm_fma_stream_kernel<false, false, 5>)
+                : nc == 6 ? run(tc::ttm_fma_stream_kernel<false, false, 6>)
+                          : nc == 7 ? run(tc::ttm_fma_stream_kernel<false, false, 7>)
+                                    : run(tc::ttm_fma_stream_kernel<false, false, 8>);
+    }
     c.counted();
     c.check_launch();
 }
