@@ -307,7 +307,8 @@ TK_API tk_status tucker_orth(tk_handle* h, const tk_matrix* Y, tk_matrix* Q, int
  * min(rows, cols), F64 or F32, both device pointers on the current device.
  * info (host, may be NULL; non-NULL synchronises the stream): 0 CholeskyQR2,
  * 1 Householder, 2 identity.  Other errors: TK_ERR_ARG (also a stream of
- * another device), TK_ERR_DTYPE, TK_ERR_ALIGN, TK_ERR_CUDA. */
+ * another device, and a non-NULL info on a stream that is recording a CUDA
+ * graph: nothing is queued then), TK_ERR_DTYPE, TK_ERR_ALIGN, TK_ERR_CUDA. */
 TK_API tk_status tucker_orth_noalloc(void* cuda_stream, const tk_matrix* Y, tk_matrix* Q, int* info);
 
 /* Core multi-TTM Ghat = X x_1 Q_1^T x_2 Q_2^T ... x_d Q_d^T (Algorithm

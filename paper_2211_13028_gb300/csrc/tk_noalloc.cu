@@ -74,6 +74,10 @@ extern "C" tk_status tucker_orth_noalloc(void* cuda_stream, const tk_matrix* Y, 
         TK_CUDA(cudaGetDevice(&cur));
         TK_CUDA(cudaStreamGetDevice(static_cast<cudaStream_t>(cuda_stream), &sdev));
         if (sdev != cur) return TK_ERR_ARG;
+        // reading info back synchronises the stream, which a stream recording a CUDA graph must not do
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        TK_CUDA(cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cap));
+        if (info && cap != cudaStreamCaptureStatusNone) return TK_ERR_ARG;
         char* base = nullptr;
         tk_status st = scratch_for_current_device(&base);
         if (st != TK_OK) return st;

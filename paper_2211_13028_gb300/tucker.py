@@ -504,7 +504,8 @@ def tucker_orth(Y: torch.Tensor, qr_method: int = 0, out_dtype=None) -> Tuple[to
     return Q, info.value
 
 
-def tucker_orth_noalloc(Y: torch.Tensor, out_dtype=None, Q: torch.Tensor | None = None) -> Tuple[torch.Tensor, int]:
+def tucker_orth_noalloc(Y: torch.Tensor, out_dtype=None, Q: torch.Tensor | None = None,
+                        read_info: bool = True) -> Tuple[torch.Tensor, Optional[int]]:
     """Thin QR like tucker_orth, computed without any device allocation by the
     library (a fixed internal scratch array; rows <= 4096, min(rows, cols) <= 64).
     For callers that cannot allocate device memory at the call site: memory
@@ -512,17 +513,19 @@ def tucker_orth_noalloc(Y: torch.Tensor, out_dtype=None, Q: torch.Tensor | None 
     synchronisation of cudaMalloc / cudaFree.  Q (column-major, rows x
     min(rows, cols)) may be passed in so that nothing is allocated here either.
     Calls must not overlap on the GPU (they share the scratch).  Returns
-    (Q, info); info is read back, which synchronises the stream."""
+    (Q, info); with read_info the method taken is read back, which synchronises
+    the stream, else info is None and the call only queues work."""
     rows, cols = Y.shape
     if Q is None:
         Q = _colmajor_matrix(rows, min(rows, cols), out_dtype or Y.dtype, Y.device)
     info = ctypes.c_int(-1)
     with torch.cuda.device(Y.device):
         st = load().tucker_orth_noalloc(ctypes.c_void_p(torch.cuda.current_stream(Y.device).cuda_stream),
-                                        ctypes.byref(_matrix(Y)), ctypes.byref(_matrix(Q)), ctypes.byref(info))
+                                        ctypes.byref(_matrix(Y)), ctypes.byref(_matrix(Q)),
+                                        ctypes.byref(info) if read_info else None)
     if st != 0:
         raise TuckerError(st, "tucker_orth_noalloc failed")
-    return Q, info.value
+    return Q, (info.value if read_info else None)
 
 
 def tucker_core(X: torch.Tensor, Q: Sequence[torch.Tensor], out_dtype=None, scale: float = 1.0) -> torch.Tensor:

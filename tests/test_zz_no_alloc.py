@@ -69,3 +69,13 @@ def test_noalloc_rejects_oversized(dev):
     with pytest.raises(T.TuckerError) as e:
         T.tucker_orth_noalloc(Y)
     assert e.value.status == 2
+
+
+def test_noalloc_without_reading_info(dev):
+    # info = NULL: the call only queues work; Q equals the synchronising call's
+    y = synth.round_to(_inputs(13)[0], "f64")
+    Y = synth.fmat(y, "f64", dev)
+    Q_ref, _ = T.tucker_orth_noalloc(Y, out_dtype=torch.float64)
+    Q, info = T.tucker_orth_noalloc(Y, out_dtype=torch.float64, read_info=False)
+    torch.cuda.synchronize()
+    assert info is None and torch.equal(Q, Q_ref)
