@@ -487,8 +487,15 @@ static void eig_top(Ctx& c, int64_t k, const double* A, int64_t r, double* Vr, b
 // discarded energy, which the resolving stage, run on the Gram of the core
 // as truncated so far, absorbs.  The result is that of the sequential
 // algorithm to the resolving stage's threshold.
+static void truncate_modes(Ctx& c, const Tens& G0, Tens& G, const int64_t* r, const std::vector<int>& order,
+                           std::vector<double*>& V, bool fp64_path, const std::vector<double*>& C0,
+                           const std::vector<double*>& V1);
+
+// beside (optional): work for the call's side stream, started once the Grams
+// of the seeding stage are queued (so that it does not take their SMs) and
+// joined before this returns.
 static Tens sthosvd_core(Ctx& c, const Tens& G0, const int64_t* r, const std::vector<int>& order,
-                         std::vector<double*>& V, bool fp64_path) {
+                         std::vector<double*>& V, bool fp64_path, const std::function<void()>* beside = nullptr) {
     Tens G = G0;
     const int d = G0.d;
     V.assign(d, nullptr);
@@ -503,9 +510,26 @@ static Tens sthosvd_core(Ctx& c, const Tens& G0, const int64_t* r, const std::ve
             C0[j] = c.alloc<double>(kj * kj);
             const View2 A = view_unfold_rows(G0, j);
             gemm_nt_f64(c, kj, kj, K, A, A, 1.0, 0.0, C0[j], kj);
-            V1[j] = eig_seed(c, kj, C0[j]);
         });
     }
+    auto body = [&]() {
+        if (!fp64_path) {
+            c.fork(d, [&](int j) {
+                if (C0[j]) V1[j] = eig_seed(c, G0.n[j], C0[j]);
+            });
+        }
+        truncate_modes(c, G0, G, r, order, V, fp64_path, C0, V1);
+    };
+    if (beside && *beside) c.side(body, *beside);
+    else body();
+    return G;
+}
+
+// The sequential part of sthosvd_core: mode by mode in `order`, the leading
+// eigenvectors of the current core's Gram and the truncation of that mode.
+static void truncate_modes(Ctx& c, const Tens& G0, Tens& G, const int64_t* r, const std::vector<int>& order,
+                           std::vector<double*>& V, bool fp64_path, const std::vector<double*>& C0,
+                           const std::vector<double*>& V1) {
     for (int j : order) {
         int64_t kj = G.n[j];
         int64_t K = kj ? G.numel() / kj : 0;
@@ -533,7 +557,6 @@ static Tens sthosvd_core(Ctx& c, const Tens& G0, const int64_t* r, const std::ve
         Vm.ld = kj;
         G = ttm_to(c, G, j, Vm, false, TK_F64);
     }
-    return G;
 }
 
 // ||X - G x_1 U_1 ... x_d U_d||^2 and ||X||^2 into err2 (device, 2 doubles); with
@@ -1534,19 +1557,13 @@ static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, c
     Tens Gh = cm.empty() ? Xt : multi_ttm(c, Xt, cm, Qa.data(), false, acc, nullptr, tr ? &tr->chain : nullptr);
     // 4. STHOSVD of the core in FP64, U_j = Q_j V_j, gauge, casts, error
     std::vector<double*> V;
-    auto truncate = [&]() {
-        Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
-        Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64);
-        finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, errd, tr ? &tr->sg : nullptr);
-    };
     std::vector<int> tm;
     if (tr && tr->want_T && !tr->chain.empty())
         for (int j : cm)
             if (j != tr->chain[0].first) tm.push_back(j);
-    if (tm.empty()) {
-        truncate();
-    } else {
-        c.side(truncate, [&]() {
+    std::function<void()> tpass;
+    if (!tm.empty()) {
+        tpass = [&]() {
             // the side stream's pass leaves most SMs to the truncation's kernels; the splits it makes
             // are its own (the main stream must not find them in the cache)
             const int keep = c.grid_sms;
@@ -1559,8 +1576,11 @@ static void rhkron_from_sketches(Ctx& c, const Tens& Xt, std::vector<Tens>& Y, c
             c.splits.resize(ns);
             tr->Tapplied.assign(d, 0);
             for (int j : tm) tr->Tapplied[j] = 1;
-        });
+        };
     }
+    Tens G64 = (Gh.dt == TK_F64 && Gh.p != Xt.p) ? Gh : tens_to(c, Gh, TK_F64);
+    Tens Gt64 = sthosvd_core(c, G64, r, o.order, V, Xt.dt == TK_F64, tpass ? &tpass : nullptr);
+    finish(c, Xt, Qd, k, Gt64, V, r, Gt, Um, errd, tr ? &tr->sg : nullptr);
     if (tr) tr->V = V;
 }
 
