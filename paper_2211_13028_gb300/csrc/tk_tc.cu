@@ -6,18 +6,23 @@
 // x = x_hi + x_lo and M = M_hi + M_lo with every part a TF32 value (round to
 // nearest), and x*M ~ x_hi*M_hi + x_hi*M_lo + x_lo*M_hi with FP32 accumulation.
 //
-// Kernel structure (persistent, one CTA of 12 warps per SM):
+// Kernel structure (persistent, one CTA per SM; warp counts in Warps<EPI> below):
 //   warp 0      TMA producer: 32-deep K chunks of a 128-row tile of X (16 KB) plus the
 //               matching 32 x NPAD chunks of M_hi and M_lo, into an SMEM ring.
 //   warp 1      allocates TMEM; lane 0 issues tcgen05.mma.
-//   warps 4-7   converters: lane l of the tile reads its 32 values of the chunk from
-//               SMEM, splits them into TF32 hi / lo and writes them to TMEM with
-//               tcgen05.st.  The MMA reads A from TMEM, so X is read from SMEM
-//               exactly once, and a contraction over a non-contiguous mode
-//               (MN-major X) needs no transpose: only the element each lane reads
-//               differs.
-//   warps 8-11  epilogue: tcgen05.ld of a double-buffered accumulator, hi+lo column
-//               halves summed, rows written to global memory.
+//   converters  (16 warps for a plain product, 8 with the residual epilogue): each
+//               lane reads its row's values of the chunk from SMEM, splits them into
+//               TF32 hi / lo and writes them to TMEM with tcgen05.st.  The MMA reads A
+//               from TMEM, so X is read from SMEM exactly once, and a contraction over
+//               a non-contiguous mode (MN-major X) needs no transpose: only the
+//               element each lane reads differs.
+//   epilogue    (4 warps, 16 with the residual): tcgen05.ld of a double-buffered
+//               accumulator, hi+lo column halves summed, rows written to global memory
+//               (or compared with X: EPI 1, 2).
+// A plain product along a strided mode with fewer than 64 rows before it packs
+// several slabs into each 128-row tile, and one with too few tiles for the SMs
+// splits each tile's K chunks over several work items, whose partial products a
+// second kernel sums in order (TcArgs::pack, TcArgs::ksplit).
 // One MMA per 8-deep K step computes A_hi * [M_hi ; M_lo] (N = 2*NPAD, the two halves
 // land in separate TMEM columns); a second adds A_lo * M_hi into the second half, with
 // the other small term.  The tensor core's FP32 accumulation rounds each addition
