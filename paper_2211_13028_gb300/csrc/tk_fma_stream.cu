@@ -1,6 +1,7 @@
 // Narrow TTMs that stream FP32 data: out = X x_j M^T with at most 8 output
 // columns (the widths of the Kronecker sketch factors).  At that width each
-// element needs 8 fused multiply-adds, well inside the FP32 pipe at HBM rate,
+// element needs at most 8 fused multiply-adds (one per column of M: the
+// kernel is instantiated for 5..8 computed columns), well inside the FP32 pipe at HBM rate,
 // so the data is streamed by TMA into a ring of shared-memory stages (as the
 // tensor-core kernels do; the registers of a plain SIMT kernel cannot keep
 // enough bytes in flight) and consumed by FP32 FMA warps, with M held in
