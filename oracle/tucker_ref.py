@@ -18,9 +18,11 @@ Pins (tests/test_oracle_*.py):
     (which fixes Q uniquely), classical Gram-Schmidt on tiny inputs.
   * sthosvd: closed-form error 0.4^r on the Section 7.1 tensor, the STHOSVD
     error identity (sum of discarded squared singular values).
-  * rademacher_signs / rhkron_srht: the Kronecker-SRHT sketch Y_(n) =
-    X_(n) D_n (kron H_j) checked against the explicitly formed matrix on tiny
-    inputs, balanced signs, exact recovery of exactly low-rank tensors.
+  * fmix32 / rademacher_signs / rhkron_srht: the published MurmurHash3_x86_32
+    results for the empty input (= fmix32 of the seed); each sign is the top
+    bit of fmix32; the Kronecker-SRHT sketch Y_(n) = X_(n) D_n (kron H_j)
+    checked against the explicitly formed matrix on tiny inputs, balanced
+    signs, exact recovery of exactly low-rank tensors.
   * rhkron / rsthkron / rhkron_noreuse: exact recovery of exactly low-rank
     tensors, the Section 5 invariants (core singular values bounded by those
     of X, the core error bound Eq. core_svals, Pythagoras for orthonormal
@@ -44,7 +46,7 @@ __all__ = [
     "unfold", "fold", "ttm", "ttm_loops", "multi_ttm", "kron_unfolded_multi_ttm", "kron_omega",
     "thin_qr", "leading_left_singular_vectors", "sthosvd", "canonical_signs",
     "subranks_reuse", "subranks_matrix", "balanced_factors",
-    "rhkron", "rsthkron", "rhkron_noreuse", "rademacher_signs", "srht_sign_tensor", "rhkron_srht",
+    "rhkron", "rsthkron", "rhkron_noreuse", "fmix32", "rademacher_signs", "srht_sign_tensor", "rhkron_srht",
     "philox4x32_10", "philox_blocks", "gaussian_factor",
     "reconstruct", "rel_err", "loss", "loss_grads",
 ]
@@ -365,6 +367,19 @@ def gaussian_factor(rows: int, cols: int, seed: int, stream: int) -> np.ndarray:
 
 # ---------------------------------------------------------------- Section 5, Eq. srht_kron
 
+def fmix32(x: np.ndarray) -> np.ndarray:
+    """The 32-bit finalizer of MurmurHash3 (Appleby): x ^= x >> 16, x *= 0x85EBCA6B,
+    x ^= x >> 13, x *= 0xC2B2AE35, x ^= x >> 16, all mod 2^32.  On its own it is
+    MurmurHash3_x86_32 of the empty input with seed x."""
+    M32 = np.uint64(0xFFFFFFFF)
+    x = np.asarray(x, dtype=np.uint64) & M32
+    x = x ^ (x >> np.uint64(16))
+    x = (x * np.uint64(0x85EBCA6B)) & M32
+    x = x ^ (x >> np.uint64(13))
+    x = (x * np.uint64(0xC2B2AE35)) & M32
+    return x ^ (x >> np.uint64(16))
+
+
 def rademacher_signs(seed: int, n: int, c: np.ndarray) -> np.ndarray:
     """Entries c of the Rademacher diagonal D_n of the Kronecker-SRHT sketch.
 
@@ -376,12 +391,7 @@ def rademacher_signs(seed: int, n: int, c: np.ndarray) -> np.ndarray:
     """
     M32 = np.uint64(0xFFFFFFFF)
     u = (np.uint64(seed) + np.uint64(0x9E3779B9) * np.uint64(n + 1)) & M32
-    x = (np.asarray(c, dtype=np.uint64) & M32) ^ u
-    x ^= x >> np.uint64(16)
-    x = (x * np.uint64(0x85EBCA6B)) & M32
-    x ^= x >> np.uint64(13)
-    x = (x * np.uint64(0xC2B2AE35)) & M32
-    x ^= x >> np.uint64(16)
+    x = fmix32((np.asarray(c, dtype=np.uint64) & M32) ^ u)
     return np.where((x >> np.uint64(31)) & np.uint64(1), -1.0, 1.0)
 
 

@@ -1,4 +1,7 @@
 """Oracle pins for the Kronecker-SRHT sketch (Section 5, Eq. srht_kron)."""
+import json
+import os
+
 import numpy as np
 
 import oracle as O
@@ -16,6 +19,27 @@ def test_hadamard_columns_orthonormal():
     h8 = synth.hadamard_columns(8, 8, seed=5) * np.sqrt(8.0)
     h16 = full * 4.0
     assert np.array_equal(h16, np.block([[h8, h8], [h8, -h8]]))
+
+
+def test_fmix32_known_answers():
+    # the published MurmurHash3_x86_32 results for the empty input are fmix32(seed)
+    with open(os.path.join(os.path.dirname(__file__), "golden", "murmur3_x86_32_empty_kat.json")) as f:
+        kat = json.load(f)
+    seeds = np.array([int(v["seed"], 16) for v in kat["vectors"]], dtype=np.uint64)
+    want = [int(v["hash"], 16) for v in kat["vectors"]]
+    assert [int(h) for h in O.fmix32(seeds)] == want
+
+
+def test_rademacher_sign_is_the_top_bit_of_fmix32():
+    # with the per-mode offset u = seed + 0x9E3779B9 (n + 1) cancelled (seed = -u0 mod 2^32), entry c
+    # of D_n is -1 exactly when fmix32(c) has its top bit set
+    c = np.arange(4096, dtype=np.uint64) * np.uint64(2654435761) & np.uint64(0xFFFFFFFF)
+    for n in (0, 2):
+        seed = (-(0x9E3779B9 * (n + 1))) % (1 << 32)
+        sg = O.rademacher_signs(seed, n, c)
+        top = (O.fmix32(c) >> np.uint64(31)).astype(bool)
+        assert np.array_equal(sg == -1.0, top)
+    assert int(O.fmix32(np.uint64(1))) >> 31 == 0 and O.rademacher_signs(-0x9E3779B9 % (1 << 32), 0, [1])[0] == 1.0
 
 
 def test_rademacher_signs_balanced():
