@@ -38,13 +38,21 @@ def _check(G, U, err, ref, xv, tol):
         assert werr <= tol, (j, werr)
 
 
+def _same_draws(dev_factor, ref):
+    # the device's FP64 Box-Muller and the oracle's differ by a few FP64 ulps, so the FP32 values agree
+    # to the last bit except where a value straddles a rounding boundary: at most one FP32 ulp apart
+    a = to_np(dev_factor)
+    assert np.mean(a == ref) > 0.999
+    assert np.all(np.abs(a - ref) <= 2.0 ** -23 * np.maximum(np.abs(ref), 2.0 ** -126))
+
+
 def test_rhkron_full_size_device_factors(dev, field):
     X, xv = field
     s = O.subranks_reuse(R, P)[0]
     om_dev = T.gaussian_factors(X.shape, s, SEED + 1, torch.float32, dev)
     om_ref = [synth.round_to(O.gaussian_factor(N, s[j], SEED + 1, j), "f32") for j in range(3)]
     for a, b in zip(om_dev, om_ref):
-        assert np.mean(to_np(a) == b) > 0.999
+        _same_draws(a, b)
     G, U, err = T.tucker_rhkron(X, R, P, om_dev)
     ref = O.rhkron(xv, R, om_ref)
     _check(G, U, err, ref, xv, 1e-5)
@@ -64,7 +72,7 @@ def test_rsthkron_full_size_device_factors(dev, field):
                 oms_ref[(j, kk)] = synth.round_to(O.gaussian_factor(cur, int(S[j][kk]), SEED + 2, 8 * j + kk), "f32")
         done.add(j)
     for key, a in oms_dev.items():
-        assert np.mean(to_np(a) == oms_ref[key]) > 0.999
+        _same_draws(a, oms_ref[key])
     G, U, err = T.tucker_rsthkron(X, R, P, oms_dev)
     ref = O.rsthkron(xv, R, oms_ref)
     _check(G, U, err, ref, xv, 1e-5)
